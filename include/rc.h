@@ -1,0 +1,282 @@
+/*
+ * rc.h -- C ABI of the GB300 (sm_103a) hemispherical ray-casting library.
+ *
+ * The library implements the hot path of the milling-accessibility method of
+ * Baltadouros, Lauwers and Duflou, "Hemispherical Ray-Casting Analysis for
+ * Milling Configuration Classification and Machinability Assessment":
+ * every surface sample point of a triangulated part casts N hemisphere
+ * directions about its normal as any-hit occlusion rays against the part's
+ * own triangles (Section 3.1), the visible directions are reduced to
+ * directional indicators (Section 3.3), the part is classified as 3-axis or
+ * multi-axis (Section 3.3), and 3-axis parts get a six-axis orthogonal cast
+ * (Section 3.2) and a minimum-setup search (Section 3.3).
+ *
+ * Conventions (apply to every call):
+ *  - Status: every call returns rc_status.  RC_OK is 0.  A failing call
+ *    stores a message retrievable with rc_last_error() (thread-local).
+ *    Argument errors are detected on the host and returned before any work
+ *    is queued.
+ *  - Memory: arrays named d_* are DEVICE pointers owned by the caller
+ *    (e.g. torch CUDA tensors); arrays named h_* are host pointers owned by
+ *    the caller.  The library owns only the opaque handles it returns and
+ *    internal scratch, which it allocates and frees itself.  No call keeps
+ *    a caller pointer after it returns, except where stated (batches).
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Work is queued asynchronously on it unless the call
+ *    says it synchronises.  Calls never use another stream.
+ *  - Layouts: points, normals and vertices are row-major float32 xyz
+ *    ([n][3]); faces are int32 vertex indices ([T][3]), wound
+ *    counter-clockwise seen from outside (the normal is the right-hand rule
+ *    on the stored winding).  Visibility bits: row i has W = n_dirs/32
+ *    uint32 words; bit (j & 31) of word (j >> 5) is 1 iff hemisphere
+ *    direction j of point i is unobstructed.
+ *  - Precision: traversal and intersection run in FP32 with a forward error
+ *    bound per ray/triangle test; tests whose FP32 outcome is not certain
+ *    are re-decided in FP64 (Section 3.1's intersection test made exact
+ *    outside a 1e-9 relative ambiguity band).
+ *  - Every kernel is hand-written CUDA for sm_103a.  There is no CPU
+ *    fallback: without a usable GB300 the calls fail with RC_E_CUDA.
+ */
+#ifndef RC_H
+#define RC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RC_OK = 0,
+    RC_E_ARG = 1,          /* invalid argument (null pointer, bad size, bad mesh) */
+    RC_E_CUDA = 2,         /* a CUDA runtime call failed */
+    RC_E_OOM = 3,          /* device allocation failed or budget exceeded */
+    RC_E_TIMEOUT = 4,      /* a bounded device wait ran out */
+    RC_E_DEGENERATE = 5,   /* the part has no positive-area face to sample */
+    RC_E_UNSUPPORTED = 6,  /* a limit of this implementation was exceeded */
+    RC_E_DEVICE = 7        /* a kernel reported an internal error (see counters) */
+} rc_status;
+
+typedef struct rc_bvh_s* rc_bvh;
+
+/* Sampling modes (Section 3.1 samples one point per face at its centroid;
+ * the area-weighted random mode draws points in proportion to area). */
+enum { RC_SAMPLE_AREA_RANDOM = 0, RC_SAMPLE_FACE_CENTROID = 1 };
+
+/* Analysis parameters.  Fill with rc_params_default() and override. */
+typedef struct {
+    int32_t n_dirs;          /* N: hemisphere directions per point; multiple of 32, 32..65536 */
+    int32_t sample_mode;     /* RC_SAMPLE_* */
+    double origin_offset;    /* mm; rays start at fl32(p + origin_offset * n) (Section 3.1) */
+    uint64_t seed;           /* area-random sampling seed */
+    float frame[9];          /* row-major 3x3 machining frame; its columns are X', Y', Z' (Section 3.2) */
+    float tool_length;       /* mm; reachability threshold (Section 3.3) */
+    int32_t conc_mode;       /* 0: share of visible rays along the dominant axis; 1: |mean direction| along it */
+    double t_acc;            /* multi-axis if overall accessibility < t_acc (Section 3.3) */
+    double t_share;          /* ... or the largest dominant-axis share < t_share */
+    double t_conc;           /* ... or the mean axis concentration > t_conc */
+    int32_t block_threads;   /* traversal kernel: threads per block (0 = tuned default) */
+    int32_t blocks_per_sm;   /* traversal kernel: resident blocks per SM (0 = tuned default) */
+    int32_t reserved[6];
+} rc_params;
+
+/* Part-level indicators (Sections 3.1 and 3.3). */
+typedef struct {
+    double overall_access;            /* sum w_i count_i / (N sum w_i), w in 2^-24 fixed point of max w */
+    double overall_access_unweighted; /* sum count_i / (N n) */
+    double axis_share[3];             /* fraction of counted points whose dominant axis is x, y, z */
+    double mean_conc;                 /* mean axis concentration over counted points */
+    int64_t n_points;                 /* n */
+    int64_t n_counted;                /* points with at least one visible direction */
+    int64_t n_zero_visible;           /* n - n_counted */
+    int64_t dom_count[3];             /* counted points per dominant axis */
+    int64_t count_sum;                /* sum of unobstructed counts */
+    int64_t weighted_count_q;         /* sum wq_i * count_i (fixed-point weights) */
+    int64_t weight_sum_q;             /* sum wq_i */
+    int64_t conc_sum_q;               /* sum llrint(conc_i * 2^40) over counted points */
+} rc_summary;
+
+/* Minimum-setup result (Section 3.3). */
+typedef struct {
+    int32_t setups_exact;    /* smallest number of axes covering every viable point (Section 5: theoretical minimum) */
+    int32_t setups_greedy;   /* greedy set cover, ties to the lower axis (Section 3.3) */
+    uint8_t chosen_exact;    /* bit a = axis a in (+X', -X', +Y', -Y', +Z', -Z') */
+    uint8_t chosen_greedy;
+    uint8_t pad[6];
+    int64_t class_counts[4]; /* viable, over-threshold, inaccessible, fixture */
+    int64_t mask_hist[64];   /* viable points per reachable-axis mask */
+} rc_setups;
+
+/* Geometry summary of a built BVH. */
+typedef struct {
+    int64_t n_tris;
+    int64_t n_nodes;         /* packed internal nodes */
+    int64_t node_bytes;
+    int64_t tri_bytes;
+    int32_t max_depth;       /* deepest leaf (root = 0) */
+    int32_t leaf_size;       /* largest triangles per leaf */
+    float scene_lo[3];
+    float scene_hi[3];
+} rc_bvh_info;
+
+/* ---------------------------------------------------------------------- */
+/* Library                                                                */
+/* ---------------------------------------------------------------------- */
+
+/* Fills *p with the defaults: n_dirs 256, area-random sampling, seed 0,
+ * origin_offset 1e-4 mm, identity frame, tool_length 100 mm, conc_mode 0,
+ * thresholds 0.60 / 0.45 / 0.41.  Returns RC_E_ARG if p is NULL. */
+rc_status rc_params_default(rc_params* p);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* rc_last_error(void);
+
+/* Number of kernels this library has launched in this process (all threads).
+ * Used by benchmarks to report launch counts; never fails. */
+int64_t rc_launch_count(void);
+
+/* ---------------------------------------------------------------------- */
+/* Geometry and acceleration structure                                    */
+/* ---------------------------------------------------------------------- */
+
+/* Build the part's device acceleration structure (Section 3.1: "for each
+ * triangular face, the centroid, surface normal and area are computed";
+ * the BVH itself is not in the paper).  Steps, all on `stream`: FP64 face
+ * normal/area/centroid, 63-bit Morton codes of triangle-box centres, LSD
+ * radix sort, Karras binary radix tree, bottom-up AABB refit, packing into
+ * the traversal layout, integer area CDF for sampling.
+ *   d_V [nV][3] float32, d_F [T][3] int32 (device, caller-owned; read
+ *   during the call only -- the handle keeps its own copies).
+ * Synchronises `stream` before returning (validation result).
+ * Errors: RC_E_ARG for NULL pointers, nV < 3, T < 1, T > 2^28, an index
+ * outside [0, nV) or a non-finite vertex; RC_E_UNSUPPORTED if the tree is
+ * deeper than the traversal stack (64); RC_E_OOM; RC_E_CUDA. */
+rc_status rc_build_bvh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t T, void* stream,
+                       rc_bvh* out);
+
+/* Refit an existing handle to moved vertices of the same triangle list
+ * (same F, same nV): recomputes face data, leaf and node boxes bottom-up
+ * and the area CDF; the tree topology is kept.  Synchronises `stream`.
+ * Errors as rc_build_bvh (non-finite vertices -> RC_E_ARG). */
+rc_status rc_refit_bvh(rc_bvh h, const float* d_V, void* stream);
+
+/* Release a handle and its device memory.  NULL is accepted. */
+rc_status rc_destroy_bvh(rc_bvh h);
+
+/* Sizes, depth and scene bounds of a built handle (host struct). */
+rc_status rc_bvh_get_info(rc_bvh h, rc_bvh_info* out);
+
+/* ---------------------------------------------------------------------- */
+/* Section 3.1: sampling, directions, hemispherical cast                  */
+/* ---------------------------------------------------------------------- */
+
+/* Sample points on the part (Section 3.1).
+ * RC_SAMPLE_FACE_CENTROID: n must equal T; point f = fl32((A+B+C)/3),
+ *   normal = face normal, face = f, weight = FP64 face area.
+ * RC_SAMPLE_AREA_RANDOM: point i draws u0,u1,u2 from splitmix64 counters
+ *   (seed XOR golden*(3i+k)); the face is the first f whose inclusive
+ *   2^32-quantised area prefix exceeds floor(u0*total); the point is Osada
+ *   et al.'s (1-s)A + s(1-u2)B + s*u2*C with s = sqrt(u1), in FP64; weight 1.
+ *   d_P, d_N [n][3] float32; d_face [n] int32; d_weight [n] double (may be NULL).
+ * n == 0 is a no-op.  Errors: RC_E_ARG (NULL, n < 0, centroid n != T),
+ * RC_E_DEGENERATE (no positive-area face), RC_E_CUDA. */
+rc_status rc_sample_points(rc_bvh h, int64_t n, const rc_params* p, float* d_P, float* d_N,
+                           int32_t* d_face, double* d_weight, void* stream);
+
+/* The canonical hemisphere direction set (Section 3.1, Fig. 1: a uniformly
+ * sampled hemisphere; here the Fibonacci set z_j = 1-(j+1/2)/N,
+ * phi_j = j*pi*(3-sqrt5), computed in FP64 on the host and rounded to
+ * float32).  h_dirs [n_dirs][3] float32, host.  Errors: RC_E_ARG. */
+rc_status rc_direction_table(int32_t n_dirs, float* h_dirs);
+
+/* Hemispherical cast (Section 3.1: hemisphere samples rotated to each
+ * normal, rays cast from an offset point, "GPU-accelerated ray-triangle
+ * intersection tests determine whether rays are obstructed").
+ * For point i and direction j the ray is o_i = fl32(p_i + eps*n_i) (FP64),
+ * d_ij = (t1*hx + t2*hy) + n*hz in float32 with (t1, t2) the orthonormal
+ * basis of Duff et al. (2017); it is obstructed iff some triangle meets it
+ * at t > 0.
+ *   d_P, d_N [n][3]; d_bits [n][n_dirs/32] uint32 (written); d_count [n]
+ *   int32 unobstructed counts (written); d_counters int64[4] (written, may be
+ *   NULL): rays cast, rays decided by an ambiguous pair, ray/triangle pairs
+ *   re-tested in FP64, internal errors (must be 0).
+ * n == 0 is a no-op.  Asynchronous.  Errors: RC_E_ARG, RC_E_CUDA. */
+rc_status rc_hemisphere_cast(rc_bvh h, const float* d_P, const float* d_N, int64_t n,
+                             const rc_params* p, uint32_t* d_bits, int32_t* d_count,
+                             int64_t* d_counters, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Section 3.3: directional variability and classification                */
+/* ---------------------------------------------------------------------- */
+
+/* Per-point and part-level directional indicators from the visibility
+ * bits (Section 3.3: "directional biases in unobstructed rays are analyzed
+ * to identify dominant axis alignment and directional concentration").
+ * Per point: acc = count/N; M_k = sum over visible j of llrint(d_ij,k*2^40);
+ * dom = argmax_k |M_k| (ties to the lower axis; -1 if nothing is visible);
+ * conc (conc_mode 0) = share of visible rays whose largest |component| is
+ * axis dom, (conc_mode 1) = |M_dom| / (2^40 count).
+ *   d_bits [n][N/32], d_N [n][3]; d_weight [n] (NULL = unit weights);
+ *   outputs (each may be NULL): d_acc [n] float32, d_dom [n] int8,
+ *   d_conc [n] float32, d_dir_area [N] double (sum over points of weight
+ *   times visibility of direction j, weights in 2^-24 fixed point of max w);
+ *   h_summary (host, may be NULL).
+ * Synchronises `stream` when h_summary is not NULL.  Errors: RC_E_ARG,
+ * RC_E_UNSUPPORTED (non-unit weights with n > 2^21), RC_E_CUDA. */
+rc_status rc_direction_variability(const uint32_t* d_bits, const float* d_N,
+                                   const double* d_weight, int64_t n, const rc_params* p,
+                                   float* d_acc, int8_t* d_dom, float* d_conc, double* d_dir_area,
+                                   rc_summary* h_summary, void* stream);
+
+/* Threshold classification (Section 3.3: "if any threshold is exceeded, the
+ * part is classified as requiring multi-axis machining").  *label = 1
+ * (multi-axis) iff overall_access < t_acc, or max axis_share < t_share, or
+ * mean_conc > t_conc; else 0 (3-axis).  Host only.  Errors: RC_E_ARG. */
+rc_status rc_classify(const rc_summary* s, const rc_params* p, int32_t* label);
+
+/* ---------------------------------------------------------------------- */
+/* Section 3.2 / 3.3: orthogonal cast, reachability, setups                */
+/* ---------------------------------------------------------------------- */
+
+/* Orthogonal (directional) cast (Section 3.2: rays along the six principal
+ * directions of the canonical frame from the offset point, with the same
+ * intersection kernel).  Axis a in (+X', -X', +Y', -Y', +Z', -Z') is
+ * eligible iff n.a >= 0 (FP64) and accessible iff also unobstructed.
+ * Travel (Section 3.3, tool travel distance) = distance from p to the
+ * part's bounding box (in frame coordinates) along a.
+ *   d_mask [n] uint8 (bit a = accessible), d_travel [n][6] float32,
+ *   d_counters int64[4] as for rc_hemisphere_cast (may be NULL).
+ * Asynchronous.  Errors: RC_E_ARG, RC_E_CUDA. */
+rc_status rc_orthogonal_cast(rc_bvh h, const float* d_P, const float* d_N, int64_t n,
+                             const rc_params* p, uint8_t* d_mask, float* d_travel,
+                             int64_t* d_counters, void* stream);
+
+/* Reachability, fixture exclusion, face classes and setup count (Section
+ * 3.3: directions whose travel exceeds the tool length are discarded,
+ * bounding-box faces are excluded as fixture surfaces, faces are viable /
+ * over-threshold / fully inaccessible, and a set cover picks the setups).
+ * A face is a fixture face when its three vertices lie within 1e-6*diag of
+ * one bounding-box plane of the frame and its normal points out through
+ * that plane to within 1e-6.
+ *   d_mask [n], d_travel [n][6], d_face [n]: from the calls above;
+ *   d_class [n] uint8 written (0 viable, 1 over-threshold, 2 inaccessible,
+ *   3 fixture; may be NULL); h_out (host) receives counts, the 64-bin
+ *   histogram of viable reachable masks and both covers.
+ * Synchronises `stream`.  Errors: RC_E_ARG, RC_E_CUDA. */
+rc_status rc_min_setups(rc_bvh h, const uint8_t* d_mask, const float* d_travel,
+                        const int32_t* d_face, int64_t n, const rc_params* p, uint8_t* d_class,
+                        rc_setups* h_out, void* stream);
+
+/* The two setup covers of Section 3.3 from a 64-bin histogram of viable
+ * points per reachable-axis mask (bin 0 is ignored): the exact minimum
+ * (smallest |S|, ties to the smallest bitmask) and the greedy cover (most
+ * uncovered points first, ties to the lower axis).  Fills setups_* and
+ * chosen_* of *out; other fields are left unchanged.  Host only, no GPU.
+ * Errors: RC_E_ARG (NULL, negative count). */
+rc_status rc_setup_cover(const int64_t* h_mask_hist, rc_setups* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RC_H */

@@ -1,0 +1,273 @@
+"""GB300 (sm_103a) hemispherical ray-casting for milling accessibility.
+
+A thin binding over the C ABI of ``include/rc.h`` (``librc.so``, built
+in-tree by :mod:`paper_2609_05467_gb300.build`).  Every function here has
+the name of the C entry point it calls and does argument marshalling only:
+torch CUDA tensors are passed as raw device pointers together with the
+current CUDA stream, and every per-face, per-point and per-ray step runs in
+the library's CUDA kernels.  There is no CPU fallback: if the library or a
+CUDA device is missing, the calls raise.
+
+Paper: Baltadouros, Lauwers, Duflou, "Hemispherical Ray-Casting Analysis for
+Milling Configuration Classification and Machinability Assessment"
+(Section 3.1 hemispherical accessibility, Section 3.2 directional
+accessibility, Section 3.3 indicators, classification and setups).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = [
+    "RcError", "Params", "Summary", "Setups", "BvhInfo", "load", "lib_path",
+    "rc_params_default", "rc_build_bvh", "rc_refit_bvh", "rc_destroy_bvh", "rc_bvh_get_info",
+    "rc_sample_points", "rc_direction_table", "rc_hemisphere_cast", "rc_direction_variability",
+    "rc_classify", "rc_orthogonal_cast", "rc_min_setups", "rc_setup_cover", "rc_launch_count", "Bvh",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+_lock = threading.Lock()
+
+STATUS = {0: "RC_OK", 1: "RC_E_ARG", 2: "RC_E_CUDA", 3: "RC_E_OOM", 4: "RC_E_TIMEOUT",
+          5: "RC_E_DEGENERATE", 6: "RC_E_UNSUPPORTED", 7: "RC_E_DEVICE"}
+RC_SAMPLE_AREA_RANDOM, RC_SAMPLE_FACE_CENTROID = 0, 1
+
+
+class RcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("n_dirs", ctypes.c_int32), ("sample_mode", ctypes.c_int32), ("origin_offset", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("frame", ctypes.c_float * 9), ("tool_length", ctypes.c_float),
+        ("conc_mode", ctypes.c_int32), ("t_acc", ctypes.c_double), ("t_share", ctypes.c_double),
+        ("t_conc", ctypes.c_double), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
+    ]
+
+
+class Summary(ctypes.Structure):
+    _fields_ = [
+        ("overall_access", ctypes.c_double), ("overall_access_unweighted", ctypes.c_double),
+        ("axis_share", ctypes.c_double * 3), ("mean_conc", ctypes.c_double),
+        ("n_points", ctypes.c_int64), ("n_counted", ctypes.c_int64), ("n_zero_visible", ctypes.c_int64),
+        ("dom_count", ctypes.c_int64 * 3), ("count_sum", ctypes.c_int64), ("weighted_count_q", ctypes.c_int64),
+        ("weight_sum_q", ctypes.c_int64), ("conc_sum_q", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {
+            "overall_access": self.overall_access,
+            "overall_access_unweighted": self.overall_access_unweighted,
+            "axis_share": list(self.axis_share), "mean_conc": self.mean_conc,
+            "n_points": self.n_points, "n_counted": self.n_counted, "n_zero_visible": self.n_zero_visible,
+            "dom_count": list(self.dom_count), "count_sum": self.count_sum,
+        }
+
+
+class Setups(ctypes.Structure):
+    _fields_ = [
+        ("setups_exact", ctypes.c_int32), ("setups_greedy", ctypes.c_int32), ("chosen_exact", ctypes.c_uint8),
+        ("chosen_greedy", ctypes.c_uint8), ("pad", ctypes.c_uint8 * 6), ("class_counts", ctypes.c_int64 * 4),
+        ("mask_hist", ctypes.c_int64 * 64),
+    ]
+
+
+class BvhInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_tris", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("node_bytes", ctypes.c_int64),
+        ("tri_bytes", ctypes.c_int64), ("max_depth", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+        ("scene_lo", ctypes.c_float * 3), ("scene_hi", ctypes.c_float * 3),
+    ]
+
+
+def lib_path():
+    return os.path.join(_HERE, "librc.so")
+
+
+def load(build_if_missing=True):
+    """Load ``librc.so`` (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            from . import build as _b
+            _b.build()
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RcError(2, "librc.so is not built (run paper_2609_05467_gb300.build.build())")
+        L = ctypes.CDLL(path)
+        P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        st = ctypes.c_int
+        sig = {
+            "rc_params_default": ([ctypes.POINTER(Params)], st),
+            "rc_last_error": ([], ctypes.c_char_p),
+            "rc_launch_count": ([], i64),
+            "rc_build_bvh": ([P, i64, P, i64, P, ctypes.POINTER(P)], st),
+            "rc_refit_bvh": ([P, P, P], st),
+            "rc_destroy_bvh": ([P], st),
+            "rc_bvh_get_info": ([P, ctypes.POINTER(BvhInfo)], st),
+            "rc_sample_points": ([P, i64, ctypes.POINTER(Params), P, P, P, P, P], st),
+            "rc_direction_table": ([i32, P], st),
+            "rc_hemisphere_cast": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P], st),
+            "rc_direction_variability": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P,
+                                          ctypes.POINTER(Summary), P], st),
+            "rc_classify": ([ctypes.POINTER(Summary), ctypes.POINTER(Params), ctypes.POINTER(i32)], st),
+            "rc_orthogonal_cast": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P], st),
+            "rc_min_setups": ([P, P, P, P, i64, ctypes.POINTER(Params), P, ctypes.POINTER(Setups), P], st),
+            "rc_setup_cover": ([P, ctypes.POINTER(Setups)], st),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+        return _lib
+
+
+def _check(status):
+    if status != 0:
+        msg = load().rc_last_error()
+        raise RcError(status, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    """Device pointer of a CUDA tensor (None -> NULL); checks contiguity."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one function per entry point
+# ---------------------------------------------------------------------------
+
+def rc_params_default(**kw):
+    """Default :class:`Params` with keyword overrides (``frame`` takes 9
+    floats, row-major)."""
+    p = Params()
+    _check(load().rc_params_default(ctypes.byref(p)))
+    for k, v in kw.items():
+        if k == "frame":
+            for i, x in enumerate(v):
+                p.frame[i] = float(x)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def rc_build_bvh(V, F, stream=None):
+    """Build the device BVH of mesh ``V`` (float32 [nV,3] CUDA) / ``F``
+    (int32 [T,3] CUDA); returns an opaque handle (int)."""
+    h = ctypes.c_void_p()
+    _check(load().rc_build_bvh(_ptr(V), V.shape[0], _ptr(F), F.shape[0], _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def rc_refit_bvh(h, V, stream=None):
+    _check(load().rc_refit_bvh(ctypes.c_void_p(h), _ptr(V), _stream(stream)))
+
+
+def rc_destroy_bvh(h):
+    _check(load().rc_destroy_bvh(ctypes.c_void_p(h)))
+
+
+def rc_bvh_get_info(h):
+    info = BvhInfo()
+    _check(load().rc_bvh_get_info(ctypes.c_void_p(h), ctypes.byref(info)))
+    return info
+
+
+def rc_sample_points(h, n, params, P, N, face, weight=None, stream=None):
+    _check(load().rc_sample_points(ctypes.c_void_p(h), n, ctypes.byref(params), _ptr(P), _ptr(N), _ptr(face),
+                                   _ptr(weight), _stream(stream)))
+
+
+def rc_direction_table(n_dirs):
+    """Canonical fp32 direction table [n_dirs, 3] (host numpy array)."""
+    import numpy as np
+    out = np.zeros((n_dirs, 3), np.float32)
+    _check(load().rc_direction_table(n_dirs, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def rc_hemisphere_cast(h, P, N, params, bits, count, counters=None, stream=None):
+    _check(load().rc_hemisphere_cast(ctypes.c_void_p(h), _ptr(P), _ptr(N), P.shape[0], ctypes.byref(params),
+                                     _ptr(bits), _ptr(count), _ptr(counters), _stream(stream)))
+
+
+def rc_direction_variability(bits, N, params, weight=None, acc=None, dom=None, conc=None, dir_area=None,
+                             summary=True, stream=None):
+    s = Summary() if summary else None
+    _check(load().rc_direction_variability(_ptr(bits), _ptr(N), _ptr(weight), N.shape[0], ctypes.byref(params),
+                                           _ptr(acc), _ptr(dom), _ptr(conc), _ptr(dir_area),
+                                           ctypes.byref(s) if s is not None else None, _stream(stream)))
+    return s
+
+
+def rc_classify(summary, params):
+    lab = ctypes.c_int32()
+    _check(load().rc_classify(ctypes.byref(summary), ctypes.byref(params), ctypes.byref(lab)))
+    return lab.value
+
+
+def rc_orthogonal_cast(h, P, N, params, mask, travel, counters=None, stream=None):
+    _check(load().rc_orthogonal_cast(ctypes.c_void_p(h), _ptr(P), _ptr(N), P.shape[0], ctypes.byref(params),
+                                     _ptr(mask), _ptr(travel), _ptr(counters), _stream(stream)))
+
+
+def rc_min_setups(h, mask, travel, face, params, cls=None, stream=None):
+    out = Setups()
+    _check(load().rc_min_setups(ctypes.c_void_p(h), _ptr(mask), _ptr(travel), _ptr(face), mask.shape[0],
+                                ctypes.byref(params), _ptr(cls), ctypes.byref(out), _stream(stream)))
+    return out
+
+
+def rc_setup_cover(mask_hist):
+    """Exact and greedy covers from a 64-bin histogram (host only)."""
+    import numpy as np
+    h = np.ascontiguousarray(mask_hist, dtype=np.int64)
+    if h.shape != (64,):
+        raise ValueError("mask_hist must have 64 bins")
+    out = Setups()
+    _check(load().rc_setup_cover(h.ctypes.data_as(ctypes.c_void_p), ctypes.byref(out)))
+    return out
+
+
+def rc_launch_count():
+    return int(load().rc_launch_count())
+
+
+class Bvh:
+    """Owning wrapper of an ``rc_bvh`` handle (destroyed on ``close``)."""
+
+    def __init__(self, V, F, stream=None):
+        self.h = rc_build_bvh(V, F, stream)
+        self.T = F.shape[0]
+
+    def close(self):
+        if self.h:
+            rc_destroy_bvh(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,428 @@
+// api.cu -- the C ABI of include/rc.h: argument validation, handle
+// management, the host-side direction table, classification and the setup
+// cover.  Every per-face, per-point and per-ray step runs in the kernels of
+// build.cu, cast.cu and reduce.cu.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "rc_internal.cuh"
+
+namespace rc {
+
+rc_status build_bvh(rc_bvh h, cudaStream_t s);
+rc_status refit_bvh(rc_bvh h, cudaStream_t s);
+rc_status sample_points(rc_bvh h, int64_t n, const rc_params* p, float* P, float* N, int32_t* face,
+                        double* weight, cudaStream_t s);
+rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
+                            uint32_t* bits, int32_t* count, unsigned long long* counters, cudaStream_t s);
+rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
+                            uint8_t* mask, float* travel, unsigned long long* counters, cudaStream_t s);
+rc_status frame_setup(rc_bvh h, const rc_params* p, FrameDev* d, cudaStream_t s);
+rc_status launch_variability(const uint32_t* bits, const float* N, const double* weight, int64_t n,
+                             const float4* dirs, const rc_params* p, float* acc, int8_t* dom, float* conc,
+                             double* dir_area, unsigned long long* scratch, cudaStream_t s);
+rc_status launch_classes(rc_bvh h, const uint8_t* mask, const float* travel, const int32_t* face, int64_t n,
+                         const rc_params* p, uint8_t* cls, const double* frame_d, const double* fbox_d,
+                         uint8_t* fixture, unsigned long long* hist, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// errors and counters
+// ---------------------------------------------------------------------------
+static thread_local std::string t_err;
+static std::atomic<long long> g_launches{0};
+
+rc_status set_error(rc_status st, const std::string& msg)
+{
+    t_err = msg;
+    return st;
+}
+
+rc_status cuda_error(cudaError_t e, const char* what)
+{
+    t_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? RC_E_OOM : RC_E_CUDA;
+}
+
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// direction table (Section 3.1, Fig. 1): Fibonacci hemisphere in FP64 on the
+// host, rounded to fp32; cached on each device per N.
+// ---------------------------------------------------------------------------
+static void fibonacci_hemisphere(int32_t N, float* out /*N x 3*/)
+{
+    const double golden_angle = M_PI * (3.0 - sqrt(5.0));
+    for (int32_t j = 0; j < N; ++j) {
+        const double z = 1.0 - ((double)j + 0.5) / (double)N;
+        const double rad = sqrt(1.0 - z * z);
+        const double phi = (double)j * golden_angle;
+        out[3 * j + 0] = (float)(rad * cos(phi));
+        out[3 * j + 1] = (float)(rad * sin(phi));
+        out[3 * j + 2] = (float)z;
+    }
+}
+
+static std::mutex g_dir_mu;
+static std::map<std::pair<int, int>, float4*> g_dirs;
+
+static rc_status device_dirs(int32_t N, const float4** out)
+{
+    int dev = 0;
+    RC_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_dir_mu);
+    auto it = g_dirs.find({dev, N});
+    if (it != g_dirs.end()) { *out = it->second; return RC_OK; }
+    std::vector<float> h(3 * (size_t)N);
+    fibonacci_hemisphere(N, h.data());
+    std::vector<float4> h4(N);
+    for (int32_t j = 0; j < N; ++j) h4[j] = make_float4(h[3 * j], h[3 * j + 1], h[3 * j + 2], 0.0f);
+    float4* d = nullptr;
+    RC_CUDA(cudaMalloc(&d, sizeof(float4) * N));
+    RC_CUDA(cudaMemcpy(d, h4.data(), sizeof(float4) * N, cudaMemcpyHostToDevice));
+    g_dirs[{dev, N}] = d;
+    *out = d;
+    return RC_OK;
+}
+
+static rc_status check_params(const rc_params* p)
+{
+    if (!p) return set_error(RC_E_ARG, "params is NULL");
+    if (p->n_dirs < 32 || p->n_dirs > kMaxDirs || p->n_dirs % 32)
+        return set_error(RC_E_ARG, "n_dirs must be a multiple of 32 in [32, 65536]");
+    if (!(p->origin_offset >= 0.0) || !isfinite(p->origin_offset))
+        return set_error(RC_E_ARG, "origin_offset must be finite and >= 0");
+    if (p->sample_mode != RC_SAMPLE_AREA_RANDOM && p->sample_mode != RC_SAMPLE_FACE_CENTROID)
+        return set_error(RC_E_ARG, "unknown sample_mode");
+    if (p->conc_mode != 0 && p->conc_mode != 1) return set_error(RC_E_ARG, "conc_mode must be 0 or 1");
+    for (int k = 0; k < 9; ++k)
+        if (!isfinite(p->frame[k])) return set_error(RC_E_ARG, "frame must be finite");
+    if (p->block_threads < 0 || p->block_threads > 1024 || p->block_threads % 32)
+        return set_error(RC_E_ARG, "block_threads must be 0 or a multiple of 32 up to 1024");
+    if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return set_error(RC_E_ARG, "blocks_per_sm out of range");
+    return RC_OK;
+}
+
+static rc_status use_device_of(rc_bvh h)
+{
+    int dev = 0;
+    RC_CUDA(cudaGetDevice(&dev));
+    if (dev != h->device) RC_CUDA(cudaSetDevice(h->device));
+    return RC_OK;
+}
+
+static void free_handle(rc_bvh h)
+{
+    if (!h) return;
+    void* ptrs[] = {h->V, h->F, h->tris, h->nodes, h->parent, h->child, h->range, h->order, h->nbox,
+                    h->visits, h->fnorm, h->farea, h->fcent, h->cdf, h->sc};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete h;
+}
+
+}  // namespace rc
+
+using namespace rc;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+rc_status rc_params_default(rc_params* p)
+{
+    if (!p) return set_error(RC_E_ARG, "params is NULL");
+    memset(p, 0, sizeof *p);
+    p->n_dirs = 256;
+    p->sample_mode = RC_SAMPLE_AREA_RANDOM;
+    p->origin_offset = 1e-4;
+    p->seed = 0;
+    for (int k = 0; k < 9; ++k) p->frame[k] = (k % 4 == 0) ? 1.0f : 0.0f;
+    p->tool_length = 100.0f;
+    p->conc_mode = 0;
+    p->t_acc = 0.60;
+    p->t_share = 0.45;
+    p->t_conc = 0.41;
+    return RC_OK;
+}
+
+const char* rc_last_error(void) { return t_err.c_str(); }
+
+int64_t rc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+rc_status rc_build_bvh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t T, void* stream, rc_bvh* out)
+{
+    if (!out) return set_error(RC_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!d_V || !d_F) return set_error(RC_E_ARG, "vertex or face pointer is NULL");
+    if (nV < 3) return set_error(RC_E_ARG, "need at least 3 vertices");
+    if (T < 1) return set_error(RC_E_ARG, "need at least one triangle");
+    if (T > (1LL << 28) || nV > (1LL << 31) - 1) return set_error(RC_E_ARG, "mesh too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    rc_bvh h = new rc_bvh_s();
+    auto fail = [&](rc_status st) { std::string m = t_err; cudaStreamSynchronize(s); free_handle(h); t_err = m; return st; };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return fail(set_error(RC_E_CUDA, "no CUDA device"));
+    h->nV = nV;
+    h->T = T;
+#define RC_TRY(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) return fail(cuda_error(_e, #call)); } while (0)
+    RC_TRY(cudaMalloc(&h->V, sizeof(float) * 3 * nV));
+    RC_TRY(cudaMalloc(&h->F, sizeof(int32_t) * 3 * T));
+    RC_TRY(cudaMalloc(&h->fnorm, sizeof(float) * 3 * T));
+    RC_TRY(cudaMalloc(&h->farea, sizeof(double) * T));
+    RC_TRY(cudaMalloc(&h->fcent, sizeof(float) * 3 * T));
+    RC_TRY(cudaMalloc(&h->cdf, sizeof(long long) * T));
+    RC_TRY(cudaMalloc(&h->sc, sizeof(DevScalars)));
+    RC_TRY(cudaMemcpyAsync(h->V, d_V, sizeof(float) * 3 * nV, cudaMemcpyDeviceToDevice, s));
+    RC_TRY(cudaMemcpyAsync(h->F, d_F, sizeof(int32_t) * 3 * T, cudaMemcpyDeviceToDevice, s));
+#undef RC_TRY
+    rc_status st = build_bvh(h, s);
+    if (st != RC_OK) return fail(st);
+    // scene bounds = union of the root's two child boxes
+    float4 root[3];
+    if (cudaMemcpy(root, h->nodes, sizeof root, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(set_error(RC_E_CUDA, "reading the root node failed"));
+    h->lo[0] = fminf(root[0].x, root[1].x); h->hi[0] = fmaxf(root[0].y, root[1].y);
+    h->lo[1] = fminf(root[0].z, root[1].z); h->hi[1] = fmaxf(root[0].w, root[1].w);
+    h->lo[2] = fminf(root[2].x, root[2].z); h->hi[2] = fmaxf(root[2].y, root[2].w);
+    *out = h;
+    return RC_OK;
+}
+
+rc_status rc_refit_bvh(rc_bvh h, const float* d_V, void* stream)
+{
+    if (!h || !d_V) return set_error(RC_E_ARG, "handle or vertex pointer is NULL");
+    rc_status st = use_device_of(h);
+    if (st != RC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    RC_CUDA(cudaMemcpyAsync(h->V, d_V, sizeof(float) * 3 * h->nV, cudaMemcpyDeviceToDevice, s));
+    return refit_bvh(h, s);
+}
+
+rc_status rc_destroy_bvh(rc_bvh h)
+{
+    if (!h) return RC_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaSetDevice(h->device);
+    free_handle(h);
+    cudaSetDevice(dev);
+    return RC_OK;
+}
+
+rc_status rc_bvh_get_info(rc_bvh h, rc_bvh_info* out)
+{
+    if (!h || !out) return set_error(RC_E_ARG, "handle or out is NULL");
+    out->n_tris = h->T;
+    out->n_nodes = h->n_int;
+    out->node_bytes = h->n_int * 64;
+    out->tri_bytes = h->T * 48;
+    out->max_depth = h->max_depth;
+    out->leaf_size = kLeafMax;
+    for (int k = 0; k < 3; ++k) { out->scene_lo[k] = h->lo[k]; out->scene_hi[k] = h->hi[k]; }
+    return RC_OK;
+}
+
+rc_status rc_sample_points(rc_bvh h, int64_t n, const rc_params* p, float* d_P, float* d_N, int32_t* d_face,
+                           double* d_weight, void* stream)
+{
+    if (!h) return set_error(RC_E_ARG, "handle is NULL");
+    rc_status st = check_params(p);
+    if (st != RC_OK) return st;
+    if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
+    if (p->sample_mode == RC_SAMPLE_FACE_CENTROID && n != h->T)
+        return set_error(RC_E_ARG, "centroid sampling needs n == T");
+    if (n == 0) return RC_OK;
+    if (!d_P || !d_N || !d_face) return set_error(RC_E_ARG, "output pointer is NULL");
+    if (p->sample_mode == RC_SAMPLE_AREA_RANDOM && h->host_sc.amax_bits == 0)
+        return set_error(RC_E_DEGENERATE, "part has no positive-area face");
+    if ((st = use_device_of(h)) != RC_OK) return st;
+    return sample_points(h, n, p, d_P, d_N, d_face, d_weight, (cudaStream_t)stream);
+}
+
+rc_status rc_direction_table(int32_t n_dirs, float* h_dirs)
+{
+    if (!h_dirs) return set_error(RC_E_ARG, "output is NULL");
+    if (n_dirs < 1 || n_dirs > kMaxDirs) return set_error(RC_E_ARG, "n_dirs out of range");
+    fibonacci_hemisphere(n_dirs, h_dirs);
+    return RC_OK;
+}
+
+rc_status rc_hemisphere_cast(rc_bvh h, const float* d_P, const float* d_N, int64_t n, const rc_params* p,
+                             uint32_t* d_bits, int32_t* d_count, int64_t* d_counters, void* stream)
+{
+    if (!h) return set_error(RC_E_ARG, "handle is NULL");
+    rc_status st = check_params(p);
+    if (st != RC_OK) return st;
+    if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = use_device_of(h)) != RC_OK) return st;
+    if (d_counters) RC_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(int64_t) * 4, s));
+    if (n == 0) return RC_OK;
+    if (!d_P || !d_N || !d_bits || !d_count) return set_error(RC_E_ARG, "array pointer is NULL");
+    const float4* dirs = nullptr;
+    if ((st = device_dirs(p->n_dirs, &dirs)) != RC_OK) return st;
+    h->dirs = const_cast<float4*>(dirs);
+    h->dirs_n = p->n_dirs;
+    return launch_hemisphere(h, d_P, d_N, n, p, d_bits, d_count, (unsigned long long*)d_counters, s);
+}
+
+rc_status rc_direction_variability(const uint32_t* d_bits, const float* d_N, const double* d_weight, int64_t n,
+                                   const rc_params* p, float* d_acc, int8_t* d_dom, float* d_conc,
+                                   double* d_dir_area, rc_summary* h_summary, void* stream)
+{
+    rc_status st = check_params(p);
+    if (st != RC_OK) return st;
+    if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
+    if (n > 0 && (!d_bits || !d_N)) return set_error(RC_E_ARG, "bits or normals pointer is NULL");
+    if (d_weight && n > (1LL << 21))
+        return set_error(RC_E_UNSUPPORTED, "weighted summaries support at most 2^21 points");
+    cudaStream_t s = (cudaStream_t)stream;
+    const float4* dirs = nullptr;
+    if ((st = device_dirs(p->n_dirs, &dirs)) != RC_OK) return st;
+    const size_t words = 8 + 1 + (size_t)p->n_dirs;
+    unsigned long long* scratch = nullptr;
+    RC_CUDA(cudaMallocAsync(&scratch, sizeof(unsigned long long) * words, s));
+    RC_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * words, s));
+    st = launch_variability(d_bits, d_N, d_weight, n, dirs, p, d_acc, d_dom, d_conc, d_dir_area, scratch, s);
+    if (st != RC_OK) { cudaFreeAsync(scratch, s); return st; }
+    long long sums[8] = {0};
+    if (h_summary) {
+        RC_CUDA(cudaMemcpyAsync(sums, scratch, sizeof sums, cudaMemcpyDeviceToHost, s));
+    }
+    RC_CUDA(cudaFreeAsync(scratch, s));
+    if (!h_summary) return RC_OK;
+    RC_CUDA(cudaStreamSynchronize(s));
+    rc_summary& o = *h_summary;
+    memset(&o, 0, sizeof o);
+    const long long counted = sums[0];
+    o.n_points = n;
+    o.n_counted = counted;
+    o.n_zero_visible = n - counted;
+    for (int k = 0; k < 3; ++k) {
+        o.dom_count[k] = sums[1 + k];
+        o.axis_share[k] = counted ? (double)sums[1 + k] / (double)counted : 0.0;
+    }
+    o.count_sum = sums[4];
+    o.weighted_count_q = sums[5];
+    o.weight_sum_q = sums[6];
+    o.conc_sum_q = sums[7];
+    const long long den = sums[6] * (long long)p->n_dirs;
+    o.overall_access = den ? (double)sums[5] / (double)den : 0.0;
+    o.overall_access_unweighted = n ? (double)sums[4] / ((double)n * (double)p->n_dirs) : 0.0;
+    o.mean_conc = counted ? (double)sums[7] / (1099511627776.0 * (double)counted) : 0.0;
+    return RC_OK;
+}
+
+rc_status rc_classify(const rc_summary* s, const rc_params* p, int32_t* label)
+{
+    if (!s || !p || !label) return set_error(RC_E_ARG, "NULL argument");
+    const double mx = std::max(s->axis_share[0], std::max(s->axis_share[1], s->axis_share[2]));
+    *label = (s->overall_access < p->t_acc || mx < p->t_share || s->mean_conc > p->t_conc) ? 1 : 0;
+    return RC_OK;
+}
+
+rc_status rc_orthogonal_cast(rc_bvh h, const float* d_P, const float* d_N, int64_t n, const rc_params* p,
+                             uint8_t* d_mask, float* d_travel, int64_t* d_counters, void* stream)
+{
+    if (!h) return set_error(RC_E_ARG, "handle is NULL");
+    rc_status st = check_params(p);
+    if (st != RC_OK) return st;
+    if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = use_device_of(h)) != RC_OK) return st;
+    if (d_counters) RC_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(int64_t) * 4, s));
+    if (n == 0) return RC_OK;
+    if (!d_P || !d_N || !d_mask || !d_travel) return set_error(RC_E_ARG, "array pointer is NULL");
+    return launch_orthogonal(h, d_P, d_N, n, p, d_mask, d_travel, (unsigned long long*)d_counters, s);
+}
+
+rc_status rc_min_setups(rc_bvh h, const uint8_t* d_mask, const float* d_travel, const int32_t* d_face, int64_t n,
+                        const rc_params* p, uint8_t* d_class, rc_setups* h_out, void* stream)
+{
+    if (!h || !h_out) return set_error(RC_E_ARG, "handle or output is NULL");
+    rc_status st = check_params(p);
+    if (st != RC_OK) return st;
+    if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
+    if (n > 0 && (!d_mask || !d_travel || !d_face)) return set_error(RC_E_ARG, "array pointer is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = use_device_of(h)) != RC_OK) return st;
+    // scratch: frame, fixture flags, 68 counters
+    FrameDev* fd = nullptr;
+    uint8_t* fixture = nullptr;
+    unsigned long long* hist = nullptr;
+    RC_CUDA(cudaMallocAsync(&fd, sizeof(FrameDev), s));
+    RC_CUDA(cudaMallocAsync(&fixture, h->T, s));
+    RC_CUDA(cudaMallocAsync(&hist, sizeof(unsigned long long) * 68, s));
+    RC_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 68, s));
+    st = frame_setup(h, p, fd, s);
+    if (st == RC_OK)
+        st = launch_classes(h, d_mask, d_travel, d_face, n, p, d_class, fd->frame, fd->fbox, fixture, hist, s);
+    unsigned long long hh[68];
+    if (st == RC_OK) RC_CUDA(cudaMemcpyAsync(hh, hist, sizeof hh, cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(fd, s);
+    cudaFreeAsync(fixture, s);
+    cudaFreeAsync(hist, s);
+    if (st != RC_OK) return st;
+    RC_CUDA(cudaStreamSynchronize(s));
+    memset(h_out, 0, sizeof *h_out);
+    for (int k = 0; k < 64; ++k) h_out->mask_hist[k] = (int64_t)hh[k];
+    for (int k = 0; k < 4; ++k) h_out->class_counts[k] = (int64_t)hh[64 + k];
+    return rc_setup_cover(h_out->mask_hist, h_out);
+}
+
+rc_status rc_setup_cover(const int64_t* h_mask_hist, rc_setups* out)
+{
+    if (!h_mask_hist || !out) return set_error(RC_E_ARG, "NULL argument");
+    int64_t hh[64];
+    for (int m = 0; m < 64; ++m) {
+        if (h_mask_hist[m] < 0) return set_error(RC_E_ARG, "negative histogram count");
+        hh[m] = m ? h_mask_hist[m] : 0;
+    }
+    // exact cover: smallest |S|, ties to the smallest bitmask
+    out->setups_exact = 0;
+    out->chosen_exact = 0;
+    bool any = false;
+    for (int m = 1; m < 64; ++m) any |= hh[m] != 0;
+    if (any) {
+        bool done = false;
+        for (int size = 1; size <= 6 && !done; ++size)
+            for (int S = 1; S < 64 && !done; ++S) {
+                if (__builtin_popcount(S) != size) continue;
+                bool ok = true;
+                for (int m = 1; m < 64 && ok; ++m) ok = hh[m] == 0 || (m & S);
+                if (ok) { out->setups_exact = size; out->chosen_exact = (uint8_t)S; done = true; }
+            }
+    }
+    // greedy cover: the axis covering most uncovered viable points, ties to the lower axis
+    int S = 0;
+    int64_t left[64];
+    for (int m = 0; m < 64; ++m) left[m] = hh[m];
+    for (;;) {
+        bool rem = false;
+        for (int m = 1; m < 64; ++m) rem |= left[m] != 0;
+        if (!rem) break;
+        int best = -1;
+        int64_t bc = 0;
+        for (int a = 0; a < 6; ++a) {
+            if ((S >> a) & 1) continue;
+            int64_t c = 0;
+            for (int m = 1; m < 64; ++m)
+                if ((m >> a) & 1) c += left[m];
+            if (best < 0 || c > bc) { best = a; bc = c; }
+        }
+        S |= 1 << best;
+        for (int m = 1; m < 64; ++m)
+            if ((m >> best) & 1) left[m] = 0;
+    }
+    out->setups_greedy = __builtin_popcount(S);
+    out->chosen_greedy = (uint8_t)S;
+    return RC_OK;
+}
+
+}  // extern "C"

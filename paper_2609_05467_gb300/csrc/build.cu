@@ -1,0 +1,660 @@
+// build.cu -- device construction of the part's acceleration structure and
+// the per-face data of Section 3.1 (normal, area, centroid), plus sampling.
+//
+// Pipeline (one stream):
+//   face_prep   : FP64 normal / area / centroid per face, fp32 face boxes,
+//                 mesh validation, scene bounds (atomics)
+//   morton      : 63-bit Morton code of each face-box centre
+//   radix sort  : 8 passes of 8-bit LSD (histogram / scan / stable scatter)
+//   karras      : binary radix tree over the sorted codes (Karras, HPG 2012)
+//   refit       : bottom-up boxes with arrival counters
+//   pack        : BVH2 nodes holding both child boxes (64 B), leaves of up
+//                 to kLeafMax consecutive triangles, triangle records 48 B
+//   area cdf    : 2^32-quantised face areas, inclusive int64 prefix
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rc_internal.cuh"
+
+namespace rc {
+
+// ---------------------------------------------------------------------------
+// face preparation and validation
+// ---------------------------------------------------------------------------
+__global__ void k_face_prep(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ F,
+                            int64_t T, float* fnorm, double* farea, float* fcent, float* tbox,
+                            DevScalars* sc)
+{
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= T) return;
+    int32_t id[3];
+    bool bad = false;
+    for (int k = 0; k < 3; ++k) {
+        id[k] = F[3 * f + k];
+        if (id[k] < 0 || id[k] >= nV) bad = true;
+    }
+    if (bad) {
+        atomicMin(&sc->err_index, (int)f);
+        for (int k = 0; k < 6; ++k) tbox[6 * f + k] = 0.0f;
+        return;
+    }
+    float v[3][3];
+    float mabs = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        for (int k = 0; k < 3; ++k) {
+            v[a][k] = V[3 * (int64_t)id[a] + k];
+            if (!isfinite(v[a][k])) {
+                atomicMin(&sc->err_vertex, id[a]);
+                v[a][k] = 0.0f;
+            }
+            mabs = fmaxf(mabs, fabsf(v[a][k]));
+        }
+    }
+    // c = (B - A) x (C - A) in FP64, each operation rounded separately
+    double e1[3], e2[3];
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = __dsub_rn((double)v[1][k], (double)v[0][k]);
+        e2[k] = __dsub_rn((double)v[2][k], (double)v[0][k]);
+    }
+    double c0 = __dsub_rn(__dmul_rn(e1[1], e2[2]), __dmul_rn(e1[2], e2[1]));
+    double c1 = __dsub_rn(__dmul_rn(e1[2], e2[0]), __dmul_rn(e1[0], e2[2]));
+    double c2 = __dsub_rn(__dmul_rn(e1[0], e2[1]), __dmul_rn(e1[1], e2[0]));
+    double len = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(c0, c0), __dmul_rn(c1, c1)), __dmul_rn(c2, c2)));
+    farea[f] = 0.5 * len;
+    float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f;
+    if (len > 0.0) {
+        n0 = __double2float_rn(__ddiv_rn(c0, len));
+        n1 = __double2float_rn(__ddiv_rn(c1, len));
+        n2 = __double2float_rn(__ddiv_rn(c2, len));
+    }
+    fnorm[3 * f + 0] = n0;
+    fnorm[3 * f + 1] = n1;
+    fnorm[3 * f + 2] = n2;
+    for (int k = 0; k < 3; ++k) {
+        double s = __dadd_rn(__dadd_rn((double)v[0][k], (double)v[1][k]), (double)v[2][k]);
+        fcent[3 * f + k] = __double2float_rn(__ddiv_rn(s, 3.0));
+    }
+    for (int k = 0; k < 3; ++k) {
+        float lo = fminf(v[0][k], fminf(v[1][k], v[2][k]));
+        float hi = fmaxf(v[0][k], fmaxf(v[1][k], v[2][k]));
+        tbox[6 * f + k] = lo;
+        tbox[6 * f + 3 + k] = hi;
+        float c = 0.5f * (lo + hi);
+        atomicMin(&sc->cmin[k], float_to_ordered(c));
+        atomicMax(&sc->cmax[k], float_to_ordered(c));
+    }
+    atomicMax(&sc->vmaxabs, float_to_ordered(mabs));
+    atomicMax(&sc->amax_bits, (unsigned long long)__double_as_longlong(0.5 * len));
+}
+
+// ---------------------------------------------------------------------------
+// Morton codes
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long spread21(unsigned long long x)
+{
+    x &= 0x1FFFFFULL;
+    x = (x | (x << 32)) & 0x1F00000000FFFFULL;
+    x = (x | (x << 16)) & 0x1F0000FF0000FFULL;
+    x = (x | (x << 8)) & 0x100F00F00F00F00FULL;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ULL;
+    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    return x;
+}
+
+__global__ void k_morton(const float* __restrict__ tbox, int64_t T, const DevScalars* sc,
+                         unsigned long long* keys, int32_t* vals)
+{
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= T) return;
+    unsigned long long code = 0;
+    for (int k = 0; k < 3; ++k) {
+        float lo = ordered_to_float(sc->cmin[k]);
+        float hi = ordered_to_float(sc->cmax[k]);
+        float c = 0.5f * (tbox[6 * f + k] + tbox[6 * f + 3 + k]);
+        float ext = hi - lo;
+        float u = ext > 0.0f ? (c - lo) / ext : 0.0f;
+        u = fminf(fmaxf(u, 0.0f), 1.0f);
+        unsigned long long q = (unsigned long long)fminf(u * 2097152.0f, 2097151.0f);
+        code |= spread21(q) << (2 - k);
+    }
+    keys[f] = code;
+    vals[f] = (int32_t)f;
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort of (uint64 key, int32 value), 8-bit digits, stable
+// ---------------------------------------------------------------------------
+constexpr int kMaxWalk = 4096;   // bound on leaf-to-root walks
+constexpr int kSortThreads = 256;
+constexpr int kSortTile = 4096;   // keys per block
+
+__global__ void k_sort_hist(const unsigned long long* __restrict__ keys, int64_t T, int shift,
+                            int nblk, unsigned int* __restrict__ counts)
+{
+    __shared__ unsigned int h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    int64_t end = min64(T, base + kSortTile);
+    for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x)
+        atomicAdd(&h[(keys[i] >> shift) & 255], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) counts[(int64_t)i * nblk + blockIdx.x] = h[i];
+}
+
+// exclusive scan of m uint32 counts (digit-major) in one block
+__global__ void k_sort_scan(unsigned int* __restrict__ counts, int64_t m)
+{
+    __shared__ unsigned int part[1024];
+    const int t = threadIdx.x;
+    const int64_t per = (m + blockDim.x - 1) / blockDim.x;
+    const int64_t b = t * per, e = min64(m, b + per);
+    unsigned int s = 0;
+    for (int64_t i = b; i < e; ++i) s += counts[i];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        unsigned int v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned int run = part[t] - s;
+    for (int64_t i = b; i < e; ++i) {
+        unsigned int c = counts[i];
+        counts[i] = run;
+        run += c;
+    }
+}
+
+__global__ void k_sort_scatter(const unsigned long long* __restrict__ kin, const int32_t* __restrict__ vin,
+                               int64_t T, int shift, int nblk, const unsigned int* __restrict__ offs,
+                               unsigned long long* __restrict__ kout, int32_t* __restrict__ vout,
+                               unsigned int* err)
+{
+    constexpr int W = kSortThreads / 32;
+    __shared__ unsigned int base[256];
+    __shared__ unsigned int wcnt[W][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) base[i] = offs[(int64_t)i * nblk + blockIdx.x];
+    const int64_t b0 = (int64_t)blockIdx.x * kSortTile;
+    const int64_t e0 = min64(T, b0 + kSortTile);
+    for (int64_t c0 = b0; c0 < e0; c0 += kSortThreads) {
+        for (int i = threadIdx.x; i < W * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        const int64_t i = c0 + threadIdx.x;
+        const bool ok = i < e0;
+        unsigned long long key = ok ? kin[i] : 0ULL;
+        int32_t val = ok ? vin[i] : 0;
+        const unsigned int dig = ok ? (unsigned int)((key >> shift) & 255) : 256u + lane;
+        const unsigned int peers = __match_any_sync(0xFFFFFFFFu, dig);
+        const unsigned int rank = __popc(peers & ((1u << lane) - 1u));
+        if (ok && rank == 0) wcnt[warp][dig] = __popc(peers);
+        __syncthreads();
+        if (ok) {
+            unsigned int pos = base[dig] + rank;
+            for (int w = 0; w < warp; ++w) pos += wcnt[w][dig];
+            if (pos < (unsigned long long)T) {
+                kout[pos] = key;
+                vout[pos] = val;
+            } else {
+                atomicAdd(err, 1u);
+            }
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+            unsigned int s = 0;
+            for (int w = 0; w < W; ++w) s += wcnt[w][d];
+            base[d] += s;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Karras binary radix tree
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int kdelta(const unsigned long long* keys, int64_t T, int64_t i, int64_t j)
+{
+    if (j < 0 || j >= T) return -1;
+    unsigned long long a = keys[i], b = keys[j];
+    if (a == b) return 64 + __clz((unsigned int)(i ^ j));
+    return __clzll(a ^ b);
+}
+
+__global__ void k_karras(const unsigned long long* __restrict__ keys, int64_t T, int32_t* child,
+                         int32_t* range, int32_t* parent)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n_int = T - 1;
+    if (i >= n_int) return;
+    const int d = (kdelta(keys, T, i, i + 1) - kdelta(keys, T, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = kdelta(keys, T, i, i - d);
+    int64_t lmax = 2;
+    while (kdelta(keys, T, i, i + lmax * d) > dmin) lmax <<= 1;
+    int64_t l = 0;
+    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+        if (kdelta(keys, T, i, i + (l + t) * d) > dmin) l += t;
+    const int64_t j = i + l * d;
+    const int dnode = kdelta(keys, T, i, j);
+    int64_t s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (kdelta(keys, T, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+    const int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    const int32_t left = (int32_t)(lo == gamma ? n_int + gamma : gamma);
+    const int32_t right = (int32_t)(hi == gamma + 1 ? n_int + gamma + 1 : gamma + 1);
+    child[2 * i] = left;
+    child[2 * i + 1] = right;
+    range[2 * i] = (int32_t)lo;
+    range[2 * i + 1] = (int32_t)hi;
+    parent[left] = (int32_t)i;
+    parent[right] = (int32_t)i;
+    if (i == 0) parent[0] = -1;
+}
+
+// ---------------------------------------------------------------------------
+// bottom-up refit
+// ---------------------------------------------------------------------------
+__global__ void k_leaf_boxes(const float* __restrict__ tbox, const int32_t* __restrict__ order,
+                             int64_t T, int64_t n_int, float* nbox)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= T) return;
+    const int32_t f = order[k];
+    for (int c = 0; c < 6; ++c) nbox[6 * (n_int + k) + c] = tbox[6 * (int64_t)f + c];
+}
+
+__global__ void k_refit(int64_t T, int64_t n_int, const int32_t* __restrict__ parent,
+                        const int32_t* __restrict__ child, float* nbox, int32_t* visits, DevScalars* sc)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= T) return;
+    int32_t cur = (int32_t)(n_int + k);
+    // every chain ends at the root; the caps only guard against a malformed
+    // tree (the build then reports an error instead of looping)
+    int depth = 0;
+    for (int32_t p = parent[cur]; p >= 0 && depth <= kMaxWalk; p = parent[p]) ++depth;
+    atomicMax(&sc->max_depth, depth);
+    if (depth > kMaxWalk) return;
+    int32_t p = parent[cur];
+    for (int steps = 0; p >= 0 && steps <= kMaxWalk; ++steps) {
+        __threadfence();
+        if (atomicAdd(&visits[p], 1) == 0) return;   // first arrival stops
+        const int32_t a = child[2 * p], b = child[2 * p + 1];
+        float box[6];
+        for (int c = 0; c < 3; ++c) {
+            box[c] = fminf(__ldcg(&nbox[6 * (int64_t)a + c]), __ldcg(&nbox[6 * (int64_t)b + c]));
+            box[3 + c] = fmaxf(__ldcg(&nbox[6 * (int64_t)a + 3 + c]), __ldcg(&nbox[6 * (int64_t)b + 3 + c]));
+        }
+        for (int c = 0; c < 6; ++c) __stcg(&nbox[6 * (int64_t)p + c], box[c]);
+        p = parent[p];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// packing into the traversal layout
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t encode_child(int32_t c, int64_t n_int, const int32_t* range)
+{
+    if (c >= n_int) {
+        const int32_t first = (int32_t)(c - n_int);
+        return -1 - (first * 8 + 0);
+    }
+    const int32_t lo = range[2 * c], hi = range[2 * c + 1];
+    const int32_t cnt = hi - lo + 1;
+    if (cnt <= kLeafMax) return -1 - (lo * 8 + (cnt - 1));
+    return c;
+}
+
+__global__ void k_pack(int64_t n_int, const int32_t* __restrict__ child, const int32_t* __restrict__ range,
+                       const float* __restrict__ nbox, float4* nodes)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    const int32_t a = child[2 * i], b = child[2 * i + 1];
+    const float* A = nbox + 6 * (int64_t)a;
+    const float* B = nbox + 6 * (int64_t)b;
+    nodes[4 * i + 0] = make_float4(A[0], A[3], A[1], A[4]);
+    nodes[4 * i + 1] = make_float4(B[0], B[3], B[1], B[4]);
+    nodes[4 * i + 2] = make_float4(A[2], A[5], B[2], B[5]);
+    nodes[4 * i + 3] = make_float4(__int_as_float(encode_child(a, n_int, range)),
+                                   __int_as_float(encode_child(b, n_int, range)), 0.0f, 0.0f);
+}
+
+// single-leaf root for parts with at most kLeafMax triangles
+__global__ void k_pack_small(int64_t T, const float* __restrict__ tbox, float4* nodes)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t f = 0; f < T; ++f)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fminf(lo[c], tbox[6 * f + c]);
+            hi[c] = fmaxf(hi[c], tbox[6 * f + 3 + c]);
+        }
+    nodes[0] = make_float4(lo[0], hi[0], lo[1], hi[1]);
+    nodes[1] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+    nodes[2] = make_float4(lo[2], hi[2], INFINITY, -INFINITY);
+    nodes[3] = make_float4(__int_as_float(-1 - (0 * 8 + (int)(T - 1))), __int_as_float(-1), 0.0f, 0.0f);
+}
+
+__global__ void k_tri_records(const float* __restrict__ V, const int32_t* __restrict__ F,
+                              const int32_t* __restrict__ order, int64_t T, float4* tris)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= T) return;
+    const int32_t f = order[k];
+    float v[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) v[a][c] = V[3 * (int64_t)F[3 * (int64_t)f + a] + c];
+    float le = 0.0f;
+    for (int c = 0; c < 3; ++c) {
+        le = fmaxf(le, fabsf(v[1][c] - v[0][c]));
+        le = fmaxf(le, fabsf(v[2][c] - v[1][c]));
+        le = fmaxf(le, fabsf(v[0][c] - v[2][c]));
+    }
+    tris[3 * k + 0] = make_float4(v[0][0], v[0][1], v[0][2], le);
+    tris[3 * k + 1] = make_float4(v[1][0], v[1][1], v[1][2], __int_as_float(f));
+    tris[3 * k + 2] = make_float4(v[2][0], v[2][1], v[2][2], 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// area CDF (2^32-quantised areas, inclusive prefix in int64)
+// ---------------------------------------------------------------------------
+constexpr int kScanBlock = 1024;
+
+__global__ void k_quant_area(const double* __restrict__ farea, int64_t T, const DevScalars* sc,
+                             long long* q)
+{
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= T) return;
+    const double amax = __longlong_as_double((long long)sc->amax_bits);
+    q[f] = amax > 0.0 ? llround(__dmul_rn(__ddiv_rn(farea[f], amax), 4294967296.0)) : 0LL;
+}
+
+// block-wise inclusive scan, writing per-block totals
+__global__ void k_scan_block(long long* x, int64_t n, long long* bsum)
+{
+    __shared__ long long s[kScanBlock];
+    const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    s[threadIdx.x] = i < n ? x[i] : 0;
+    __syncthreads();
+    for (int off = 1; off < kScanBlock; off <<= 1) {
+        long long v = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+        __syncthreads();
+        s[threadIdx.x] += v;
+        __syncthreads();
+    }
+    if (i < n) x[i] = s[threadIdx.x];
+    if (threadIdx.x == kScanBlock - 1) bsum[blockIdx.x] = s[threadIdx.x];
+}
+
+__global__ void k_scan_add(long long* x, int64_t n, const long long* bsum_incl)
+{
+    const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    if (i >= n || blockIdx.x == 0) return;
+    x[i] += bsum_incl[blockIdx.x - 1];
+}
+
+__global__ void k_store_total(const long long* cdf, int64_t T, DevScalars* sc)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) sc->total = T > 0 ? cdf[T - 1] : 0;
+}
+
+static rc_status scan_inclusive(long long* x, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return RC_OK;
+    const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    long long* bs = nullptr;
+    RC_CUDA(cudaMallocAsync(&bs, sizeof(long long) * nb, s));
+    k_scan_block<<<(unsigned)nb, kScanBlock, 0, s>>>(x, n, bs);
+    RC_LAUNCHED();
+    if (nb > 1) {
+        rc_status st = scan_inclusive(bs, nb, s);
+        if (st != RC_OK) return st;
+        k_scan_add<<<(unsigned)nb, kScanBlock, 0, s>>>(x, n, bs);
+        RC_LAUNCHED();
+    }
+    RC_CUDA(cudaFreeAsync(bs, s));
+    return RC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sampling (Section 3.1)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double uniform01(unsigned long long seed, long long i, int k)
+{
+    const unsigned long long ctr = (unsigned long long)(3 * i + k) * 0x9E3779B97F4A7C15ULL;
+    const unsigned long long r = splitmix64(seed ^ ctr);
+    return __dmul_rn(__ull2double_rn(r >> 11), 1.0 / 9007199254740992.0);
+}
+
+__global__ void k_sample_area(const float* __restrict__ V, const int32_t* __restrict__ F, int64_t T,
+                              const long long* __restrict__ cdf, const DevScalars* sc,
+                              const float* __restrict__ fnorm, int64_t n, unsigned long long seed,
+                              float* P, float* Nout, int32_t* face, double* weight)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double u0 = uniform01(seed, i, 0), u1 = uniform01(seed, i, 1), u2 = uniform01(seed, i, 2);
+    const long long total = sc->total;
+    const long long target = (long long)floor(__dmul_rn(u0, __ll2double_rn(total)));
+    int64_t lo = 0, hi = T - 1;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (cdf[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    const int64_t f = lo;
+    const double s = __dsqrt_rn(u1);
+    const double wa = __dsub_rn(1.0, s);
+    const double wb = __dmul_rn(s, __dsub_rn(1.0, u2));
+    const double wc = __dmul_rn(s, u2);
+    for (int k = 0; k < 3; ++k) {
+        const double A = V[3 * (int64_t)F[3 * f + 0] + k];
+        const double B = V[3 * (int64_t)F[3 * f + 1] + k];
+        const double C = V[3 * (int64_t)F[3 * f + 2] + k];
+        double p = __dadd_rn(__dmul_rn(wa, A), __dmul_rn(wb, B));
+        p = __dadd_rn(p, __dmul_rn(wc, C));
+        P[3 * i + k] = __double2float_rn(p);
+        Nout[3 * i + k] = fnorm[3 * f + k];
+    }
+    face[i] = (int32_t)f;
+    if (weight) weight[i] = 1.0;
+}
+
+__global__ void k_sample_centroid(const float* __restrict__ fcent, const float* __restrict__ fnorm,
+                                  const double* __restrict__ farea, int64_t T, float* P, float* Nout,
+                                  int32_t* face, double* weight)
+{
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= T) return;
+    for (int k = 0; k < 3; ++k) {
+        P[3 * f + k] = fcent[3 * f + k];
+        Nout[3 * f + k] = fnorm[3 * f + k];
+    }
+    face[f] = (int32_t)f;
+    if (weight) weight[f] = farea[f];
+}
+
+// ---------------------------------------------------------------------------
+// host drivers
+// ---------------------------------------------------------------------------
+static inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+static rc_status init_scalars(DevScalars* sc, cudaStream_t s)
+{
+    DevScalars h;
+    h.amax_bits = 0;
+    h.total = 0;
+    for (int k = 0; k < 3; ++k) { h.cmin[k] = 0x7FFFFFFF; h.cmax[k] = (int)0x80000000; }
+    h.vmaxabs = 0;
+    h.err_index = 0x7FFFFFFF;
+    h.err_vertex = 0x7FFFFFFF;
+    h.max_depth = 0;
+    h.pad = 0;
+    RC_CUDA(cudaMemcpyAsync(sc, &h, sizeof h, cudaMemcpyHostToDevice, s));
+    RC_CUDA(cudaStreamSynchronize(s));
+    return RC_OK;
+}
+
+static rc_status face_data(rc_bvh h, float* tbox, cudaStream_t s)
+{
+    rc_status st = init_scalars(h->sc, s);
+    if (st != RC_OK) return st;
+    k_face_prep<<<nblocks(h->T, 256), 256, 0, s>>>(h->V, h->nV, h->F, h->T, h->fnorm, h->farea,
+                                                   h->fcent, tbox, h->sc);
+    RC_LAUNCHED();
+    k_quant_area<<<nblocks(h->T, 256), 256, 0, s>>>(h->farea, h->T, h->sc, h->cdf);
+    RC_LAUNCHED();
+    st = scan_inclusive(h->cdf, h->T, s);
+    if (st != RC_OK) return st;
+    k_store_total<<<1, 1, 0, s>>>(h->cdf, h->T, h->sc);
+    RC_LAUNCHED();
+    return RC_OK;
+}
+
+static rc_status check_scalars(rc_bvh h, cudaStream_t s)
+{
+    RC_CUDA(cudaMemcpyAsync(&h->host_sc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    RC_CUDA(cudaStreamSynchronize(s));
+    const DevScalars& d = h->host_sc;
+    if (d.err_index != 0x7FFFFFFF)
+        return set_error(RC_E_ARG, "face " + std::to_string(d.err_index) + " has a vertex index outside [0, nV)");
+    if (d.err_vertex != 0x7FFFFFFF)
+        return set_error(RC_E_ARG, "vertex " + std::to_string(d.err_vertex) + " is not finite");
+    h->scene_maxabs = std::max(1.0f, ordered_to_float(d.vmaxabs));
+    h->max_depth = d.max_depth;
+    return RC_OK;
+}
+
+rc_status build_bvh(rc_bvh h, cudaStream_t s)
+{
+    const int64_t T = h->T;
+    float* tbox = nullptr;
+    RC_CUDA(cudaMallocAsync(&tbox, sizeof(float) * 6 * T, s));
+    rc_status st = face_data(h, tbox, s);
+    if (st != RC_OK) return st;
+    st = check_scalars(h, s);
+    if (st != RC_OK) { cudaFreeAsync(tbox, s); return st; }
+
+    h->n_int = T > kLeafMax ? T - 1 : 1;
+    RC_CUDA(cudaMalloc(&h->nodes, sizeof(float4) * 4 * h->n_int));
+    RC_CUDA(cudaMalloc(&h->tris, sizeof(float4) * 3 * T));
+    RC_CUDA(cudaMalloc(&h->order, sizeof(int32_t) * T));
+
+    if (T <= kLeafMax) {
+        int32_t ord[kLeafMax];
+        for (int i = 0; i < kLeafMax; ++i) ord[i] = i;
+        RC_CUDA(cudaMemcpyAsync(h->order, ord, sizeof(int32_t) * T, cudaMemcpyHostToDevice, s));
+        k_pack_small<<<1, 32, 0, s>>>(T, tbox, h->nodes);
+        RC_LAUNCHED();
+        h->max_depth = 1;
+    } else {
+        unsigned long long *k0 = nullptr, *k1 = nullptr;
+        int32_t* v1 = nullptr;
+        unsigned int* counts = nullptr;
+        const int nblk = (int)((T + kSortTile - 1) / kSortTile);
+        RC_CUDA(cudaMallocAsync(&k0, sizeof(unsigned long long) * T, s));
+        RC_CUDA(cudaMallocAsync(&k1, sizeof(unsigned long long) * T, s));
+        RC_CUDA(cudaMallocAsync(&v1, sizeof(int32_t) * T, s));
+        RC_CUDA(cudaMallocAsync(&counts, sizeof(unsigned int) * 256 * nblk, s));
+        k_morton<<<nblocks(T, 256), 256, 0, s>>>(tbox, T, h->sc, k0, h->order);
+        RC_LAUNCHED();
+        unsigned long long *kin = k0, *kout = k1;
+        int32_t *vin = h->order, *vout = v1;
+        for (int pass = 0; pass < 8; ++pass) {
+            const int shift = 8 * pass;
+            k_sort_hist<<<nblk, kSortThreads, 0, s>>>(kin, T, shift, nblk, counts);
+            RC_LAUNCHED();
+            k_sort_scan<<<1, 1024, 0, s>>>(counts, (int64_t)256 * nblk);
+            RC_LAUNCHED();
+            k_sort_scatter<<<nblk, kSortThreads, 0, s>>>(kin, vin, T, shift, nblk, counts, kout, vout,
+                                                         (unsigned int*)&h->sc->pad);
+            RC_LAUNCHED();
+            std::swap(kin, kout);
+            std::swap(vin, vout);
+        }
+        // after 8 passes the sorted data is back in (k0, h->order)
+        const int64_t n_int = h->n_int;
+        RC_CUDA(cudaMalloc(&h->parent, sizeof(int32_t) * (n_int + T)));
+        RC_CUDA(cudaMalloc(&h->child, sizeof(int32_t) * 2 * n_int));
+        RC_CUDA(cudaMalloc(&h->range, sizeof(int32_t) * 2 * n_int));
+        RC_CUDA(cudaMalloc(&h->nbox, sizeof(float) * 6 * (n_int + T)));
+        RC_CUDA(cudaMalloc(&h->visits, sizeof(int32_t) * n_int));
+        k_karras<<<nblocks(n_int, 256), 256, 0, s>>>(k0, T, h->child, h->range, h->parent);
+        RC_LAUNCHED();
+        RC_CUDA(cudaMemsetAsync(h->visits, 0, sizeof(int32_t) * n_int, s));
+        k_leaf_boxes<<<nblocks(T, 256), 256, 0, s>>>(tbox, h->order, T, n_int, h->nbox);
+        RC_LAUNCHED();
+        k_refit<<<nblocks(T, 256), 256, 0, s>>>(T, n_int, h->parent, h->child, h->nbox, h->visits, h->sc);
+        RC_LAUNCHED();
+        k_pack<<<nblocks(n_int, 256), 256, 0, s>>>(n_int, h->child, h->range, h->nbox, h->nodes);
+        RC_LAUNCHED();
+        RC_CUDA(cudaFreeAsync(k0, s));
+        RC_CUDA(cudaFreeAsync(k1, s));
+        RC_CUDA(cudaFreeAsync(v1, s));
+        RC_CUDA(cudaFreeAsync(counts, s));
+    }
+    k_tri_records<<<nblocks(T, 256), 256, 0, s>>>(h->V, h->F, h->order, T, h->tris);
+    RC_LAUNCHED();
+    RC_CUDA(cudaFreeAsync(tbox, s));
+    RC_CUDA(cudaMemcpyAsync(&h->host_sc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    RC_CUDA(cudaStreamSynchronize(s));
+    if (h->host_sc.pad != 0) return set_error(RC_E_DEVICE, "radix sort produced an out-of-range position");
+    if (T > kLeafMax) h->max_depth = h->host_sc.max_depth;
+    for (int k = 0; k < 3; ++k) { h->lo[k] = 0; h->hi[k] = 0; }
+    if (h->max_depth >= kStack)
+        return set_error(RC_E_UNSUPPORTED, "BVH depth " + std::to_string(h->max_depth) +
+                                               " exceeds the traversal stack");
+    return RC_OK;
+}
+
+rc_status refit_bvh(rc_bvh h, cudaStream_t s)
+{
+    const int64_t T = h->T;
+    float* tbox = nullptr;
+    RC_CUDA(cudaMallocAsync(&tbox, sizeof(float) * 6 * T, s));
+    rc_status st = face_data(h, tbox, s);
+    if (st != RC_OK) return st;
+    st = check_scalars(h, s);
+    if (st != RC_OK) { cudaFreeAsync(tbox, s); return st; }
+    if (T <= kLeafMax) {
+        k_pack_small<<<1, 32, 0, s>>>(T, tbox, h->nodes);
+        RC_LAUNCHED();
+    } else {
+        const int64_t n_int = h->n_int;
+        RC_CUDA(cudaMemsetAsync(h->visits, 0, sizeof(int32_t) * n_int, s));
+        k_leaf_boxes<<<nblocks(T, 256), 256, 0, s>>>(tbox, h->order, T, n_int, h->nbox);
+        RC_LAUNCHED();
+        k_refit<<<nblocks(T, 256), 256, 0, s>>>(T, n_int, h->parent, h->child, h->nbox, h->visits, h->sc);
+        RC_LAUNCHED();
+        k_pack<<<nblocks(n_int, 256), 256, 0, s>>>(n_int, h->child, h->range, h->nbox, h->nodes);
+        RC_LAUNCHED();
+    }
+    k_tri_records<<<nblocks(T, 256), 256, 0, s>>>(h->V, h->F, h->order, T, h->tris);
+    RC_LAUNCHED();
+    RC_CUDA(cudaFreeAsync(tbox, s));
+    RC_CUDA(cudaStreamSynchronize(s));
+    return RC_OK;
+}
+
+rc_status sample_points(rc_bvh h, int64_t n, const rc_params* p, float* P, float* N, int32_t* face,
+                        double* weight, cudaStream_t s)
+{
+    if (p->sample_mode == RC_SAMPLE_FACE_CENTROID) {
+        k_sample_centroid<<<nblocks(h->T, 256), 256, 0, s>>>(h->fcent, h->fnorm, h->farea, h->T, P, N, face, weight);
+        RC_LAUNCHED();
+        return RC_OK;
+    }
+    k_sample_area<<<nblocks(n, 256), 256, 0, s>>>(h->V, h->F, h->T, h->cdf, h->sc, h->fnorm, n, p->seed,
+                                                  P, N, face, weight);
+    RC_LAUNCHED();
+    return RC_OK;
+}
+
+}  // namespace rc

@@ -1,0 +1,486 @@
+// cast.cu -- any-hit occlusion traversal (Section 3.1 hemispherical cast,
+// Section 3.2 orthogonal cast).
+//
+// Each ray/triangle pair is first decided in FP32 with the watertight test
+// of Woop, Benthin and Wald (JCGT 2013) together with a forward error bound
+// on its edge functions U, V, W, on det = U+V+W and on the unscaled
+// plane-crossing value T' = U*az + V*bz + W*cz (see tri_test32).  The FP32
+// outcome is accepted only when it is certain -- a clear hit outside the
+// 1e-9 relative ambiguity band, or certainly no hit -- otherwise the pair is
+// re-decided in FP64 (retest64), which evaluates the occlusion predicate
+// directly (signed volumes against each edge, plane crossing N.a / N.d) and
+// reports whether the pair lies inside the ambiguity band.  Box tests are
+// conservative (Ize, JCGT 2013: far distance scaled by 1 + 2*gamma_3), so
+// no triangle that can be hit at t > 0 is skipped.
+#include <math.h>
+
+#include "rc_internal.cuh"
+
+namespace rc {
+
+enum { kMiss = 0, kHit = 1, kUnsure = 2 };
+
+struct Ray {
+    float ox, oy, oz;
+    float dx, dy, dz;
+    float ix, iy, iz;   // 1/d (IEEE, +-inf for zero components)
+    float Sx, Sy;       // watertight shear
+    int kx, ky, kz;     // watertight permutation
+    float rs;           // bound on max(1, |o|inf, |vertex|inf)
+    float dkz;          // d[kz]
+};
+
+__device__ __forceinline__ float sel3(float a, float b, float c, int k)
+{
+    return k == 0 ? a : (k == 1 ? b : c);
+}
+
+__device__ __forceinline__ void setup_ray(Ray& r, float ox, float oy, float oz, float dx, float dy,
+                                          float dz, float scene_maxabs)
+{
+    r.ox = ox; r.oy = oy; r.oz = oz;
+    r.dx = dx; r.dy = dy; r.dz = dz;
+    r.ix = __fdiv_rn(1.0f, dx);
+    r.iy = __fdiv_rn(1.0f, dy);
+    r.iz = __fdiv_rn(1.0f, dz);
+    const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+    int kz = ax >= ay ? (ax >= az ? 0 : 2) : (ay >= az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    const float dk = sel3(dx, dy, dz, kz);
+    if (dk < 0.0f) { int t = kx; kx = ky; ky = t; }
+    r.kx = kx; r.ky = ky; r.kz = kz;
+    r.dkz = dk;
+    r.Sx = __fdiv_rn(sel3(dx, dy, dz, kx), dk);
+    r.Sy = __fdiv_rn(sel3(dx, dy, dz, ky), dk);
+    r.rs = fmaxf(fmaxf(1.0f, scene_maxabs), fmaxf(fabsf(ox), fmaxf(fabsf(oy), fabsf(oz))));
+}
+
+// FP32 watertight test with a forward error bound.  Returns kHit only when
+// the pair is certainly a clear hit (both outside the ambiguity band and
+// certain in sign), kMiss only when it is certainly not a hit, else kUnsure.
+//
+// Error model (u = 2^-24, all translated coordinates |.| <= M, all sheared
+// coordinates |.| <= P, |Sx|,|Sy| <= 1 because kz is the largest |d|):
+//   sheared coordinate error        E  <= 6 u M
+//   edge function error             eU <= 4 P E + 6 E^2 + 3 u P^2
+//   det error                       eD <= 3 eU + 2.01 u S        (S = sum |U|)
+//   plane-crossing error            eT <= eU Zs + 4.01 u S Zm    (Zs = sum |z|, Zm = max |z|)
+// each scaled by 1.0625 for the rounding of the bound itself.
+__device__ __forceinline__ int tri_test32(const Ray& r, const float4 v0, const float4 v1,
+                                          const float4 v2)
+{
+    const float u = 5.9604644775390625e-8f;
+    const float a0 = v0.x - r.ox, a1 = v0.y - r.oy, a2 = v0.z - r.oz;
+    const float b0 = v1.x - r.ox, b1 = v1.y - r.oy, b2 = v1.z - r.oz;
+    const float c0 = v2.x - r.ox, c1 = v2.y - r.oy, c2 = v2.z - r.oz;
+    const float ax = sel3(a0, a1, a2, r.kx), ay = sel3(a0, a1, a2, r.ky), az = sel3(a0, a1, a2, r.kz);
+    const float bx = sel3(b0, b1, b2, r.kx), by = sel3(b0, b1, b2, r.ky), bz = sel3(b0, b1, b2, r.kz);
+    const float cx = sel3(c0, c1, c2, r.kx), cy = sel3(c0, c1, c2, r.ky), cz = sel3(c0, c1, c2, r.kz);
+    const float Ax = fmaf(-r.Sx, az, ax), Ay = fmaf(-r.Sy, az, ay);
+    const float Bx = fmaf(-r.Sx, bz, bx), By = fmaf(-r.Sy, bz, by);
+    const float Cx = fmaf(-r.Sx, cz, cx), Cy = fmaf(-r.Sy, cz, cy);
+    const float U = fmaf(Cx, By, -(Cy * Bx));
+    const float V = fmaf(Ax, Cy, -(Ay * Cx));
+    const float W = fmaf(Bx, Ay, -(By * Ax));
+
+    const float M = fmaxf(fmaxf(fmaxf(fabsf(a0), fabsf(a1)), fmaxf(fabsf(a2), fabsf(b0))),
+                          fmaxf(fmaxf(fabsf(b1), fabsf(b2)), fmaxf(fmaxf(fabsf(c0), fabsf(c1)), fabsf(c2))));
+    const float P = fmaxf(fmaxf(fmaxf(fabsf(Ax), fabsf(Ay)), fmaxf(fabsf(Bx), fabsf(By))),
+                          fmaxf(fabsf(Cx), fabsf(Cy)));
+    const float E = 6.0f * u * M;
+    const float eU = (4.0f * E * P + 6.0f * E * E + 3.0f * u * P * P) * 1.0625f;
+    const bool uc = fabsf(U) > eU, vc = fabsf(V) > eU, wc = fabsf(W) > eU;
+    const bool pos = (uc && U > 0.0f) || (vc && V > 0.0f) || (wc && W > 0.0f);
+    const bool neg = (uc && U < 0.0f) || (vc && V < 0.0f) || (wc && W < 0.0f);
+    if (pos && neg) return kMiss;
+
+    const float S = fabsf(U) + fabsf(V) + fabsf(W);
+    const float det = U + V + W;
+    const float Tp = fmaf(U, az, fmaf(V, bz, W * cz));
+    const float Zs = fabsf(az) + fabsf(bz) + fabsf(cz);
+    const float Zm = fmaxf(fabsf(az), fmaxf(fabsf(bz), fabsf(cz)));
+    const float eD = (3.0f * eU + 2.01f * u * S) * 1.0625f;
+    const float eT = (eU * Zs + 4.01f * u * S * Zm) * 1.0625f;
+    const bool det_ok = fabsf(det) > eD;
+    const bool tp_ok = fabsf(Tp) > eT;
+    // sign of t = sign(T') * sign(det) * sign(d[kz])
+    const bool ahead = ((Tp > 0.0f) == (det > 0.0f)) == (r.dkz > 0.0f);
+    if (det_ok && tp_ok && !ahead) return kMiss;   // plane crossed behind the origin
+
+    // clear hit: every edge function beyond its error and the tau band, and
+    // the crossing ahead and beyond tau*R along the ray
+    const float tau_edge = 3.0f * 1e-9f * r.rs * v0.w * 1.01f;
+    const float thr = eU + tau_edge;
+    if (fabsf(U) > thr && fabsf(V) > thr && fabsf(W) > thr && tp_ok && ahead) {
+        const float need = eT + 1e-9f * r.rs * (fabsf(det) + eD) * 1.01f;
+        if (fabsf(Tp) > need) return kHit;
+    }
+    return kUnsure;
+}
+
+// FP64 decision of one pair, written from the definition: the ray's line
+// meets the closed triangle iff the signed volumes of the ray direction with
+// each edge (relative to the origin) do not take both signs; the plane is
+// crossed at t = (N.a)/(N.d).  `state` is kMiss / kHit / kUnsure (= the
+// pair lies in the 1e-9 relative ambiguity band); `hit64` is the plain FP64
+// sign decision (used for rays that only ambiguous pairs decide).
+struct Pair64 { int state; bool hit64; };
+
+__device__ __noinline__ Pair64 retest64(const Ray& r, const float4 v0, const float4 v1, const float4 v2)
+{
+    const double o[3] = {r.ox, r.oy, r.oz}, d[3] = {r.dx, r.dy, r.dz};
+    const double A[3] = {v0.x, v0.y, v0.z}, B[3] = {v1.x, v1.y, v1.z}, C[3] = {v2.x, v2.y, v2.z};
+    double a[3], b[3], c[3], eab[3], ebc[3], eca[3];
+    double R = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        a[k] = A[k] - o[k];
+        b[k] = B[k] - o[k];
+        c[k] = C[k] - o[k];
+        eab[k] = B[k] - A[k];
+        ebc[k] = C[k] - B[k];
+        eca[k] = A[k] - C[k];
+        R = fmax(R, fmax(fabs(o[k]), fmax(fabs(A[k]), fmax(fabs(B[k]), fabs(C[k])))));
+    }
+    const double band = kTau * R;
+    // signed volume of (p, e, d) and |e x d| for the three edges
+    const double* P3[3] = {b, c, a};
+    const double* E3[3] = {ebc, eca, eab};
+    double Ev[3], Lv[3];
+    for (int k = 0; k < 3; ++k) {
+        const double* p = P3[k];
+        const double* e = E3[k];
+        const double w0 = p[1] * e[2] - p[2] * e[1];
+        const double w1 = p[2] * e[0] - p[0] * e[2];
+        const double w2 = p[0] * e[1] - p[1] * e[0];
+        Ev[k] = w0 * d[0] + w1 * d[1] + w2 * d[2];
+        const double x0 = e[1] * d[2] - e[2] * d[1];
+        const double x1 = e[2] * d[0] - e[0] * d[2];
+        const double x2 = e[0] * d[1] - e[1] * d[0];
+        Lv[k] = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+    }
+    Pair64 res;
+    const bool spos = Ev[0] > 0.0 || Ev[1] > 0.0 || Ev[2] > 0.0;
+    const bool sneg = Ev[0] < 0.0 || Ev[1] < 0.0 || Ev[2] < 0.0;
+    // N = (B-A) x (C-A) = eab x (-eca)
+    const double N0 = -(eab[1] * eca[2] - eab[2] * eca[1]);
+    const double N1 = -(eab[2] * eca[0] - eab[0] * eca[2]);
+    const double N2 = -(eab[0] * eca[1] - eab[1] * eca[0]);
+    const double nd = N0 * d[0] + N1 * d[1] + N2 * d[2];
+    const double na = N0 * a[0] + N1 * a[1] + N2 * a[2];
+    res.hit64 = !(spos && sneg) && nd != 0.0 && na != 0.0 && ((na > 0.0) == (nd > 0.0));
+
+    bool pos = false, neg = false, small = false;
+    for (int k = 0; k < 3; ++k) {
+        if (fabs(Ev[k]) <= band * Lv[k]) { small = true; continue; }
+        if (Ev[k] > 0.0) pos = true; else neg = true;
+    }
+    if (pos && neg) { res.state = kMiss; return res; }
+    if (nd == 0.0) { res.state = small ? kUnsure : kMiss; return res; }
+    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (fabs(na) * dn <= band * fabs(nd)) { res.state = kUnsure; return res; }
+    if ((na > 0.0) != (nd > 0.0)) { res.state = kMiss; return res; }
+    res.state = small ? kUnsure : kHit;
+    return res;
+}
+
+// Conservative slab test of both children of a packed node.
+__device__ __forceinline__ void box2(const Ray& r, const float4 n0, const float4 n1, const float4 n2,
+                                     bool& h0, bool& h1, float& t0, float& t1)
+{
+    const float rob = 1.0f + 2.0f * 1.7881394e-7f;   // 1 + 2*gamma_3, gamma_3 = 3u/(1-3u)
+    const bool sx = signbit(r.ix), sy = signbit(r.iy), sz = signbit(r.iz);
+    // child 0: (n0.x lo_x, n0.y hi_x, n0.z lo_y, n0.w hi_y, n2.x lo_z, n2.y hi_z)
+    float nx = ((sx ? n0.y : n0.x) - r.ox) * r.ix, fx = ((sx ? n0.x : n0.y) - r.ox) * r.ix;
+    float ny = ((sy ? n0.w : n0.z) - r.oy) * r.iy, fy = ((sy ? n0.z : n0.w) - r.oy) * r.iy;
+    float nz = ((sz ? n2.y : n2.x) - r.oz) * r.iz, fz = ((sz ? n2.x : n2.y) - r.oz) * r.iz;
+    float tn = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.0f));
+    float tf = fminf(fminf(fx, fy), fz) * rob;
+    h0 = tn <= tf;
+    t0 = tn;
+    // child 1: (n1.x lo_x, n1.y hi_x, n1.z lo_y, n1.w hi_y, n2.z lo_z, n2.w hi_z)
+    nx = ((sx ? n1.y : n1.x) - r.ox) * r.ix; fx = ((sx ? n1.x : n1.y) - r.ox) * r.ix;
+    ny = ((sy ? n1.w : n1.z) - r.oy) * r.iy; fy = ((sy ? n1.z : n1.w) - r.oy) * r.iy;
+    nz = ((sz ? n2.w : n2.z) - r.oz) * r.iz; fz = ((sz ? n2.z : n2.w) - r.oz) * r.iz;
+    tn = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.0f));
+    tf = fminf(fminf(fx, fy), fz) * rob;
+    h1 = tn <= tf;
+    t1 = tn;
+}
+
+// Result bits of trace(): bit 0 blocked, bit 1 decided by ambiguous pairs.
+struct TraceOut { int flags; int retests; int overflow; };
+
+__device__ __forceinline__ TraceOut trace(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                          const Ray& r, int max_steps)
+{
+    TraceOut out = {0, 0, 0};
+    int stack[kStack];
+    int sp = 0;
+    int cur = 0;
+    bool amb = false, ambhit = false;
+    // a well-formed tree visits each node at most once, so max_steps (the
+    // node count) is never reached; the cap only bounds a malformed tree
+    for (int steps = 0;; ++steps) {
+        if (steps > max_steps) { out.overflow = 1; out.flags = 1; return out; }
+        if (cur >= 0) {
+            const float4 n0 = __ldg(&nodes[4 * cur + 0]);
+            const float4 n1 = __ldg(&nodes[4 * cur + 1]);
+            const float4 n2 = __ldg(&nodes[4 * cur + 2]);
+            const float4 n3 = __ldg(&nodes[4 * cur + 3]);
+            bool h0, h1;
+            float t0, t1;
+            box2(r, n0, n1, n2, h0, h1, t0, t1);
+            const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+            if (h0 && h1) {
+                const bool first0 = t0 <= t1;
+                if (sp >= kStack) { out.overflow = 1; out.flags = 1; return out; }
+                stack[sp++] = first0 ? c1 : c0;
+                cur = first0 ? c0 : c1;
+                continue;
+            }
+            if (h0) { cur = c0; continue; }
+            if (h1) { cur = c1; continue; }
+        } else {
+            const int v = -1 - cur;
+            const int first = v >> 3, cnt = (v & 7) + 1;
+            for (int k = 0; k < cnt; ++k) {
+                const float4* t = tris + 3 * (first + k);
+                const float4 v0 = __ldg(t), v1 = __ldg(t + 1), v2 = __ldg(t + 2);
+                const int s = tri_test32(r, v0, v1, v2);
+                if (s == kHit) { out.flags = 1; return out; }
+                if (s == kUnsure) {
+                    ++out.retests;
+                    const Pair64 p = retest64(r, v0, v1, v2);
+                    if (p.state == kHit) { out.flags = 1; return out; }
+                    if (p.state == kUnsure) { amb = true; ambhit |= p.hit64; }
+                }
+            }
+        }
+        if (sp == 0) break;
+        cur = stack[--sp];
+    }
+    out.flags = (ambhit ? 1 : 0) | (amb ? 2 : 0);
+    return out;
+}
+
+__device__ __forceinline__ void warp_add_counters(unsigned long long* counters, long long rays,
+                                                  int amb, int retests, int overflow)
+{
+    const unsigned full = 0xFFFFFFFFu;
+    for (int off = 16; off; off >>= 1) {
+        amb += __shfl_xor_sync(full, amb, off);
+        retests += __shfl_xor_sync(full, retests, off);
+        overflow += __shfl_xor_sync(full, overflow, off);
+    }
+    if ((threadIdx.x & 31) == 0 && counters) {
+        if (rays) atomicAdd(&counters[0], (unsigned long long)rays);
+        if (amb) atomicAdd(&counters[1], (unsigned long long)amb);
+        if (retests) atomicAdd(&counters[2], (unsigned long long)retests);
+        if (overflow) atomicAdd(&counters[3], (unsigned long long)overflow);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Section 3.1: hemispherical cast.  One warp per point (dynamic work
+// counter); lane l of word w casts direction j = 32w + l; the warp ballot is
+// the word of visibility bits, its popcount adds to the point's count.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
+             const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
+             const float4* __restrict__ dirs, int n_dirs, double eps, uint32_t* __restrict__ bits,
+             int32_t* __restrict__ count, unsigned long long* counters, unsigned long long* work)
+{
+    const int lane = threadIdx.x & 31;
+    const int W = n_dirs >> 5;
+    int amb = 0, retests = 0, overflow = 0;
+    long long rays = 0;
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0) i = atomicAdd(work, 1ULL);
+        i = __shfl_sync(0xFFFFFFFFu, i, 0);
+        if (i >= (unsigned long long)n) break;
+        const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
+        const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
+        const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
+        const Onb b = make_onb(nx, ny, nz);
+        int cnt = 0;
+        for (int w = 0; w < W; ++w) {
+            const float4 h = __ldg(&dirs[32 * w + lane]);
+            float dx, dy, dz;
+            local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
+            Ray r;
+            setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
+            const TraceOut t = trace(nodes, tris, r, max_steps);
+            retests += t.retests;
+            overflow += t.overflow;
+            amb += (t.flags >> 1) & 1;
+            const unsigned vis = __ballot_sync(0xFFFFFFFFu, (t.flags & 1) == 0);
+            if (lane == 0) bits[i * W + w] = vis;
+            cnt += __popc(vis);
+        }
+        if (lane == 0) count[i] = cnt;
+        rays += 32LL * W;
+    }
+    warp_add_counters(counters, rays, amb, retests, overflow);
+}
+
+// ---------------------------------------------------------------------------
+// Section 3.2: orthogonal cast.  Eight lanes per point, lane a < 6 casts axis
+// a of (+X', -X', +Y', -Y', +Z', -Z'); travel to the frame bounding box.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
+             const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
+             const float* __restrict__ axes /*6x3*/, const double* __restrict__ frame /*9*/,
+             const double* __restrict__ fbox /*lo3 hi3*/, double eps, uint8_t* __restrict__ mask,
+             float* __restrict__ travel, unsigned long long* counters)
+{
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & 7;
+    int amb = 0, retests = 0, overflow = 0;
+    long long rays = 0;
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
+    const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3);
+    const int64_t iters = (n + groups - 1) / groups;
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t i = g0 + it * groups;
+        bool vis = false;
+        if (i < n && sub < 6) {
+            const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
+            const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
+            const float dx = axes[3 * sub], dy = axes[3 * sub + 1], dz = axes[3 * sub + 2];
+            // travel along the axis to the frame bounding box (FP64)
+            const int k = sub >> 1;
+            double q = __dadd_rn(__dmul_rn((double)px, frame[k]), __dmul_rn((double)py, frame[3 + k]));
+            q = __dadd_rn(q, __dmul_rn((double)pz, frame[6 + k]));
+            const double tv = (sub & 1) ? __dsub_rn(q, fbox[k]) : __dsub_rn(fbox[3 + k], q);
+            travel[6 * i + sub] = __double2float_rn(tv);
+            // eligibility n.a >= 0 (FP64, x, y, z order)
+            double nd = __dadd_rn(__dmul_rn((double)nx, (double)dx), __dmul_rn((double)ny, (double)dy));
+            nd = __dadd_rn(nd, __dmul_rn((double)nz, (double)dz));
+            if (nd >= 0.0) {
+                const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps),
+                            oz = offset_coord(pz, nz, eps);
+                Ray r;
+                setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
+                const TraceOut t = trace(nodes, tris, r, max_steps);
+                retests += t.retests;
+                overflow += t.overflow;
+                amb += (t.flags >> 1) & 1;
+                vis = (t.flags & 1) == 0;
+                rays += 1;
+            }
+        }
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, vis);
+        if (i < n && sub == 0) mask[i] = (uint8_t)((bal >> (lane & ~7)) & 0x3F);
+    }
+    warp_add_counters(counters, rays, amb, retests, overflow);
+}
+
+// FP64 bounding box of the vertices in frame coordinates (orderable atomics).
+__global__ void k_frame_box(const float* __restrict__ V, int64_t nV, const double* __restrict__ frame,
+                            long long* box /*lo3 hi3 ordered*/)
+{
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nV) return;
+    for (int k = 0; k < 3; ++k) {
+        double q = __dadd_rn(__dmul_rn((double)V[3 * v], frame[k]), __dmul_rn((double)V[3 * v + 1], frame[3 + k]));
+        q = __dadd_rn(q, __dmul_rn((double)V[3 * v + 2], frame[6 + k]));
+        atomicMin(&box[k], double_to_ordered(q));
+        atomicMax(&box[3 + k], double_to_ordered(q));
+    }
+}
+
+__global__ void k_frame_box_finish(long long* box, double* fbox)
+{
+    if (threadIdx.x < 6) fbox[threadIdx.x] = ordered_to_double(box[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// host drivers
+// ---------------------------------------------------------------------------
+static int max_steps(rc_bvh h) { return (int)(2 * (h->n_int + h->T) + 64); }
+
+static int g_sm_count = 0;
+
+static int sm_count()
+{
+    if (g_sm_count == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sm_count <= 0) g_sm_count = 1;
+    }
+    return g_sm_count;
+}
+
+rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
+                            uint32_t* bits, int32_t* count, unsigned long long* counters, cudaStream_t s)
+{
+    unsigned long long* work = nullptr;
+    RC_CUDA(cudaMallocAsync(&work, sizeof(unsigned long long), s));
+    RC_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
+    const int threads = p->block_threads > 0 ? p->block_threads : 128;
+    const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : 8;
+    int64_t blocks = (int64_t)sm_count() * per_sm;
+    const int64_t need = (n * 32 + threads - 1) / threads;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    k_hemisphere<<<(unsigned)blocks, threads, 0, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N, n, h->dirs,
+                                                      p->n_dirs, p->origin_offset, bits, count, counters, work);
+    RC_LAUNCHED();
+    RC_CUDA(cudaFreeAsync(work, s));
+    return RC_OK;
+}
+
+__global__ void k_frame_init(FrameArgs a, FrameDev* d)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int k = 0; k < 9; ++k) d->frame[k] = (double)a.f[k];
+    for (int k = 0; k < 3; ++k)
+        for (int c = 0; c < 3; ++c) {
+            d->axes[3 * (2 * k) + c] = a.f[3 * c + k];
+            d->axes[3 * (2 * k + 1) + c] = -a.f[3 * c + k];
+        }
+    for (int k = 0; k < 3; ++k) {
+        d->box[k] = 0x7FFFFFFFFFFFFFFFLL;
+        d->box[3 + k] = (long long)0x8000000000000000ULL;
+    }
+}
+
+// Frame axes, frame matrix (FP64) and the vertices' frame bounding box, all
+// on the device; the frame travels as a kernel argument (no host copy).
+rc_status frame_setup(rc_bvh h, const rc_params* p, FrameDev* d, cudaStream_t s)
+{
+    FrameArgs a;
+    for (int k = 0; k < 9; ++k) a.f[k] = p->frame[k];
+    k_frame_init<<<1, 32, 0, s>>>(a, d);
+    RC_LAUNCHED();
+    k_frame_box<<<(unsigned)((h->nV + 255) / 256), 256, 0, s>>>(h->V, h->nV, d->frame, d->box);
+    RC_LAUNCHED();
+    k_frame_box_finish<<<1, 32, 0, s>>>(d->box, d->fbox);
+    RC_LAUNCHED();
+    return RC_OK;
+}
+
+rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
+                            uint8_t* mask, float* travel, unsigned long long* counters, cudaStream_t s)
+{
+    FrameDev* fd = nullptr;
+    RC_CUDA(cudaMallocAsync(&fd, sizeof(FrameDev), s));
+    rc_status st = frame_setup(h, p, fd, s);
+    if (st != RC_OK) return st;
+    int64_t blocks = (n * 8 + 127) / 128;
+    const int64_t cap = (int64_t)sm_count() * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_orthogonal<<<(unsigned)blocks, 128, 0, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N, n, fd->axes,
+                                                 fd->frame, fd->fbox, p->origin_offset, mask, travel, counters);
+    RC_LAUNCHED();
+    RC_CUDA(cudaFreeAsync(fd, s));
+    return RC_OK;
+}
+
+}  // namespace rc

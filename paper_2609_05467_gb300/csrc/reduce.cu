@@ -1,0 +1,257 @@
+// reduce.cu -- Section 3.3 reductions: directional variability of the
+// visible directions (dominant axis, axis concentration, part sums), the
+// per-direction visible-area histogram, fixture faces and face classes with
+// the 64-bin histogram of reachable-axis masks for the setup cover.
+//
+// Every part-level sum is an int64 sum of fixed-point values, so results do
+// not depend on the order in which blocks finish.
+#include <math.h>
+
+#include "rc_internal.cuh"
+
+namespace rc {
+
+enum { S_COUNTED = 0, S_DOM = 1, S_COUNT = 4, S_WCOUNT = 5, S_WSUM = 6, S_CONC = 7, S_N = 8 };
+
+__device__ __forceinline__ long long quant_weight(const double* w, int64_t i, double wmax)
+{
+    if (!w) return 1;
+    return llround(__dmul_rn(__ddiv_rn(w[i], wmax), 16777216.0));
+}
+
+// One warp per point: recompute each visible direction, sum llrint(d*2^40)
+// per axis, count visible rays per largest-|component| axis.
+__global__ void __launch_bounds__(256)
+k_variability(const uint32_t* __restrict__ bits, const float* __restrict__ Nrm,
+              const double* __restrict__ weight, const double* __restrict__ wmax_p, int64_t n,
+              const float4* __restrict__ dirs, int n_dirs, int conc_mode, float* acc, int8_t* dom,
+              float* conc, unsigned long long* sums)
+{
+    __shared__ long long blk[S_N];
+    if (threadIdx.x < S_N) blk[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int W = n_dirs >> 5;
+    const double wmax = weight ? *wmax_p : 1.0;
+    long long loc[S_N] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
+        const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
+        const Onb b = make_onb(nx, ny, nz);
+        long long M0 = 0, M1 = 0, M2 = 0;
+        int a0 = 0, a1 = 0, a2 = 0, cnt = 0;
+        for (int w = 0; w < W; ++w) {
+            const uint32_t word = bits[i * W + w];
+            if (!((word >> lane) & 1u)) continue;
+            const float4 h = __ldg(&dirs[32 * w + lane]);
+            float dx, dy, dz;
+            local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
+            M0 += llrint((double)dx * 1099511627776.0);
+            M1 += llrint((double)dy * 1099511627776.0);
+            M2 += llrint((double)dz * 1099511627776.0);
+            int best = 0;
+            float bv = fabsf(dx);
+            if (fabsf(dy) > bv) { best = 1; bv = fabsf(dy); }
+            if (fabsf(dz) > bv) best = 2;
+            a0 += best == 0;
+            a1 += best == 1;
+            a2 += best == 2;
+            ++cnt;
+        }
+        for (int off = 16; off; off >>= 1) {
+            M0 += __shfl_xor_sync(0xFFFFFFFFu, M0, off);
+            M1 += __shfl_xor_sync(0xFFFFFFFFu, M1, off);
+            M2 += __shfl_xor_sync(0xFFFFFFFFu, M2, off);
+            a0 += __shfl_xor_sync(0xFFFFFFFFu, a0, off);
+            a1 += __shfl_xor_sync(0xFFFFFFFFu, a1, off);
+            a2 += __shfl_xor_sync(0xFFFFFFFFu, a2, off);
+            cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, off);
+        }
+        if (lane == 0) {
+            const long long Ma[3] = {M0 < 0 ? -M0 : M0, M1 < 0 ? -M1 : M1, M2 < 0 ? -M2 : M2};
+            const int ac[3] = {a0, a1, a2};
+            int dm = -1;
+            double cc = 0.0;
+            if (cnt > 0) {
+                dm = 0;
+                if (Ma[1] > Ma[dm]) dm = 1;
+                if (Ma[2] > Ma[dm]) dm = 2;
+                if (conc_mode == 0)
+                    cc = __ddiv_rn((double)ac[dm], (double)cnt);
+                else
+                    cc = __ddiv_rn(__ll2double_rn(Ma[dm]), __dmul_rn(1099511627776.0, (double)cnt));
+                loc[S_COUNTED] += 1;
+                loc[S_DOM + dm] += 1;
+                loc[S_CONC] += llrint(__dmul_rn(cc, 1099511627776.0));
+            }
+            const long long wq = quant_weight(weight, i, wmax);
+            loc[S_COUNT] += cnt;
+            loc[S_WCOUNT] += wq * (long long)cnt;
+            loc[S_WSUM] += wq;
+            if (acc) acc[i] = __double2float_rn(__ddiv_rn((double)cnt, (double)n_dirs));
+            if (dom) dom[i] = (int8_t)dm;
+            if (conc) conc[i] = __double2float_rn(cc);
+        }
+    }
+    if (lane == 0)
+        for (int k = 0; k < S_N; ++k)
+            if (loc[k]) atomicAdd((unsigned long long*)&blk[k], (unsigned long long)loc[k]);
+    __syncthreads();
+    if (threadIdx.x < S_N && blk[threadIdx.x])
+        atomicAdd(&sums[threadIdx.x], (unsigned long long)blk[threadIdx.x]);
+}
+
+// max weight (weights >= 0) as ordered FP64 bits
+__global__ void k_wmax(const double* __restrict__ w, int64_t n, unsigned long long* out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double m = 0.0;
+    for (; i < n; i += (int64_t)gridDim.x * blockDim.x) m = fmax(m, w[i]);
+    for (int off = 16; off; off >>= 1) m = fmax(m, __shfl_xor_sync(0xFFFFFFFFu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// Per-direction sums of quantised weights over points where the direction is
+// visible.  One warp per (word, chunk of points); lane = bit.
+constexpr int kDirChunk = 512;
+
+__global__ void k_dir_hist(const uint32_t* __restrict__ bits, int64_t n, int W,
+                           const double* __restrict__ weight, const double* __restrict__ wmax_p,
+                           unsigned long long* dirq)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nchunks = (n + kDirChunk - 1) / kDirChunk;
+    if (wid >= nchunks * W) return;
+    const int w = (int)(wid % W);
+    const int64_t c = wid / W;
+    const double wmax = weight ? *wmax_p : 1.0;
+    long long s = 0;
+    const int64_t e = min64(n, (c + 1) * kDirChunk);
+    for (int64_t i = c * kDirChunk; i < e; ++i) {
+        const uint32_t word = __ldg(&bits[i * W + w]);
+        if ((word >> lane) & 1u) s += quant_weight(weight, i, wmax);
+    }
+    if (s) atomicAdd(&dirq[32 * w + lane], (unsigned long long)s);
+}
+
+__global__ void k_dir_finish(const unsigned long long* __restrict__ dirq, int n_dirs,
+                             const double* __restrict__ weight, const double* __restrict__ wmax_p,
+                             double* out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_dirs) return;
+    const double scale = weight ? __ddiv_rn(*wmax_p, 16777216.0) : 1.0;
+    out[j] = __dmul_rn(__ll2double_rn((long long)dirq[j]), scale);
+}
+
+// Fixture faces: all three vertices within tol of one frame bounding-box
+// plane and the normal pointing out through it to within 1e-6.
+__global__ void k_fixture(const float* __restrict__ V, const int32_t* __restrict__ F,
+                          const float* __restrict__ fnorm, int64_t T, const double* __restrict__ frame,
+                          const double* __restrict__ fbox, uint8_t* fixture)
+{
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= T) return;
+    const double d0 = __dsub_rn(fbox[3], fbox[0]), d1 = __dsub_rn(fbox[4], fbox[1]), d2 = __dsub_rn(fbox[5], fbox[2]);
+    const double diag = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2)));
+    const double tol = __dmul_rn(1e-6, diag);
+    const double lim = 1.0 - 1e-6;
+    bool fx = false;
+    for (int k = 0; k < 3; ++k) {
+        bool hi_all = true, lo_all = true;
+        for (int a = 0; a < 3; ++a) {
+            const int64_t v = F[3 * f + a];
+            double q = __dadd_rn(__dmul_rn((double)V[3 * v], frame[k]), __dmul_rn((double)V[3 * v + 1], frame[3 + k]));
+            q = __dadd_rn(q, __dmul_rn((double)V[3 * v + 2], frame[6 + k]));
+            hi_all &= fabs(__dsub_rn(q, fbox[3 + k])) <= tol;
+            lo_all &= fabs(__dsub_rn(q, fbox[k])) <= tol;
+        }
+        double nq = __dadd_rn(__dmul_rn((double)fnorm[3 * f], frame[k]), __dmul_rn((double)fnorm[3 * f + 1], frame[3 + k]));
+        nq = __dadd_rn(nq, __dmul_rn((double)fnorm[3 * f + 2], frame[6 + k]));
+        fx |= (hi_all && nq >= lim) || (lo_all && nq <= -lim);
+    }
+    fixture[f] = fx ? 1 : 0;
+}
+
+// Face classes and the 64-bin histogram of viable reachable masks.
+__global__ void k_classes(const uint8_t* __restrict__ mask, const float* __restrict__ travel,
+                          const int32_t* __restrict__ face, const uint8_t* __restrict__ fixture, int64_t T, int64_t n,
+                          float tool_length, uint8_t* cls_out, unsigned long long* hist /*64 + 4*/)
+{
+    __shared__ unsigned int h[68];
+    for (int k = threadIdx.x; k < 68; k += blockDim.x) h[k] = 0;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned m = mask[i];
+        unsigned reach = 0;
+        for (int a = 0; a < 6; ++a)
+            if (((m >> a) & 1u) && travel[6 * i + a] <= tool_length) reach |= 1u << a;
+        unsigned c = reach ? 0u : (m ? 1u : 2u);
+        const int32_t fi = face[i];
+        if (fi >= 0 && fi < T && fixture[fi]) c = 3u;
+        if (cls_out) cls_out[i] = (uint8_t)c;
+        atomicAdd(&h[64 + c], 1u);
+        if (c == 0u) atomicAdd(&h[reach], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 68; k += blockDim.x)
+        if (h[k]) atomicAdd(&hist[k], (unsigned long long)h[k]);
+}
+
+// ---------------------------------------------------------------------------
+// host drivers
+// ---------------------------------------------------------------------------
+rc_status launch_variability(const uint32_t* bits, const float* N, const double* weight, int64_t n,
+                             const float4* dirs, const rc_params* p, float* acc, int8_t* dom, float* conc,
+                             double* dir_area, unsigned long long* scratch /*S_N + 1 + n_dirs*/,
+                             cudaStream_t s)
+{
+    const int nd = p->n_dirs;
+    unsigned long long* sums = scratch;
+    unsigned long long* wmaxb = scratch + S_N;
+    unsigned long long* dirq = scratch + S_N + 1;
+    const double* wmax_p = (const double*)wmaxb;
+    if (weight && n > 0) {
+        k_wmax<<<256, 256, 0, s>>>(weight, n, wmaxb);
+        RC_LAUNCHED();
+    }
+    if (n > 0) {
+        int sm = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+        int64_t blocks = (n + 7) / 8;
+        if (blocks > (int64_t)sm * 8) blocks = (int64_t)sm * 8;
+        k_variability<<<(unsigned)blocks, 256, 0, s>>>(bits, N, weight, wmax_p, n, dirs, nd, p->conc_mode, acc,
+                                                       dom, conc, sums);
+        RC_LAUNCHED();
+    }
+    if (dir_area) {
+        const int W = nd / 32;
+        const int64_t warps = ((n + kDirChunk - 1) / kDirChunk) * W;
+        if (warps > 0) {
+            k_dir_hist<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(bits, n, W, weight, wmax_p, dirq);
+            RC_LAUNCHED();
+        }
+        k_dir_finish<<<(nd + 255) / 256, 256, 0, s>>>(dirq, nd, weight, wmax_p, dir_area);
+        RC_LAUNCHED();
+    }
+    return RC_OK;
+}
+
+rc_status launch_classes(rc_bvh h, const uint8_t* mask, const float* travel, const int32_t* face, int64_t n,
+                         const rc_params* p, uint8_t* cls, const double* frame_d, const double* fbox_d,
+                         uint8_t* fixture, unsigned long long* hist, cudaStream_t s)
+{
+    k_fixture<<<(unsigned)((h->T + 255) / 256), 256, 0, s>>>(h->V, h->F, h->fnorm, h->T, frame_d, fbox_d, fixture);
+    RC_LAUNCHED();
+    if (n > 0) {
+        int64_t blocks = (n + 255) / 256;
+        if (blocks > 1024) blocks = 1024;
+        k_classes<<<(unsigned)blocks, 256, 0, s>>>(mask, travel, face, fixture, h->T, n, p->tool_length, cls, hist);
+        RC_LAUNCHED();
+    }
+    return RC_OK;
+}
+
+}  // namespace rc

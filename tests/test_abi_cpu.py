@@ -1,0 +1,143 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports
+every entry point that ``include/*.h`` declares, and its host-only logic
+(parameters, direction table, classification, setup cover, argument
+validation) agrees with the oracle.  No kernel is launched here."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rc():
+    import paper_2609_05467_gb300 as rc
+    rc.load()
+    return rc
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(rc_\w+)\s*\(", txt, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("rc_build_bvh", "rc_sample_points", "rc_hemisphere_cast", "rc_direction_variability",
+                 "rc_orthogonal_cast", "rc_classify", "rc_min_setups"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(rc):
+    L = ctypes.CDLL(rc.lib_path())
+    missing = [n for n in sorted(declared_symbols()) if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_header_compiles_as_c(tmp_path):
+    src = tmp_path / "t.c"
+    src.write_text('#include "rc.h"\nint main(void){rc_params p; return rc_params_default(&p);}\n')
+    import subprocess
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-fsyntax-only",
+                           "-I", os.path.join(ROOT, "include"), str(src)])
+
+
+def test_struct_layouts_match_header(rc, tmp_path):
+    src = tmp_path / "s.c"
+    src.write_text('#include <stdio.h>\n#include "rc.h"\nint main(void){printf("%zu %zu %zu %zu", '
+                   'sizeof(rc_params), sizeof(rc_summary), sizeof(rc_setups), sizeof(rc_bvh_info));}\n')
+    import subprocess
+    exe = tmp_path / "s"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split()
+    assert [int(x) for x in out] == [ctypes.sizeof(rc.Params), ctypes.sizeof(rc.Summary),
+                                     ctypes.sizeof(rc.Setups), ctypes.sizeof(rc.BvhInfo)]
+
+
+def test_params_default(rc):
+    p = rc.rc_params_default()
+    assert p.n_dirs == 256 and p.origin_offset == 1e-4 and list(p.frame) == [1, 0, 0, 0, 1, 0, 0, 0, 1]
+    assert (p.t_acc, p.t_share, p.t_conc) == (0.60, 0.45, 0.41)
+
+
+def test_direction_table_bit_equal_to_oracle(rc):
+    for N in (1, 32, 150, 256, 1024, 2048, 65536):
+        _, h32 = oracle.direction_table(N)
+        assert np.array_equal(rc.rc_direction_table(N).view(np.uint32), h32.view(np.uint32))
+    with pytest.raises(rc.RcError):
+        rc.rc_direction_table(0)
+
+
+def test_classify_matches_oracle(rc):
+    rng = np.random.default_rng(0)
+    p = rc.rc_params_default()
+    for _ in range(2000):
+        s = rc.Summary()
+        s.overall_access = float(rng.choice([rng.uniform(0, 1), 0.60]))
+        sh = rng.dirichlet([1, 1, 1])
+        for k in range(3):
+            s.axis_share[k] = float(sh[k])
+        s.mean_conc = float(rng.choice([rng.uniform(0.2, 0.7), 0.41]))
+        d = {"overall_access": s.overall_access, "axis_share": list(s.axis_share), "mean_conc": s.mean_conc}
+        assert rc.rc_classify(s, p) == oracle.classify(d)
+
+
+def test_setup_cover_matches_oracle_brute_force(rc):
+    rng = np.random.default_rng(1)
+    for it in range(400):
+        k = rng.integers(1, 12)
+        masks = rng.integers(1, 64, size=k)
+        if it % 3 == 0:
+            masks = np.array([1 << rng.integers(0, 6) for _ in range(k)]) | (masks & rng.integers(0, 64))
+            masks[masks == 0] = 1
+        hist = np.zeros(64, np.int64)
+        for m in masks:
+            hist[m] += rng.integers(1, 5)
+        pts = [m for m in range(64) for _ in range(hist[m])]
+        out = rc.rc_setup_cover(hist)
+        assert (out.setups_exact, out.chosen_exact) == oracle.setups_exact(pts)
+        g, S = oracle.setups_greedy(pts)
+        assert (out.setups_greedy, out.chosen_greedy) == (g, S)
+    out = rc.rc_setup_cover(np.zeros(64, np.int64))
+    assert out.setups_exact == 0 and out.setups_greedy == 0
+    # the classic instance where greedy is not optimal
+    hist = np.zeros(64, np.int64)
+    for m in (0b011, 0b011, 0b101, 0b101, 0b010, 0b100):
+        hist[m] += 1
+    out = rc.rc_setup_cover(hist)
+    assert out.setups_exact == 2 and out.setups_greedy == 3
+
+
+def test_argument_validation_needs_no_gpu(rc):
+    L = rc.load()
+    h = ctypes.c_void_p()
+    assert L.rc_build_bvh(None, 10, None, 10, None, ctypes.byref(h)) == 1
+    assert b"NULL" in L.rc_last_error()
+    assert L.rc_build_bvh(ctypes.c_void_p(16), 2, ctypes.c_void_p(16), 1, None, ctypes.byref(h)) == 1
+    assert L.rc_build_bvh(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 0, None, ctypes.byref(h)) == 1
+    p = rc.rc_params_default(n_dirs=100)
+    assert L.rc_hemisphere_cast(ctypes.c_void_p(16), None, None, 1, ctypes.byref(p), None, None, None,
+                                None) == 1
+    assert L.rc_classify(None, None, None) == 1
+    assert rc.rc_launch_count() == 0
+
+
+def test_product_path_does_not_touch_the_oracle():
+    """The library package imports nothing from oracle/ and its sources name
+    no oracle file."""
+    pkg = os.path.join(ROOT, "paper_2609_05467_gb300")
+    for f in glob.glob(os.path.join(pkg, "**", "*"), recursive=True):
+        if f.endswith((".py", ".cu", ".cuh", ".h")):
+            txt = open(f).read()
+            assert "import oracle" not in txt and "from oracle" not in txt and "oracle.c" not in txt, f

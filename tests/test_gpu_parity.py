@@ -1,0 +1,359 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Bar: bit-exact for the integer / bit / index outputs (sample points, face
+ids, visibility bits outside the oracle's ambiguous rays, counts, dominant
+axes, masks, classes, setup counts); accessibility fractions within 1e-4
+absolute.  Run on a GB300 with ``pytest -m gpu``."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from common import compare_bits, gpu_cast, gpu_mesh, unpack
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2609_05467_gb300 as rc
+    rc.load()
+    return rc
+
+
+def _build(rc, V, F):
+    Vt, Ft = gpu_mesh(V, F)
+    return rc.Bvh(Vt, Ft)
+
+
+def _sample(rc, bvh, n, params):
+    P = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    N = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    f = torch.zeros(n, dtype=torch.int32, device="cuda")
+    w = torch.zeros(n, dtype=torch.float64, device="cuda")
+    rc.rc_sample_points(bvh.h, n, params, P, N, f, w)
+    torch.cuda.synchronize()
+    return P.cpu().numpy(), N.cpu().numpy(), f.cpu().numpy(), w.cpu().numpy()
+
+
+PARTS = {
+    "pocket": lambda: synth.pocket_block(3),
+    "cube": lambda: synth.cube(20.0, 2),
+    "icosphere": lambda: synth.icosphere(10.0, 3),
+    "cavity": lambda: synth.cavity_box(subdiv=2),
+    "prismatic_coarse": lambda: synth.prismatic(h=4.0),
+    "impeller_coarse": lambda: synth.impeller(h=2.5),
+    "multi_pocket": lambda: synth.box_with_pockets((100.0, 60.0, 40.0), (
+        ("+z", (35.0, 65.0), (15.0, 45.0), 15.0), ("+x", (10.0, 50.0), (10.0, 30.0), 10.0),
+        ("-y", (20.0, 40.0), (5.0, 15.0), 10.0)), subdiv=2),
+}
+
+
+# ---------------------------------------------------------------------------
+# Section 3.1 face data and sampling: bit-exact
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["pocket", "prismatic_coarse", "impeller_coarse"])
+def test_sampling_bit_exact(rc, name):
+    V, F = PARTS[name]()
+    bvh = _build(rc, V, F)
+    for n, seed in ((1, 0), (1000, 0), (4099, 12345)):
+        p = rc.rc_params_default(seed=seed)
+        P, N, f, w = _sample(rc, bvh, n, p)
+        oP, oN, of, ow = oracle.sample_area(V, F, n, seed=seed)
+        assert np.array_equal(P.view(np.uint32), oP.view(np.uint32))
+        assert np.array_equal(N.view(np.uint32), oN.view(np.uint32))
+        assert np.array_equal(f, of) and np.all(w == 1.0)
+    p = rc.rc_params_default(sample_mode=rc.RC_SAMPLE_FACE_CENTROID)
+    P, N, f, w = _sample(rc, bvh, len(F), p)
+    oP, oN, of, ow = oracle.sample_centroid(V, F)
+    assert np.array_equal(P.view(np.uint32), oP.view(np.uint32))
+    assert np.array_equal(N.view(np.uint32), oN.view(np.uint32))
+    assert np.array_equal(w.view(np.uint64), ow.view(np.uint64))
+    bvh.close()
+
+
+def test_direction_table_matches_oracle(rc):
+    for N in (32, 256, 1024, 2048, 65536):
+        _, h32 = oracle.direction_table(N)
+        assert np.array_equal(rc.rc_direction_table(N).view(np.uint32), h32.view(np.uint32))
+
+
+# ---------------------------------------------------------------------------
+# Section 3.1 hemispherical cast: visibility bits exact outside ambiguity
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,n,N", [
+    ("pocket", 1000, 256),          # configuration-1 geometry and sizes
+    ("pocket", 37, 32),
+    ("cube", 200, 64),
+    ("icosphere", 300, 96),
+    ("cavity", 300, 64),
+    ("prismatic_coarse", 777, 160),
+    ("impeller_coarse", 500, 128),
+    ("multi_pocket", 400, 256),
+])
+def test_hemisphere_parity(rc, name, n, N):
+    V, F = PARTS[name]()
+    bvh = _build(rc, V, F)
+    p = rc.rc_params_default(n_dirs=N)
+    P, Nn, f, w = _sample(rc, bvh, n, p)
+    gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
+    ob, oa, oc = oracle.Mesh(V, F).hemisphere(P, Nn, N)
+    cmp_, amb = compare_bits(gb, gc, ob, oa, oc, N)
+    assert cmp_ + amb == n * N
+    assert amb <= max(1, 1e-5 * n * N) + 2
+    assert ctr[0] == n * N and ctr[3] == 0
+    # accessibility fractions within 1e-4
+    assert abs(gc.sum() - oc.sum()) / (n * N) <= 1e-4
+    bvh.close()
+
+
+def test_hemisphere_closed_forms_on_gpu(rc):
+    """Convex parts: every ray escapes; sealed cavity: every ray is blocked."""
+    for V, F, expect in ((*synth.cube(20.0, 2), 1), (*synth.icosphere(10.0, 3), 1)):
+        bvh = _build(rc, V, F)
+        p = rc.rc_params_default(n_dirs=128)
+        P, Nn, f, w = _sample(rc, bvh, 500, p)
+        gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
+        assert (gc == 128).all()
+        bvh.close()
+    V, F = synth.cavity_box(subdiv=1)
+    bvh = _build(rc, V, F)
+    p = rc.rc_params_default(n_dirs=64)
+    P, Nn, f, w = _sample(rc, bvh, 600, p)
+    inner = (P.min(1) > 5) & (P.max(1) < 35)
+    gb, gc, ctr = gpu_cast(rc, bvh.h, P[inner], Nn[inner], p)
+    assert (gc == 0).all()
+    bvh.close()
+
+
+def test_pocket_floor_centre_fraction_on_gpu(rc):
+    V, F = synth.pocket_block(3)
+    bvh = _build(rc, V, F)
+    p = rc.rc_params_default(n_dirs=65536)
+    P = np.array([[50.0, 30.0, 25.0]], np.float32)
+    Nn = np.array([[0, 0, 1]], np.float32)
+    gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
+    assert abs(gc[0] / 65536 - 1 / 3) < 1e-3
+    ob, oa, oc = oracle.Mesh(V, F).hemisphere(P, Nn, 65536)
+    compare_bits(gb, gc, ob, oa, oc, 65536)
+    bvh.close()
+
+
+def test_cast_is_deterministic(rc):
+    V, F = PARTS["prismatic_coarse"]()
+    bvh = _build(rc, V, F)
+    p = rc.rc_params_default(n_dirs=256)
+    P, Nn, f, w = _sample(rc, bvh, 2000, p)
+    a = gpu_cast(rc, bvh.h, P, Nn, p)
+    b = gpu_cast(rc, bvh.h, P, Nn, p)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    bvh.close()
+
+
+# ---------------------------------------------------------------------------
+# Section 3.3 variability, classification
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("conc_mode", [0, 1])
+@pytest.mark.parametrize("mode", ["area", "centroid"])
+def test_variability_parity(rc, conc_mode, mode):
+    V, F = PARTS["multi_pocket"]()
+    bvh = _build(rc, V, F)
+    N = 256
+    if mode == "area":
+        p = rc.rc_params_default(n_dirs=N, conc_mode=conc_mode)
+        P, Nn, f, w = _sample(rc, bvh, 3000, p)
+        wt = None
+    else:
+        p = rc.rc_params_default(n_dirs=N, conc_mode=conc_mode, sample_mode=rc.RC_SAMPLE_FACE_CENTROID)
+        P, Nn, f, w = _sample(rc, bvh, len(F), p)
+        wt = torch.from_numpy(w).cuda()
+    gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
+    n = len(P)
+    bits = torch.from_numpy(gb.view(np.int32).copy()).cuda()
+    Nt = torch.from_numpy(Nn).cuda()
+    acc = torch.zeros(n, dtype=torch.float32, device="cuda")
+    dom = torch.zeros(n, dtype=torch.int8, device="cuda")
+    conc = torch.zeros(n, dtype=torch.float32, device="cuda")
+    dira = torch.zeros(N, dtype=torch.float64, device="cuda")
+    s = rc.rc_direction_variability(bits, Nt, p, weight=wt, acc=acc, dom=dom, conc=conc, dir_area=dira)
+    # the oracle on the same bits
+    M, ac, odom, oconc, ocnt = oracle.variability(gb, Nn, N, conc_mode=conc_mode)
+    assert np.array_equal(dom.cpu().numpy(), odom)
+    assert np.array_equal(conc.cpu().numpy(), oconc.astype(np.float32))
+    assert np.array_equal(acc.cpu().numpy(), (ocnt / N).astype(np.float32))
+    os_ = oracle.summary(ocnt, odom, oconc, N, weight=None if wt is None else w)
+    assert s.overall_access == os_["overall_access"]
+    assert list(s.axis_share) == os_["axis_share"]
+    assert s.mean_conc == os_["mean_conc"]
+    assert s.n_counted == os_["n_counted"] and s.n_zero_visible == os_["n_zero_visible"]
+    lab = rc.rc_classify(s, p)
+    assert lab == oracle.classify(os_)
+    # per-direction visible weight
+    wq = oracle.quantised_weights(np.ones(n) if wt is None else w)
+    scale = 1.0 if wt is None else w.max() / 16777216.0
+    expect = (unpack(gb, N) * wq[:, None]).sum(0).astype(np.float64) * scale
+    assert np.array_equal(dira.cpu().numpy(), expect)
+    bvh.close()
+
+
+# ---------------------------------------------------------------------------
+# Sections 3.2 / 3.3: orthogonal cast, classes, setups
+# ---------------------------------------------------------------------------
+
+FRAMES = {
+    "identity": None,
+    "quarter_z": [0, -1, 0, 1, 0, 0, 0, 0, 1],
+    "tilted": [0.8, -0.6, 0, 0.6, 0.8, 0, 0, 0, 1],
+}
+
+
+@pytest.mark.parametrize("frame", list(FRAMES))
+@pytest.mark.parametrize("name", ["pocket", "multi_pocket", "prismatic_coarse"])
+def test_orthogonal_and_setups_parity(rc, name, frame):
+    V, F = PARTS[name]()
+    bvh = _build(rc, V, F)
+    fr = FRAMES[frame]
+    kw = {} if fr is None else {"frame": fr}
+    for mode in (rc.RC_SAMPLE_FACE_CENTROID, rc.RC_SAMPLE_AREA_RANDOM):
+        p = rc.rc_params_default(sample_mode=mode, tool_length=30.0, **kw)
+        n = len(F) if mode == rc.RC_SAMPLE_FACE_CENTROID else 2500
+        P, Nn, f, w = _sample(rc, bvh, n, p)
+        Pt, Nt = torch.from_numpy(P).cuda(), torch.from_numpy(Nn).cuda()
+        mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        trav = torch.zeros((n, 6), dtype=torch.float32, device="cuda")
+        ctr = torch.zeros(4, dtype=torch.int64, device="cuda")
+        rc.rc_orthogonal_cast(bvh.h, Pt, Nt, p, mask, trav, ctr)
+        ft = torch.from_numpy(f).cuda()
+        cls = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        su = rc.rc_min_setups(bvh.h, mask, trav, ft, p, cls)
+        gm = mask.cpu().numpy()
+        gt = trav.cpu().numpy()
+        om, oam = oracle.Mesh(V, F).orthogonal(P, Nn, frame=fr)
+        ot = oracle.travel(V, P, frame=fr)
+        assert np.array_equal(gt.view(np.uint32), ot.view(np.uint32))
+        clean = oam == 0
+        assert np.array_equal(gm[clean], om[clean])
+        assert (~clean).sum() <= max(2, 1e-5 * 6 * n)
+        fx = oracle.fixture_faces(V, F, frame=fr)
+        ocls, oreach = oracle.face_classes(gm, gt, f, fx, 30.0)
+        assert np.array_equal(cls.cpu().numpy(), ocls)
+        viable = oreach[ocls == 0]
+        assert su.setups_exact == oracle.setups_exact(viable)[0]
+        assert su.chosen_exact == oracle.setups_exact(viable)[1]
+        assert su.setups_greedy == oracle.setups_greedy(viable)[0]
+        assert list(su.class_counts) == [int((ocls == k).sum()) for k in range(4)]
+        assert ctr.cpu().numpy()[3] == 0
+    bvh.close()
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_edge_cases(rc):
+    # single triangle and tiny parts (single-leaf root)
+    for T in (1, 2, 4, 5):
+        V, F = synth.cube(10.0, 0)
+        F = F[:T]
+        bvh = _build(rc, V, F)
+        p = rc.rc_params_default(n_dirs=64)
+        P, Nn, f, w = _sample(rc, bvh, 50, p)
+        gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
+        ob, oa, oc = oracle.Mesh(V, F).hemisphere(P, Nn, 64)
+        compare_bits(gb, gc, ob, oa, oc, 64)
+        bvh.close()
+    V, F = synth.pocket_block(1)
+    bvh = _build(rc, V, F)
+    p = rc.rc_params_default(n_dirs=64)
+    # n == 0 is a no-op
+    e = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    rc.rc_hemisphere_cast(bvh.h, e, e, p, torch.zeros((0, 2), dtype=torch.int32, device="cuda"),
+                          torch.zeros(0, dtype=torch.int32, device="cuda"))
+    # bad n_dirs
+    with pytest.raises(rc.RcError) as ei:
+        rc.rc_hemisphere_cast(bvh.h, e, e, rc.rc_params_default(n_dirs=100), e, e)
+    assert ei.value.status == 1
+    bvh.close()
+    # invalid meshes are rejected
+    Vt, Ft = gpu_mesh(V, F)
+    bad = Ft.clone()
+    bad[3, 1] = len(V)
+    with pytest.raises(rc.RcError):
+        rc.rc_build_bvh(Vt, bad)
+    Vn = Vt.clone()
+    Vn[5, 2] = float("nan")
+    with pytest.raises(rc.RcError):
+        rc.rc_build_bvh(Vn, Ft)
+    # zero-area part cannot be sampled
+    Vz = torch.zeros((3, 3), dtype=torch.float32, device="cuda")
+    Fz = torch.tensor([[0, 1, 2]], dtype=torch.int32, device="cuda")
+    h = rc.rc_build_bvh(Vz, Fz)
+    with pytest.raises(rc.RcError) as ei:
+        P = torch.zeros((4, 3), dtype=torch.float32, device="cuda")
+        rc.rc_sample_points(h, 4, rc.rc_params_default(), P, P.clone(), torch.zeros(4, dtype=torch.int32, device="cuda"))
+    assert ei.value.status == 5
+    rc.rc_destroy_bvh(h)
+
+
+def test_refit_matches_rebuild(rc):
+    V0, F = synth.perturbed_part(2, 0.0)
+    V1, F1 = synth.perturbed_part(2, 3.5)
+    assert np.array_equal(F, F1)
+    Vt0, Ft = gpu_mesh(V0, F)
+    Vt1, _ = gpu_mesh(V1, F)
+    a = rc.Bvh(Vt0, Ft)
+    rc.rc_refit_bvh(a.h, Vt1)
+    b = rc.Bvh(Vt1, Ft)
+    p = rc.rc_params_default(n_dirs=128)
+    P, Nn, f, w = _sample(rc, b, 800, p)
+    ra = gpu_cast(rc, a.h, P, Nn, p)
+    rb = gpu_cast(rc, b.h, P, Nn, p)
+    assert np.array_equal(ra[0], rb[0])
+    Pa, Na, fa, wa = _sample(rc, a, 800, p)
+    assert np.array_equal(Pa, P) and np.array_equal(fa, f)
+    a.close()
+    b.close()
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, sampled outputs (the benchmark's launch configuration)
+# ---------------------------------------------------------------------------
+
+def _full_size(rc, V, F, n, N, n_check, seed=0):
+    bvh = _build(rc, V, F)
+    p = rc.rc_params_default(n_dirs=N, seed=seed)
+    P, Nn, f, w = _sample(rc, bvh, n, p)
+    gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
+    assert ctr[0] == n * N and ctr[3] == 0
+    rng = np.random.default_rng(seed + 1)
+    idx = np.sort(rng.choice(n, size=n_check, replace=False))
+    ob, oa, oc = oracle.Mesh(V, F).hemisphere(P[idx], Nn[idx], N)
+    compare_bits(gb[idx], gc[idx], ob, oa, oc, N)
+    # whole-part properties that hold at any size
+    assert np.array_equal(unpack(gb, N).sum(1), gc)
+    assert int(unpack(oa, N).sum()) <= max(2, 1e-5 * n_check * N)
+    bvh.close()
+    return ctr
+
+
+def test_full_size_prismatic(rc):
+    """Prismatic part: ~200k triangles, 100k points x 1,024 directions."""
+    V, F = synth.prismatic()
+    assert 150_000 < len(F) < 260_000
+    _full_size(rc, V, F, 100_000, 1024, 400)
+
+
+@pytest.mark.slow
+def test_full_size_impeller(rc):
+    """Freeform impeller: ~2M triangles, 1M points x 2,048 directions."""
+    V, F = synth.impeller()
+    _full_size(rc, V, F, 1_000_000, 2048, 60)
