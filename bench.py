@@ -1,0 +1,430 @@
+"""Benchmark of the hemispherical ray-casting hot path on GB300.
+
+One step = one pass of the whole path over one part: BVH build from the
+device-resident mesh, area-weighted sampling, hemispherical cast,
+directional variability + classification, orthogonal cast, reachability and
+setups.  The default workload is the prismatic part (150x100x50 mm block
+with a T-slot, four 20-degree through-holes and two side pockets, ~203k
+triangles), 100,000 area-weighted points (seed 0), 1,024 Fibonacci
+hemisphere directions, origin offset 1e-4 mm, six-axis orthogonal cast.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line (rank 0).  ``value`` = occlusion rays cast per second
+(hemispherical + orthogonal rays, whole job), timed with CUDA events per
+step on the launching stream, L2 flushed (256 MB write) between steps.
+``e2e`` = the same metric through ``rc_analyze_part`` with pinned host
+buffers, host<->device copies inside the timed region.  ``--impl reference``
+times the FP64 CPU oracle on the host cores instead.
+Multi-GPU (torchrun): every rank analyses its own copy of the part (replicas;
+the path has no exchange step), time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "occlusion rays/s"
+UNIT = "rays/s"
+L2_FLUSH_BYTES = 256 << 20
+
+WORKLOADS = {
+    "prismatic": dict(desc="prismatic part 150x100x50 mm (T-slot, four 20-deg through-holes, two side "
+                           "pockets), marching-tetrahedra mesh", n=100_000, n_dirs=1024),
+    "pocket": dict(desc="pocket block 100x60x40 mm with a 30x30x15 mm centred pocket", n=1_000, n_dirs=256),
+    "impeller": dict(desc="impeller, hub r=40 mm, 12 wrapped blades (35-deg twist, 0.8 mm tip gap)",
+                     n=1_000_000, n_dirs=2048),
+}
+
+
+def make_mesh(name):
+    import synth
+    if name == "prismatic":
+        return synth.prismatic()
+    if name == "pocket":
+        return synth.pocket_block(3)
+    if name == "impeller":
+        return synth.impeller()
+    raise ValueError(name)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = [[p.strip() for p in ln.split(",")] for ln in self.lines]
+        rows = [r for r in rows if len(r) >= 9]
+        mine = [r for r in rows if self.uuid and r[0].lower() == self.uuid.lower()]
+        if not mine and len({r[0] for r in rows}) == 1:
+            mine = rows
+        for parts in mine:
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                pw.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": float(max(pw))}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(V, F, n_dirs, n_points, seed=0, build_each=True):
+    """Rays/s of the FP64 oracle (CPU BVH, all host cores) on the first
+    n_points area-weighted points of the workload."""
+    import oracle
+    t0 = time.perf_counter()
+    m = oracle.Mesh(V, F)
+    P, Nn, _, _ = oracle.sample_area(V, F, n_points, seed=seed)
+    t1 = time.perf_counter()
+    m.hemisphere(P, Nn, n_dirs)
+    t2 = time.perf_counter()
+    rays = n_points * n_dirs
+    return rays, (t2 - t0) if build_each else (t2 - t1), oracle.num_cores()
+
+
+def cpu_baseline(V, F, n_dirs, target_s=12.0):
+    import oracle
+    oracle.build()
+    probe = 100
+    rays, t, cores = oracle_rate(V, F, n_dirs, probe)
+    pts = int(max(probe, min(200_000, probe * target_s / max(t, 1e-3))))
+    rays, t, cores = oracle_rate(V, F, n_dirs, pts)
+    return {"value": rays / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d of the workload's area-weighted points x %d directions (%d rays), CPU BVH "
+                      "build + cast, FP64, %.1f s" % (pts, n_dirs, rays, t)}
+
+
+def run_reference(args, wl, V, F):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n_dirs = wl["n_dirs"]
+    rays, t, cores = oracle_rate(V, F, n_dirs, 50)
+    per_step_s = max(1.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    pts = int(max(50, min(wl["n"], 50 * per_step_s / max(t, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_rate(V, F, n_dirs, pts)
+    tot_r = tot_t = 0.0
+    for _ in range(args.steps):
+        r, t, cores = oracle_rate(V, F, n_dirs, pts)
+        tot_r += r
+        tot_t += t
+    value = tot_r / tot_t
+    sample = ("per step: CPU BVH build + %d of the workload's %d points x %d directions (%d rays), FP64 oracle"
+              % (pts, wl["n"], n_dirs, pts * n_dirs))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + wl["desc"], "tris": int(len(F)), "points": wl["n"],
+                   "dirs": n_dirs, "sampled_points_per_step": pts},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def committed_traffic(kernel_src, workload):
+    """DRAM bytes per launch of the traversal kernel from the committed ncu
+    summary, if it was taken on the current kernel source (sha256 match)."""
+    path = os.path.join(ROOT, "profiles", "k_hemisphere_%s_ncu.md" % workload)
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None, None
+    m = re.search(r"kernel source sha256:\s*([0-9a-f]{64})", txt)
+    b = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", txt)
+    if not m or not b:
+        return None, None
+    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    if m.group(1) != cur:
+        return None, "stale"
+    return float(b.group(1)), "ncu"
+
+
+def run_gpu(args, wl, V, F):
+    import torch
+    import paper_2609_05467_gb300 as rc
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    rc.load(build_if_missing=(rank == 0))
+    if ws > 1:
+        torch.distributed.barrier()
+        rc.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    n, N = wl["n"], wl["n_dirs"]
+    W = N // 32
+    p = rc.rc_params_default(n_dirs=N, seed=rank, tool_length=60.0, always_setups=1)
+
+    Vh = torch.from_numpy(V).pin_memory()
+    Fh = torch.from_numpy(F).pin_memory()
+    Vd = Vh.to(dev)
+    Fd = Fh.to(dev)
+    P = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    Nn = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    face = torch.empty(n, dtype=torch.int32, device=dev)
+    bits = torch.empty((n, W), dtype=torch.int32, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    mask = torch.empty(n, dtype=torch.uint8, device=dev)
+    trav = torch.empty((n, 6), dtype=torch.float32, device=dev)
+    cls = torch.empty(n, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    total_steps = args.warmup + args.steps
+    ctr = torch.zeros((total_steps, 2, 4), dtype=torch.int64, device=dev)
+
+    def step(k, ev):
+        h = rc.rc_build_bvh(Vd, Fd, stream)
+        rc.rc_sample_points(h, n, p, P, Nn, face, None, stream)
+        ev[0].record(stream)
+        rc.rc_hemisphere_cast(h, P, Nn, p, bits, cnt, ctr[k, 0], stream)
+        ev[1].record(stream)
+        s = rc.rc_direction_variability(bits, Nn, p, stream=stream)
+        label = rc.rc_classify(s, p)
+        rc.rc_orthogonal_cast(h, P, Nn, p, mask, trav, ctr[k, 1], stream)
+        su = rc.rc_min_setups(h, mask, trav, face, p, cls, stream)
+        rc.rc_destroy_bvh(h)
+        return s, label, su
+
+    # instrumented traversal (outside any timed region): algorithmic bytes per ray
+    h = rc.rc_build_bvh(Vd, Fd, stream)
+    info = rc.rc_bvh_get_info(h)
+    rc.rc_sample_points(h, n, p, P, Nn, face, None, stream)
+    st = torch.zeros(8, dtype=torch.int64, device=dev)
+    ps = rc.rc_params_default(n_dirs=N, seed=rank, collect_stats=1)
+    rc.rc_hemisphere_cast(h, P, Nn, ps, bits, cnt, st, stream)
+    st = st.cpu().numpy()
+    rc.rc_destroy_bvh(h)
+    rays_cast = float(st[0])
+    nodes_per_ray = st[4] / rays_cast
+    tris_per_ray = st[5] / rays_cast
+    bytes_per_ray = 64.0 * nodes_per_ray + 48.0 * tris_per_ray + 24.0 / N + 1.0 / 8.0
+
+    # warm-up
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(total_steps)]
+    for k in range(args.warmup):
+        step(k, evs[k][2:])
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", "") or "")
+    if uuid and not uuid.startswith("GPU-"):
+        uuid = "GPU-" + uuid
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = rc.rc_launch_count()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    step_ms, cast_ms = [], []
+    for k in range(args.warmup, total_steps):
+        flush.zero_()                       # L2 flush, outside the step's events
+        e = evs[k]
+        e[0].record(stream)
+        s, label, su = step(k, e[2:])
+        e[1].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - wall0
+    launches = rc.rc_launch_count() - launches0
+    clocks = sampler.stop()
+    for k in range(args.warmup, total_steps):
+        step_ms.append(evs[k][0].elapsed_time(evs[k][1]))
+        cast_ms.append(evs[k][2].elapsed_time(evs[k][3]))
+    c = ctr.cpu().numpy()
+    rays_per_step = c[args.warmup:, 0, 0] + c[args.warmup:, 1, 0]
+    errors = int(c[:, :, 3].sum())
+    amb_rays = int(c[args.warmup:, 0, 1].sum() + c[args.warmup:, 1, 1].sum())
+    retests = int(c[args.warmup:, 0, 2].sum() + c[args.warmup:, 1, 2].sum())
+    t_dev = sum(step_ms) / 1e3
+    rays_total = float(rays_per_step.sum())
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_dev, rays_total], dtype=torch.float64, device=dev)
+        tmax = tt[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+        t_dev, rays_total = float(tmax.item()), float(tt[1].item())
+    value = rays_total / t_dev
+
+    # end to end through rc_analyze_part with pinned host buffers
+    hb = torch.empty((n, W), dtype=torch.int32).pin_memory()
+    hc = torch.empty(n, dtype=torch.int32).pin_memory()
+    hm = torch.empty(n, dtype=torch.uint8).pin_memory()
+    hk = torch.empty(n, dtype=torch.uint8).pin_memory()
+    for _ in range(0 if args.no_e2e else min(2, args.warmup)):
+        rc.rc_analyze_part(Vh, Fh, n, p, hb, hc, hm, hk, stream)
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 20))
+    e2e_t, e2e_rays = 0.0, 0.0
+    for _ in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = rc.rc_analyze_part(Vh, Fh, n, p, hb, hc, hm, hk, stream)
+        e2e_t += time.perf_counter() - t0
+        e2e_rays += r.cast_counters[0] + r.ortho_counters[0]
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([e2e_t, e2e_rays], dtype=torch.float64, device=dev)
+        tmax = tt[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+        e2e_t, e2e_rays = float(tmax.item()), float(tt[1].item())
+    h2d = V.nbytes + F.nbytes
+    d2h = hb.numel() * 4 + hc.numel() * 4 + hm.numel() + hk.numel() + 2 * 1024
+
+    # roofline of the dominant kernel (the traversal)
+    peak, peak_src = peaks()
+    cast_s = float(np.mean(cast_ms)) / 1e3
+    rays_cast_step = float(np.mean(c[args.warmup:, 0, 0]))
+    alg_bytes = bytes_per_ray * rays_cast_step
+    achieved = alg_bytes / cast_s / 1e9
+    traffic, tsrc = committed_traffic(os.path.join(ROOT, "paper_2609_05467_gb300", "csrc", "cast.cu"),
+                                      args.workload)
+
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(V, F, N)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + wl["desc"], "tris": int(len(F)), "points": n,
+                   "dirs": N, "origin_offset_mm": 1e-4, "sampling": "area-weighted random, seed = rank",
+                   "orthogonal": "6 axes, identity frame", "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "e2e": {"value": e2e_rays / e2e_t if e2e_t > 0 else None, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
+                "api": "rc_analyze_part (pinned host mesh in, bits/counts/masks/classes out)"},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                     "kernel": "k_hemisphere", "kernel_ms": 1e3 * cast_s,
+                     "bytes_per_ray": bytes_per_ray, "nodes_per_ray": nodes_per_ray, "tris_per_ray": tris_per_ray,
+                     "traffic_source": tsrc},
+        "quality": {"ambiguous_rays": amb_rays, "fp64_retests": retests, "errors": errors,
+                    "rays_per_step": float(np.mean(rays_per_step)), "wall_s": wall,
+                    "overall_access": s.overall_access, "label": label, "setups_exact": su.setups_exact,
+                    "bvh_depth": info.max_depth},
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="prismatic", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--points", type=int, default=0, help="override the workload's point count (profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    wl = dict(WORKLOADS[args.workload])
+    if args.points > 0:
+        wl["n"] = args.points
+    V, F = make_mesh(args.workload)
+    if args.impl == "reference":
+        run_reference(args, wl, V, F)
+    else:
+        run_gpu(args, wl, V, F)
+
+
+if __name__ == "__main__":
+    main()

@@ -75,9 +75,12 @@ typedef struct {
     double t_acc;            /* multi-axis if overall accessibility < t_acc (Section 3.3) */
     double t_share;          /* ... or the largest dominant-axis share < t_share */
     double t_conc;           /* ... or the mean axis concentration > t_conc */
-    int32_t block_threads;   /* traversal kernel: threads per block (0 = tuned default) */
+    int32_t block_threads;   /* traversal kernel: threads per block (0 = default; only 128 is supported) */
     int32_t blocks_per_sm;   /* traversal kernel: resident blocks per SM (0 = tuned default) */
-    int32_t reserved[6];
+    int32_t collect_stats;   /* 1: hemispherical cast runs the instrumented traversal (counters[4..5]) */
+    int32_t always_setups;   /* rc_analyze_part: 1 = orthogonal cast and setups for every part, 0 = 3-axis parts only */
+    int32_t point_order;     /* hemispherical cast: 0 = cast points in Morton order (default), 1 = in index order */
+    int32_t reserved[3];
 } rc_params;
 
 /* Part-level indicators (Sections 3.1 and 3.3). */
@@ -199,7 +202,10 @@ rc_status rc_direction_table(int32_t n_dirs, float* h_dirs);
  *   d_P, d_N [n][3]; d_bits [n][n_dirs/32] uint32 (written); d_count [n]
  *   int32 unobstructed counts (written); d_counters int64[4] (written, may be
  *   NULL): rays cast, rays decided by an ambiguous pair, ray/triangle pairs
- *   re-tested in FP64, internal errors (must be 0).
+ *   re-tested in FP64, internal errors (must be 0).  With p->collect_stats
+ *   the counters array must hold 8 entries and [4] receives the interior
+ *   nodes fetched (64 B each) and [5] the triangles tested (48 B each) over
+ *   all rays, from an instrumented copy of the same traversal.
  * n == 0 is a no-op.  Asynchronous.  Errors: RC_E_ARG, RC_E_CUDA. */
 rc_status rc_hemisphere_cast(rc_bvh h, const float* d_P, const float* d_N, int64_t n,
                              const rc_params* p, uint32_t* d_bits, int32_t* d_count,
@@ -266,6 +272,32 @@ rc_status rc_orthogonal_cast(rc_bvh h, const float* d_P, const float* d_N, int64
 rc_status rc_min_setups(rc_bvh h, const uint8_t* d_mask, const float* d_travel,
                         const int32_t* d_face, int64_t n, const rc_params* p, uint8_t* d_class,
                         rc_setups* h_out, void* stream);
+
+/* Result of rc_analyze_part (host struct). */
+typedef struct {
+    rc_summary summary;          /* Section 3.3 indicators */
+    rc_setups setups;            /* zero unless the setup stage ran */
+    int32_t label;               /* 0 = 3-axis, 1 = multi-axis */
+    int32_t setups_ran;          /* 1 if the orthogonal cast and setup search ran */
+    int64_t cast_counters[4];    /* hemispherical cast: rays, ambiguous rays, FP64 re-tests, errors */
+    int64_t ortho_counters[4];   /* orthogonal cast: same */
+} rc_part_result;
+
+/* The whole pipeline of Sections 3.1-3.3 on HOST arrays, in one call: copy
+ * the mesh to the device, build the BVH, sample n points (centroid mode
+ * needs n == T), cast n*N hemisphere rays, reduce them to the indicators,
+ * classify, and -- for 3-axis parts, or for every part if
+ * p->always_setups -- cast the six axes and search the setups; then copy
+ * the requested per-point results back.
+ *   h_V [nV][3], h_F [T][3] (host; pinned memory makes the copies
+ *   asynchronous); outputs h_bits [n][N/32], h_count [n], h_mask [n],
+ *   h_class [n] are host arrays and may each be NULL; h_out receives the
+ *   part-level result.
+ * Device memory is allocated on `stream` and released before returning.
+ * Synchronises `stream`.  Errors: as the individual calls. */
+rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int64_t T, int64_t n,
+                          const rc_params* p, uint32_t* h_bits, int32_t* h_count, uint8_t* h_mask,
+                          uint8_t* h_class, rc_part_result* h_out, void* stream);
 
 /* The two setup covers of Section 3.3 from a 64-bin histogram of viable
  * points per reachable-axis mask (bin 0 is ignored): the exact minimum

@@ -23,7 +23,8 @@ __all__ = [
     "RcError", "Params", "Summary", "Setups", "BvhInfo", "load", "lib_path",
     "rc_params_default", "rc_build_bvh", "rc_refit_bvh", "rc_destroy_bvh", "rc_bvh_get_info",
     "rc_sample_points", "rc_direction_table", "rc_hemisphere_cast", "rc_direction_variability",
-    "rc_classify", "rc_orthogonal_cast", "rc_min_setups", "rc_setup_cover", "rc_launch_count", "Bvh",
+    "rc_classify", "rc_orthogonal_cast", "rc_min_setups", "rc_setup_cover", "rc_analyze_part",
+    "rc_launch_count", "Bvh", "PartResult",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -47,7 +48,8 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("frame", ctypes.c_float * 9), ("tool_length", ctypes.c_float),
         ("conc_mode", ctypes.c_int32), ("t_acc", ctypes.c_double), ("t_share", ctypes.c_double),
         ("t_conc", ctypes.c_double), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("collect_stats", ctypes.c_int32), ("always_setups", ctypes.c_int32), ("point_order", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -75,6 +77,13 @@ class Setups(ctypes.Structure):
         ("setups_exact", ctypes.c_int32), ("setups_greedy", ctypes.c_int32), ("chosen_exact", ctypes.c_uint8),
         ("chosen_greedy", ctypes.c_uint8), ("pad", ctypes.c_uint8 * 6), ("class_counts", ctypes.c_int64 * 4),
         ("mask_hist", ctypes.c_int64 * 64),
+    ]
+
+
+class PartResult(ctypes.Structure):
+    _fields_ = [
+        ("summary", Summary), ("setups", Setups), ("label", ctypes.c_int32), ("setups_ran", ctypes.c_int32),
+        ("cast_counters", ctypes.c_int64 * 4), ("ortho_counters", ctypes.c_int64 * 4),
     ]
 
 
@@ -122,6 +131,8 @@ def load(build_if_missing=True):
             "rc_orthogonal_cast": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P], st),
             "rc_min_setups": ([P, P, P, P, i64, ctypes.POINTER(Params), P, ctypes.POINTER(Setups), P], st),
             "rc_setup_cover": ([P, ctypes.POINTER(Setups)], st),
+            "rc_analyze_part": ([P, i64, P, i64, i64, ctypes.POINTER(Params), P, P, P, P,
+                                 ctypes.POINTER(PartResult), P], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -247,6 +258,29 @@ def rc_setup_cover(mask_hist):
         raise ValueError("mask_hist must have 64 bins")
     out = Setups()
     _check(load().rc_setup_cover(h.ctypes.data_as(ctypes.c_void_p), ctypes.byref(out)))
+    return out
+
+
+def _hptr(a):
+    """Host pointer of a numpy array or CPU tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("expected a contiguous CPU tensor")
+        return ctypes.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous array")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def rc_analyze_part(V, F, n, params, bits=None, count=None, mask=None, cls=None, stream=None):
+    """Whole pipeline on HOST arrays (numpy or pinned CPU tensors): returns a
+    :class:`PartResult`; the optional per-point outputs are host arrays."""
+    out = PartResult()
+    _check(load().rc_analyze_part(_hptr(V), V.shape[0], _hptr(F), F.shape[0], n, ctypes.byref(params),
+                                  _hptr(bits), _hptr(count), _hptr(mask), _hptr(cls), ctypes.byref(out),
+                                  _stream(stream)))
     return out
 
 

@@ -20,7 +20,8 @@ rc_status refit_bvh(rc_bvh h, cudaStream_t s);
 rc_status sample_points(rc_bvh h, int64_t n, const rc_params* p, float* P, float* N, int32_t* face,
                         double* weight, cudaStream_t s);
 rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
-                            uint32_t* bits, int32_t* count, unsigned long long* counters, cudaStream_t s);
+                            uint32_t* bits, int32_t* count, unsigned long long* counters, bool stats,
+                            cudaStream_t s);
 rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
                             uint8_t* mask, float* travel, unsigned long long* counters, cudaStream_t s);
 rc_status frame_setup(rc_bvh h, const rc_params* p, FrameDev* d, cudaStream_t s);
@@ -68,25 +69,58 @@ static void fibonacci_hemisphere(int32_t N, float* out /*N x 3*/)
     }
 }
 
-static std::mutex g_dir_mu;
-static std::map<std::pair<int, int>, float4*> g_dirs;
+// Tile order for the cast: directions sorted by the Morton code of their
+// Lambert equal-area projection (ties by index), so each run of 32 is a
+// compact patch of the hemisphere.  Returns the canonical index per slot.
+static std::vector<int32_t> tile_order(int32_t N, const float* h)
+{
+    std::vector<std::pair<uint64_t, int32_t>> key(N);
+    for (int32_t j = 0; j < N; ++j) {
+        const double x = h[3 * j], y = h[3 * j + 1], z = h[3 * j + 2];
+        const double s = sqrt(2.0 / (1.0 + z));
+        const double X = x * s, Y = y * s;                         // disk of radius sqrt(2)
+        const double r2 = sqrt(2.0);
+        uint32_t qx = (uint32_t)std::min(65535.0, std::max(0.0, (X + r2) / (2 * r2) * 65536.0));
+        uint32_t qy = (uint32_t)std::min(65535.0, std::max(0.0, (Y + r2) / (2 * r2) * 65536.0));
+        uint64_t code = 0;
+        for (int b = 0; b < 16; ++b) code |= (uint64_t)((qx >> b) & 1) << (2 * b) | (uint64_t)((qy >> b) & 1) << (2 * b + 1);
+        key[j] = {code, j};
+    }
+    std::sort(key.begin(), key.end());
+    std::vector<int32_t> ord(N);
+    for (int32_t k = 0; k < N; ++k) ord[k] = key[k].second;
+    return ord;
+}
 
-static rc_status device_dirs(int32_t N, const float4** out)
+struct DirTables { float4* canon; float4* tiled; };
+static std::mutex g_dir_mu;
+static std::map<std::pair<int, int>, DirTables> g_dirs;
+
+static rc_status device_dirs(int32_t N, const float4** canon, const float4** tiled = nullptr)
 {
     int dev = 0;
     RC_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(g_dir_mu);
     auto it = g_dirs.find({dev, N});
-    if (it != g_dirs.end()) { *out = it->second; return RC_OK; }
-    std::vector<float> h(3 * (size_t)N);
-    fibonacci_hemisphere(N, h.data());
-    std::vector<float4> h4(N);
-    for (int32_t j = 0; j < N; ++j) h4[j] = make_float4(h[3 * j], h[3 * j + 1], h[3 * j + 2], 0.0f);
-    float4* d = nullptr;
-    RC_CUDA(cudaMalloc(&d, sizeof(float4) * N));
-    RC_CUDA(cudaMemcpy(d, h4.data(), sizeof(float4) * N, cudaMemcpyHostToDevice));
-    g_dirs[{dev, N}] = d;
-    *out = d;
+    if (it == g_dirs.end()) {
+        std::vector<float> h(3 * (size_t)N);
+        fibonacci_hemisphere(N, h.data());
+        const std::vector<int32_t> ord = tile_order(N, h.data());
+        std::vector<float4> h4(2 * (size_t)N);
+        for (int32_t j = 0; j < N; ++j) h4[j] = make_float4(h[3 * j], h[3 * j + 1], h[3 * j + 2], 0.0f);
+        for (int32_t k = 0; k < N; ++k) {
+            const int32_t j = ord[k];
+            float w;
+            memcpy(&w, &j, sizeof w);
+            h4[N + k] = make_float4(h[3 * j], h[3 * j + 1], h[3 * j + 2], w);
+        }
+        float4* d = nullptr;
+        RC_CUDA(cudaMalloc(&d, sizeof(float4) * 2 * N));
+        RC_CUDA(cudaMemcpy(d, h4.data(), sizeof(float4) * 2 * N, cudaMemcpyHostToDevice));
+        it = g_dirs.emplace(std::make_pair(dev, N), DirTables{d, d + N}).first;
+    }
+    *canon = it->second.canon;
+    if (tiled) *tiled = it->second.tiled;
     return RC_OK;
 }
 
@@ -102,9 +136,11 @@ static rc_status check_params(const rc_params* p)
     if (p->conc_mode != 0 && p->conc_mode != 1) return set_error(RC_E_ARG, "conc_mode must be 0 or 1");
     for (int k = 0; k < 9; ++k)
         if (!isfinite(p->frame[k])) return set_error(RC_E_ARG, "frame must be finite");
-    if (p->block_threads < 0 || p->block_threads > 1024 || p->block_threads % 32)
-        return set_error(RC_E_ARG, "block_threads must be 0 or a multiple of 32 up to 1024");
+    if (p->block_threads != 0 && p->block_threads != 128)
+        return set_error(RC_E_UNSUPPORTED, "block_threads must be 0 (default) or 128");
+    if (p->point_order != 0 && p->point_order != 1) return set_error(RC_E_ARG, "point_order must be 0 or 1");
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return set_error(RC_E_ARG, "blocks_per_sm out of range");
+    if (p->collect_stats != 0 && p->collect_stats != 1) return set_error(RC_E_ARG, "collect_stats must be 0 or 1");
     return RC_OK;
 }
 
@@ -262,14 +298,17 @@ rc_status rc_hemisphere_cast(rc_bvh h, const float* d_P, const float* d_N, int64
     if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = use_device_of(h)) != RC_OK) return st;
-    if (d_counters) RC_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(int64_t) * 4, s));
+    const bool stats = p->collect_stats != 0;
+    if (stats && !d_counters) return set_error(RC_E_ARG, "collect_stats needs the counters array");
+    if (d_counters) RC_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(int64_t) * (stats ? 8 : 4), s));
     if (n == 0) return RC_OK;
     if (!d_P || !d_N || !d_bits || !d_count) return set_error(RC_E_ARG, "array pointer is NULL");
-    const float4* dirs = nullptr;
-    if ((st = device_dirs(p->n_dirs, &dirs)) != RC_OK) return st;
-    h->dirs = const_cast<float4*>(dirs);
+    const float4 *dirs = nullptr, *tdirs = nullptr;
+    if ((st = device_dirs(p->n_dirs, &dirs, &tdirs)) != RC_OK) return st;
+    h->dirs = dirs;
+    h->tdirs = tdirs;
     h->dirs_n = p->n_dirs;
-    return launch_hemisphere(h, d_P, d_N, n, p, d_bits, d_count, (unsigned long long*)d_counters, s);
+    return launch_hemisphere(h, d_P, d_N, n, p, d_bits, d_count, (unsigned long long*)d_counters, stats, s);
 }
 
 rc_status rc_direction_variability(const uint32_t* d_bits, const float* d_N, const double* d_weight, int64_t n,
@@ -374,6 +413,78 @@ rc_status rc_min_setups(rc_bvh h, const uint8_t* d_mask, const float* d_travel, 
     for (int k = 0; k < 64; ++k) h_out->mask_hist[k] = (int64_t)hh[k];
     for (int k = 0; k < 4; ++k) h_out->class_counts[k] = (int64_t)hh[64 + k];
     return rc_setup_cover(h_out->mask_hist, h_out);
+}
+
+rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int64_t T, int64_t n,
+                          const rc_params* p, uint32_t* h_bits, int32_t* h_count, uint8_t* h_mask,
+                          uint8_t* h_class, rc_part_result* h_out, void* stream)
+{
+    if (!h_V || !h_F || !h_out) return set_error(RC_E_ARG, "NULL argument");
+    rc_status st = check_params(p);
+    if (st != RC_OK) return st;
+    if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
+    if (p->sample_mode == RC_SAMPLE_FACE_CENTROID && n != T)
+        return set_error(RC_E_ARG, "centroid sampling needs n == T");
+    if (nV < 3 || T < 1) return set_error(RC_E_ARG, "empty mesh");
+    cudaStream_t s = (cudaStream_t)stream;
+    memset(h_out, 0, sizeof *h_out);
+    const int W = p->n_dirs / 32;
+    const bool centroid = p->sample_mode == RC_SAMPLE_FACE_CENTROID;
+    // one device block for everything, carved into aligned pieces
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+    const size_t oV = take(sizeof(float) * 3 * nV), oF = take(sizeof(int32_t) * 3 * T);
+    const size_t oP = take(sizeof(float) * 3 * n), oN = take(sizeof(float) * 3 * n);
+    const size_t oface = take(sizeof(int32_t) * n), ow = take(centroid ? sizeof(double) * n : 0);
+    const size_t obits = take(sizeof(uint32_t) * W * n), ocnt = take(sizeof(int32_t) * n);
+    const size_t octr = take(sizeof(int64_t) * 8), omask = take(n), otrav = take(sizeof(float) * 6 * n);
+    const size_t ocls = take(n);
+    char* base = nullptr;
+    RC_CUDA(cudaMallocAsync((void**)&base, off ? off : 256, s));
+    float* dV = (float*)(base + oV);
+    int32_t* dF = (int32_t*)(base + oF);
+    float* dP = (float*)(base + oP);
+    float* dN = (float*)(base + oN);
+    int32_t* dface = (int32_t*)(base + oface);
+    double* dw = centroid ? (double*)(base + ow) : nullptr;
+    uint32_t* dbits = (uint32_t*)(base + obits);
+    int32_t* dcnt = (int32_t*)(base + ocnt);
+    int64_t* dctr = (int64_t*)(base + octr);
+    uint8_t* dmask = (uint8_t*)(base + omask);
+    float* dtrav = (float*)(base + otrav);
+    uint8_t* dcls = (uint8_t*)(base + ocls);
+    rc_bvh h = nullptr;
+    auto done = [&](rc_status r) {
+        std::string m = t_err;
+        cudaFreeAsync(base, s);
+        cudaStreamSynchronize(s);
+        if (h) rc_destroy_bvh(h);
+        t_err = m;
+        return r;
+    };
+#define RC_STEP(call) do { rc_status _r = (call); if (_r != RC_OK) return done(_r); } while (0)
+#define RC_CSTEP(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) return done(cuda_error(_e, #call)); } while (0)
+    RC_CSTEP(cudaMemcpyAsync(dV, h_V, sizeof(float) * 3 * nV, cudaMemcpyHostToDevice, s));
+    RC_CSTEP(cudaMemcpyAsync(dF, h_F, sizeof(int32_t) * 3 * T, cudaMemcpyHostToDevice, s));
+    RC_STEP(rc_build_bvh(dV, nV, dF, T, stream, &h));
+    RC_STEP(rc_sample_points(h, n, p, dP, dN, dface, dw, stream));
+    RC_STEP(rc_hemisphere_cast(h, dP, dN, n, p, dbits, dcnt, dctr, stream));
+    RC_CSTEP(cudaMemcpyAsync(h_out->cast_counters, dctr, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost, s));
+    RC_STEP(rc_direction_variability(dbits, dN, dw, n, p, nullptr, nullptr, nullptr, nullptr, &h_out->summary, stream));
+    RC_STEP(rc_classify(&h_out->summary, p, &h_out->label));
+    if (h_bits && n) RC_CSTEP(cudaMemcpyAsync(h_bits, dbits, sizeof(uint32_t) * W * n, cudaMemcpyDeviceToHost, s));
+    if (h_count && n) RC_CSTEP(cudaMemcpyAsync(h_count, dcnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    if (p->always_setups || h_out->label == 0) {
+        RC_STEP(rc_orthogonal_cast(h, dP, dN, n, p, dmask, dtrav, dctr + 4, stream));
+        RC_CSTEP(cudaMemcpyAsync(h_out->ortho_counters, dctr + 4, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost, s));
+        RC_STEP(rc_min_setups(h, dmask, dtrav, dface, n, p, dcls, &h_out->setups, stream));
+        h_out->setups_ran = 1;
+        if (h_mask && n) RC_CSTEP(cudaMemcpyAsync(h_mask, dmask, n, cudaMemcpyDeviceToHost, s));
+        if (h_class && n) RC_CSTEP(cudaMemcpyAsync(h_class, dcls, n, cudaMemcpyDeviceToHost, s));
+    }
+#undef RC_STEP
+#undef RC_CSTEP
+    return done(RC_OK);
 }
 
 rc_status rc_setup_cover(const int64_t* h_mask_hist, rc_setups* out)

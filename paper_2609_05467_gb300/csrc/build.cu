@@ -481,10 +481,84 @@ __global__ void k_sample_centroid(const float* __restrict__ fcent, const float* 
     if (weight) weight[f] = farea[f];
 }
 
+// Morton code (10 bits per axis) of each point inside the box [lo, hi]
+__global__ void k_point_morton(const float* __restrict__ P, int64_t n, float lx, float ly, float lz, float sx,
+                               float sy, float sz, unsigned long long* keys, int32_t* vals)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float lo[3] = {lx, ly, lz}, sc[3] = {sx, sy, sz};
+    unsigned long long code = 0;
+    for (int k = 0; k < 3; ++k) {
+        float u = (P[3 * i + k] - lo[k]) * sc[k];
+        u = fminf(fmaxf(u, 0.0f), 1023.0f);
+        unsigned long long q = (unsigned long long)u;
+        q = (q | (q << 16)) & 0x030000FFULL;
+        q = (q | (q << 8)) & 0x0300F00FULL;
+        q = (q | (q << 4)) & 0x030C30C3ULL;
+        q = (q | (q << 2)) & 0x09249249ULL;
+        code |= q << (2 - k);
+    }
+    keys[i] = code;
+    vals[i] = (int32_t)i;
+}
+
 // ---------------------------------------------------------------------------
 // host drivers
 // ---------------------------------------------------------------------------
 static inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Stable LSD sort of (key, value) pairs by the low `passes` bytes of the key;
+// the result is back in (keys, vals) when `passes` is even.
+static rc_status sort_pairs(unsigned long long* keys, int32_t* vals, int64_t n, int passes, unsigned int* err,
+                            cudaStream_t s)
+{
+    if (n <= 1) return RC_OK;
+    unsigned long long* k1 = nullptr;
+    int32_t* v1 = nullptr;
+    unsigned int* counts = nullptr;
+    const int nblk = (int)((n + kSortTile - 1) / kSortTile);
+    RC_CUDA(cudaMallocAsync(&k1, sizeof(unsigned long long) * n, s));
+    RC_CUDA(cudaMallocAsync(&v1, sizeof(int32_t) * n, s));
+    RC_CUDA(cudaMallocAsync(&counts, sizeof(unsigned int) * 256 * nblk, s));
+    unsigned long long *kin = keys, *kout = k1;
+    int32_t *vin = vals, *vout = v1;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        k_sort_hist<<<nblk, kSortThreads, 0, s>>>(kin, n, shift, nblk, counts);
+        RC_LAUNCHED();
+        k_sort_scan<<<1, 1024, 0, s>>>(counts, (int64_t)256 * nblk);
+        RC_LAUNCHED();
+        k_sort_scatter<<<nblk, kSortThreads, 0, s>>>(kin, vin, n, shift, nblk, counts, kout, vout, err);
+        RC_LAUNCHED();
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    RC_CUDA(cudaFreeAsync(k1, s));
+    RC_CUDA(cudaFreeAsync(v1, s));
+    RC_CUDA(cudaFreeAsync(counts, s));
+    return RC_OK;
+}
+
+// Processing order of sample points: indices sorted by the Morton code of
+// the point within the part's bounding box (written to `order`).
+rc_status point_order(rc_bvh h, const float* P, int64_t n, int32_t* order, cudaStream_t s)
+{
+    unsigned long long* keys = nullptr;
+    RC_CUDA(cudaMallocAsync(&keys, sizeof(unsigned long long) * n, s));
+    float sc[3];
+    for (int k = 0; k < 3; ++k) {
+        const float ext = h->hi[k] - h->lo[k];
+        sc[k] = ext > 0.0f ? 1024.0f / ext : 0.0f;
+    }
+    k_point_morton<<<nblocks(n, 256), 256, 0, s>>>(P, n, h->lo[0], h->lo[1], h->lo[2], sc[0], sc[1], sc[2], keys,
+                                                   order);
+    RC_LAUNCHED();
+    rc_status st = sort_pairs(keys, order, n, 4, (unsigned int*)&h->sc->pad, s);
+    if (st != RC_OK) return st;
+    RC_CUDA(cudaFreeAsync(keys, s));
+    return RC_OK;
+}
 
 static rc_status init_scalars(DevScalars* sc, cudaStream_t s)
 {
@@ -555,30 +629,12 @@ rc_status build_bvh(rc_bvh h, cudaStream_t s)
         RC_LAUNCHED();
         h->max_depth = 1;
     } else {
-        unsigned long long *k0 = nullptr, *k1 = nullptr;
-        int32_t* v1 = nullptr;
-        unsigned int* counts = nullptr;
-        const int nblk = (int)((T + kSortTile - 1) / kSortTile);
+        unsigned long long* k0 = nullptr;
         RC_CUDA(cudaMallocAsync(&k0, sizeof(unsigned long long) * T, s));
-        RC_CUDA(cudaMallocAsync(&k1, sizeof(unsigned long long) * T, s));
-        RC_CUDA(cudaMallocAsync(&v1, sizeof(int32_t) * T, s));
-        RC_CUDA(cudaMallocAsync(&counts, sizeof(unsigned int) * 256 * nblk, s));
         k_morton<<<nblocks(T, 256), 256, 0, s>>>(tbox, T, h->sc, k0, h->order);
         RC_LAUNCHED();
-        unsigned long long *kin = k0, *kout = k1;
-        int32_t *vin = h->order, *vout = v1;
-        for (int pass = 0; pass < 8; ++pass) {
-            const int shift = 8 * pass;
-            k_sort_hist<<<nblk, kSortThreads, 0, s>>>(kin, T, shift, nblk, counts);
-            RC_LAUNCHED();
-            k_sort_scan<<<1, 1024, 0, s>>>(counts, (int64_t)256 * nblk);
-            RC_LAUNCHED();
-            k_sort_scatter<<<nblk, kSortThreads, 0, s>>>(kin, vin, T, shift, nblk, counts, kout, vout,
-                                                         (unsigned int*)&h->sc->pad);
-            RC_LAUNCHED();
-            std::swap(kin, kout);
-            std::swap(vin, vout);
-        }
+        rc_status sst = sort_pairs(k0, h->order, T, 8, (unsigned int*)&h->sc->pad, s);
+        if (sst != RC_OK) return sst;
         // after 8 passes the sorted data is back in (k0, h->order)
         const int64_t n_int = h->n_int;
         RC_CUDA(cudaMalloc(&h->parent, sizeof(int32_t) * (n_int + T)));
@@ -596,9 +652,6 @@ rc_status build_bvh(rc_bvh h, cudaStream_t s)
         k_pack<<<nblocks(n_int, 256), 256, 0, s>>>(n_int, h->child, h->range, h->nbox, h->nodes);
         RC_LAUNCHED();
         RC_CUDA(cudaFreeAsync(k0, s));
-        RC_CUDA(cudaFreeAsync(k1, s));
-        RC_CUDA(cudaFreeAsync(v1, s));
-        RC_CUDA(cudaFreeAsync(counts, s));
     }
     k_tri_records<<<nblocks(T, 256), 256, 0, s>>>(h->V, h->F, h->order, T, h->tris);
     RC_LAUNCHED();

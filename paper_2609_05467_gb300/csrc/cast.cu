@@ -14,6 +14,8 @@
 // no triangle that can be hit at t > 0 is skipped.
 #include <math.h>
 
+#include <algorithm>
+
 #include "rc_internal.cuh"
 
 namespace rc {
@@ -28,6 +30,7 @@ struct Ray {
     int kx, ky, kz;     // watertight permutation
     float rs;           // bound on max(1, |o|inf, |vertex|inf)
     float dkz;          // d[kz]
+    float ef;           // sheared-coordinate error per unit of max |translated coordinate|
 };
 
 __device__ __forceinline__ float sel3(float a, float b, float c, int k)
@@ -53,6 +56,11 @@ __device__ __forceinline__ void setup_ray(Ray& r, float ox, float oy, float oz, 
     r.dkz = dk;
     r.Sx = __fdiv_rn(sel3(dx, dy, dz, kx), dk);
     r.Sy = __fdiv_rn(sel3(dx, dy, dz, ky), dk);
+    // translation rounds once (u|a|); a non-zero shear adds the rounding of
+    // S (u|S||a_z|), of the product and of the fused subtraction
+    const float sm = fmaxf(fabsf(r.Sx), fabsf(r.Sy));
+    const float u = 5.9604644775390625e-8f;
+    r.ef = sm == 0.0f ? 1.01f * u : (2.0f + 3.0f * sm) * 1.01f * u;
     r.rs = fmaxf(fmaxf(1.0f, scene_maxabs), fmaxf(fabsf(ox), fmaxf(fabsf(oy), fabsf(oz))));
 }
 
@@ -61,8 +69,9 @@ __device__ __forceinline__ void setup_ray(Ray& r, float ox, float oy, float oz, 
 // certain in sign), kMiss only when it is certainly not a hit, else kUnsure.
 //
 // Error model (u = 2^-24, all translated coordinates |.| <= M, all sheared
-// coordinates |.| <= P, |Sx|,|Sy| <= 1 because kz is the largest |d|):
-//   sheared coordinate error        E  <= 6 u M
+// coordinates |.| <= P, S = max(|Sx|,|Sy|) <= 1 because kz is the largest |d|):
+//   sheared coordinate error        E  <= (2 + 3 S) u M, and u M when S = 0
+//                                        (the fused subtraction is then exact)
 //   edge function error             eU <= 4 P E + 6 E^2 + 3 u P^2
 //   det error                       eD <= 3 eU + 2.01 u S        (S = sum |U|)
 //   plane-crossing error            eT <= eU Zs + 4.01 u S Zm    (Zs = sum |z|, Zm = max |z|)
@@ -88,7 +97,7 @@ __device__ __forceinline__ int tri_test32(const Ray& r, const float4 v0, const f
                           fmaxf(fmaxf(fabsf(b1), fabsf(b2)), fmaxf(fmaxf(fabsf(c0), fabsf(c1)), fabsf(c2))));
     const float P = fmaxf(fmaxf(fmaxf(fabsf(Ax), fabsf(Ay)), fmaxf(fabsf(Bx), fabsf(By))),
                           fmaxf(fabsf(Cx), fabsf(Cy)));
-    const float E = 6.0f * u * M;
+    const float E = r.ef * M;
     const float eU = (4.0f * E * P + 6.0f * E * E + 3.0f * u * P * P) * 1.0625f;
     const bool uc = fabsf(U) > eU, vc = fabsf(V) > eU, wc = fabsf(W) > eU;
     const bool pos = (uc && U > 0.0f) || (vc && V > 0.0f) || (wc && W > 0.0f);
@@ -209,12 +218,15 @@ __device__ __forceinline__ void box2(const Ray& r, const float4 n0, const float4
 }
 
 // Result bits of trace(): bit 0 blocked, bit 1 decided by ambiguous pairs.
-struct TraceOut { int flags; int retests; int overflow; };
+// With kStats the walk also counts interior-node fetches and triangle tests
+// (the instrumented build used to measure algorithmic bytes per ray).
+struct TraceOut { int flags; int retests; int overflow; int nodes; int tris; };
 
+template <bool kStats>
 __device__ __forceinline__ TraceOut trace(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                           const Ray& r, int max_steps)
 {
-    TraceOut out = {0, 0, 0};
+    TraceOut out = {0, 0, 0, 0, 0};
     int stack[kStack];
     int sp = 0;
     int cur = 0;
@@ -224,6 +236,7 @@ __device__ __forceinline__ TraceOut trace(const float4* __restrict__ nodes, cons
     for (int steps = 0;; ++steps) {
         if (steps > max_steps) { out.overflow = 1; out.flags = 1; return out; }
         if (cur >= 0) {
+            if (kStats) ++out.nodes;
             const float4 n0 = __ldg(&nodes[4 * cur + 0]);
             const float4 n1 = __ldg(&nodes[4 * cur + 1]);
             const float4 n2 = __ldg(&nodes[4 * cur + 2]);
@@ -247,6 +260,7 @@ __device__ __forceinline__ TraceOut trace(const float4* __restrict__ nodes, cons
             for (int k = 0; k < cnt; ++k) {
                 const float4* t = tris + 3 * (first + k);
                 const float4 v0 = __ldg(t), v1 = __ldg(t + 1), v2 = __ldg(t + 2);
+                if (kStats) ++out.tris;
                 const int s = tri_test32(r, v0, v1, v2);
                 if (s == kHit) { out.flags = 1; return out; }
                 if (s == kUnsure) {
@@ -265,65 +279,91 @@ __device__ __forceinline__ TraceOut trace(const float4* __restrict__ nodes, cons
 }
 
 __device__ __forceinline__ void warp_add_counters(unsigned long long* counters, long long rays,
-                                                  int amb, int retests, int overflow)
+                                                  int amb, int retests, int overflow, long long nvis = 0,
+                                                  long long ntri = 0)
 {
     const unsigned full = 0xFFFFFFFFu;
     for (int off = 16; off; off >>= 1) {
+        rays += __shfl_xor_sync(full, rays, off);
         amb += __shfl_xor_sync(full, amb, off);
         retests += __shfl_xor_sync(full, retests, off);
         overflow += __shfl_xor_sync(full, overflow, off);
+        nvis += __shfl_xor_sync(full, nvis, off);
+        ntri += __shfl_xor_sync(full, ntri, off);
     }
     if ((threadIdx.x & 31) == 0 && counters) {
         if (rays) atomicAdd(&counters[0], (unsigned long long)rays);
         if (amb) atomicAdd(&counters[1], (unsigned long long)amb);
         if (retests) atomicAdd(&counters[2], (unsigned long long)retests);
         if (overflow) atomicAdd(&counters[3], (unsigned long long)overflow);
+        if (nvis) atomicAdd(&counters[4], (unsigned long long)nvis);
+        if (ntri) atomicAdd(&counters[5], (unsigned long long)ntri);
     }
 }
 
 // ---------------------------------------------------------------------------
 // Section 3.1: hemispherical cast.  One warp per point (dynamic work
-// counter); lane l of word w casts direction j = 32w + l; the warp ballot is
-// the word of visibility bits, its popcount adds to the point's count.
+// counter).  The warp casts the point's N directions in N/32 tiles of 32
+// spatially close directions (the table is stored in tile order, each entry
+// carrying its canonical index j), so that the lanes of a warp walk nearly
+// the same part of the tree.  Each visible direction sets bit j & 31 of word
+// j >> 5 in the warp's shared-memory row, which is written out in canonical
+// order once the point is done; the count is the sum of the tile ballots.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
+#ifndef RC_HEMI_MIN_BLOCKS
+#define RC_HEMI_MIN_BLOCKS 8
+#endif
+
+template <bool kStats>
+__global__ void __launch_bounds__(128, RC_HEMI_MIN_BLOCKS)
 k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
              const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
-             const float4* __restrict__ dirs, int n_dirs, double eps, uint32_t* __restrict__ bits,
-             int32_t* __restrict__ count, unsigned long long* counters, unsigned long long* work)
+             const int32_t* __restrict__ order, const float4* __restrict__ tdirs, int n_dirs, double eps,
+             uint32_t* __restrict__ bits, int32_t* __restrict__ count, unsigned long long* counters,
+             unsigned long long* work)
 {
+    extern __shared__ uint32_t s_rows[];
     const int lane = threadIdx.x & 31;
     const int W = n_dirs >> 5;
+    uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
     int amb = 0, retests = 0, overflow = 0;
-    long long rays = 0;
+    long long rays = 0, nvis = 0, ntri = 0;
     for (;;) {
-        unsigned long long i = 0;
-        if (lane == 0) i = atomicAdd(work, 1ULL);
-        i = __shfl_sync(0xFFFFFFFFu, i, 0);
-        if (i >= (unsigned long long)n) break;
+        unsigned long long k = 0;
+        if (lane == 0) k = atomicAdd(work, 1ULL);
+        k = __shfl_sync(0xFFFFFFFFu, k, 0);
+        if (k >= (unsigned long long)n) break;
+        const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
+        for (int w = lane; w < W; w += 32) row[w] = 0u;
+        __syncwarp();
         const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
         const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
         const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
         const Onb b = make_onb(nx, ny, nz);
         int cnt = 0;
-        for (int w = 0; w < W; ++w) {
-            const float4 h = __ldg(&dirs[32 * w + lane]);
+        for (int t = 0; t < W; ++t) {
+            const float4 h = __ldg(&tdirs[32 * t + lane]);
+            const int j = __float_as_int(h.w);
             float dx, dy, dz;
             local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
             Ray r;
             setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-            const TraceOut t = trace(nodes, tris, r, max_steps);
-            retests += t.retests;
-            overflow += t.overflow;
-            amb += (t.flags >> 1) & 1;
-            const unsigned vis = __ballot_sync(0xFFFFFFFFu, (t.flags & 1) == 0);
-            if (lane == 0) bits[i * W + w] = vis;
-            cnt += __popc(vis);
+            const TraceOut tr = trace<kStats>(nodes, tris, r, max_steps);
+            retests += tr.retests;
+            overflow += tr.overflow;
+            amb += (tr.flags >> 1) & 1;
+            if (kStats) { nvis += tr.nodes; ntri += tr.tris; }
+            const bool visible = (tr.flags & 1) == 0;
+            if (visible) atomicOr(&row[j >> 5], 1u << (j & 31));
+            cnt += __popc(__ballot_sync(0xFFFFFFFFu, visible));
         }
+        __syncwarp();
+        for (int w = lane; w < W; w += 32) bits[i * W + w] = row[w];
+        __syncwarp();
         if (lane == 0) count[i] = cnt;
-        rays += 32LL * W;
+        rays += W;   // per lane
     }
-    warp_add_counters(counters, rays, amb, retests, overflow);
+    warp_add_counters(counters, rays, amb, retests, overflow, nvis, ntri);
 }
 
 // ---------------------------------------------------------------------------
@@ -365,7 +405,7 @@ k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
                             oz = offset_coord(pz, nz, eps);
                 Ray r;
                 setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-                const TraceOut t = trace(nodes, tris, r, max_steps);
+                const TraceOut t = trace<false>(nodes, tris, r, max_steps);
                 retests += t.retests;
                 overflow += t.overflow;
                 amb += (t.flags >> 1) & 1;
@@ -379,18 +419,32 @@ k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
     warp_add_counters(counters, rays, amb, retests, overflow);
 }
 
-// FP64 bounding box of the vertices in frame coordinates (orderable atomics).
+// FP64 bounding box of the vertices in frame coordinates: per-thread
+// min/max over a grid-stride range, warp reduction, one atomic per warp.
 __global__ void k_frame_box(const float* __restrict__ V, int64_t nV, const double* __restrict__ frame,
                             long long* box /*lo3 hi3 ordered*/)
 {
-    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (v >= nV) return;
-    for (int k = 0; k < 3; ++k) {
-        double q = __dadd_rn(__dmul_rn((double)V[3 * v], frame[k]), __dmul_rn((double)V[3 * v + 1], frame[3 + k]));
-        q = __dadd_rn(q, __dmul_rn((double)V[3 * v + 2], frame[6 + k]));
-        atomicMin(&box[k], double_to_ordered(q));
-        atomicMax(&box[3 + k], double_to_ordered(q));
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nV; v += (int64_t)gridDim.x * blockDim.x) {
+        for (int k = 0; k < 3; ++k) {
+            double q = __dadd_rn(__dmul_rn((double)V[3 * v], frame[k]), __dmul_rn((double)V[3 * v + 1], frame[3 + k]));
+            q = __dadd_rn(q, __dmul_rn((double)V[3 * v + 2], frame[6 + k]));
+            lo[k] = fmin(lo[k], q);
+            hi[k] = fmax(hi[k], q);
+        }
     }
+    for (int off = 16; off; off >>= 1)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], __shfl_xor_sync(0xFFFFFFFFu, lo[k], off));
+            hi[k] = fmax(hi[k], __shfl_xor_sync(0xFFFFFFFFu, hi[k], off));
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 3; ++k) {
+            if (lo[k] <= hi[k]) {
+                atomicMin(&box[k], double_to_ordered(lo[k]));
+                atomicMax(&box[3 + k], double_to_ordered(hi[k]));
+            }
+        }
 }
 
 __global__ void k_frame_box_finish(long long* box, double* fbox)
@@ -416,22 +470,43 @@ static int sm_count()
     return g_sm_count;
 }
 
+rc_status point_order(rc_bvh h, const float* P, int64_t n, int32_t* order, cudaStream_t s);
+
 rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
-                            uint32_t* bits, int32_t* count, unsigned long long* counters, cudaStream_t s)
+                            uint32_t* bits, int32_t* count, unsigned long long* counters, bool stats,
+                            cudaStream_t s)
 {
     unsigned long long* work = nullptr;
     RC_CUDA(cudaMallocAsync(&work, sizeof(unsigned long long), s));
     RC_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
-    const int threads = p->block_threads > 0 ? p->block_threads : 128;
+    int32_t* order = nullptr;
+    if (p->point_order == 0 && n > 1) {
+        RC_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * n, s));
+        rc_status st = point_order(h, P, n, order, s);
+        if (st != RC_OK) return st;
+    }
+    const int threads = 128;
     const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : 8;
     int64_t blocks = (int64_t)sm_count() * per_sm;
     const int64_t need = (n * 32 + threads - 1) / threads;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    k_hemisphere<<<(unsigned)blocks, threads, 0, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N, n, h->dirs,
-                                                      p->n_dirs, p->origin_offset, bits, count, counters, work);
+    const size_t smem = (size_t)(threads / 32) * (p->n_dirs / 32) * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        RC_CUDA(cudaFuncSetAttribute(k_hemisphere<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RC_CUDA(cudaFuncSetAttribute(k_hemisphere<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    if (stats)
+        k_hemisphere<true><<<(unsigned)blocks, threads, smem, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N,
+                                                                n, order, h->tdirs, p->n_dirs, p->origin_offset, bits,
+                                                                count, counters, work);
+    else
+        k_hemisphere<false><<<(unsigned)blocks, threads, smem, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N,
+                                                                 n, order, h->tdirs, p->n_dirs, p->origin_offset, bits,
+                                                                 count, counters, work);
     RC_LAUNCHED();
     RC_CUDA(cudaFreeAsync(work, s));
+    if (order) RC_CUDA(cudaFreeAsync(order, s));
     return RC_OK;
 }
 
@@ -458,7 +533,8 @@ rc_status frame_setup(rc_bvh h, const rc_params* p, FrameDev* d, cudaStream_t s)
     for (int k = 0; k < 9; ++k) a.f[k] = p->frame[k];
     k_frame_init<<<1, 32, 0, s>>>(a, d);
     RC_LAUNCHED();
-    k_frame_box<<<(unsigned)((h->nV + 255) / 256), 256, 0, s>>>(h->V, h->nV, d->frame, d->box);
+    const int64_t fb = std::min<int64_t>((h->nV + 255) / 256, (int64_t)sm_count() * 4);
+    k_frame_box<<<(unsigned)std::max<int64_t>(fb, 1), 256, 0, s>>>(h->V, h->nV, d->frame, d->box);
     RC_LAUNCHED();
     k_frame_box_finish<<<1, 32, 0, s>>>(d->box, d->fbox);
     RC_LAUNCHED();

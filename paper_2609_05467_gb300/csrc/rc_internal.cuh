@@ -89,9 +89,11 @@ struct rc_bvh_s {
     float scene_maxabs = 1.0f;     // max(1, max |vertex coordinate|)
     int max_depth = 0;
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-    // direction table cache (fp32 x, y, z, 0)
+    // direction tables of the last cast (device, cached per device and N):
+    // canonical order (x, y, z, 0) and tile order (x, y, z, canonical index)
     int32_t dirs_n = 0;
-    float4* dirs = nullptr;
+    const float4* dirs = nullptr;
+    const float4* tdirs = nullptr;
 };
 
 // ---------------------------------------------------------------------------
