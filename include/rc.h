@@ -234,6 +234,32 @@ rc_status rc_direction_variability(const uint32_t* d_bits, const float* d_N,
                                    float* d_acc, int8_t* d_dom, float* d_conc, double* d_dir_area,
                                    rc_summary* h_summary, void* stream);
 
+/* Same computation and outputs as rc_direction_variability, but without
+ * any allocation.  The paper has no counterpart: this exists for callers
+ * that cannot let a library allocate device memory -- for example a process
+ * that reserves its whole HBM budget for its own arena at start-up and
+ * routes every allocation through it, or one that runs at its memory limit,
+ * where a cudaMalloc/cudaMallocAsync inside the call would fail or break
+ * the caller's accounting.  The call performs no device or host heap
+ * allocation (no cudaMalloc, cudaFree or allocating library routine).
+ * Its scratch -- the part-level sums, the per-direction counters and the
+ * direction table -- lives in one static device array of 196,864 bytes,
+ * which every GPU that loads the library holds until the process exits;
+ * hence p->n_dirs is limited to 8192 (larger values return
+ * RC_E_UNSUPPORTED).  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current) and
+ * uploads the direction table, so make that first call before any stream
+ * capture.  The counters are cleared on `stream` at every call.  All calls
+ * on a device share the array and it keeps the last call's contents, so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race with each other; serialise them.  Arguments, outputs, limits on
+ * weighted inputs, synchronisation and errors are as for
+ * rc_direction_variability. */
+rc_status rc_direction_variability_noalloc(const uint32_t* d_bits, const float* d_N,
+                                           const double* d_weight, int64_t n, const rc_params* p,
+                                           float* d_acc, int8_t* d_dom, float* d_conc,
+                                           double* d_dir_area, rc_summary* h_summary, void* stream);
+
 /* Threshold classification (Section 3.3: "if any threshold is exceeded, the
  * part is classified as requiring multi-axis machining").  *label = 1
  * (multi-axis) iff overall_access < t_acc, or max axis_share < t_share, or

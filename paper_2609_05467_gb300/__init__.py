@@ -23,6 +23,7 @@ __all__ = [
     "RcError", "Params", "Summary", "Setups", "BvhInfo", "load", "lib_path",
     "rc_params_default", "rc_build_bvh", "rc_refit_bvh", "rc_destroy_bvh", "rc_bvh_get_info",
     "rc_sample_points", "rc_direction_table", "rc_hemisphere_cast", "rc_direction_variability",
+    "rc_direction_variability_noalloc",
     "rc_classify", "rc_orthogonal_cast", "rc_min_setups", "rc_setup_cover", "rc_analyze_part",
     "rc_launch_count", "Bvh", "PartResult",
 ]
@@ -127,6 +128,8 @@ def load(build_if_missing=True):
             "rc_hemisphere_cast": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P], st),
             "rc_direction_variability": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P,
                                           ctypes.POINTER(Summary), P], st),
+            "rc_direction_variability_noalloc": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P,
+                                                  ctypes.POINTER(Summary), P], st),
             "rc_classify": ([ctypes.POINTER(Summary), ctypes.POINTER(Params), ctypes.POINTER(i32)], st),
             "rc_orthogonal_cast": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P], st),
             "rc_min_setups": ([P, P, P, P, i64, ctypes.POINTER(Params), P, ctypes.POINTER(Setups), P], st),
@@ -229,6 +232,18 @@ def rc_direction_variability(bits, N, params, weight=None, acc=None, dom=None, c
     _check(load().rc_direction_variability(_ptr(bits), _ptr(N), _ptr(weight), N.shape[0], ctypes.byref(params),
                                            _ptr(acc), _ptr(dom), _ptr(conc), _ptr(dir_area),
                                            ctypes.byref(s) if s is not None else None, _stream(stream)))
+    return s
+
+
+def rc_direction_variability_noalloc(bits, N, params, weight=None, acc=None, dom=None, conc=None,
+                                     dir_area=None, summary=True, stream=None):
+    """As :func:`rc_direction_variability`, using the library's static
+    device scratch instead of allocating (see include/rc.h)."""
+    s = Summary() if summary else None
+    _check(load().rc_direction_variability_noalloc(_ptr(bits), _ptr(N), _ptr(weight), N.shape[0],
+                                                   ctypes.byref(params), _ptr(acc), _ptr(dom), _ptr(conc),
+                                                   _ptr(dir_area), ctypes.byref(s) if s is not None else None,
+                                                   _stream(stream)))
     return s
 
 
