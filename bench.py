@@ -130,9 +130,10 @@ class ClockSampler:
 # the oracle on the host cores (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_rate(V, F, n_dirs, n_points, seed=0, build_each=True):
-    """Rays/s of the FP64 oracle (CPU BVH, all host cores) on the first
-    n_points area-weighted points of the workload."""
+def oracle_rate(V, F, n_dirs, n_points, seed=0):
+    """Time of the FP64 oracle (CPU BVH, all host cores) on the first
+    n_points area-weighted points of the workload: (rays, build+sampling
+    seconds, cast seconds, cores)."""
     import oracle
     t0 = time.perf_counter()
     m = oracle.Mesh(V, F)
@@ -140,20 +141,20 @@ def oracle_rate(V, F, n_dirs, n_points, seed=0, build_each=True):
     t1 = time.perf_counter()
     m.hemisphere(P, Nn, n_dirs)
     t2 = time.perf_counter()
-    rays = n_points * n_dirs
-    return rays, (t2 - t0) if build_each else (t2 - t1), oracle.num_cores()
+    return n_points * n_dirs, t1 - t0, t2 - t1, oracle.num_cores()
 
 
 def cpu_baseline(V, F, n_dirs, target_s=12.0):
+    """The oracle on a bounded sample sized to about target_s seconds of cast."""
     import oracle
     oracle.build()
-    probe = 100
-    rays, t, cores = oracle_rate(V, F, n_dirs, probe)
-    pts = int(max(probe, min(200_000, probe * target_s / max(t, 1e-3))))
-    rays, t, cores = oracle_rate(V, F, n_dirs, pts)
-    return {"value": rays / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "first %d of the workload's area-weighted points x %d directions (%d rays), CPU BVH "
-                      "build + cast, FP64, %.1f s" % (pts, n_dirs, rays, t)}
+    probe = 500
+    rays, tb, tc, cores = oracle_rate(V, F, n_dirs, probe)
+    pts = int(max(probe, min(2_000_000, probe * target_s / max(tc, 1e-3))))
+    rays, tb, tc, cores = oracle_rate(V, F, n_dirs, pts)
+    return {"value": rays / (tb + tc), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d of the workload's area-weighted points x %d directions (%d rays): CPU BVH build "
+                      "+ sampling %.2f s + cast %.1f s, FP64, all host cores" % (pts, n_dirs, rays, tb, tc)}
 
 
 def run_reference(args, wl, V, F):
@@ -163,16 +164,16 @@ def run_reference(args, wl, V, F):
     import oracle
     oracle.build()
     n_dirs = wl["n_dirs"]
-    rays, t, cores = oracle_rate(V, F, n_dirs, 50)
+    rays, tb, tc, cores = oracle_rate(V, F, n_dirs, 200)
     per_step_s = max(1.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
-    pts = int(max(50, min(wl["n"], 50 * per_step_s / max(t, 1e-3))))
+    pts = int(max(200, min(wl["n"], 200 * max(0.2, per_step_s - tb) / max(tc, 1e-3))))
     for _ in range(args.warmup):
         oracle_rate(V, F, n_dirs, pts)
     tot_r = tot_t = 0.0
     for _ in range(args.steps):
-        r, t, cores = oracle_rate(V, F, n_dirs, pts)
+        r, tb, tc, cores = oracle_rate(V, F, n_dirs, pts)
         tot_r += r
-        tot_t += t
+        tot_t += tb + tc
     value = tot_r / tot_t
     sample = ("per step: CPU BVH build + %d of the workload's %d points x %d directions (%d rays), FP64 oracle"
               % (pts, wl["n"], n_dirs, pts * n_dirs))

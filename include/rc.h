@@ -80,7 +80,9 @@ typedef struct {
     int32_t collect_stats;   /* 1: hemispherical cast runs the instrumented traversal (counters[4..5]) */
     int32_t always_setups;   /* rc_analyze_part: 1 = orthogonal cast and setups for every part, 0 = 3-axis parts only */
     int32_t point_order;     /* hemispherical cast: 0 = cast points in Morton order (default), 1 = in index order */
-    int32_t reserved[3];
+    int32_t tile_mode;       /* hemispherical cast: 0 = directions in coherent tiles of 32 (default), 1 = index order */
+    int32_t points_per_item; /* batched cast: points per work item (0 = 1) */
+    int32_t reserved[1];
 } rc_params;
 
 /* Part-level indicators (Sections 3.1 and 3.3). */
@@ -298,6 +300,51 @@ rc_status rc_orthogonal_cast(rc_bvh h, const float* d_P, const float* d_N, int64
 rc_status rc_min_setups(rc_bvh h, const uint8_t* d_mask, const float* d_travel,
                         const int32_t* d_face, int64_t n, const rc_params* p, uint8_t* d_class,
                         rc_setups* h_out, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Batches: many parts in one persistent launch                           */
+/* ---------------------------------------------------------------------- */
+
+typedef struct rc_batch_s* rc_batch;
+
+/* Create an empty batch for the hemispherical cast of many parts with the
+ * parameters *p (copied).  The paper casts one part at a time; a batch puts
+ * the points of all its parts on one ray-work queue and casts them in one
+ * persistent launch, replayed from a CUDA graph.  Errors: RC_E_ARG,
+ * RC_E_CUDA. */
+rc_status rc_batch_create(const rc_params* p, rc_batch* out);
+
+/* Add a part: its handle and the device arrays of rc_hemisphere_cast
+ * (points, normals, n, bits, counts, counters int64[4] or NULL).  The batch
+ * keeps these pointers until rc_batch_clear/rc_batch_destroy: they must stay
+ * valid.  *part_id (may be NULL) receives the part's index.  Errors:
+ * RC_E_ARG. */
+rc_status rc_batch_add_part(rc_batch b, rc_bvh h, const float* d_P, const float* d_N, int64_t n,
+                            uint32_t* d_bits, int32_t* d_count, int64_t* d_counters, int64_t* part_id);
+
+/* Remove every part (the batch can then be refilled). */
+rc_status rc_batch_clear(rc_batch b);
+
+/* Replace the batch's parameters (the next launch re-captures its graph). */
+rc_status rc_batch_set_params(rc_batch b, const rc_params* p);
+
+/* Cast every part of the batch on `stream`: the first launch after a change
+ * uploads the part descriptors, computes the parts' point orders and
+ * captures [reset counters, batched kernel] as a CUDA graph (on a private
+ * stream); every launch replays that graph on `stream`.  Outputs per part are
+ * exactly those of rc_hemisphere_cast.  Asynchronous after the first
+ * launch.  Errors: RC_E_ARG, RC_E_CUDA. */
+rc_status rc_batch_launch(rc_batch b, void* stream);
+
+/* Autotuner: time the batch under every combination of point order (Morton
+ * / index), direction order (tiles / index), resident blocks per SM (4, 6,
+ * 8) and points per work item (1, 2, 4), `repeats` graph launches each, on
+ * `stream`, and keep the fastest; *best (may be NULL) receives it.  The
+ * batch's outputs hold the last timed run.  Synchronises `stream`. */
+rc_status rc_batch_autotune(rc_batch b, void* stream, int32_t repeats, rc_params* best);
+
+/* Release a batch (not its parts' handles or arrays). */
+rc_status rc_batch_destroy(rc_batch b);
 
 /* Result of rc_analyze_part (host struct). */
 typedef struct {

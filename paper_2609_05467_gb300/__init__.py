@@ -25,7 +25,8 @@ __all__ = [
     "rc_sample_points", "rc_direction_table", "rc_hemisphere_cast", "rc_direction_variability",
     "rc_direction_variability_noalloc",
     "rc_classify", "rc_orthogonal_cast", "rc_min_setups", "rc_setup_cover", "rc_analyze_part",
-    "rc_launch_count", "Bvh", "PartResult",
+    "rc_launch_count", "Bvh", "PartResult", "rc_batch_create", "rc_batch_add_part", "rc_batch_clear",
+    "rc_batch_set_params", "rc_batch_launch", "rc_batch_autotune", "rc_batch_destroy",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -50,7 +51,7 @@ class Params(ctypes.Structure):
         ("conc_mode", ctypes.c_int32), ("t_acc", ctypes.c_double), ("t_share", ctypes.c_double),
         ("t_conc", ctypes.c_double), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
         ("collect_stats", ctypes.c_int32), ("always_setups", ctypes.c_int32), ("point_order", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("tile_mode", ctypes.c_int32), ("points_per_item", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
     ]
 
 
@@ -134,6 +135,13 @@ def load(build_if_missing=True):
             "rc_orthogonal_cast": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P], st),
             "rc_min_setups": ([P, P, P, P, i64, ctypes.POINTER(Params), P, ctypes.POINTER(Setups), P], st),
             "rc_setup_cover": ([P, ctypes.POINTER(Setups)], st),
+            "rc_batch_create": ([ctypes.POINTER(Params), ctypes.POINTER(P)], st),
+            "rc_batch_add_part": ([P, P, P, P, i64, P, P, P, ctypes.POINTER(i64)], st),
+            "rc_batch_clear": ([P], st),
+            "rc_batch_set_params": ([P, ctypes.POINTER(Params)], st),
+            "rc_batch_launch": ([P, P], st),
+            "rc_batch_autotune": ([P, P, i32, ctypes.POINTER(Params)], st),
+            "rc_batch_destroy": ([P], st),
             "rc_analyze_part": ([P, i64, P, i64, i64, ctypes.POINTER(Params), P, P, P, P,
                                  ctypes.POINTER(PartResult), P], st),
         }
@@ -297,6 +305,41 @@ def rc_analyze_part(V, F, n, params, bits=None, count=None, mask=None, cls=None,
                                   _hptr(bits), _hptr(count), _hptr(mask), _hptr(cls), ctypes.byref(out),
                                   _stream(stream)))
     return out
+
+
+def rc_batch_create(params):
+    b = ctypes.c_void_p()
+    _check(load().rc_batch_create(ctypes.byref(params), ctypes.byref(b)))
+    return b.value
+
+
+def rc_batch_add_part(b, h, P, N, bits, count, counters=None):
+    pid = ctypes.c_int64()
+    _check(load().rc_batch_add_part(ctypes.c_void_p(b), ctypes.c_void_p(h), _ptr(P), _ptr(N), P.shape[0], _ptr(bits),
+                                    _ptr(count), _ptr(counters), ctypes.byref(pid)))
+    return pid.value
+
+
+def rc_batch_clear(b):
+    _check(load().rc_batch_clear(ctypes.c_void_p(b)))
+
+
+def rc_batch_set_params(b, params):
+    _check(load().rc_batch_set_params(ctypes.c_void_p(b), ctypes.byref(params)))
+
+
+def rc_batch_launch(b, stream=None):
+    _check(load().rc_batch_launch(ctypes.c_void_p(b), _stream(stream)))
+
+
+def rc_batch_autotune(b, repeats=2, stream=None):
+    best = Params()
+    _check(load().rc_batch_autotune(ctypes.c_void_p(b), _stream(stream), repeats, ctypes.byref(best)))
+    return best
+
+
+def rc_batch_destroy(b):
+    _check(load().rc_batch_destroy(ctypes.c_void_p(b)))
 
 
 def rc_launch_count():

@@ -107,7 +107,11 @@ static rc_status device_dirs(int32_t N, const float4** canon, const float4** til
         fibonacci_hemisphere(N, h.data());
         const std::vector<int32_t> ord = tile_order(N, h.data());
         std::vector<float4> h4(2 * (size_t)N);
-        for (int32_t j = 0; j < N; ++j) h4[j] = make_float4(h[3 * j], h[3 * j + 1], h[3 * j + 2], 0.0f);
+        for (int32_t j = 0; j < N; ++j) {
+            float w;
+            memcpy(&w, &j, sizeof w);
+            h4[j] = make_float4(h[3 * j], h[3 * j + 1], h[3 * j + 2], w);
+        }
         for (int32_t k = 0; k < N; ++k) {
             const int32_t j = ord[k];
             float w;
@@ -139,8 +143,23 @@ static rc_status check_params(const rc_params* p)
     if (p->block_threads != 0 && p->block_threads != 128)
         return set_error(RC_E_UNSUPPORTED, "block_threads must be 0 (default) or 128");
     if (p->point_order != 0 && p->point_order != 1) return set_error(RC_E_ARG, "point_order must be 0 or 1");
+    if (p->tile_mode != 0 && p->tile_mode != 1) return set_error(RC_E_ARG, "tile_mode must be 0 or 1");
+    if (p->points_per_item < 0 || p->points_per_item > 64)
+        return set_error(RC_E_ARG, "points_per_item must be in [0, 64]");
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return set_error(RC_E_ARG, "blocks_per_sm out of range");
     if (p->collect_stats != 0 && p->collect_stats != 1) return set_error(RC_E_ARG, "collect_stats must be 0 or 1");
+    return RC_OK;
+}
+
+rc_status check_params_public(const rc_params* p) { return check_params(p); }
+
+// Direction table a cast uses: tile order (default) or canonical order.
+rc_status device_dirs_for_cast(const rc_params* p, const float4** tdirs)
+{
+    const float4 *canon = nullptr, *tiled = nullptr;
+    rc_status st = device_dirs(p->n_dirs, &canon, &tiled);
+    if (st != RC_OK) return st;
+    *tdirs = p->tile_mode == 1 ? canon : tiled;
     return RC_OK;
 }
 
@@ -306,7 +325,7 @@ rc_status rc_hemisphere_cast(rc_bvh h, const float* d_P, const float* d_N, int64
     const float4 *dirs = nullptr, *tdirs = nullptr;
     if ((st = device_dirs(p->n_dirs, &dirs, &tdirs)) != RC_OK) return st;
     h->dirs = dirs;
-    h->tdirs = tdirs;
+    h->tdirs = p->tile_mode == 1 ? dirs : tdirs;
     h->dirs_n = p->n_dirs;
     return launch_hemisphere(h, d_P, d_N, n, p, d_bits, d_count, (unsigned long long*)d_counters, stats, s);
 }

@@ -43,9 +43,9 @@ __device__ __forceinline__ void setup_ray(Ray& r, float ox, float oy, float oz, 
 {
     r.ox = ox; r.oy = oy; r.oz = oz;
     r.dx = dx; r.dy = dy; r.dz = dz;
-    r.ix = __fdiv_rn(1.0f, dx);
-    r.iy = __fdiv_rn(1.0f, dy);
-    r.iz = __fdiv_rn(1.0f, dz);
+    r.ix = __frcp_rn(dx);
+    r.iy = __frcp_rn(dy);
+    r.iz = __frcp_rn(dz);
     const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
     int kz = ax >= ay ? (ax >= az ? 0 : 2) : (ay >= az ? 1 : 2);
     int kx = kz == 2 ? 0 : kz + 1;
@@ -54,13 +54,15 @@ __device__ __forceinline__ void setup_ray(Ray& r, float ox, float oy, float oz, 
     if (dk < 0.0f) { int t = kx; kx = ky; ky = t; }
     r.kx = kx; r.ky = ky; r.kz = kz;
     r.dkz = dk;
-    r.Sx = __fdiv_rn(sel3(dx, dy, dz, kx), dk);
-    r.Sy = __fdiv_rn(sel3(dx, dy, dz, ky), dk);
+    const float rk = __frcp_rn(dk);
+    r.Sx = __fmul_rn(sel3(dx, dy, dz, kx), rk);
+    r.Sy = __fmul_rn(sel3(dx, dy, dz, ky), rk);
     // translation rounds once (u|a|); a non-zero shear adds the rounding of
-    // S (u|S||a_z|), of the product and of the fused subtraction
+    // S (2u|S||a_z|: reciprocal and product), of a_z (u|S||a_z|) and of the
+    // fused subtraction (u|A|); a zero shear leaves the subtraction exact
     const float sm = fmaxf(fabsf(r.Sx), fabsf(r.Sy));
     const float u = 5.9604644775390625e-8f;
-    r.ef = sm == 0.0f ? 1.01f * u : (2.0f + 3.0f * sm) * 1.01f * u;
+    r.ef = sm == 0.0f ? 1.01f * u : (2.0f + 4.0f * sm) * 1.01f * u;
     r.rs = fmaxf(fmaxf(1.0f, scene_maxabs), fmaxf(fabsf(ox), fmaxf(fabsf(oy), fabsf(oz))));
 }
 
@@ -70,7 +72,7 @@ __device__ __forceinline__ void setup_ray(Ray& r, float ox, float oy, float oz, 
 //
 // Error model (u = 2^-24, all translated coordinates |.| <= M, all sheared
 // coordinates |.| <= P, S = max(|Sx|,|Sy|) <= 1 because kz is the largest |d|):
-//   sheared coordinate error        E  <= (2 + 3 S) u M, and u M when S = 0
+//   sheared coordinate error        E  <= (2 + 4 S) u M, and u M when S = 0
 //                                        (the fused subtraction is then exact)
 //   edge function error             eU <= 4 P E + 6 E^2 + 3 u P^2
 //   det error                       eD <= 3 eU + 2.01 u S        (S = sum |U|)
@@ -314,6 +316,51 @@ __device__ __forceinline__ void warp_add_counters(unsigned long long* counters, 
 #define RC_HEMI_MIN_BLOCKS 8
 #endif
 
+struct CastAcc {
+    int amb = 0, retests = 0, overflow = 0;
+    long long rays = 0, nvis = 0, ntri = 0;
+};
+
+// The hemispherical cast of one point by one warp (see above).  `tdirs` is
+// the tile-ordered table, `row` the warp's shared-memory row of W words.
+template <bool kStats>
+__device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                           int max_steps, float scene_maxabs, const float* __restrict__ P,
+                                           const float* __restrict__ Nrm, int64_t i,
+                                           const float4* __restrict__ tdirs, int W, double eps, uint32_t* row,
+                                           uint32_t* __restrict__ bits, int32_t* __restrict__ count, CastAcc& acc)
+{
+    const int lane = threadIdx.x & 31;
+    for (int w = lane; w < W; w += 32) row[w] = 0u;
+    __syncwarp();
+    const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
+    const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
+    const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
+    const Onb b = make_onb(nx, ny, nz);
+    int cnt = 0;
+    for (int t = 0; t < W; ++t) {
+        const float4 h = __ldg(&tdirs[32 * t + lane]);
+        const int j = __float_as_int(h.w);
+        float dx, dy, dz;
+        local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
+        Ray r;
+        setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
+        const TraceOut tr = trace<kStats>(nodes, tris, r, max_steps);
+        acc.retests += tr.retests;
+        acc.overflow += tr.overflow;
+        acc.amb += (tr.flags >> 1) & 1;
+        if (kStats) { acc.nvis += tr.nodes; acc.ntri += tr.tris; }
+        const bool visible = (tr.flags & 1) == 0;
+        if (visible) atomicOr(&row[j >> 5], 1u << (j & 31));
+        cnt += __popc(__ballot_sync(0xFFFFFFFFu, visible));
+    }
+    __syncwarp();
+    for (int w = lane; w < W; w += 32) bits[i * W + w] = row[w];
+    __syncwarp();
+    if (lane == 0) count[i] = cnt;
+    acc.rays += W;   // per lane
+}
+
 template <bool kStats>
 __global__ void __launch_bounds__(128, RC_HEMI_MIN_BLOCKS)
 k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
@@ -326,95 +373,115 @@ k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
     const int lane = threadIdx.x & 31;
     const int W = n_dirs >> 5;
     uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
-    int amb = 0, retests = 0, overflow = 0;
-    long long rays = 0, nvis = 0, ntri = 0;
+    CastAcc acc;
     for (;;) {
         unsigned long long k = 0;
         if (lane == 0) k = atomicAdd(work, 1ULL);
         k = __shfl_sync(0xFFFFFFFFu, k, 0);
         if (k >= (unsigned long long)n) break;
         const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
-        for (int w = lane; w < W; w += 32) row[w] = 0u;
-        __syncwarp();
-        const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
-        const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
-        const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
-        const Onb b = make_onb(nx, ny, nz);
-        int cnt = 0;
-        for (int t = 0; t < W; ++t) {
-            const float4 h = __ldg(&tdirs[32 * t + lane]);
-            const int j = __float_as_int(h.w);
-            float dx, dy, dz;
-            local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
-            Ray r;
-            setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-            const TraceOut tr = trace<kStats>(nodes, tris, r, max_steps);
-            retests += tr.retests;
-            overflow += tr.overflow;
-            amb += (tr.flags >> 1) & 1;
-            if (kStats) { nvis += tr.nodes; ntri += tr.tris; }
-            const bool visible = (tr.flags & 1) == 0;
-            if (visible) atomicOr(&row[j >> 5], 1u << (j & 31));
-            cnt += __popc(__ballot_sync(0xFFFFFFFFu, visible));
-        }
-        __syncwarp();
-        for (int w = lane; w < W; w += 32) bits[i * W + w] = row[w];
-        __syncwarp();
-        if (lane == 0) count[i] = cnt;
-        rays += W;   // per lane
+        cast_point<kStats>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits, count, acc);
     }
-    warp_add_counters(counters, rays, amb, retests, overflow, nvis, ntri);
+    warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow, acc.nvis, acc.ntri);
 }
 
 // ---------------------------------------------------------------------------
-// Section 3.2: orthogonal cast.  Eight lanes per point, lane a < 6 casts axis
-// a of (+X', -X', +Y', -Y', +Z', -Z'); travel to the frame bounding box.
+// Batched hemispherical cast: one persistent launch over the points of many
+// parts.  Work items are runs of `ppi` consecutive points (in each part's
+// processing order) of one part; a warp takes items from one global counter,
+// finds the part by binary search over the parts' first item, and casts the
+// points as k_hemisphere does.  Counters are kept per part.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
+__device__ __forceinline__ void flush_part_counters(unsigned long long* c, CastAcc& a)
+{
+    warp_add_counters(c, a.rays, a.amb, a.retests, a.overflow);
+    a = CastAcc();
+}
+
+template <bool kStats>
+__global__ void __launch_bounds__(128, RC_HEMI_MIN_BLOCKS)
+k_batch(const BatchPart* __restrict__ parts, int n_parts, long long n_items, int ppi,
+        const float4* __restrict__ tdirs, int n_dirs, double eps, unsigned long long* work)
+{
+    extern __shared__ uint32_t s_rows[];
+    const int lane = threadIdx.x & 31;
+    const int W = n_dirs >> 5;
+    uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
+    CastAcc acc;
+    int cur = -1;
+    for (;;) {
+        unsigned long long k = 0;
+        if (lane == 0) k = atomicAdd(work, 1ULL);
+        k = __shfl_sync(0xFFFFFFFFu, k, 0);
+        if (k >= (unsigned long long)n_items) break;
+        int lo = 0, hi = n_parts - 1;            // last part with first_item <= k
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((unsigned long long)parts[mid].first_item <= k) lo = mid; else hi = mid - 1;
+        }
+        const BatchPart& bp = parts[lo];
+        if (lo != cur) {
+            if (cur >= 0) flush_part_counters(parts[cur].counters, acc);
+            cur = lo;
+        }
+        const long long q0 = ((long long)k - bp.first_item) * ppi;
+        const long long q1 = q0 + ppi < bp.n ? q0 + ppi : bp.n;
+        for (long long q = q0; q < q1; ++q) {
+            const int64_t i = bp.order ? (int64_t)__ldg(&bp.order[q]) : (int64_t)q;
+            cast_point<kStats>(bp.nodes, bp.tris, bp.max_steps, bp.scene_maxabs, bp.P, bp.N, i, tdirs, W, eps,
+                               row, bp.bits, bp.count, acc);
+        }
+    }
+    if (cur >= 0) flush_part_counters(parts[cur].counters, acc);
+}
+
+// ---------------------------------------------------------------------------
+// Section 3.2: orthogonal cast.  A warp holds 32 points (Morton order) and
+// casts the six axes (+X', -X', +Y', -Y', +Z', -Z') one after the other, so
+// all lanes follow the same direction at a time; each lane keeps its point's
+// six-bit mask in a register.  Travel to the frame bounding box is FP64.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128, RC_HEMI_MIN_BLOCKS)
 k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
              const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
-             const float* __restrict__ axes /*6x3*/, const double* __restrict__ frame /*9*/,
-             const double* __restrict__ fbox /*lo3 hi3*/, double eps, uint8_t* __restrict__ mask,
-             float* __restrict__ travel, unsigned long long* counters)
+             const int32_t* __restrict__ order, const float* __restrict__ axes /*6x3*/,
+             const double* __restrict__ frame /*9*/, const double* __restrict__ fbox /*lo3 hi3*/, double eps,
+             uint8_t* __restrict__ mask, float* __restrict__ travel, unsigned long long* counters)
 {
     const int lane = threadIdx.x & 31;
-    const int sub = lane & 7;
     int amb = 0, retests = 0, overflow = 0;
     long long rays = 0;
-    const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
-    const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3);
-    const int64_t iters = (n + groups - 1) / groups;
-    for (int64_t it = 0; it < iters; ++it) {
-        const int64_t i = g0 + it * groups;
-        bool vis = false;
-        if (i < n && sub < 6) {
-            const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
-            const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
-            const float dx = axes[3 * sub], dy = axes[3 * sub + 1], dz = axes[3 * sub + 2];
-            // travel along the axis to the frame bounding box (FP64)
-            const int k = sub >> 1;
-            double q = __dadd_rn(__dmul_rn((double)px, frame[k]), __dmul_rn((double)py, frame[3 + k]));
-            q = __dadd_rn(q, __dmul_rn((double)pz, frame[6 + k]));
-            const double tv = (sub & 1) ? __dsub_rn(q, fbox[k]) : __dsub_rn(fbox[3 + k], q);
-            travel[6 * i + sub] = __double2float_rn(tv);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t wv = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wv * 32 < n; wv += nwarps) {
+        const int64_t k = wv * 32 + lane;
+        if (k >= n) continue;
+        const int64_t i = order ? (int64_t)__ldg(&order[k]) : k;
+        const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
+        const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
+        const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
+        unsigned m = 0;
+        for (int a = 0; a < 6; ++a) {
+            const float dx = axes[3 * a], dy = axes[3 * a + 1], dz = axes[3 * a + 2];
+            const int kk = a >> 1;
+            double q = __dadd_rn(__dmul_rn((double)px, frame[kk]), __dmul_rn((double)py, frame[3 + kk]));
+            q = __dadd_rn(q, __dmul_rn((double)pz, frame[6 + kk]));
+            const double tv = (a & 1) ? __dsub_rn(q, fbox[kk]) : __dsub_rn(fbox[3 + kk], q);
+            travel[6 * i + a] = __double2float_rn(tv);
             // eligibility n.a >= 0 (FP64, x, y, z order)
             double nd = __dadd_rn(__dmul_rn((double)nx, (double)dx), __dmul_rn((double)ny, (double)dy));
             nd = __dadd_rn(nd, __dmul_rn((double)nz, (double)dz));
             if (nd >= 0.0) {
-                const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps),
-                            oz = offset_coord(pz, nz, eps);
                 Ray r;
                 setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
                 const TraceOut t = trace<false>(nodes, tris, r, max_steps);
                 retests += t.retests;
                 overflow += t.overflow;
                 amb += (t.flags >> 1) & 1;
-                vis = (t.flags & 1) == 0;
+                if ((t.flags & 1) == 0) m |= 1u << a;
                 rays += 1;
             }
         }
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, vis);
-        if (i < n && sub == 0) mask[i] = (uint8_t)((bal >> (lane & ~7)) & 0x3F);
+        mask[i] = (uint8_t)m;
     }
     warp_add_counters(counters, rays, amb, retests, overflow);
 }
@@ -486,7 +553,7 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
         if (st != RC_OK) return st;
     }
     const int threads = 128;
-    const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : 8;
+    const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_HEMI_MIN_BLOCKS;
     int64_t blocks = (int64_t)sm_count() * per_sm;
     const int64_t need = (n * 32 + threads - 1) / threads;
     if (blocks > need) blocks = need;
@@ -548,14 +615,46 @@ rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n,
     RC_CUDA(cudaMallocAsync(&fd, sizeof(FrameDev), s));
     rc_status st = frame_setup(h, p, fd, s);
     if (st != RC_OK) return st;
-    int64_t blocks = (n * 8 + 127) / 128;
-    const int64_t cap = (int64_t)sm_count() * 16;
+    int32_t* order = nullptr;
+    if (p->point_order == 0 && n > 1) {
+        RC_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * n, s));
+        rc_status pst = point_order(h, P, n, order, s);
+        if (pst != RC_OK) return pst;
+    }
+    int64_t blocks = (n + 127) / 128;
+    const int64_t cap = (int64_t)sm_count() * RC_HEMI_MIN_BLOCKS;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_orthogonal<<<(unsigned)blocks, 128, 0, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N, n, fd->axes,
-                                                 fd->frame, fd->fbox, p->origin_offset, mask, travel, counters);
+    k_orthogonal<<<(unsigned)blocks, 128, 0, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N, n, order,
+                                                 fd->axes, fd->frame, fd->fbox, p->origin_offset, mask, travel,
+                                                 counters);
     RC_LAUNCHED();
     RC_CUDA(cudaFreeAsync(fd, s));
+    if (order) RC_CUDA(cudaFreeAsync(order, s));
+    return RC_OK;
+}
+
+rc_status launch_batch(const BatchPart* d_parts, int n_parts, long long n_items, int ppi, const float4* tdirs,
+                       const rc_params* p, unsigned long long* work, cudaStream_t s)
+{
+    const int threads = 128;
+    const size_t smem = (size_t)(threads / 32) * (p->n_dirs / 32) * sizeof(uint32_t);
+    const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_HEMI_MIN_BLOCKS;
+    int64_t blocks = (int64_t)sm_count() * per_sm;
+    const int64_t need = (n_items * 32 + threads - 1) / threads;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    k_batch<false><<<(unsigned)blocks, threads, smem, s>>>(d_parts, n_parts, n_items, ppi, tdirs, p->n_dirs,
+                                                          p->origin_offset, work);
+    RC_LAUNCHED();
+    return RC_OK;
+}
+
+rc_status prepare_batch_kernel(int n_dirs)
+{
+    const size_t smem = (size_t)4 * (n_dirs / 32) * sizeof(uint32_t);
+    if (smem > 48 * 1024)
+        RC_CUDA(cudaFuncSetAttribute(k_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return RC_OK;
 }
 

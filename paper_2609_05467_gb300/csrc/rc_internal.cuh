@@ -64,6 +64,22 @@ struct FrameDev {
     long long box[6];   // ordered-integer accumulators for fbox
 };
 
+// one part of a batched cast (device descriptor)
+struct BatchPart {
+    const float4* nodes;
+    const float4* tris;
+    const float* P;
+    const float* N;
+    const int32_t* order;          // processing order of the part's points, or null
+    uint32_t* bits;
+    int32_t* count;
+    unsigned long long* counters;  // [4] per part, or null
+    long long n;                   // points
+    long long first_item;          // first global work item of the part
+    int max_steps;
+    float scene_maxabs;
+};
+
 }  // namespace rc
 
 struct rc_bvh_s {

@@ -19,6 +19,29 @@ __device__ __forceinline__ long long quant_weight(const double* w, int64_t i, do
     return llround(__dmul_rn(__ddiv_rn(w[i], wmax), 16777216.0));
 }
 
+// round(x * 2^40) to nearest, ties to even, for an fp32 x with |x| <= 2^22,
+// in integer arithmetic (equal to llrint((double)x * 2^40), whose product is
+// exact in FP64)
+__device__ __forceinline__ long long fixed40(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xFFu);
+    if (e == 0) return 0;                           // zero or subnormal: |x * 2^40| < 2^-86
+    const long long mant = (long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int sh = e - 110;                         // x * 2^40 = mant * 2^(e - 110)
+    long long q;
+    if (sh >= 0) {
+        q = mant << sh;
+    } else {
+        const int r = -sh;
+        if (r > 24) return 0;                       // mant / 2^r < 1/2
+        q = mant >> r;
+        const long long rem = mant & ((1LL << r) - 1), half = 1LL << (r - 1);
+        if (rem > half || (rem == half && (q & 1))) ++q;
+    }
+    return (b >> 31) ? -q : q;
+}
+
 // One warp per point: recompute each visible direction, sum llrint(d*2^40)
 // per axis, count visible rays per largest-|component| axis.
 __global__ void __launch_bounds__(256)
@@ -46,9 +69,9 @@ k_variability(const uint32_t* __restrict__ bits, const float* __restrict__ Nrm,
             const float4 h = __ldg(&dirs[32 * w + lane]);
             float dx, dy, dz;
             local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
-            M0 += llrint((double)dx * 1099511627776.0);
-            M1 += llrint((double)dy * 1099511627776.0);
-            M2 += llrint((double)dz * 1099511627776.0);
+            M0 += fixed40(dx);
+            M1 += fixed40(dy);
+            M2 += fixed40(dz);
             int best = 0;
             float bv = fabsf(dx);
             if (fabsf(dy) > bv) { best = 1; bv = fabsf(dy); }
