@@ -82,7 +82,8 @@ typedef struct {
     int32_t point_order;     /* hemispherical cast: 0 = cast points in Morton order (default), 1 = in index order */
     int32_t tile_mode;       /* hemispherical cast: 0 = directions in coherent tiles of 32 (default), 1 = index order */
     int32_t points_per_item; /* batched cast: points per work item (0 = 1) */
-    int32_t reserved[1];
+    int32_t launch_mode;     /* casts: 0 = persistent grid (default), 1 = one warp per point, grid sized to the work
+                                (short blocks, so concurrent casts on other streams interleave) */
 } rc_params;
 
 /* Part-level indicators (Sections 3.1 and 3.3). */
@@ -165,7 +166,11 @@ rc_status rc_build_bvh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t
  * Errors as rc_build_bvh (non-finite vertices -> RC_E_ARG). */
 rc_status rc_refit_bvh(rc_bvh h, const float* d_V, void* stream);
 
-/* Release a handle and its device memory.  NULL is accepted. */
+/* Release a handle and its device memory.  NULL is accepted.  The memory
+ * comes from CUDA's stream-ordered pool and is returned asynchronously, in
+ * order on the legacy default stream, so destroying a handle never stalls
+ * other streams; do not destroy a handle while work that uses it may still
+ * run on another (non-blocking) stream. */
 rc_status rc_destroy_bvh(rc_bvh h);
 
 /* Sizes, depth and scene bounds of a built handle (host struct). */
@@ -371,6 +376,78 @@ typedef struct {
 rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int64_t T, int64_t n,
                           const rc_params* p, uint32_t* h_bits, int32_t* h_count, uint8_t* h_mask,
                           uint8_t* h_class, rc_part_result* h_out, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: a persistent request loop for part analyses                   */
+/* ---------------------------------------------------------------------- */
+/* The paper aims at interactive use inside CAD (Sections 1 and 5).  A
+ * server keeps worker slots (one host thread and one CUDA stream each)
+ * that take requests as they arrive: a queued request is admitted as soon
+ * as a slot is free and its device bytes fit into the budget (idle resident
+ * parts are evicted, least recently used first), so requests that arrive
+ * while others are on the GPU run concurrently with them.  Each part's BVH,
+ * sample points and visibility maps stay resident under the caller's part
+ * key; a re-submission with the same triangle list is refitted, otherwise
+ * rebuilt.  Each request runs the pipeline of rc_analyze_part.  Every slot has
+ * one stream per device priority level and a request runs on the level its
+ * size gives it (smaller = higher, see cfg->small_rays), so the blocks of
+ * small requests are scheduled ahead of a large request's; with
+ * p->launch_mode = 1 the casts use short-lived blocks and concurrent
+ * requests interleave on the SMs. */
+
+typedef struct rc_server_s* rc_server;
+
+typedef struct {
+    int32_t slots;              /* concurrent requests (1..64) */
+    int32_t cast_blocks_per_sm; /* blocks per SM of each request's cast (0 = the params' value) */
+    int64_t hbm_budget_bytes;   /* admission budget for resident parts plus running requests */
+    int64_t small_rays;         /* requests with at most this many hemisphere rays run at the highest
+                                   stream priority, each doubling one level lower (0 = all at the lowest) */
+} rc_server_config;
+
+typedef struct {
+    int64_t request_id;
+    uint64_t part_key;
+    rc_status status;           /* RC_OK, RC_E_OOM (never fits the budget), or the failing call's status */
+    int32_t slot;               /* worker slot that ran it */
+    int32_t rebuilt;            /* 1 = BVH built, 0 = refitted */
+    int32_t priority_level;     /* stream priority level it ran at (0 = highest) */
+    double t_submit, t_admit, t_start, t_end;   /* steady-clock seconds */
+    int64_t resident_bytes;     /* device bytes the part keeps resident */
+    rc_part_result result;
+    char message[128];          /* error text when status != RC_OK */
+} rc_request_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, rejected, evicted;
+    int64_t running, queued, resident_parts, used_bytes;
+} rc_server_stats;
+
+/* Start a server with parameters *p (copied; p->always_setups applies) on
+ * the current device.  Errors: RC_E_ARG, RC_E_CUDA. */
+rc_status rc_server_create(const rc_params* p, const rc_server_config* cfg, rc_server* out);
+
+/* Queue an analysis of the host mesh (h_V [nV][3], h_F [T][3], copied before
+ * returning) with n sample points, under part_key.  Returns at once with
+ * *req_id.  Errors: RC_E_ARG. */
+rc_status rc_server_submit(rc_server s, uint64_t part_key, const float* h_V, int64_t nV, const int32_t* h_F,
+                           int64_t T, int64_t n, int64_t* req_id);
+
+/* Wait up to timeout_s seconds for a request; on completion copy its result
+ * to *out and forget the request.  Errors: RC_E_TIMEOUT (still running or
+ * queued; the request stays known), RC_E_ARG (unknown id). */
+rc_status rc_server_wait(rc_server s, int64_t req_id, double timeout_s, rc_request_result* out);
+
+/* Copy a resident part's visibility bits [n][N/32] and counts [n] to host
+ * arrays (either may be NULL).  Errors: RC_E_ARG (not resident, in use, or
+ * n differs). */
+rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, int32_t* h_count, int64_t n);
+
+/* Counters of the server (host struct). */
+rc_status rc_server_get_stats(rc_server s, rc_server_stats* out);
+
+/* Stop the workers after their current requests and free everything. */
+rc_status rc_server_destroy(rc_server s);
 
 /* The two setup covers of Section 3.3 from a 64-bin histogram of viable
  * points per reachable-axis mask (bin 0 is ignored): the exact minimum

@@ -26,7 +26,8 @@ __all__ = [
     "rc_direction_variability_noalloc",
     "rc_classify", "rc_orthogonal_cast", "rc_min_setups", "rc_setup_cover", "rc_analyze_part",
     "rc_launch_count", "Bvh", "PartResult", "rc_batch_create", "rc_batch_add_part", "rc_batch_clear",
-    "rc_batch_set_params", "rc_batch_launch", "rc_batch_autotune", "rc_batch_destroy",
+    "rc_batch_set_params", "rc_batch_launch", "rc_batch_autotune", "rc_batch_destroy", "rc_server_create",
+    "rc_server_submit", "rc_server_wait", "rc_server_read_bits", "rc_server_get_stats", "rc_server_destroy",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -51,7 +52,7 @@ class Params(ctypes.Structure):
         ("conc_mode", ctypes.c_int32), ("t_acc", ctypes.c_double), ("t_share", ctypes.c_double),
         ("t_conc", ctypes.c_double), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
         ("collect_stats", ctypes.c_int32), ("always_setups", ctypes.c_int32), ("point_order", ctypes.c_int32),
-        ("tile_mode", ctypes.c_int32), ("points_per_item", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
+        ("tile_mode", ctypes.c_int32), ("points_per_item", ctypes.c_int32), ("launch_mode", ctypes.c_int32),
     ]
 
 
@@ -87,6 +88,26 @@ class PartResult(ctypes.Structure):
         ("summary", Summary), ("setups", Setups), ("label", ctypes.c_int32), ("setups_ran", ctypes.c_int32),
         ("cast_counters", ctypes.c_int64 * 4), ("ortho_counters", ctypes.c_int64 * 4),
     ]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("cast_blocks_per_sm", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_int64), ("small_rays", ctypes.c_int64)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [
+        ("request_id", ctypes.c_int64), ("part_key", ctypes.c_uint64), ("status", ctypes.c_int),
+        ("slot", ctypes.c_int32), ("rebuilt", ctypes.c_int32), ("priority_level", ctypes.c_int32),
+        ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_start", ctypes.c_double),
+        ("t_end", ctypes.c_double), ("resident_bytes", ctypes.c_int64), ("result", PartResult),
+        ("message", ctypes.c_char * 128),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "failed", "rejected", "evicted", "running",
+                                               "queued", "resident_parts", "used_bytes")]
 
 
 class BvhInfo(ctypes.Structure):
@@ -142,6 +163,12 @@ def load(build_if_missing=True):
             "rc_batch_launch": ([P, P], st),
             "rc_batch_autotune": ([P, P, i32, ctypes.POINTER(Params)], st),
             "rc_batch_destroy": ([P], st),
+            "rc_server_create": ([ctypes.POINTER(Params), ctypes.POINTER(ServerConfig), ctypes.POINTER(P)], st),
+            "rc_server_submit": ([P, ctypes.c_uint64, P, i64, P, i64, i64, ctypes.POINTER(i64)], st),
+            "rc_server_wait": ([P, i64, ctypes.c_double, ctypes.POINTER(RequestResult)], st),
+            "rc_server_read_bits": ([P, ctypes.c_uint64, P, P, i64], st),
+            "rc_server_get_stats": ([P, ctypes.POINTER(ServerStats)], st),
+            "rc_server_destroy": ([P], st),
             "rc_analyze_part": ([P, i64, P, i64, i64, ctypes.POINTER(Params), P, P, P, P,
                                  ctypes.POINTER(PartResult), P], st),
         }
@@ -340,6 +367,48 @@ def rc_batch_autotune(b, repeats=2, stream=None):
 
 def rc_batch_destroy(b):
     _check(load().rc_batch_destroy(ctypes.c_void_p(b)))
+
+
+def rc_server_create(params, slots=4, hbm_budget_bytes=120 << 30, cast_blocks_per_sm=0, small_rays=0):
+    cfg = ServerConfig(slots, cast_blocks_per_sm, hbm_budget_bytes, small_rays)
+    s = ctypes.c_void_p()
+    _check(load().rc_server_create(ctypes.byref(params), ctypes.byref(cfg), ctypes.byref(s)))
+    return s.value
+
+
+def rc_server_submit(s, part_key, V, F, n):
+    """Queue an analysis of host mesh (numpy float32 [nV,3], int32 [T,3])."""
+    import numpy as np
+    V = np.ascontiguousarray(V, np.float32)
+    F = np.ascontiguousarray(F, np.int32)
+    rid = ctypes.c_int64()
+    _check(load().rc_server_submit(ctypes.c_void_p(s), ctypes.c_uint64(part_key), _hptr(V), V.shape[0], _hptr(F),
+                                   F.shape[0], n, ctypes.byref(rid)))
+    return rid.value
+
+
+def rc_server_wait(s, req_id, timeout_s=60.0):
+    out = RequestResult()
+    _check(load().rc_server_wait(ctypes.c_void_p(s), req_id, float(timeout_s), ctypes.byref(out)))
+    return out
+
+
+def rc_server_read_bits(s, part_key, n, n_dirs):
+    import numpy as np
+    bits = np.zeros((n, n_dirs // 32), np.uint32)
+    cnt = np.zeros(n, np.int32)
+    _check(load().rc_server_read_bits(ctypes.c_void_p(s), ctypes.c_uint64(part_key), _hptr(bits), _hptr(cnt), n))
+    return bits, cnt
+
+
+def rc_server_get_stats(s):
+    out = ServerStats()
+    _check(load().rc_server_get_stats(ctypes.c_void_p(s), ctypes.byref(out)))
+    return out
+
+
+def rc_server_destroy(s):
+    _check(load().rc_server_destroy(ctypes.c_void_p(s)))
 
 
 def rc_launch_count():

@@ -146,6 +146,7 @@ static rc_status check_params(const rc_params* p)
     if (p->tile_mode != 0 && p->tile_mode != 1) return set_error(RC_E_ARG, "tile_mode must be 0 or 1");
     if (p->points_per_item < 0 || p->points_per_item > 64)
         return set_error(RC_E_ARG, "points_per_item must be in [0, 64]");
+    if (p->launch_mode != 0 && p->launch_mode != 1) return set_error(RC_E_ARG, "launch_mode must be 0 or 1");
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return set_error(RC_E_ARG, "blocks_per_sm out of range");
     if (p->collect_stats != 0 && p->collect_stats != 1) return set_error(RC_E_ARG, "collect_stats must be 0 or 1");
     return RC_OK;
@@ -171,14 +172,35 @@ static rc_status use_device_of(rc_bvh h)
     return RC_OK;
 }
 
+// Handle memory comes from the stream-ordered pool: it is returned with
+// cudaFreeAsync on the legacy default stream, which does not stall other
+// streams' work (cudaFree would synchronise the whole device).
 static void free_handle(rc_bvh h)
 {
     if (!h) return;
     void* ptrs[] = {h->V, h->F, h->tris, h->nodes, h->parent, h->child, h->range, h->order, h->nbox,
                     h->visits, h->fnorm, h->farea, h->fcent, h->cdf, h->sc};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, 0);
     delete h;
+}
+
+// Keep freed pool memory for reuse instead of returning it to the driver at
+// every synchronisation (once per device; a process-local setting).
+void keep_pool_memory()
+{
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done[dev] = true;
 }
 
 }  // namespace rc
@@ -223,16 +245,17 @@ rc_status rc_build_bvh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t
     rc_bvh h = new rc_bvh_s();
     auto fail = [&](rc_status st) { std::string m = t_err; cudaStreamSynchronize(s); free_handle(h); t_err = m; return st; };
     if (cudaGetDevice(&h->device) != cudaSuccess) return fail(set_error(RC_E_CUDA, "no CUDA device"));
+    keep_pool_memory();
     h->nV = nV;
     h->T = T;
 #define RC_TRY(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) return fail(cuda_error(_e, #call)); } while (0)
-    RC_TRY(cudaMalloc(&h->V, sizeof(float) * 3 * nV));
-    RC_TRY(cudaMalloc(&h->F, sizeof(int32_t) * 3 * T));
-    RC_TRY(cudaMalloc(&h->fnorm, sizeof(float) * 3 * T));
-    RC_TRY(cudaMalloc(&h->farea, sizeof(double) * T));
-    RC_TRY(cudaMalloc(&h->fcent, sizeof(float) * 3 * T));
-    RC_TRY(cudaMalloc(&h->cdf, sizeof(long long) * T));
-    RC_TRY(cudaMalloc(&h->sc, sizeof(DevScalars)));
+    RC_TRY(cudaMallocAsync(&h->V, sizeof(float) * 3 * nV, s));
+    RC_TRY(cudaMallocAsync(&h->F, sizeof(int32_t) * 3 * T, s));
+    RC_TRY(cudaMallocAsync(&h->fnorm, sizeof(float) * 3 * T, s));
+    RC_TRY(cudaMallocAsync(&h->farea, sizeof(double) * T, s));
+    RC_TRY(cudaMallocAsync(&h->fcent, sizeof(float) * 3 * T, s));
+    RC_TRY(cudaMallocAsync(&h->cdf, sizeof(long long) * T, s));
+    RC_TRY(cudaMallocAsync(&h->sc, sizeof(DevScalars), s));
     RC_TRY(cudaMemcpyAsync(h->V, d_V, sizeof(float) * 3 * nV, cudaMemcpyDeviceToDevice, s));
     RC_TRY(cudaMemcpyAsync(h->F, d_F, sizeof(int32_t) * 3 * T, cudaMemcpyDeviceToDevice, s));
 #undef RC_TRY

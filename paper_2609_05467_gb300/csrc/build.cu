@@ -617,9 +617,9 @@ rc_status build_bvh(rc_bvh h, cudaStream_t s)
     if (st != RC_OK) { cudaFreeAsync(tbox, s); return st; }
 
     h->n_int = T > kLeafMax ? T - 1 : 1;
-    RC_CUDA(cudaMalloc(&h->nodes, sizeof(float4) * 4 * h->n_int));
-    RC_CUDA(cudaMalloc(&h->tris, sizeof(float4) * 3 * T));
-    RC_CUDA(cudaMalloc(&h->order, sizeof(int32_t) * T));
+    RC_CUDA(cudaMallocAsync(&h->nodes, sizeof(float4) * 4 * h->n_int, s));
+    RC_CUDA(cudaMallocAsync(&h->tris, sizeof(float4) * 3 * T, s));
+    RC_CUDA(cudaMallocAsync(&h->order, sizeof(int32_t) * T, s));
 
     if (T <= kLeafMax) {
         int32_t ord[kLeafMax];
@@ -637,11 +637,11 @@ rc_status build_bvh(rc_bvh h, cudaStream_t s)
         if (sst != RC_OK) return sst;
         // after 8 passes the sorted data is back in (k0, h->order)
         const int64_t n_int = h->n_int;
-        RC_CUDA(cudaMalloc(&h->parent, sizeof(int32_t) * (n_int + T)));
-        RC_CUDA(cudaMalloc(&h->child, sizeof(int32_t) * 2 * n_int));
-        RC_CUDA(cudaMalloc(&h->range, sizeof(int32_t) * 2 * n_int));
-        RC_CUDA(cudaMalloc(&h->nbox, sizeof(float) * 6 * (n_int + T)));
-        RC_CUDA(cudaMalloc(&h->visits, sizeof(int32_t) * n_int));
+        RC_CUDA(cudaMallocAsync(&h->parent, sizeof(int32_t) * (n_int + T), s));
+        RC_CUDA(cudaMallocAsync(&h->child, sizeof(int32_t) * 2 * n_int, s));
+        RC_CUDA(cudaMallocAsync(&h->range, sizeof(int32_t) * 2 * n_int, s));
+        RC_CUDA(cudaMallocAsync(&h->nbox, sizeof(float) * 6 * (n_int + T), s));
+        RC_CUDA(cudaMallocAsync(&h->visits, sizeof(int32_t) * n_int, s));
         k_karras<<<nblocks(n_int, 256), 256, 0, s>>>(k0, T, h->child, h->range, h->parent);
         RC_LAUNCHED();
         RC_CUDA(cudaMemsetAsync(h->visits, 0, sizeof(int32_t) * n_int, s));

@@ -374,13 +374,24 @@ k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
     const int W = n_dirs >> 5;
     uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
     CastAcc acc;
-    for (;;) {
-        unsigned long long k = 0;
-        if (lane == 0) k = atomicAdd(work, 1ULL);
-        k = __shfl_sync(0xFFFFFFFFu, k, 0);
-        if (k >= (unsigned long long)n) break;
-        const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
-        cast_point<kStats>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits, count, acc);
+    if (!work) {
+        // one point per warp, grid sized to the work: blocks are short-lived,
+        // so kernels of concurrent requests interleave block by block
+        const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        if (k < n) {
+            const int64_t i = order ? (int64_t)__ldg(&order[k]) : k;
+            cast_point<kStats>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits, count, acc);
+        }
+    } else {
+        for (;;) {
+            unsigned long long k = 0;
+            if (lane == 0) k = atomicAdd(work, 1ULL);
+            k = __shfl_sync(0xFFFFFFFFu, k, 0);
+            if (k >= (unsigned long long)n) break;
+            const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
+            cast_point<kStats>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits, count,
+                               acc);
+        }
     }
     warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow, acc.nvis, acc.ntri);
 }
@@ -398,8 +409,12 @@ __device__ __forceinline__ void flush_part_counters(unsigned long long* c, CastA
     a = CastAcc();
 }
 
+#ifndef RC_BATCH_MIN_BLOCKS
+#define RC_BATCH_MIN_BLOCKS 6
+#endif
+
 template <bool kStats>
-__global__ void __launch_bounds__(128, RC_HEMI_MIN_BLOCKS)
+__global__ void __launch_bounds__(128, RC_BATCH_MIN_BLOCKS)
 k_batch(const BatchPart* __restrict__ parts, int n_parts, long long n_items, int ppi,
         const float4* __restrict__ tdirs, int n_dirs, double eps, unsigned long long* work)
 {
@@ -441,7 +456,7 @@ k_batch(const BatchPart* __restrict__ parts, int n_parts, long long n_items, int
 // all lanes follow the same direction at a time; each lane keeps its point's
 // six-bit mask in a register.  Travel to the frame bounding box is FP64.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, RC_HEMI_MIN_BLOCKS)
+__global__ void __launch_bounds__(128, RC_BATCH_MIN_BLOCKS)
 k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
              const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
              const int32_t* __restrict__ order, const float* __restrict__ axes /*6x3*/,
@@ -544,8 +559,12 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
                             cudaStream_t s)
 {
     unsigned long long* work = nullptr;
-    RC_CUDA(cudaMallocAsync(&work, sizeof(unsigned long long), s));
-    RC_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
+    unsigned long long* work_alloc = nullptr;
+    if (p->launch_mode == 0) {
+        RC_CUDA(cudaMallocAsync(&work_alloc, sizeof(unsigned long long), s));
+        RC_CUDA(cudaMemsetAsync(work_alloc, 0, sizeof(unsigned long long), s));
+        work = work_alloc;
+    }
     int32_t* order = nullptr;
     if (p->point_order == 0 && n > 1) {
         RC_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * n, s));
@@ -556,8 +575,10 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
     const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_HEMI_MIN_BLOCKS;
     int64_t blocks = (int64_t)sm_count() * per_sm;
     const int64_t need = (n * 32 + threads - 1) / threads;
-    if (blocks > need) blocks = need;
+    if (blocks > need || p->launch_mode == 1) blocks = need;
     if (blocks < 1) blocks = 1;
+    if (blocks > 0x7FFFFFFF) return set_error(RC_E_UNSUPPORTED, "too many points for one launch");
+    if (p->launch_mode == 1) work = nullptr;
     const size_t smem = (size_t)(threads / 32) * (p->n_dirs / 32) * sizeof(uint32_t);
     if (smem > 48 * 1024) {
         RC_CUDA(cudaFuncSetAttribute(k_hemisphere<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -572,7 +593,7 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
                                                                  n, order, h->tdirs, p->n_dirs, p->origin_offset, bits,
                                                                  count, counters, work);
     RC_LAUNCHED();
-    RC_CUDA(cudaFreeAsync(work, s));
+    if (work_alloc) RC_CUDA(cudaFreeAsync(work_alloc, s));
     if (order) RC_CUDA(cudaFreeAsync(order, s));
     return RC_OK;
 }
@@ -622,8 +643,8 @@ rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n,
         if (pst != RC_OK) return pst;
     }
     int64_t blocks = (n + 127) / 128;
-    const int64_t cap = (int64_t)sm_count() * RC_HEMI_MIN_BLOCKS;
-    if (blocks > cap) blocks = cap;
+    const int64_t cap = (int64_t)sm_count() * RC_BATCH_MIN_BLOCKS;
+    if (blocks > cap && p->launch_mode == 0) blocks = cap;
     if (blocks < 1) blocks = 1;
     k_orthogonal<<<(unsigned)blocks, 128, 0, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N, n, order,
                                                  fd->axes, fd->frame, fd->fbox, p->origin_offset, mask, travel,

@@ -464,13 +464,11 @@ def part_family(family, target_tris, rng):
         return pocket_block(lv, size=size, width=w, depth=15.0 * s[2])
     if family == 1:
         sc = float(np.cbrt(s.prod()))
-        area = 75000.0 * sc * sc
-        h = math.sqrt(area * 2.9 / max(target_tris, 1000))
-        return prismatic(h=h, scale=sc)
+        # about 203k triangles at h = 1.67 mm and unit scale, T ~ 1/h^2
+        return prismatic(h=1.67 * sc * math.sqrt(203000.0 / max(target_tris, 1000)), scale=sc)
     sc = float(np.cbrt(s.prod()))
-    area = 130000.0 * sc * sc
-    h = math.sqrt(area * 0.11 / max(target_tris, 1000))
-    return impeller(h=max(h, 0.12), scale=sc)
+    # about 1.93M triangles at h = 0.69 mm and unit scale
+    return impeller(h=0.69 * sc * math.sqrt(1.93e6 / max(target_tris, 1000)), scale=sc)
 
 
 def perturbed_part(subdiv, shift_mm, size=(100.0, 60.0, 40.0), width=30.0, depth=15.0):

@@ -55,16 +55,18 @@ def test_header_compiles_as_c(tmp_path):
 
 def test_struct_layouts_match_header(rc, tmp_path):
     src = tmp_path / "s.c"
-    src.write_text('#include <stdio.h>\n#include "rc.h"\nint main(void){printf("%zu %zu %zu %zu %zu", '
+    src.write_text('#include <stdio.h>\n#include "rc.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu", '
                    'sizeof(rc_params), sizeof(rc_summary), sizeof(rc_setups), sizeof(rc_bvh_info), '
-                   'sizeof(rc_part_result));}\n')
+                   'sizeof(rc_part_result), sizeof(rc_server_config), sizeof(rc_request_result), '
+                   'sizeof(rc_server_stats));}\n')
     import subprocess
     exe = tmp_path / "s"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     out = subprocess.check_output([str(exe)]).decode().split()
     assert [int(x) for x in out] == [ctypes.sizeof(rc.Params), ctypes.sizeof(rc.Summary),
                                      ctypes.sizeof(rc.Setups), ctypes.sizeof(rc.BvhInfo),
-                                     ctypes.sizeof(rc.PartResult)]
+                                     ctypes.sizeof(rc.PartResult), ctypes.sizeof(rc.ServerConfig),
+                                     ctypes.sizeof(rc.RequestResult), ctypes.sizeof(rc.ServerStats)]
 
 
 def test_params_default(rc):

@@ -1,0 +1,95 @@
+"""Serving loop: requests admitted while others run give exactly the result
+of the same request analysed alone (rc_analyze_part), resident parts are
+refitted when their triangle list is unchanged, a request that can never fit
+the budget is rejected, and a failing request does not disturb the others."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2609_05467_gb300 as rc
+    rc.load()
+    return rc
+
+
+def _alone(rc, V, F, n, p):
+    W = p.n_dirs // 32
+    bits = np.zeros((n, W), np.uint32)
+    cnt = np.zeros(n, np.int32)
+    r = rc.rc_analyze_part(V, F, n, p, bits=bits, count=cnt)
+    return r, bits, cnt
+
+
+def _same(a, b):
+    sa, sb = a.summary, b.summary
+    assert sa.overall_access == sb.overall_access and sa.mean_conc == sb.mean_conc
+    assert list(sa.axis_share) == list(sb.axis_share) and sa.count_sum == sb.count_sum
+    assert a.label == b.label and a.setups_ran == b.setups_ran
+    assert a.setups.setups_exact == b.setups.setups_exact and a.setups.setups_greedy == b.setups.setups_greedy
+    assert list(a.setups.class_counts) == list(b.setups.class_counts)
+    assert list(a.cast_counters)[:1] == list(b.cast_counters)[:1]
+
+
+def test_requests_in_a_mix_equal_requests_alone(rc):
+    p = rc.rc_params_default(n_dirs=256, always_setups=1, tool_length=40.0)
+    jobs = [
+        (1, synth.perturbed_part(3, 0.0), 3000),
+        (2, synth.prismatic(h=3.0), 5000),
+        (3, synth.impeller(h=2.0), 4000),
+        (1, synth.perturbed_part(3, 2.5), 3000),    # same triangle list: refit
+        (4, synth.cube(20.0, 2), 500),
+        (5, synth.deep_hole(), 800),
+        (2, synth.prismatic(h=3.0), 2500),          # same part, fewer points
+    ]
+    srv = rc.rc_server_create(p, slots=3, hbm_budget_bytes=8 << 30)
+    ids = [rc.rc_server_submit(srv, key, V, F, n) for key, (V, F), n in jobs]
+    res = [rc.rc_server_wait(srv, i, timeout_s=300.0) for i in ids]
+    for r, (key, (V, F), n) in zip(res, jobs):
+        assert r.status == 0, r.message
+        assert r.t_submit <= r.t_admit <= r.t_start <= r.t_end
+        alone, bits, cnt = _alone(rc, V, F, n, p)
+        _same(r.result, alone)
+    assert res[0].rebuilt == 1 and res[3].rebuilt == 0 and res[6].rebuilt == 0
+    # the resident maps are those of each key's last request
+    for key, (V, F), n in [jobs[3], jobs[2], jobs[6], jobs[4], jobs[5]]:
+        rb, rcnt = rc.rc_server_read_bits(srv, key, n, p.n_dirs)
+        alone, bits, cnt = _alone(rc, V, F, n, p)
+        assert np.array_equal(rb, bits) and np.array_equal(rcnt, cnt)
+    st = rc.rc_server_get_stats(srv)
+    assert st.completed == len(jobs) and st.failed == 0 and st.resident_parts == 5
+    rc.rc_server_destroy(srv)
+
+
+def test_budget_rejection_and_failure_isolation(rc):
+    p = rc.rc_params_default(n_dirs=64)
+    V, F = synth.pocket_block(2)
+    srv = rc.rc_server_create(p, slots=2, hbm_budget_bytes=1 << 20)
+    big = rc.rc_server_submit(srv, 9, *synth.prismatic(h=3.0), 20000)
+    r = rc.rc_server_wait(srv, big, timeout_s=60.0)
+    assert r.status == 3                                        # RC_E_OOM: never fits
+    rc.rc_server_destroy(srv)
+
+    srv = rc.rc_server_create(p, slots=2, hbm_budget_bytes=1 << 30)
+    bad = F.copy()
+    bad[5, 1] = len(V) + 7                                      # index out of range
+    ids = [rc.rc_server_submit(srv, 1, V, F, 300), rc.rc_server_submit(srv, 2, V, bad, 300),
+           rc.rc_server_submit(srv, 3, V, F, 400)]
+    res = [rc.rc_server_wait(srv, i, timeout_s=60.0) for i in ids]
+    assert res[0].status == 0 and res[2].status == 0
+    assert res[1].status == 1 and b"outside" in res[1].message
+    alone, _, _ = _alone(rc, V, F, 400, p)
+    _same(res[2].result, alone)
+    st = rc.rc_server_get_stats(srv)
+    assert st.failed == 1 and st.completed == 2
+    with pytest.raises(rc.RcError):
+        rc.rc_server_wait(srv, 12345, timeout_s=0.1)            # unknown id
+    rc.rc_server_destroy(srv)
