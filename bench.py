@@ -504,7 +504,7 @@ def run_served(args):
         res = rc.rc_server_wait(srv, rid, timeout_s=600.0)
         return dict(lat=res.t_end - res.t_submit, rays=res.result.cast_counters[0] + res.result.ortho_counters[0],
                     rebuilt=res.rebuilt, status=res.status, wait=res.t_start - res.t_submit,
-                    level=res.priority_level, tris=len(r["F"]))
+                    level=res.priority_level, tris=len(r["F"]), n=r["n"], arrival=r["t"])
     # warm-up pass over a few requests (module load, tables, pools)
     for r in reqs[:3]:
         rc.rc_server_wait(srv, rc.rc_server_submit(srv, 10**9 + r["key"], r["V"], r["F"], r["n"]), 600.0)
@@ -520,10 +520,13 @@ def run_served(args):
         return time.perf_counter()
 
     def p_collect(tsub, r, t0):
+        t_start = time.perf_counter()
         with lock:
+            t_run = time.perf_counter()
             res = rc.rc_analyze_part(r["V"], r["F"], r["n"], p)
-        return dict(lat=time.perf_counter() - tsub, rays=res.cast_counters[0] + res.ortho_counters[0],
-                    rebuilt=1, status=0, wait=0.0, level=0, tris=len(r["F"]))
+        t_end = time.perf_counter()
+        return dict(lat=t_end - tsub, rays=res.cast_counters[0] + res.ortho_counters[0],
+                    rebuilt=1, status=0, wait=t_run - tsub, level=0, tris=len(r["F"]), n=r["n"], arrival=r["t"])
     plain, wall_p = replay(p_submit, p_collect)
 
     def summ(x, wall):
@@ -533,6 +536,14 @@ def run_served(args):
         out = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                "mean_ms": float(lat.mean()), "rays_per_s": rays / wall, "wall_s": wall,
                "failed": int(sum(d["status"] != 0 for d in x))}
+        wait = np.array([d["wait"] for d in x]) * 1e3
+        out["wait_p99_ms"] = float(np.percentile(wait, 99))
+        out["service_p99_ms"] = float(np.percentile(lat - wait, 99))
+        slow = np.argsort(-lat)[:6]
+        out["slowest"] = [{"lat_ms": round(float(lat[k]), 2), "wait_ms": round(float(wait[k]), 2),
+                           "tris": int(x[k]["tris"]), "points": int(x[k]["n"]), "level": int(x[k]["level"]),
+                           "rebuilt": int(x[k]["rebuilt"]), "arrival_s": round(float(x[k]["arrival"]), 3)}
+                          for k in slow]
         for name, lo, hi in (("lt_50k", 0, 5e4), ("100k_400k", 1e5, 4e5), ("gt_400k", 4e5, 1e12)):
             sel = lat[(tr >= lo) & (tr < hi)]
             if len(sel):

@@ -397,6 +397,197 @@ k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
 }
 
 // ---------------------------------------------------------------------------
+// Hemispherical cast with dynamic ray fetch (after Aila and Laine, HPG 2009):
+// the same rays and decisions as k_hemisphere, but a lane whose ray has
+// finished takes the next ray at once instead of waiting for the rest of its
+// tile.  A warp owns up to two points ("slots") at a time: it hands out the
+// current point's rays in tile order to idle lanes, opens the next point in
+// the free slot when the current one is exhausted, and writes a slot's bits
+// (shared-memory row, canonical order) and count once all of its rays are
+// done.  Each outer iteration every busy lane walks interior nodes until it
+// reaches a leaf (or finishes), then all such lanes test their leaves
+// together ("while-while").
+// ---------------------------------------------------------------------------
+#ifndef RC_DYN_MIN_BLOCKS
+#define RC_DYN_MIN_BLOCKS 6
+#endif
+
+struct SlotInfo {
+    long long i;               // point index
+    float ox, oy, oz;          // offset origin
+    float nx, ny, nz;          // normal
+    float t1x, t1y, t1z, t2x, t2y, t2z;
+    int pending;               // rays handed out and not finished
+    int count;                 // unobstructed rays so far
+};
+
+__global__ void __launch_bounds__(128, RC_DYN_MIN_BLOCKS)
+k_hemisphere_dyn(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps,
+                 float scene_maxabs, const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
+                 const int32_t* __restrict__ order, const float4* __restrict__ tdirs, int n_dirs, double eps,
+                 uint32_t* __restrict__ bits, int32_t* __restrict__ count, unsigned long long* counters,
+                 unsigned long long* work)
+{
+    extern __shared__ uint32_t s_mem[];
+    __shared__ SlotInfo s_slot[4][2];
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int W = n_dirs >> 5;
+    uint32_t* rows = s_mem + wid * (2 * W);
+    SlotInfo* si = s_slot[wid];
+
+    // per-lane ray state
+    bool has = false;
+    int slot = 0, j = 0, cur = 0, sp = 0, steps = 0;
+    bool amb = false, ambhit = false;
+    Ray r;
+    int stack[kStack];
+    // warp-uniform fetch state
+    int fetch = -1, next_k = 0;
+    bool live0 = false, live1 = false, exhausted = false;
+    CastAcc acc;
+
+    for (;;) {
+        // retire slots whose rays are all handed out and finished
+        __syncwarp();
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const bool live = s2 ? live1 : live0;
+            if (!live || (s2 == fetch && next_k < n_dirs) || si[s2].pending != 0) continue;
+            const long long i = si[s2].i;
+            for (int w = lane; w < W; w += 32) bits[i * W + w] = rows[s2 * W + w];
+            if (lane == 0) count[i] = si[s2].count;
+            if (s2) live1 = false; else live0 = false;
+            if (s2 == fetch) fetch = -1;
+        }
+        __syncwarp();
+        // hand out rays to idle lanes, opening new points as needed
+        unsigned need = __ballot_sync(FULL, !has);
+        while (need && !exhausted) {
+            if (fetch < 0 || next_k == n_dirs) {
+                const int f = !live0 ? 0 : (!live1 ? 1 : -1);
+                if (f < 0) break;                     // both slots busy: traverse first
+                unsigned long long kk = 0;
+                if (lane == 0) kk = atomicAdd(work, 1ULL);
+                kk = __shfl_sync(FULL, kk, 0);
+                if (kk >= (unsigned long long)n) { exhausted = true; break; }
+                if (lane == 0) {
+                    const long long i = order ? (long long)__ldg(&order[kk]) : (long long)kk;
+                    const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
+                    const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
+                    const Onb b = make_onb(nx, ny, nz);
+                    SlotInfo& q = si[f];
+                    q.i = i;
+                    q.ox = offset_coord(px, nx, eps);
+                    q.oy = offset_coord(py, ny, eps);
+                    q.oz = offset_coord(pz, nz, eps);
+                    q.nx = nx; q.ny = ny; q.nz = nz;
+                    q.t1x = b.t1x; q.t1y = b.t1y; q.t1z = b.t1z;
+                    q.t2x = b.t2x; q.t2y = b.t2y; q.t2z = b.t2z;
+                    q.pending = 0;
+                    q.count = 0;
+                }
+                for (int w = lane; w < W; w += 32) rows[f * W + w] = 0u;
+                if (f) live1 = true; else live0 = true;
+                fetch = f;
+                next_k = 0;
+                __syncwarp();
+            }
+            const int take = min(__popc(need), n_dirs - next_k);
+            const int rank = __popc(need & ((1u << lane) - 1u));
+            if (!has && rank < take) {
+                const SlotInfo& q = si[fetch];
+                const float4 h = __ldg(&tdirs[next_k + rank]);
+                j = __float_as_int(h.w);
+                Onb b;
+                b.t1x = q.t1x; b.t1y = q.t1y; b.t1z = q.t1z;
+                b.t2x = q.t2x; b.t2y = q.t2y; b.t2z = q.t2z;
+                float dx, dy, dz;
+                local_to_world(b, q.nx, q.ny, q.nz, h.x, h.y, h.z, dx, dy, dz);
+                setup_ray(r, q.ox, q.oy, q.oz, dx, dy, dz, scene_maxabs);
+                slot = fetch;
+                cur = 0;
+                sp = 0;
+                steps = 0;
+                amb = ambhit = false;
+                has = true;
+            }
+            if (lane == 0) si[fetch].pending += take;
+            next_k += take;
+            __syncwarp();
+            need = __ballot_sync(FULL, !has);
+        }
+        if (!__any_sync(FULL, has)) {
+            if (exhausted && !live0 && !live1) break;
+            continue;
+        }
+        // walk interior nodes until a leaf (or the end of the walk)
+        bool fin = false, blocked = false;
+        if (has) {
+            while (cur >= 0) {
+                if (++steps > max_steps) { ++acc.overflow; fin = true; blocked = true; break; }
+                const float4 n0 = __ldg(&nodes[4 * cur + 0]);
+                const float4 n1 = __ldg(&nodes[4 * cur + 1]);
+                const float4 n2 = __ldg(&nodes[4 * cur + 2]);
+                const float4 n3 = __ldg(&nodes[4 * cur + 3]);
+                bool h0, h1;
+                float t0, t1;
+                box2(r, n0, n1, n2, h0, h1, t0, t1);
+                const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+                if (h0 && h1) {
+                    const bool first0 = t0 <= t1;
+                    if (sp >= kStack) { ++acc.overflow; fin = true; blocked = true; break; }
+                    stack[sp++] = first0 ? c1 : c0;
+                    cur = first0 ? c0 : c1;
+                } else if (h0) {
+                    cur = c0;
+                } else if (h1) {
+                    cur = c1;
+                } else if (sp == 0) {
+                    fin = true;
+                    break;
+                } else {
+                    cur = stack[--sp];
+                }
+            }
+        }
+        // test the leaves the lanes have reached
+        if (has && !fin) {
+            const int v = -1 - cur;
+            const int first = v >> 3, cnt = (v & 7) + 1;
+            for (int k = 0; k < cnt && !fin; ++k) {
+                const float4* t = tris + 3 * (first + k);
+                const float4 v0 = __ldg(t), v1 = __ldg(t + 1), v2 = __ldg(t + 2);
+                const int s = tri_test32(r, v0, v1, v2);
+                if (s == kHit) { fin = true; blocked = true; break; }
+                if (s == kUnsure) {
+                    ++acc.retests;
+                    const Pair64 pr = retest64(r, v0, v1, v2);
+                    if (pr.state == kHit) { fin = true; blocked = true; break; }
+                    if (pr.state == kUnsure) { amb = true; ambhit |= pr.hit64; }
+                }
+            }
+            if (!fin) {
+                if (sp == 0) fin = true;
+                else cur = stack[--sp];
+            }
+        }
+        // retire finished rays
+        if (has && fin) {
+            const bool hit = blocked || ambhit;
+            if (!blocked && amb) ++acc.amb;
+            if (!hit) {
+                atomicOr(&rows[slot * W + (j >> 5)], 1u << (j & 31));
+                atomicAdd(&si[slot].count, 1);
+            }
+            atomicSub(&si[slot].pending, 1);
+            ++acc.rays;
+            has = false;
+        }
+    }
+    warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow);
+}
+
+// ---------------------------------------------------------------------------
 // Batched hemispherical cast: one persistent launch over the points of many
 // parts.  Work items are runs of `ppi` consecutive points (in each part's
 // processing order) of one part; a warp takes items from one global counter,
@@ -584,7 +775,17 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
         RC_CUDA(cudaFuncSetAttribute(k_hemisphere<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         RC_CUDA(cudaFuncSetAttribute(k_hemisphere<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    if (stats)
+    if (p->fetch_mode == 1 && !stats && work) {
+        const size_t dsmem = 2 * smem;
+        if (dsmem > 48 * 1024)
+            RC_CUDA(cudaFuncSetAttribute(k_hemisphere_dyn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+        int64_t dblocks = (int64_t)sm_count() * (p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_DYN_MIN_BLOCKS);
+        if (dblocks > need) dblocks = need;
+        if (dblocks < 1) dblocks = 1;
+        k_hemisphere_dyn<<<(unsigned)dblocks, threads, dsmem, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs,
+                                                                   P, N, n, order, h->tdirs, p->n_dirs,
+                                                                   p->origin_offset, bits, count, counters, work);
+    } else if (stats)
         k_hemisphere<true><<<(unsigned)blocks, threads, smem, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N,
                                                                 n, order, h->tdirs, p->n_dirs, p->origin_offset, bits,
                                                                 count, counters, work);

@@ -106,8 +106,9 @@ def test_single_part_knobs_do_not_change_results(rc):
     res = []
     for order in (0, 1):
         for tile in (0, 1):
-            for per_sm in (0, 4):
-                q = rc.rc_params_default(n_dirs=N, point_order=order, tile_mode=tile, blocks_per_sm=per_sm)
+            for per_sm, fetch, launch in ((0, 0, 0), (4, 0, 0), (0, 1, 0), (3, 1, 0), (0, 0, 1)):
+                q = rc.rc_params_default(n_dirs=N, point_order=order, tile_mode=tile, blocks_per_sm=per_sm,
+                                         fetch_mode=fetch, launch_mode=launch)
                 bits = torch.zeros((n, N // 32), dtype=torch.int32, device="cuda")
                 cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
                 rc.rc_hemisphere_cast(bvh.h, P, Nn, q, bits, cnt)

@@ -115,6 +115,21 @@ def test_hemisphere_parity(rc, name, n, N):
     bvh.close()
 
 
+@pytest.mark.parametrize("name,n,N", [("pocket", 1000, 256), ("prismatic_coarse", 777, 160),
+                                       ("impeller_coarse", 500, 128), ("cavity", 300, 64)])
+def test_hemisphere_parity_dynamic_fetch(rc, name, n, N):
+    """The dynamic-fetch traversal gives the oracle's bits too."""
+    V, F = PARTS[name]()
+    bvh = _build(rc, V, F)
+    p = rc.rc_params_default(n_dirs=N, fetch_mode=1)
+    P, Nn, f, w = _sample(rc, bvh, n, p)
+    gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
+    ob, oa, oc = oracle.Mesh(V, F).hemisphere(P, Nn, N)
+    compare_bits(gb, gc, ob, oa, oc, N)
+    assert ctr[0] == n * N and ctr[3] == 0
+    bvh.close()
+
+
 def test_hemisphere_closed_forms_on_gpu(rc):
     """Convex parts: every ray escapes; sealed cavity: every ray is blocked."""
     for V, F, expect in ((*synth.cube(20.0, 2), 1), (*synth.icosphere(10.0, 3), 1)):
