@@ -281,7 +281,10 @@ def run_gpu(args, wl, V, F):
     rays_cast = float(st[0])
     nodes_per_ray = st[4] / rays_cast
     tris_per_ray = st[5] / rays_cast
-    bytes_per_ray = 64.0 * nodes_per_ray + 48.0 * tris_per_ray + 24.0 / N + 1.0 / 8.0
+    # a 4-wide node fetch reads 7 float4 (four child boxes + child indices),
+    # a binary node 4 float4; a triangle record 3 float4
+    node_bytes = 64.0 if ps.tree_width == 2 else 112.0
+    bytes_per_ray = node_bytes * nodes_per_ray + 48.0 * tris_per_ray + 24.0 / N + 1.0 / 8.0
 
     # warm-up
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(total_steps)]
@@ -391,6 +394,7 @@ def run_gpu(args, wl, V, F):
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
                      "kernel": "k_hemisphere", "kernel_ms": 1e3 * cast_s,
                      "bytes_per_ray": bytes_per_ray, "nodes_per_ray": nodes_per_ray, "tris_per_ray": tris_per_ray,
+                     "node_bytes": node_bytes, "tree": "4-wide" if ps.tree_width != 2 else "binary",
                      "traffic_source": tsrc},
         "quality": {"ambiguous_rays": amb_rays, "fp64_retests": retests, "errors": errors,
                     "rays_per_step": float(np.mean(rays_per_step)), "wall_s": wall,

@@ -84,9 +84,10 @@ typedef struct {
     int32_t points_per_item; /* batched cast: points per work item (0 = 1) */
     int32_t launch_mode;     /* casts: 0 = persistent grid (default), 1 = one warp per point, grid sized to the work
                                 (short blocks, so concurrent casts on other streams interleave) */
-    int32_t fetch_mode;      /* hemispherical cast (persistent grid): 0 = lanes wait for their tile of 32 rays,
-                                1 = a lane takes the next ray as soon as its ray finishes (dynamic fetch) */
-    int32_t reserved[3];
+    int32_t fetch_mode;      /* hemispherical cast (persistent grid, binary tree): 0 = lanes wait for their tile
+                                of 32 rays, 1 = a lane takes the next ray as soon as its ray finishes */
+    int32_t tree_width;      /* casts: 0 or 4 = 4-wide tree (default), 2 = binary tree */
+    int32_t reserved[2];
 } rc_params;
 
 /* Part-level indicators (Sections 3.1 and 3.3). */

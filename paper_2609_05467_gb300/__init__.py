@@ -53,7 +53,7 @@ class Params(ctypes.Structure):
         ("t_conc", ctypes.c_double), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
         ("collect_stats", ctypes.c_int32), ("always_setups", ctypes.c_int32), ("point_order", ctypes.c_int32),
         ("tile_mode", ctypes.c_int32), ("points_per_item", ctypes.c_int32), ("launch_mode", ctypes.c_int32),
-        ("fetch_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+        ("fetch_mode", ctypes.c_int32), ("tree_width", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
     ]
 
 

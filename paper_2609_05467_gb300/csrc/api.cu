@@ -148,6 +148,8 @@ static rc_status check_params(const rc_params* p)
         return set_error(RC_E_ARG, "points_per_item must be in [0, 64]");
     if (p->launch_mode != 0 && p->launch_mode != 1) return set_error(RC_E_ARG, "launch_mode must be 0 or 1");
     if (p->fetch_mode != 0 && p->fetch_mode != 1) return set_error(RC_E_ARG, "fetch_mode must be 0 or 1");
+    if (p->tree_width != 0 && p->tree_width != 2 && p->tree_width != 4)
+        return set_error(RC_E_ARG, "tree_width must be 0 (default), 2 or 4");
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return set_error(RC_E_ARG, "blocks_per_sm out of range");
     if (p->collect_stats != 0 && p->collect_stats != 1) return set_error(RC_E_ARG, "collect_stats must be 0 or 1");
     return RC_OK;
@@ -179,7 +181,7 @@ static rc_status use_device_of(rc_bvh h)
 static void free_handle(rc_bvh h)
 {
     if (!h) return;
-    void* ptrs[] = {h->V, h->F, h->tris, h->nodes, h->parent, h->child, h->range, h->order, h->nbox,
+    void* ptrs[] = {h->V, h->F, h->tris, h->nodes, h->wnodes, h->parent, h->child, h->range, h->order, h->nbox,
                     h->visits, h->fnorm, h->farea, h->fcent, h->cdf, h->sc};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, 0);

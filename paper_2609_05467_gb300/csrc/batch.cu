@@ -15,6 +15,7 @@ rc_status launch_batch(const BatchPart* d_parts, int n_parts, long long n_items,
 rc_status prepare_batch_kernel(int n_dirs);
 rc_status device_dirs_for_cast(const rc_params* p, const float4** tdirs);
 rc_status check_params_public(const rc_params* p);
+bool use_wide(const rc_params* p);
 
 struct HostPart {
     rc_bvh h;
@@ -71,7 +72,7 @@ static rc_status prepare(rc_batch b, cudaStream_t s)
             if (st != RC_OK) return st;
         }
         BatchPart& d = hp[k];
-        d.nodes = q.h->nodes;
+        d.nodes = use_wide(&b->p) ? q.h->wnodes : q.h->nodes;
         d.tris = q.h->tris;
         d.P = q.P;
         d.N = q.N;

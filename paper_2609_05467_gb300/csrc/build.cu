@@ -15,6 +15,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "rc_internal.cuh"
@@ -128,6 +129,7 @@ __global__ void k_morton(const float* __restrict__ tbox, int64_t T, const DevSca
 // LSD radix sort of (uint64 key, int32 value), 8-bit digits, stable
 // ---------------------------------------------------------------------------
 constexpr int kMaxWalk = 4096;   // bound on leaf-to-root walks
+constexpr int kMaxWalkHost = kMaxWalk;
 constexpr int kSortThreads = 256;
 constexpr int kSortTile = 4096;   // keys per block
 
@@ -325,6 +327,118 @@ __global__ void k_pack(int64_t n_int, const int32_t* __restrict__ child, const i
     nodes[4 * i + 2] = make_float4(A[2], A[5], B[2], B[5]);
     nodes[4 * i + 3] = make_float4(__int_as_float(encode_child(a, n_int, range)),
                                    __int_as_float(encode_child(b, n_int, range)), 0.0f, 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// 4-wide tree: top-down collapse of the binary tree, one level per launch.
+// A wide node starts from a binary interior node's two children and keeps
+// replacing its interior child of largest box surface area by that child's
+// two children until it has four children or only leaves.  Wide node layout
+// (8 float4, 128 B): lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the four
+// children, then the four child indices (>= 0 wide node, < 0 leaf as in the
+// binary layout), then padding.  Empty slots have an empty box.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool bin_is_leaf(int32_t c, int64_t n_int, const int32_t* range)
+{
+    return c >= n_int || range[2 * c + 1] - range[2 * c] + 1 <= kLeafMax;
+}
+
+__device__ __forceinline__ float half_area(const float* b)
+{
+    const float dx = b[3] - b[0], dy = b[4] - b[1], dz = b[5] - b[2];
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void k_wide_level(int64_t n_int, const int32_t* __restrict__ child, const int32_t* __restrict__ range,
+                             const float* __restrict__ nbox, const int32_t* __restrict__ qin_bin,
+                             const int32_t* __restrict__ qin_wide, const int* __restrict__ qin_count,
+                             int32_t* qout_bin, int32_t* qout_wide, int* qout_count, int* wide_count,
+                             float4* wnodes, DevScalars* sc, int level)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *qin_count) return;
+    const int32_t b = qin_bin[t], w = qin_wide[t];
+    int32_t ch[4];
+    int nch = 2;
+    ch[0] = child[2 * b];
+    ch[1] = child[2 * b + 1];
+    while (nch < 4) {
+        int best = -1;
+        float ba = -1.0f;
+        for (int k = 0; k < nch; ++k) {
+            if (bin_is_leaf(ch[k], n_int, range)) continue;
+            const float a = half_area(nbox + 6 * (int64_t)ch[k]);
+            if (a > ba) { ba = a; best = k; }
+        }
+        if (best < 0) break;
+        const int32_t c = ch[best];
+        ch[best] = child[2 * c];
+        ch[nch++] = child[2 * c + 1];
+    }
+    float lo[3][4], hi[3][4];
+    int32_t idx[4];
+    for (int k = 0; k < 4; ++k) {
+        if (k < nch) {
+            const float* bb = nbox + 6 * (int64_t)ch[k];
+            for (int a = 0; a < 3; ++a) { lo[a][k] = bb[a]; hi[a][k] = bb[3 + a]; }
+            if (bin_is_leaf(ch[k], n_int, range)) {
+                idx[k] = encode_child(ch[k], n_int, range);
+            } else {
+                const int nw = atomicAdd(wide_count, 1);
+                const int q = atomicAdd(qout_count, 1);
+                qout_bin[q] = ch[k];
+                qout_wide[q] = nw;
+                idx[k] = nw;
+            }
+        } else {
+            for (int a = 0; a < 3; ++a) { lo[a][k] = INFINITY; hi[a][k] = -INFINITY; }
+            idx[k] = -1;
+        }
+    }
+    float4* nd = wnodes + 8 * (int64_t)w;
+    nd[0] = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
+    nd[1] = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
+    nd[2] = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
+    nd[3] = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
+    nd[4] = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
+    nd[5] = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
+    nd[6] = make_float4(__int_as_float(idx[0]), __int_as_float(idx[1]), __int_as_float(idx[2]), __int_as_float(idx[3]));
+    nd[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    atomicMax(&sc->wide_depth, level + 1);
+}
+
+// wide root for parts with at most kLeafMax triangles: one leaf child
+__global__ void k_wide_small(int64_t T, const float* __restrict__ tbox, float4* wnodes, DevScalars* sc)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t f = 0; f < T; ++f)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fminf(lo[c], tbox[6 * f + c]);
+            hi[c] = fmaxf(hi[c], tbox[6 * f + 3 + c]);
+        }
+    const float I = INFINITY;
+    wnodes[0] = make_float4(lo[0], I, I, I);
+    wnodes[1] = make_float4(hi[0], -I, -I, -I);
+    wnodes[2] = make_float4(lo[1], I, I, I);
+    wnodes[3] = make_float4(hi[1], -I, -I, -I);
+    wnodes[4] = make_float4(lo[2], I, I, I);
+    wnodes[5] = make_float4(hi[2], -I, -I, -I);
+    wnodes[6] = make_float4(__int_as_float(-1 - (int)(T - 1)), __int_as_float(-1), __int_as_float(-1),
+                            __int_as_float(-1));
+    wnodes[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    sc->wide_depth = 1;
+}
+
+__global__ void k_wide_init(int32_t* q_bin, int32_t* q_wide, int* counts)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        q_bin[0] = 0;
+        q_wide[0] = 0;
+        counts[0] = 1;   // queue A size
+        counts[1] = 0;   // queue B size
+        counts[2] = 1;   // wide nodes allocated
+    }
 }
 
 // single-leaf root for parts with at most kLeafMax triangles
@@ -571,6 +685,8 @@ static rc_status init_scalars(DevScalars* sc, cudaStream_t s)
     h.err_vertex = 0x7FFFFFFF;
     h.max_depth = 0;
     h.pad = 0;
+    h.wide_depth = 0;
+    h.pad2 = 0;
     RC_CUDA(cudaMemcpyAsync(sc, &h, sizeof h, cudaMemcpyHostToDevice, s));
     RC_CUDA(cudaStreamSynchronize(s));
     return RC_OK;
@@ -602,7 +718,45 @@ static rc_status check_scalars(rc_bvh h, cudaStream_t s)
     if (d.err_vertex != 0x7FFFFFFF)
         return set_error(RC_E_ARG, "vertex " + std::to_string(d.err_vertex) + " is not finite");
     h->scene_maxabs = std::max(1.0f, ordered_to_float(d.vmaxabs));
-    h->max_depth = d.max_depth;
+    // the tree depth is set by the build once the tree exists (a refit keeps
+    // the topology and hence the depth)
+    return RC_OK;
+}
+
+// Collapse the binary tree into the 4-wide layout (wnodes), or make the
+// one-leaf wide root for tiny parts.  Needs the binary tree and its boxes.
+static rc_status build_wide(rc_bvh h, const float* tbox, cudaStream_t s)
+{
+    const int64_t T = h->T;
+    if (!h->wnodes) RC_CUDA(cudaMallocAsync(&h->wnodes, sizeof(float4) * 8 * h->n_int, s));
+    if (T <= kLeafMax) {
+        k_wide_small<<<1, 32, 0, s>>>(T, tbox, h->wnodes, h->sc);
+        RC_LAUNCHED();
+        return RC_OK;
+    }
+    const int64_t n_int = h->n_int;
+    int32_t* q = nullptr;
+    int* counts = nullptr;
+    RC_CUDA(cudaMallocAsync(&q, sizeof(int32_t) * 4 * n_int, s));
+    RC_CUDA(cudaMallocAsync(&counts, sizeof(int) * 4, s));
+    int32_t *qa_bin = q, *qa_wide = q + n_int, *qb_bin = q + 2 * n_int, *qb_wide = q + 3 * n_int;
+    int *ca = counts, *cb = counts + 1;
+    k_wide_init<<<1, 32, 0, s>>>(qa_bin, qa_wide, counts);
+    RC_LAUNCHED();
+    // a wide level consumes at least one binary level: max_depth + 1 launches suffice
+    for (int level = 0; level <= h->max_depth; ++level) {
+        const double cap = std::min((double)n_int, std::pow(4.0, (double)std::min(level, 30)));
+        const unsigned grid = (unsigned)std::max(1.0, std::ceil(cap / 256.0));
+        RC_CUDA(cudaMemsetAsync(cb, 0, sizeof(int), s));
+        k_wide_level<<<grid, 256, 0, s>>>(n_int, h->child, h->range, h->nbox, qa_bin, qa_wide, ca, qb_bin, qb_wide,
+                                          cb, counts + 2, h->wnodes, h->sc, level);
+        RC_LAUNCHED();
+        std::swap(qa_bin, qb_bin);
+        std::swap(qa_wide, qb_wide);
+        std::swap(ca, cb);
+    }
+    RC_CUDA(cudaFreeAsync(q, s));
+    RC_CUDA(cudaFreeAsync(counts, s));
     return RC_OK;
 }
 
@@ -652,7 +806,13 @@ rc_status build_bvh(rc_bvh h, cudaStream_t s)
         k_pack<<<nblocks(n_int, 256), 256, 0, s>>>(n_int, h->child, h->range, h->nbox, h->nodes);
         RC_LAUNCHED();
         RC_CUDA(cudaFreeAsync(k0, s));
+        // the collapse needs the depth bound on the host
+        RC_CUDA(cudaMemcpyAsync(&h->host_sc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+        RC_CUDA(cudaStreamSynchronize(s));
+        h->max_depth = std::min(h->host_sc.max_depth, kMaxWalkHost);
     }
+    st = build_wide(h, tbox, s);
+    if (st != RC_OK) return st;
     k_tri_records<<<nblocks(T, 256), 256, 0, s>>>(h->V, h->F, h->order, T, h->tris);
     RC_LAUNCHED();
     RC_CUDA(cudaFreeAsync(tbox, s));
@@ -660,9 +820,13 @@ rc_status build_bvh(rc_bvh h, cudaStream_t s)
     RC_CUDA(cudaStreamSynchronize(s));
     if (h->host_sc.pad != 0) return set_error(RC_E_DEVICE, "radix sort produced an out-of-range position");
     if (T > kLeafMax) h->max_depth = h->host_sc.max_depth;
+    h->wide_depth = h->host_sc.wide_depth;
     for (int k = 0; k < 3; ++k) { h->lo[k] = 0; h->hi[k] = 0; }
     if (h->max_depth >= kStack)
         return set_error(RC_E_UNSUPPORTED, "BVH depth " + std::to_string(h->max_depth) +
+                                               " exceeds the traversal stack");
+    if (3 * h->wide_depth + 1 >= kStack4)
+        return set_error(RC_E_UNSUPPORTED, "4-wide BVH depth " + std::to_string(h->wide_depth) +
                                                " exceeds the traversal stack");
     return RC_OK;
 }
@@ -689,10 +853,16 @@ rc_status refit_bvh(rc_bvh h, cudaStream_t s)
         k_pack<<<nblocks(n_int, 256), 256, 0, s>>>(n_int, h->child, h->range, h->nbox, h->nodes);
         RC_LAUNCHED();
     }
+    st = build_wide(h, tbox, s);
+    if (st != RC_OK) return st;
     k_tri_records<<<nblocks(T, 256), 256, 0, s>>>(h->V, h->F, h->order, T, h->tris);
     RC_LAUNCHED();
     RC_CUDA(cudaFreeAsync(tbox, s));
+    RC_CUDA(cudaMemcpyAsync(&h->host_sc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaStreamSynchronize(s));
+    h->wide_depth = h->host_sc.wide_depth;
+    if (3 * h->wide_depth + 1 >= kStack4)
+        return set_error(RC_E_UNSUPPORTED, "4-wide BVH depth exceeds the traversal stack after refit");
     return RC_OK;
 }
 

@@ -280,6 +280,97 @@ __device__ __forceinline__ TraceOut trace(const float4* __restrict__ nodes, cons
     return out;
 }
 
+// Any-hit walk of the 4-wide tree: the same ray, box and triangle decisions
+// as trace(); per node the four child boxes are tested together, the
+// nearest hit child is visited next and the others are pushed far-to-near.
+template <bool kStats>
+__device__ __forceinline__ TraceOut trace4(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
+                                           const Ray& r, int max_steps)
+{
+    TraceOut out = {0, 0, 0, 0, 0};
+    int stack[kStack4];
+    int sp = 0;
+    int cur = 0;
+    bool amb = false, ambhit = false;
+    const float rob = 1.0f + 2.0f * 1.7881394e-7f;
+    const bool sx = signbit(r.ix), sy = signbit(r.iy), sz = signbit(r.iz);
+    for (int steps = 0;; ++steps) {
+        if (steps > max_steps) { out.overflow = 1; out.flags = 1; return out; }
+        if (cur >= 0) {
+            if (kStats) ++out.nodes;
+            const float4* nd = wnodes + 8 * cur;
+            const float4 lox = __ldg(nd + 0), hix = __ldg(nd + 1), loy = __ldg(nd + 2), hiy = __ldg(nd + 3);
+            const float4 loz = __ldg(nd + 4), hiz = __ldg(nd + 5), ci = __ldg(nd + 6);
+            float d[4];
+            int c[4];
+            const float lx[4] = {lox.x, lox.y, lox.z, lox.w}, hx[4] = {hix.x, hix.y, hix.z, hix.w};
+            const float ly[4] = {loy.x, loy.y, loy.z, loy.w}, hy[4] = {hiy.x, hiy.y, hiy.z, hiy.w};
+            const float lz[4] = {loz.x, loz.y, loz.z, loz.w}, hz[4] = {hiz.x, hiz.y, hiz.z, hiz.w};
+            const int cc[4] = {__float_as_int(ci.x), __float_as_int(ci.y), __float_as_int(ci.z), __float_as_int(ci.w)};
+            int nh = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float nx = ((sx ? hx[k] : lx[k]) - r.ox) * r.ix, fx = ((sx ? lx[k] : hx[k]) - r.ox) * r.ix;
+                const float ny = ((sy ? hy[k] : ly[k]) - r.oy) * r.iy, fy = ((sy ? ly[k] : hy[k]) - r.oy) * r.iy;
+                const float nz = ((sz ? hz[k] : lz[k]) - r.oz) * r.iz, fz = ((sz ? lz[k] : hz[k]) - r.oz) * r.iz;
+                const float tn = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.0f));
+                const float tf = fminf(fminf(fx, fy), fz) * rob;
+                const bool hit = tn <= tf;
+                d[k] = hit ? tn : INFINITY;
+                c[k] = cc[k];
+                nh += hit;
+            }
+            if (nh == 0) {
+                if (sp == 0) break;
+                cur = stack[--sp];
+                continue;
+            }
+            // sort the four (distance, child) pairs: misses (inf) go last
+#define RC_CSWAP(a, b)                                              \
+    if (d[b] < d[a]) {                                              \
+        const float td = d[a]; d[a] = d[b]; d[b] = td;              \
+        const int tc = c[a]; c[a] = c[b]; c[b] = tc;                \
+    }
+            RC_CSWAP(0, 1) RC_CSWAP(2, 3) RC_CSWAP(0, 2) RC_CSWAP(1, 3) RC_CSWAP(1, 2)
+#undef RC_CSWAP
+            if (sp + nh - 1 > kStack4) { out.overflow = 1; out.flags = 1; return out; }
+            if (nh > 3) stack[sp++] = c[3];
+            if (nh > 2) stack[sp++] = c[2];
+            if (nh > 1) stack[sp++] = c[1];
+            cur = c[0];
+            continue;
+        } else {
+            const int v = -1 - cur;
+            const int first = v >> 3, cnt = (v & 7) + 1;
+            for (int k = 0; k < cnt; ++k) {
+                const float4* t = tris + 3 * (first + k);
+                const float4 v0 = __ldg(t), v1 = __ldg(t + 1), v2 = __ldg(t + 2);
+                if (kStats) ++out.tris;
+                const int s = tri_test32(r, v0, v1, v2);
+                if (s == kHit) { out.flags = 1; return out; }
+                if (s == kUnsure) {
+                    ++out.retests;
+                    const Pair64 p = retest64(r, v0, v1, v2);
+                    if (p.state == kHit) { out.flags = 1; return out; }
+                    if (p.state == kUnsure) { amb = true; ambhit |= p.hit64; }
+                }
+            }
+        }
+        if (sp == 0) break;
+        cur = stack[--sp];
+    }
+    out.flags = (ambhit ? 1 : 0) | (amb ? 2 : 0);
+    return out;
+}
+
+template <bool kStats, bool kWide>
+__device__ __forceinline__ TraceOut trace_any(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                              const Ray& r, int max_steps)
+{
+    if (kWide) return trace4<kStats>(nodes, tris, r, max_steps);
+    return trace<kStats>(nodes, tris, r, max_steps);
+}
+
 __device__ __forceinline__ void warp_add_counters(unsigned long long* counters, long long rays,
                                                   int amb, int retests, int overflow, long long nvis = 0,
                                                   long long ntri = 0)
@@ -313,7 +404,7 @@ __device__ __forceinline__ void warp_add_counters(unsigned long long* counters, 
 // order once the point is done; the count is the sum of the tile ballots.
 // ---------------------------------------------------------------------------
 #ifndef RC_HEMI_MIN_BLOCKS
-#define RC_HEMI_MIN_BLOCKS 8
+#define RC_HEMI_MIN_BLOCKS 6
 #endif
 
 struct CastAcc {
@@ -323,7 +414,7 @@ struct CastAcc {
 
 // The hemispherical cast of one point by one warp (see above).  `tdirs` is
 // the tile-ordered table, `row` the warp's shared-memory row of W words.
-template <bool kStats>
+template <bool kStats, bool kWide>
 __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                            int max_steps, float scene_maxabs, const float* __restrict__ P,
                                            const float* __restrict__ Nrm, int64_t i,
@@ -345,7 +436,7 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
         local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
         Ray r;
         setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-        const TraceOut tr = trace<kStats>(nodes, tris, r, max_steps);
+        const TraceOut tr = trace_any<kStats, kWide>(nodes, tris, r, max_steps);
         acc.retests += tr.retests;
         acc.overflow += tr.overflow;
         acc.amb += (tr.flags >> 1) & 1;
@@ -361,7 +452,7 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
     acc.rays += W;   // per lane
 }
 
-template <bool kStats>
+template <bool kStats, bool kWide>
 __global__ void __launch_bounds__(128, RC_HEMI_MIN_BLOCKS)
 k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
              const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
@@ -374,24 +465,22 @@ k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
     const int W = n_dirs >> 5;
     uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
     CastAcc acc;
-    if (!work) {
-        // one point per warp, grid sized to the work: blocks are short-lived,
-        // so kernels of concurrent requests interleave block by block
-        const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-        if (k < n) {
-            const int64_t i = order ? (int64_t)__ldg(&order[k]) : k;
-            cast_point<kStats>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits, count, acc);
-        }
-    } else {
-        for (;;) {
-            unsigned long long k = 0;
+    // with a work counter the warps take points until none are left; without
+    // one (grid sized to the work) each warp casts exactly its own point, so
+    // blocks are short-lived and kernels of concurrent requests interleave
+    const unsigned long long own = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (bool first = true;; first = false) {
+        unsigned long long k = (unsigned long long)n;
+        if (work) {
             if (lane == 0) k = atomicAdd(work, 1ULL);
             k = __shfl_sync(0xFFFFFFFFu, k, 0);
-            if (k >= (unsigned long long)n) break;
-            const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
-            cast_point<kStats>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits, count,
-                               acc);
+        } else if (first) {
+            k = own;
         }
+        if (k >= (unsigned long long)n) break;
+        const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
+        cast_point<kStats, kWide>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits, count,
+                                  acc);
     }
     warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow, acc.nvis, acc.ntri);
 }
@@ -604,7 +693,7 @@ __device__ __forceinline__ void flush_part_counters(unsigned long long* c, CastA
 #define RC_BATCH_MIN_BLOCKS 6
 #endif
 
-template <bool kStats>
+template <bool kStats, bool kWide>
 __global__ void __launch_bounds__(128, RC_BATCH_MIN_BLOCKS)
 k_batch(const BatchPart* __restrict__ parts, int n_parts, long long n_items, int ppi,
         const float4* __restrict__ tdirs, int n_dirs, double eps, unsigned long long* work)
@@ -634,8 +723,8 @@ k_batch(const BatchPart* __restrict__ parts, int n_parts, long long n_items, int
         const long long q1 = q0 + ppi < bp.n ? q0 + ppi : bp.n;
         for (long long q = q0; q < q1; ++q) {
             const int64_t i = bp.order ? (int64_t)__ldg(&bp.order[q]) : (int64_t)q;
-            cast_point<kStats>(bp.nodes, bp.tris, bp.max_steps, bp.scene_maxabs, bp.P, bp.N, i, tdirs, W, eps,
-                               row, bp.bits, bp.count, acc);
+            cast_point<kStats, kWide>(bp.nodes, bp.tris, bp.max_steps, bp.scene_maxabs, bp.P, bp.N, i, tdirs, W,
+                                      eps, row, bp.bits, bp.count, acc);
         }
     }
     if (cur >= 0) flush_part_counters(parts[cur].counters, acc);
@@ -647,6 +736,7 @@ k_batch(const BatchPart* __restrict__ parts, int n_parts, long long n_items, int
 // all lanes follow the same direction at a time; each lane keeps its point's
 // six-bit mask in a register.  Travel to the frame bounding box is FP64.
 // ---------------------------------------------------------------------------
+template <bool kWide>
 __global__ void __launch_bounds__(128, RC_BATCH_MIN_BLOCKS)
 k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
              const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
@@ -679,7 +769,7 @@ k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
             if (nd >= 0.0) {
                 Ray r;
                 setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-                const TraceOut t = trace<false>(nodes, tris, r, max_steps);
+                const TraceOut t = trace_any<false, kWide>(nodes, tris, r, max_steps);
                 retests += t.retests;
                 overflow += t.overflow;
                 amb += (t.flags >> 1) & 1;
@@ -730,6 +820,9 @@ __global__ void k_frame_box_finish(long long* box, double* fbox)
 // ---------------------------------------------------------------------------
 static int max_steps(rc_bvh h) { return (int)(2 * (h->n_int + h->T) + 64); }
 
+// the 4-wide tree is the default; tree_width 2 selects the binary tree
+bool use_wide(const rc_params* p) { return p->tree_width != 2; }
+
 static int g_sm_count = 0;
 
 static int sm_count()
@@ -771,11 +864,15 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
     if (blocks > 0x7FFFFFFF) return set_error(RC_E_UNSUPPORTED, "too many points for one launch");
     if (p->launch_mode == 1) work = nullptr;
     const size_t smem = (size_t)(threads / 32) * (p->n_dirs / 32) * sizeof(uint32_t);
+    const bool wide = use_wide(p);
     if (smem > 48 * 1024) {
-        RC_CUDA(cudaFuncSetAttribute(k_hemisphere<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        RC_CUDA(cudaFuncSetAttribute(k_hemisphere<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RC_CUDA(cudaFuncSetAttribute(k_hemisphere<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RC_CUDA(cudaFuncSetAttribute(k_hemisphere<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RC_CUDA(cudaFuncSetAttribute(k_hemisphere<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RC_CUDA(cudaFuncSetAttribute(k_hemisphere<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    if (p->fetch_mode == 1 && !stats && work) {
+    const float4* tree = wide ? h->wnodes : h->nodes;
+    if (p->fetch_mode == 1 && !stats && work && !wide) {
         const size_t dsmem = 2 * smem;
         if (dsmem > 48 * 1024)
             RC_CUDA(cudaFuncSetAttribute(k_hemisphere_dyn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
@@ -785,14 +882,17 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
         k_hemisphere_dyn<<<(unsigned)dblocks, threads, dsmem, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs,
                                                                    P, N, n, order, h->tdirs, p->n_dirs,
                                                                    p->origin_offset, bits, count, counters, work);
-    } else if (stats)
-        k_hemisphere<true><<<(unsigned)blocks, threads, smem, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N,
-                                                                n, order, h->tdirs, p->n_dirs, p->origin_offset, bits,
-                                                                count, counters, work);
-    else
-        k_hemisphere<false><<<(unsigned)blocks, threads, smem, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N,
-                                                                 n, order, h->tdirs, p->n_dirs, p->origin_offset, bits,
-                                                                 count, counters, work);
+    } else {
+#define RC_HEMI(ST, WD)                                                                                            \
+    k_hemisphere<ST, WD><<<(unsigned)blocks, threads, smem, s>>>(tree, h->tris, max_steps(h), h->scene_maxabs, P, N, \
+                                                                 n, order, h->tdirs, p->n_dirs, p->origin_offset,  \
+                                                                 bits, count, counters, work)
+        if (stats && wide) RC_HEMI(true, true);
+        else if (stats) RC_HEMI(true, false);
+        else if (wide) RC_HEMI(false, true);
+        else RC_HEMI(false, false);
+#undef RC_HEMI
+    }
     RC_LAUNCHED();
     if (work_alloc) RC_CUDA(cudaFreeAsync(work_alloc, s));
     if (order) RC_CUDA(cudaFreeAsync(order, s));
@@ -847,9 +947,14 @@ rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n,
     const int64_t cap = (int64_t)sm_count() * RC_BATCH_MIN_BLOCKS;
     if (blocks > cap && p->launch_mode == 0) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_orthogonal<<<(unsigned)blocks, 128, 0, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N, n, order,
-                                                 fd->axes, fd->frame, fd->fbox, p->origin_offset, mask, travel,
-                                                 counters);
+    if (use_wide(p))
+        k_orthogonal<true><<<(unsigned)blocks, 128, 0, s>>>(h->wnodes, h->tris, max_steps(h), h->scene_maxabs, P, N,
+                                                           n, order, fd->axes, fd->frame, fd->fbox, p->origin_offset,
+                                                           mask, travel, counters);
+    else
+        k_orthogonal<false><<<(unsigned)blocks, 128, 0, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N,
+                                                            n, order, fd->axes, fd->frame, fd->fbox, p->origin_offset,
+                                                            mask, travel, counters);
     RC_LAUNCHED();
     RC_CUDA(cudaFreeAsync(fd, s));
     if (order) RC_CUDA(cudaFreeAsync(order, s));
@@ -866,8 +971,12 @@ rc_status launch_batch(const BatchPart* d_parts, int n_parts, long long n_items,
     const int64_t need = (n_items * 32 + threads - 1) / threads;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    k_batch<false><<<(unsigned)blocks, threads, smem, s>>>(d_parts, n_parts, n_items, ppi, tdirs, p->n_dirs,
-                                                          p->origin_offset, work);
+    if (use_wide(p))
+        k_batch<false, true><<<(unsigned)blocks, threads, smem, s>>>(d_parts, n_parts, n_items, ppi, tdirs,
+                                                                    p->n_dirs, p->origin_offset, work);
+    else
+        k_batch<false, false><<<(unsigned)blocks, threads, smem, s>>>(d_parts, n_parts, n_items, ppi, tdirs,
+                                                                     p->n_dirs, p->origin_offset, work);
     RC_LAUNCHED();
     return RC_OK;
 }
@@ -875,8 +984,10 @@ rc_status launch_batch(const BatchPart* d_parts, int n_parts, long long n_items,
 rc_status prepare_batch_kernel(int n_dirs)
 {
     const size_t smem = (size_t)4 * (n_dirs / 32) * sizeof(uint32_t);
-    if (smem > 48 * 1024)
-        RC_CUDA(cudaFuncSetAttribute(k_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) {
+        RC_CUDA(cudaFuncSetAttribute(k_batch<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RC_CUDA(cudaFuncSetAttribute(k_batch<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
     return RC_OK;
 }
 

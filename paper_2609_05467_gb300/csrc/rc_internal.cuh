@@ -36,7 +36,8 @@ void count_launch(int k = 1);
 // constants
 // ---------------------------------------------------------------------------
 constexpr int kLeafMax = 4;        // triangles per packed leaf
-constexpr int kStack = 64;         // traversal stack entries (>= max tree depth)
+constexpr int kStack = 64;         // binary traversal stack entries (>= max tree depth)
+constexpr int kStack4 = 96;        // 4-wide traversal stack entries (>= 3 * wide depth + 1)
 constexpr double kTau = 1e-9;      // relative ambiguity band of the occlusion test
 constexpr int kMaxDirs = 65536;
 
@@ -52,6 +53,8 @@ struct DevScalars {
     int err_vertex;                // first bad vertex (non-finite), else -1
     int max_depth;
     int pad;
+    int wide_depth;
+    int pad2;
 };
 
 // machining frame on the device (Section 3.2)
@@ -89,6 +92,8 @@ struct rc_bvh_s {
     int32_t* F = nullptr;          // [T][3] copy of the faces
     float4* tris = nullptr;        // [T][3] triangle records in Morton order
     float4* nodes = nullptr;       // [n_int][4] packed BVH2 nodes
+    float4* wnodes = nullptr;      // [<= n_int][8] packed 4-wide nodes
+    int wide_depth = 0;
     int64_t n_int = 0;             // internal nodes (>= 1)
     int32_t* parent = nullptr;     // [n_int + T]: parent of internal i at i, of leaf k at n_int+k
     int32_t* child = nullptr;      // [n_int][2] combined indices (leaf k -> n_int+k)

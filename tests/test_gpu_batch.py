@@ -81,6 +81,12 @@ def test_batch_equals_single_part(rc, N):
                     q["b"].fill_(-1)
                 rc.rc_batch_launch(b)
                 _check(parts, N)
+    for width in (2, 4):
+        rc.rc_batch_set_params(b, rc.rc_params_default(n_dirs=N, tree_width=width))
+        for q in parts:
+            q["b"].fill_(-1)
+        rc.rc_batch_launch(b)
+        _check(parts, N)
     best = rc.rc_batch_autotune(b, repeats=1)
     assert best.blocks_per_sm in (4, 6, 8) and best.points_per_item in (1, 2, 4)
     for q in parts:
@@ -106,9 +112,10 @@ def test_single_part_knobs_do_not_change_results(rc):
     res = []
     for order in (0, 1):
         for tile in (0, 1):
-            for per_sm, fetch, launch in ((0, 0, 0), (4, 0, 0), (0, 1, 0), (3, 1, 0), (0, 0, 1)):
+            for per_sm, fetch, launch, width in ((0, 0, 0, 0), (4, 0, 0, 0), (0, 1, 0, 2), (3, 1, 0, 2),
+                                                 (0, 0, 1, 0), (0, 0, 0, 2), (0, 0, 1, 2)):
                 q = rc.rc_params_default(n_dirs=N, point_order=order, tile_mode=tile, blocks_per_sm=per_sm,
-                                         fetch_mode=fetch, launch_mode=launch)
+                                         fetch_mode=fetch, launch_mode=launch, tree_width=width)
                 bits = torch.zeros((n, N // 32), dtype=torch.int32, device="cuda")
                 cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
                 rc.rc_hemisphere_cast(bvh.h, P, Nn, q, bits, cnt)
