@@ -35,7 +35,10 @@ void count_launch(int k = 1);
 // ---------------------------------------------------------------------------
 // constants
 // ---------------------------------------------------------------------------
-constexpr int kLeafMax = 4;        // triangles per packed leaf
+#ifndef RC_LEAF_MAX
+#define RC_LEAF_MAX 2
+#endif
+constexpr int kLeafMax = RC_LEAF_MAX;   // triangles per packed leaf (1..8)
 constexpr int kStack = 64;         // binary traversal stack entries (>= max tree depth)
 constexpr int kStack4 = 96;        // 4-wide traversal stack entries (>= 3 * wide depth + 1)
 constexpr double kTau = 1e-9;      // relative ambiguity band of the occlusion test
