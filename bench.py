@@ -203,9 +203,21 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def committed_traffic(kernel_src, workload):
+TRAVERSAL_SOURCES = ("cast.cu", "build.cu", "rc_internal.cuh")
+
+
+def traversal_hash():
+    """sha256 over the sources that define the traversal kernel and the tree
+    layout it walks."""
+    h = hashlib.sha256()
+    for f in TRAVERSAL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2609_05467_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def committed_traffic(workload):
     """DRAM bytes per launch of the traversal kernel from the committed ncu
-    summary, if it was taken on the current kernel source (sha256 match)."""
+    summary, if it was taken on the current sources (sha256 match)."""
     path = os.path.join(ROOT, "profiles", "k_hemisphere_%s_ncu.md" % workload)
     try:
         txt = open(path).read()
@@ -215,8 +227,7 @@ def committed_traffic(kernel_src, workload):
     b = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", txt)
     if not m or not b:
         return None, None
-    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    if m.group(1) != cur:
+    if m.group(1) != traversal_hash():
         return None, "stale"
     return float(b.group(1)), "ncu"
 
@@ -368,8 +379,7 @@ def run_gpu(args, wl, V, F):
     rays_cast_step = float(np.mean(c[args.warmup:, 0, 0]))
     alg_bytes = bytes_per_ray * rays_cast_step
     achieved = alg_bytes / cast_s / 1e9
-    traffic, tsrc = committed_traffic(os.path.join(ROOT, "paper_2609_05467_gb300", "csrc", "cast.cu"),
-                                      args.workload)
+    traffic, tsrc = committed_traffic(args.workload)
 
     if rank != 0:
         return
