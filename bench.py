@@ -232,6 +232,19 @@ def committed_traffic(workload):
     return float(b.group(1)), "ncu"
 
 
+def job_totals(seconds, units, device):
+    """Whole-job figures of replicas: the slowest rank's time and the sum of
+    the units all ranks processed (the path has no exchange step, so this is
+    the only collective)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_gpu(args, wl, V, F):
     import torch
     import paper_2609_05467_gb300 as rc
@@ -339,12 +352,7 @@ def run_gpu(args, wl, V, F):
     t_dev = sum(step_ms) / 1e3
     rays_total = float(rays_per_step.sum())
     if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_dev, rays_total], dtype=torch.float64, device=dev)
-        tmax = tt[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        t_dev, rays_total = float(tmax.item()), float(tt[1].item())
+        t_dev, rays_total = job_totals(t_dev, rays_total, dev)
     value = rays_total / t_dev
 
     # end to end through rc_analyze_part with pinned host buffers
@@ -364,12 +372,7 @@ def run_gpu(args, wl, V, F):
         e2e_t += time.perf_counter() - t0
         e2e_rays += r.cast_counters[0] + r.ortho_counters[0]
     if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_t, e2e_rays], dtype=torch.float64, device=dev)
-        tmax = tt[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        e2e_t, e2e_rays = float(tmax.item()), float(tt[1].item())
+        e2e_t, e2e_rays = job_totals(e2e_t, e2e_rays, dev)
     h2d = V.nbytes + F.nbytes
     d2h = hb.numel() * 4 + hc.numel() * 4 + hm.numel() + hk.numel() + 2 * 1024
 

@@ -84,8 +84,10 @@ typedef struct {
     int32_t points_per_item; /* batched cast: points per work item (0 = 1) */
     int32_t launch_mode;     /* casts: 0 = persistent grid (default), 1 = one warp per point, grid sized to the work
                                 (short blocks, so concurrent casts on other streams interleave) */
-    int32_t fetch_mode;      /* hemispherical cast (persistent grid, binary tree): 0 = lanes wait for their tile
-                                of 32 rays, 1 = a lane takes the next ray as soon as its ray finishes */
+    int32_t fetch_mode;      /* hemispherical cast, persistent grid: 0 = lanes wait for their tile of 32 rays;
+                                1 (binary tree) = a lane takes the next ray of the warp's points as soon as its
+                                ray finishes; 2 (4-wide tree) = each lane walks its own list of the point's rays;
+                                3 = a warp casts one direction at a time from 32 Morton-adjacent points */
     int32_t tree_width;      /* casts: 0 or 4 = 4-wide tree (default), 2 = binary tree */
     int32_t reserved[2];
 } rc_params;

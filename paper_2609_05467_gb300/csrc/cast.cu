@@ -219,6 +219,12 @@ __device__ __forceinline__ void box2(const Ray& r, const float4 n0, const float4
     t1 = tn;
 }
 
+// Per-warp-lane counters of a cast.
+struct CastAccFwd {
+    int amb = 0, retests = 0, overflow = 0;
+    long long rays = 0, nvis = 0, ntri = 0;
+};
+
 // Result bits of trace(): bit 0 blocked, bit 1 decided by ambiguous pairs.
 // With kStats the walk also counts interior-node fetches and triangle tests
 // (the instrumented build used to measure algorithmic bytes per ray).
@@ -284,7 +290,7 @@ __device__ __forceinline__ TraceOut trace(const float4* __restrict__ nodes, cons
 // as trace(); per node the four child boxes are tested together, the
 // nearest hit child is visited next and the others are pushed far-to-near.
 template <bool kStats>
-__device__ __forceinline__ TraceOut trace4(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
+__device__ __forceinline__ TraceOut trace4_ifif(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
                                            const Ray& r, int max_steps)
 {
     TraceOut out = {0, 0, 0, 0, 0};
@@ -363,11 +369,177 @@ __device__ __forceinline__ TraceOut trace4(const float4* __restrict__ wnodes, co
     return out;
 }
 
+#ifndef RC_WHILE_WHILE
+#define RC_WHILE_WHILE 0
+#endif
+
+template <bool kStats>
+__device__ __forceinline__ TraceOut trace4(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
+                                           const Ray& r, int max_steps)
+{
+    TraceOut out = {0, 0, 0, 0, 0};
+    int stack[kStack4];
+    int sp = 0;
+    int cur = 0;
+    bool amb = false, ambhit = false;
+    const float rob = 1.0f + 2.0f * 1.7881394e-7f;
+    const bool sx = signbit(r.ix), sy = signbit(r.iy), sz = signbit(r.iz);
+    int steps = 0;
+    for (;;) {
+        // descend through interior nodes until a leaf is current (or the
+        // walk ends); lanes then test their leaves together
+        while (cur >= 0) {
+            if (++steps > max_steps) { out.overflow = 1; out.flags = 1; return out; }
+            if (kStats) ++out.nodes;
+            const float4* nd = wnodes + 8 * cur;
+            const float4 lox = __ldg(nd + 0), hix = __ldg(nd + 1), loy = __ldg(nd + 2), hiy = __ldg(nd + 3);
+            const float4 loz = __ldg(nd + 4), hiz = __ldg(nd + 5), ci = __ldg(nd + 6);
+            float d[4];
+            int c[4];
+            const float lx[4] = {lox.x, lox.y, lox.z, lox.w}, hx[4] = {hix.x, hix.y, hix.z, hix.w};
+            const float ly[4] = {loy.x, loy.y, loy.z, loy.w}, hy[4] = {hiy.x, hiy.y, hiy.z, hiy.w};
+            const float lz[4] = {loz.x, loz.y, loz.z, loz.w}, hz[4] = {hiz.x, hiz.y, hiz.z, hiz.w};
+            const int cc[4] = {__float_as_int(ci.x), __float_as_int(ci.y), __float_as_int(ci.z), __float_as_int(ci.w)};
+            int nh = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float nx = ((sx ? hx[k] : lx[k]) - r.ox) * r.ix, fx = ((sx ? lx[k] : hx[k]) - r.ox) * r.ix;
+                const float ny = ((sy ? hy[k] : ly[k]) - r.oy) * r.iy, fy = ((sy ? ly[k] : hy[k]) - r.oy) * r.iy;
+                const float nz = ((sz ? hz[k] : lz[k]) - r.oz) * r.iz, fz = ((sz ? lz[k] : hz[k]) - r.oz) * r.iz;
+                const float tn = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.0f));
+                const float tf = fminf(fminf(fx, fy), fz) * rob;
+                const bool hit = tn <= tf;
+                d[k] = hit ? tn : INFINITY;
+                c[k] = cc[k];
+                nh += hit;
+            }
+            if (nh == 0) {
+                if (sp == 0) {
+                    out.flags = (ambhit ? 1 : 0) | (amb ? 2 : 0);
+                    return out;
+                }
+                cur = stack[--sp];
+                continue;
+            }
+#define RC_CSWAP(a, b)                                              \
+    if (d[b] < d[a]) {                                              \
+        const float td = d[a]; d[a] = d[b]; d[b] = td;              \
+        const int tc = c[a]; c[a] = c[b]; c[b] = tc;                \
+    }
+            RC_CSWAP(0, 1) RC_CSWAP(2, 3) RC_CSWAP(0, 2) RC_CSWAP(1, 3) RC_CSWAP(1, 2)
+#undef RC_CSWAP
+            if (sp + nh - 1 > kStack4) { out.overflow = 1; out.flags = 1; return out; }
+            if (nh > 3) stack[sp++] = c[3];
+            if (nh > 2) stack[sp++] = c[2];
+            if (nh > 1) stack[sp++] = c[1];
+            cur = c[0];
+        }
+        // leaf
+        if (++steps > max_steps) { out.overflow = 1; out.flags = 1; return out; }
+        const int v = -1 - cur;
+        const int first = v >> 3, cnt = (v & 7) + 1;
+        for (int k = 0; k < cnt; ++k) {
+            const float4* t = tris + 3 * (first + k);
+            const float4 v0 = __ldg(t), v1 = __ldg(t + 1), v2 = __ldg(t + 2);
+            if (kStats) ++out.tris;
+            const int s = tri_test32(r, v0, v1, v2);
+            if (s == kHit) { out.flags = 1; return out; }
+            if (s == kUnsure) {
+                ++out.retests;
+                const Pair64 p = retest64(r, v0, v1, v2);
+                if (p.state == kHit) { out.flags = 1; return out; }
+                if (p.state == kUnsure) { amb = true; ambhit |= p.hit64; }
+            }
+        }
+        if (sp == 0) break;
+        cur = stack[--sp];
+    }
+    out.flags = (ambhit ? 1 : 0) | (amb ? 2 : 0);
+    return out;
+}
+
+// One step of the 4-wide walk (a node or a leaf) on explicit state, for the
+// flat per-lane ray loop.  Returns 0 while the walk goes on, 1 when the ray
+// is decided.  On return 1, *blocked tells whether it is obstructed.
+struct Walk4 {
+    int cur, sp, steps;
+    bool amb, ambhit;
+};
+
+__device__ __forceinline__ int step4(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
+                                     const Ray& r, int max_steps, Walk4& w, int* stack, bool& blocked,
+                                     CastAccFwd& acc)
+{
+    const float rob = 1.0f + 2.0f * 1.7881394e-7f;
+    if (++w.steps > max_steps) { ++acc.overflow; blocked = true; return 1; }
+    if (w.cur >= 0) {
+        const bool sx = signbit(r.ix), sy = signbit(r.iy), sz = signbit(r.iz);
+        const float4* nd = wnodes + 8 * w.cur;
+        const float4 lox = __ldg(nd + 0), hix = __ldg(nd + 1), loy = __ldg(nd + 2), hiy = __ldg(nd + 3);
+        const float4 loz = __ldg(nd + 4), hiz = __ldg(nd + 5), ci = __ldg(nd + 6);
+        float d[4];
+        int c[4];
+        const float lx[4] = {lox.x, lox.y, lox.z, lox.w}, hx[4] = {hix.x, hix.y, hix.z, hix.w};
+        const float ly[4] = {loy.x, loy.y, loy.z, loy.w}, hy[4] = {hiy.x, hiy.y, hiy.z, hiy.w};
+        const float lz[4] = {loz.x, loz.y, loz.z, loz.w}, hz[4] = {hiz.x, hiz.y, hiz.z, hiz.w};
+        const int cc[4] = {__float_as_int(ci.x), __float_as_int(ci.y), __float_as_int(ci.z), __float_as_int(ci.w)};
+        int nh = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float nx = ((sx ? hx[k] : lx[k]) - r.ox) * r.ix, fx = ((sx ? lx[k] : hx[k]) - r.ox) * r.ix;
+            const float ny = ((sy ? hy[k] : ly[k]) - r.oy) * r.iy, fy = ((sy ? ly[k] : hy[k]) - r.oy) * r.iy;
+            const float nz = ((sz ? hz[k] : lz[k]) - r.oz) * r.iz, fz = ((sz ? lz[k] : hz[k]) - r.oz) * r.iz;
+            const float tn = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.0f));
+            const float tf = fminf(fminf(fx, fy), fz) * rob;
+            const bool hit = tn <= tf;
+            d[k] = hit ? tn : INFINITY;
+            c[k] = cc[k];
+            nh += hit;
+        }
+        if (nh == 0) {
+            if (w.sp == 0) { blocked = w.ambhit; return 1; }
+            w.cur = stack[--w.sp];
+            return 0;
+        }
+#define RC_CSWAP(a, b)                                              \
+    if (d[b] < d[a]) {                                              \
+        const float td = d[a]; d[a] = d[b]; d[b] = td;              \
+        const int tc = c[a]; c[a] = c[b]; c[b] = tc;                \
+    }
+        RC_CSWAP(0, 1) RC_CSWAP(2, 3) RC_CSWAP(0, 2) RC_CSWAP(1, 3) RC_CSWAP(1, 2)
+#undef RC_CSWAP
+        if (w.sp + nh - 1 > kStack4) { ++acc.overflow; blocked = true; return 1; }
+        if (nh > 3) stack[w.sp++] = c[3];
+        if (nh > 2) stack[w.sp++] = c[2];
+        if (nh > 1) stack[w.sp++] = c[1];
+        w.cur = c[0];
+        return 0;
+    }
+    const int v = -1 - w.cur;
+    const int first = v >> 3, cnt = (v & 7) + 1;
+    for (int k = 0; k < cnt; ++k) {
+        const float4* t = tris + 3 * (first + k);
+        const float4 v0 = __ldg(t), v1 = __ldg(t + 1), v2 = __ldg(t + 2);
+        const int s = tri_test32(r, v0, v1, v2);
+        if (s == kHit) { blocked = true; return 1; }
+        if (s == kUnsure) {
+            ++acc.retests;
+            const Pair64 p = retest64(r, v0, v1, v2);
+            if (p.state == kHit) { blocked = true; return 1; }
+            if (p.state == kUnsure) { w.amb = true; w.ambhit |= p.hit64; }
+        }
+    }
+    if (w.sp == 0) { blocked = w.ambhit; return 1; }
+    w.cur = stack[--w.sp];
+    return 0;
+}
+
 template <bool kStats, bool kWide>
 __device__ __forceinline__ TraceOut trace_any(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                               const Ray& r, int max_steps)
 {
-    if (kWide) return trace4<kStats>(nodes, tris, r, max_steps);
+    if (kWide) return RC_WHILE_WHILE ? trace4<kStats>(nodes, tris, r, max_steps)
+                                     : trace4_ifif<kStats>(nodes, tris, r, max_steps);
     return trace<kStats>(nodes, tris, r, max_steps);
 }
 
@@ -407,10 +579,7 @@ __device__ __forceinline__ void warp_add_counters(unsigned long long* counters, 
 #define RC_HEMI_MIN_BLOCKS 6
 #endif
 
-struct CastAcc {
-    int amb = 0, retests = 0, overflow = 0;
-    long long rays = 0, nvis = 0, ntri = 0;
-};
+using CastAcc = CastAccFwd;
 
 // The hemispherical cast of one point by one warp (see above).  `tdirs` is
 // the tile-ordered table, `row` the warp's shared-memory row of W words.
@@ -450,6 +619,149 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
     __syncwarp();
     if (lane == 0) count[i] = cnt;
     acc.rays += W;   // per lane
+}
+
+// The hemispherical cast of one point with each lane walking its own list
+// of rays (tile-order indices lane, lane+32, ...) in one flat loop: every
+// iteration a lane either starts its next ray or takes one step of its walk,
+// so a lane never waits for the other lanes' rays, only for the end of the
+// point.  Same rays and decisions as cast_point (4-wide tree only).
+__device__ __forceinline__ void cast_point_flat(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                                int max_steps, float scene_maxabs, const float* __restrict__ P,
+                                                const float* __restrict__ Nrm, int64_t i,
+                                                const float4* __restrict__ tdirs, int W, double eps, uint32_t* row,
+                                                uint32_t* __restrict__ bits, int32_t* __restrict__ count,
+                                                CastAcc& acc)
+{
+    const int lane = threadIdx.x & 31;
+    for (int w = lane; w < W; w += 32) row[w] = 0u;
+    __syncwarp();
+    const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
+    const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
+    const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
+    const Onb b = make_onb(nx, ny, nz);
+    int cnt = 0, m = 0, j = 0;
+    bool active = false;
+    Ray r;
+    Walk4 wk;
+    int stack[kStack4];
+    for (;;) {
+        if (!active) {
+            if (m >= W) break;
+            const float4 h = __ldg(&tdirs[32 * m + lane]);
+            ++m;
+            j = __float_as_int(h.w);
+            float dx, dy, dz;
+            local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
+            setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
+            wk.cur = 0;
+            wk.sp = 0;
+            wk.steps = 0;
+            wk.amb = wk.ambhit = false;
+            active = true;
+        }
+        bool blocked = false;
+        if (step4(nodes, tris, r, max_steps, wk, stack, blocked, acc)) {
+            if (!blocked && wk.amb) ++acc.amb;
+            if (!blocked) {
+                atomicOr(&row[j >> 5], 1u << (j & 31));
+                ++cnt;
+            }
+            active = false;
+        }
+    }
+    for (int off = 16; off; off >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, off);
+    __syncwarp();
+    for (int w = lane; w < W; w += 32) bits[i * W + w] = row[w];
+    __syncwarp();
+    if (lane == 0) count[i] = cnt;
+    acc.rays += W;   // per lane
+}
+
+#ifndef RC_FLAT_MIN_BLOCKS
+#define RC_FLAT_MIN_BLOCKS 6
+#endif
+
+__global__ void __launch_bounds__(128, RC_FLAT_MIN_BLOCKS)
+k_hemisphere_flat(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps,
+                  float scene_maxabs, const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
+                  const int32_t* __restrict__ order, const float4* __restrict__ tdirs, int n_dirs, double eps,
+                  uint32_t* __restrict__ bits, int32_t* __restrict__ count, unsigned long long* counters,
+                  unsigned long long* work)
+{
+    extern __shared__ uint32_t s_rows[];
+    const int lane = threadIdx.x & 31;
+    const int W = n_dirs >> 5;
+    uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
+    CastAcc acc;
+    for (;;) {
+        unsigned long long k = 0;
+        if (lane == 0) k = atomicAdd(work, 1ULL);
+        k = __shfl_sync(0xFFFFFFFFu, k, 0);
+        if (k >= (unsigned long long)n) break;
+        const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
+        cast_point_flat(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits, count, acc);
+    }
+    warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow);
+}
+
+// Hemispherical cast by point packets: a warp holds 32 points that are
+// adjacent in Morton order, and all lanes cast the same local direction j at
+// a time -- near-parallel rays from nearby origins, which walk nearly the
+// same nodes.  Each lane assembles its own point's bit words in a register
+// (canonical j order) and writes them whole.  Same rays and decisions as
+// k_hemisphere.
+template <bool kWide>
+__global__ void __launch_bounds__(128, RC_HEMI_MIN_BLOCKS)
+k_hemisphere_pkt(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps,
+                 float scene_maxabs, const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
+                 const int32_t* __restrict__ order, const float4* __restrict__ dirs, int n_dirs, double eps,
+                 uint32_t* __restrict__ bits, int32_t* __restrict__ count, unsigned long long* counters,
+                 unsigned long long* work)
+{
+    const int lane = threadIdx.x & 31;
+    const int W = n_dirs >> 5;
+    const unsigned long long chunks = (unsigned long long)((n + 31) / 32);
+    CastAcc acc;
+    // work item = (chunk of 32 points, word of 32 directions)
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(work, 1ULL);
+        it = __shfl_sync(0xFFFFFFFFu, it, 0);
+        if (it >= chunks * (unsigned long long)W) break;
+        const unsigned long long c = it / (unsigned long long)W;
+        const int w = (int)(it % (unsigned long long)W);
+        const int64_t k = (int64_t)c * 32 + lane;
+        const bool valid = k < n;
+        const int64_t i = valid ? (order ? (int64_t)__ldg(&order[k]) : k) : 0;
+        float px = 0.0f, py = 0.0f, pz = 0.0f, nx = 0.0f, ny = 0.0f, nz = 1.0f;
+        if (valid) {
+            px = P[3 * i]; py = P[3 * i + 1]; pz = P[3 * i + 2];
+            nx = Nrm[3 * i]; ny = Nrm[3 * i + 1]; nz = Nrm[3 * i + 2];
+        }
+        const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
+        const Onb b = make_onb(nx, ny, nz);
+        uint32_t word = 0;
+        for (int bit = 0; bit < 32; ++bit) {
+            if (!valid) break;
+            const float4 h = __ldg(&dirs[32 * w + bit]);
+            float dx, dy, dz;
+            local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
+            Ray r;
+            setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
+            const TraceOut tr = trace_any<false, kWide>(nodes, tris, r, max_steps);
+            acc.retests += tr.retests;
+            acc.overflow += tr.overflow;
+            acc.amb += (tr.flags >> 1) & 1;
+            if ((tr.flags & 1) == 0) word |= 1u << bit;
+        }
+        if (valid) {
+            bits[i * W + w] = word;
+            atomicAdd(&count[i], __popc(word));
+            acc.rays += 32;
+        }
+    }
+    warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow);
 }
 
 template <bool kStats, bool kWide>
@@ -872,7 +1184,33 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
         RC_CUDA(cudaFuncSetAttribute(k_hemisphere<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     const float4* tree = wide ? h->wnodes : h->nodes;
-    if (p->fetch_mode == 1 && !stats && work && !wide) {
+    if (p->fetch_mode == 3 && !stats && work) {
+        RC_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * n, s));
+        const int64_t chunks = (n + 31) / 32;
+        int64_t pblocks = (int64_t)sm_count() * (p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_HEMI_MIN_BLOCKS);
+        const int64_t pneed = (chunks * (p->n_dirs / 32) * 32 + threads - 1) / threads;
+        if (pblocks > pneed) pblocks = pneed;
+        if (pblocks < 1) pblocks = 1;
+        if (wide)
+            k_hemisphere_pkt<true><<<(unsigned)pblocks, threads, 0, s>>>(tree, h->tris, max_steps(h),
+                                                                        h->scene_maxabs, P, N, n, order, h->dirs,
+                                                                        p->n_dirs, p->origin_offset, bits, count,
+                                                                        counters, work);
+        else
+            k_hemisphere_pkt<false><<<(unsigned)pblocks, threads, 0, s>>>(tree, h->tris, max_steps(h),
+                                                                         h->scene_maxabs, P, N, n, order, h->dirs,
+                                                                         p->n_dirs, p->origin_offset, bits, count,
+                                                                         counters, work);
+    } else if (p->fetch_mode == 2 && !stats && work && wide) {
+        if (smem > 48 * 1024)
+            RC_CUDA(cudaFuncSetAttribute(k_hemisphere_flat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int64_t fblocks = (int64_t)sm_count() * (p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_FLAT_MIN_BLOCKS);
+        if (fblocks > need) fblocks = need;
+        if (fblocks < 1) fblocks = 1;
+        k_hemisphere_flat<<<(unsigned)fblocks, threads, smem, s>>>(h->wnodes, h->tris, max_steps(h), h->scene_maxabs,
+                                                                   P, N, n, order, h->tdirs, p->n_dirs,
+                                                                   p->origin_offset, bits, count, counters, work);
+    } else if (p->fetch_mode == 1 && !stats && work && !wide) {
         const size_t dsmem = 2 * smem;
         if (dsmem > 48 * 1024)
             RC_CUDA(cudaFuncSetAttribute(k_hemisphere_dyn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));

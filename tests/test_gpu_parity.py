@@ -115,14 +115,19 @@ def test_hemisphere_parity(rc, name, n, N):
     bvh.close()
 
 
-@pytest.mark.parametrize("mode", ["binary", "dynamic_fetch"])
+@pytest.mark.parametrize("mode", ["binary", "dynamic_fetch", "lane_lists", "packets", "packets_binary"])
 @pytest.mark.parametrize("name,n,N", [("pocket", 1000, 256), ("prismatic_coarse", 777, 160),
                                        ("impeller_coarse", 500, 128), ("cavity", 300, 64)])
 def test_hemisphere_parity_other_traversals(rc, name, n, N, mode):
     """The binary-tree and dynamic-fetch traversals give the oracle's bits too."""
     V, F = PARTS[name]()
     bvh = _build(rc, V, F)
-    p = rc.rc_params_default(n_dirs=N, tree_width=2, fetch_mode=1 if mode == "dynamic_fetch" else 0)
+    if mode == "lane_lists":
+        p = rc.rc_params_default(n_dirs=N, tree_width=4, fetch_mode=2)
+    elif mode.startswith("packets"):
+        p = rc.rc_params_default(n_dirs=N, tree_width=2 if mode.endswith("binary") else 4, fetch_mode=3)
+    else:
+        p = rc.rc_params_default(n_dirs=N, tree_width=2, fetch_mode=1 if mode == "dynamic_fetch" else 0)
     P, Nn, f, w = _sample(rc, bvh, n, p)
     gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
     ob, oa, oc = oracle.Mesh(V, F).hemisphere(P, Nn, N)
