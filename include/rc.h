@@ -89,7 +89,9 @@ typedef struct {
                                 ray finishes; 2 (4-wide tree) = each lane walks its own list of the point's rays;
                                 3 = a warp casts one direction at a time from 32 Morton-adjacent points */
     int32_t tree_width;      /* casts: 0 or 4 = 4-wide tree (default), 2 = binary tree */
-    int32_t reserved[2];
+    double parallel_tol;     /* orthogonal cast: axis a is eligible when n.a >= -parallel_tol (FP64); a face
+                                parallel to the axis is side-milled, and the tolerance absorbs the tilt that
+                                fp32 vertex rounding gives such faces' normals; 0 .. 0.5, default 1e-4 */
 } rc_params;
 
 /* Part-level indicators (Sections 3.1 and 3.3). */
@@ -137,7 +139,7 @@ typedef struct {
 
 /* Fills *p with the defaults: n_dirs 256, area-random sampling, seed 0,
  * origin_offset 1e-4 mm, identity frame, tool_length 100 mm, conc_mode 0,
- * thresholds 0.60 / 0.45 / 0.41.  Returns RC_E_ARG if p is NULL. */
+ * thresholds 0.60 / 0.45 / 0.41, parallel_tol 1e-4.  Returns RC_E_ARG if p is NULL. */
 rc_status rc_params_default(rc_params* p);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
@@ -286,7 +288,8 @@ rc_status rc_classify(const rc_summary* s, const rc_params* p, int32_t* label);
 /* Orthogonal (directional) cast (Section 3.2: rays along the six principal
  * directions of the canonical frame from the offset point, with the same
  * intersection kernel).  Axis a in (+X', -X', +Y', -Y', +Z', -Z') is
- * eligible iff n.a >= 0 (FP64) and accessible iff also unobstructed.
+ * eligible iff n.a >= -parallel_tol (FP64) and accessible iff also
+ * unobstructed.
  * Travel (Section 3.3, tool travel distance) = distance from p to the
  * part's bounding box (in frame coordinates) along a.
  *   d_mask [n] uint8 (bit a = accessible), d_travel [n][6] float32,
@@ -462,6 +465,70 @@ rc_status rc_server_destroy(rc_server s);
  * chosen_* of *out; other fields are left unchanged.  Host only, no GPU.
  * Errors: RC_E_ARG (NULL, negative count). */
 rc_status rc_setup_cover(const int64_t* h_mask_hist, rc_setups* out);
+
+/* ---------------------------------------------------------------------- */
+/* Automatic machining frame (Section 3.2 assumes the part sits in a      */
+/* canonical frame whose axes are the machine axes; how that frame is     */
+/* found is not stated -- the definitions below are this library's)       */
+/* ---------------------------------------------------------------------- */
+
+#define RC_MAX_FRAMES 6
+#define RC_BOX_STEPS 128
+
+/* Candidate sources.  A box-minimising rotation of base b has source
+ * RC_FRAME_BOX + b. */
+enum { RC_FRAME_GIVEN = 0, RC_FRAME_PRINCIPAL = 1, RC_FRAME_NORMALS = 2, RC_FRAME_BOX = 3 };
+
+/* Candidate frames and, after rc_frame_select, their setups. */
+typedef struct {
+    int32_t k;                          /* candidates in frame[0 .. k) */
+    int32_t best;                       /* rc_frame_select: the chosen candidate; -1 before */
+    int32_t source[RC_MAX_FRAMES];      /* RC_FRAME_* */
+    int32_t box_axis[RC_MAX_FRAMES];    /* box rotations: the base column held (0..2), else -1 */
+    int32_t box_step[RC_MAX_FRAMES];    /* box rotations: j with tan(theta/2) = j / RC_BOX_STEPS, else -1 */
+    float frame[RC_MAX_FRAMES][9];      /* row-major 3x3, columns X', Y', Z' (the rc_params.frame layout) */
+    double volume[RC_MAX_FRAMES];       /* volume of the vertices' bounding box in the frame (mm^3, FP64) */
+    double principal[3];                /* eigenvalues of the surface second moment (mm^4), descending */
+    rc_setups setups[RC_MAX_FRAMES];    /* rc_frame_select: per candidate, as rc_min_setups */
+} rc_frames;
+
+/* Candidate machining frames of the part, in this order (a candidate whose
+ * axes are, up to sign and order, those of an earlier one has the same six
+ * machining directions and is dropped):
+ *   1. p->frame (RC_FRAME_GIVEN);
+ *   2. principal axes (RC_FRAME_PRINCIPAL): eigenvectors of the surface's
+ *      area second moment about its area centroid, sum over faces of the
+ *      exact triangle integral A/12 (a a^T + b b^T + c c^T + s s^T),
+ *      s = a + b + c; X' = largest eigenvalue, Y' = second, Z' = X' x Y';
+ *      absent when two eigenvalues lie within 1e-3 of the largest;
+ *   3. dominant normals (RC_FRAME_NORMALS): face normals binned as lines on
+ *      a 3 x 32 x 32 cube map, weighted by llround(A / A_max * 2^32); Z' =
+ *      normal of the largest face of the heaviest cell, X' = that of the
+ *      heaviest cell whose centre w has |w . Z'| <= 0.2 |w|, orthogonalised;
+ *   4. after each base frame, its box-minimising rotation (RC_FRAME_BOX +
+ *      base): one column held, the other two turned by theta with
+ *      tan(theta/2) = j/128, j = 0..127; smallest vertex bounding-box
+ *      volume, ties to the lower column, then the lower j.
+ * Axes of 2 and 3 are rounded to multiples of 2^-20 per component, signed
+ * so the largest component is positive, orthonormalised in FP64 and
+ * rounded to fp32; no candidate holds a negative zero.  Fills k, source, box_axis, box_step, frame, volume,
+ * principal; best = -1.  Synchronises `stream`.
+ * Errors: RC_E_ARG, RC_E_CUDA. */
+rc_status rc_frame_candidates(rc_bvh h, const rc_params* p, rc_frames* out, void* stream);
+
+/* Evaluate io->frame[0 .. io->k) on the part's sample points: orthogonal
+ * cast, reachability, fixture faces, classes and both setup covers per
+ * frame (the steps of rc_orthogonal_cast and rc_min_setups, all frames in
+ * one cast launch), then choose: fewest setups (exact cover), then fewest
+ * over-threshold plus inaccessible points, then the smallest bounding-box
+ * volume, then the lowest index.  Fills io->setups, io->volume, io->best.
+ *   d_P, d_N [n][3], d_face [n] (device, as from rc_sample_points);
+ *   d_counters int64[4] (rays, ambiguous, FP64 re-tests, overflow; may be
+ *   NULL).  The frames may come from rc_frame_candidates or the caller.
+ * Synchronises `stream`.  Errors: RC_E_ARG (k outside 1..RC_MAX_FRAMES,
+ * non-finite frame), RC_E_CUDA. */
+rc_status rc_frame_select(rc_bvh h, const float* d_P, const float* d_N, const int32_t* d_face, int64_t n,
+                          const rc_params* p, rc_frames* io, int64_t* d_counters, void* stream);
 
 #ifdef __cplusplus
 }

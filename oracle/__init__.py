@@ -30,6 +30,7 @@ _lock = threading.Lock()
 
 MISS, HIT, AMB = 0, 1, 2
 TAU = 1e-9
+PARALLEL_TOL = 1e-4     # orthogonal eligibility tolerance on n . a (reading R8 of oracle.c)
 
 
 def build(force=False):
@@ -70,7 +71,7 @@ def _L():
             lib.or_bvh_nodes.restype = i64
             lib.or_cast_rays.argtypes = [P, P, P, i64, P, P, i64, P, ctypes.c_int]
             lib.or_hemisphere.argtypes = [P, P, P, i64, P, P, i64, i32, f64, P, P, P, ctypes.c_int]
-            lib.or_orthogonal.argtypes = [P, P, P, i64, P, P, i64, P, f64, P, P, ctypes.c_int]
+            lib.or_orthogonal.argtypes = [P, P, P, i64, P, P, i64, P, f64, f64, P, P, ctypes.c_int]
             lib.or_variability.argtypes = [P, P, i64, i32, P, P, P]
             lib.or_num_cores.restype = ctypes.c_int
             _lib = lib
@@ -208,16 +209,17 @@ class Mesh:
                            float(eps), _p(bits), _p(amb), _p(cnt), threads)
         return bits, amb, cnt
 
-    def orthogonal(self, P, Nrm, frame=None, eps=1e-4, threads=0):
+    def orthogonal(self, P, Nrm, frame=None, eps=1e-4, threads=0, parallel_tol=PARALLEL_TOL):
         """Section 3.2: six-direction accessibility mask (bit a set = axis a
-        eligible and unobstructed) plus the ambiguity mask."""
+        eligible -- n . a >= -parallel_tol -- and unobstructed) plus the
+        ambiguity mask."""
         P, Nrm = _c(P, np.float32), _c(Nrm, np.float32)
         axes = frame_axes(frame)
         n = len(P)
         m = np.zeros(n, np.uint8)
         am = np.zeros(n, np.uint8)
         _L().or_orthogonal(self.handle, _p(self.V), _p(self.F), self.T, _p(P), _p(Nrm), n,
-                           _p(axes), float(eps), _p(m), _p(am), threads)
+                           _p(axes), float(eps), float(parallel_tol), _p(m), _p(am), threads)
         return m, am
 
 

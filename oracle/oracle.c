@@ -41,6 +41,10 @@
  *      otherwise AMBIGUOUS if some pair is ambiguous, otherwise MISS.
  *   R7 area sampling: splitmix64 counter stream; triangle chosen by an
  *      integer (2^32-quantised) area CDF; point by Osada et al. (2002).
+ *   R8 orthogonal eligibility: axis a is eligible for a point with normal n
+ *      when n.a >= -parallel_tol (FP64, x, y, z order); a face parallel to
+ *      the axis is side-milled, and the tolerance absorbs the tilt that fp32
+ *      vertex rounding gives the normals of such faces.
  */
 #include <math.h>
 #include <pthread.h>
@@ -506,6 +510,7 @@ typedef struct {
     int64_t T;
     /* work */
     int kind;            /* 0 rays, 1 hemisphere, 2 orthogonal */
+    double par_tol;      /* orthogonal eligibility tolerance (R8) */
     int64_t n;           /* work items */
     int64_t next;        /* shared cursor (atomic) */
     /* rays */
@@ -564,10 +569,10 @@ static void* or_worker(void* arg)
                 for (int a = 0; a < 6; ++a) {
                     const float* ax = J->axes + 3 * a;
                     const float* n = J->Nrm + 3 * i;
-                    /* eligibility: n . a >= 0 in FP64 (x, y, z order) */
+                    /* eligibility (R8): n . a >= -parallel_tol in FP64 (x, y, z order) */
                     double nd = (double)n[0] * ax[0] + (double)n[1] * ax[1];
                     nd = nd + (double)n[2] * ax[2];
-                    if (!(nd >= 0.0)) continue;
+                    if (!(nd >= -J->par_tol)) continue;
                     int r = or_trace(J, o, ax);
                     if (r == OR_MISS) m |= (uint8_t)(1u << a);
                     if (r == OR_AMB) am |= (uint8_t)(1u << a);
@@ -624,13 +629,13 @@ void or_hemisphere(void* bvh, const float* V, const int32_t* F, int64_t T, const
 /* Orthogonal cast (Section 3.2): axes are six fp32 directions
  * (+X', -X', +Y', -Y', +Z', -Z' of the machining frame). */
 void or_orthogonal(void* bvh, const float* V, const int32_t* F, int64_t T, const float* P,
-                   const float* Nrm, int64_t n, const float* axes, double eps, uint8_t* mask,
-                   uint8_t* amask, int nthreads)
+                   const float* Nrm, int64_t n, const float* axes, double eps, double par_tol,
+                   uint8_t* mask, uint8_t* amask, int nthreads)
 {
     or_job J;
     memset(&J, 0, sizeof J);
     J.bvh = (const or_bvh*)bvh; J.V = V; J.F = F; J.T = T;
-    J.kind = 2; J.n = n; J.P = P; J.Nrm = Nrm; J.eps = eps; J.axes = axes;
+    J.kind = 2; J.n = n; J.P = P; J.Nrm = Nrm; J.eps = eps; J.axes = axes; J.par_tol = par_tol;
     J.mask = mask; J.amask = amask;
     or_run(&J, nthreads);
 }

@@ -53,7 +53,7 @@ class Params(ctypes.Structure):
         ("t_conc", ctypes.c_double), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
         ("collect_stats", ctypes.c_int32), ("always_setups", ctypes.c_int32), ("point_order", ctypes.c_int32),
         ("tile_mode", ctypes.c_int32), ("points_per_item", ctypes.c_int32), ("launch_mode", ctypes.c_int32),
-        ("fetch_mode", ctypes.c_int32), ("tree_width", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+        ("fetch_mode", ctypes.c_int32), ("tree_width", ctypes.c_int32), ("parallel_tol", ctypes.c_double),
     ]
 
 
@@ -82,6 +82,25 @@ class Setups(ctypes.Structure):
         ("chosen_greedy", ctypes.c_uint8), ("pad", ctypes.c_uint8 * 6), ("class_counts", ctypes.c_int64 * 4),
         ("mask_hist", ctypes.c_int64 * 64),
     ]
+
+
+RC_MAX_FRAMES = 6
+RC_BOX_STEPS = 128
+RC_FRAME_GIVEN, RC_FRAME_PRINCIPAL, RC_FRAME_NORMALS, RC_FRAME_BOX = 0, 1, 2, 3
+
+
+class Frames(ctypes.Structure):
+    """Candidate machining frames and their setups (``rc_frames``)."""
+    _fields_ = [
+        ("k", ctypes.c_int32), ("best", ctypes.c_int32), ("source", ctypes.c_int32 * RC_MAX_FRAMES),
+        ("box_axis", ctypes.c_int32 * RC_MAX_FRAMES), ("box_step", ctypes.c_int32 * RC_MAX_FRAMES),
+        ("frame", (ctypes.c_float * 9) * RC_MAX_FRAMES), ("volume", ctypes.c_double * RC_MAX_FRAMES),
+        ("principal", ctypes.c_double * 3), ("setups", Setups * RC_MAX_FRAMES),
+    ]
+
+    def frame_array(self, c):
+        import numpy as np
+        return np.array(list(self.frame[c]), np.float32)
 
 
 class PartResult(ctypes.Structure):
@@ -310,6 +329,22 @@ def rc_setup_cover(mask_hist):
     out = Setups()
     _check(load().rc_setup_cover(h.ctypes.data_as(ctypes.c_void_p), ctypes.byref(out)))
     return out
+
+
+def rc_frame_candidates(h, params, stream=None):
+    """Candidate machining frames of the part (see include/rc.h)."""
+    out = Frames()
+    _check(load().rc_frame_candidates(ctypes.c_void_p(h), ctypes.byref(params), ctypes.byref(out),
+                                      _stream(stream)))
+    return out
+
+
+def rc_frame_select(h, P, N, face, params, frames, counters=None, stream=None):
+    """Evaluate ``frames`` (a :class:`Frames`, updated in place) on the
+    sample points and choose one; returns ``frames``."""
+    _check(load().rc_frame_select(ctypes.c_void_p(h), _ptr(P), _ptr(N), _ptr(face), P.shape[0],
+                                  ctypes.byref(params), ctypes.byref(frames), _ptr(counters), _stream(stream)))
+    return frames
 
 
 def _hptr(a):

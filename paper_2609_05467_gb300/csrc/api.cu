@@ -152,6 +152,8 @@ static rc_status check_params(const rc_params* p)
         return set_error(RC_E_ARG, "tree_width must be 0 (default), 2 or 4");
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return set_error(RC_E_ARG, "blocks_per_sm out of range");
     if (p->collect_stats != 0 && p->collect_stats != 1) return set_error(RC_E_ARG, "collect_stats must be 0 or 1");
+    if (!(p->parallel_tol >= 0.0 && p->parallel_tol <= 0.5))
+        return set_error(RC_E_ARG, "parallel_tol must be in [0, 0.5]");
     return RC_OK;
 }
 
@@ -229,6 +231,7 @@ rc_status rc_params_default(rc_params* p)
     p->t_acc = 0.60;
     p->t_share = 0.45;
     p->t_conc = 0.41;
+    p->parallel_tol = 1e-4;
     return RC_OK;
 }
 

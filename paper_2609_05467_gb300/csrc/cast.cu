@@ -1044,17 +1044,17 @@ k_batch(const BatchPart* __restrict__ parts, int n_parts, long long n_items, int
 
 // ---------------------------------------------------------------------------
 // Section 3.2: orthogonal cast.  A warp holds 32 points (Morton order) and
-// casts the six axes (+X', -X', +Y', -Y', +Z', -Z') one after the other, so
-// all lanes follow the same direction at a time; each lane keeps its point's
-// six-bit mask in a register.  Travel to the frame bounding box is FP64.
+// casts, frame after frame, the six axes (+X', -X', +Y', -Y', +Z', -Z') one
+// after the other, so all lanes follow the same direction at a time; each
+// lane keeps its point's six-bit mask in a register.  Travel to the frame
+// bounding box is FP64.  Frame f writes mask[f n + i] and travel[f n + i][6].
 // ---------------------------------------------------------------------------
 template <bool kWide>
 __global__ void __launch_bounds__(128, RC_BATCH_MIN_BLOCKS)
 k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
              const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
-             const int32_t* __restrict__ order, const float* __restrict__ axes /*6x3*/,
-             const double* __restrict__ frame /*9*/, const double* __restrict__ fbox /*lo3 hi3*/, double eps,
-             uint8_t* __restrict__ mask, float* __restrict__ travel, unsigned long long* counters)
+             const int32_t* __restrict__ order, const FrameDev* __restrict__ fds, int nf, double eps,
+             double par_tol, uint8_t* __restrict__ mask, float* __restrict__ travel, unsigned long long* counters)
 {
     const int lane = threadIdx.x & 31;
     int amb = 0, retests = 0, overflow = 0;
@@ -1067,29 +1067,35 @@ k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
         const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
         const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
         const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
-        unsigned m = 0;
-        for (int a = 0; a < 6; ++a) {
-            const float dx = axes[3 * a], dy = axes[3 * a + 1], dz = axes[3 * a + 2];
-            const int kk = a >> 1;
-            double q = __dadd_rn(__dmul_rn((double)px, frame[kk]), __dmul_rn((double)py, frame[3 + kk]));
-            q = __dadd_rn(q, __dmul_rn((double)pz, frame[6 + kk]));
-            const double tv = (a & 1) ? __dsub_rn(q, fbox[kk]) : __dsub_rn(fbox[3 + kk], q);
-            travel[6 * i + a] = __double2float_rn(tv);
-            // eligibility n.a >= 0 (FP64, x, y, z order)
-            double nd = __dadd_rn(__dmul_rn((double)nx, (double)dx), __dmul_rn((double)ny, (double)dy));
-            nd = __dadd_rn(nd, __dmul_rn((double)nz, (double)dz));
-            if (nd >= 0.0) {
-                Ray r;
-                setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-                const TraceOut t = trace_any<false, kWide>(nodes, tris, r, max_steps);
-                retests += t.retests;
-                overflow += t.overflow;
-                amb += (t.flags >> 1) & 1;
-                if ((t.flags & 1) == 0) m |= 1u << a;
-                rays += 1;
+        for (int f = 0; f < nf; ++f) {
+            const float* axes = fds[f].axes;
+            const double* frame = fds[f].frame;
+            const double* fbox = fds[f].fbox;
+            const int64_t row = (int64_t)f * n + i;
+            unsigned m = 0;
+            for (int a = 0; a < 6; ++a) {
+                const float dx = axes[3 * a], dy = axes[3 * a + 1], dz = axes[3 * a + 2];
+                const int kk = a >> 1;
+                double q = __dadd_rn(__dmul_rn((double)px, frame[kk]), __dmul_rn((double)py, frame[3 + kk]));
+                q = __dadd_rn(q, __dmul_rn((double)pz, frame[6 + kk]));
+                const double tv = (a & 1) ? __dsub_rn(q, fbox[kk]) : __dsub_rn(fbox[3 + kk], q);
+                travel[6 * row + a] = __double2float_rn(tv);
+                // eligibility n.a >= -parallel_tol (FP64, x, y, z order)
+                double nd = __dadd_rn(__dmul_rn((double)nx, (double)dx), __dmul_rn((double)ny, (double)dy));
+                nd = __dadd_rn(nd, __dmul_rn((double)nz, (double)dz));
+                if (nd >= -par_tol) {
+                    Ray r;
+                    setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
+                    const TraceOut t = trace_any<false, kWide>(nodes, tris, r, max_steps);
+                    retests += t.retests;
+                    overflow += t.overflow;
+                    amb += (t.flags >> 1) & 1;
+                    if ((t.flags & 1) == 0) m |= 1u << a;
+                    rays += 1;
+                }
             }
+            mask[row] = (uint8_t)m;
         }
-        mask[i] = (uint8_t)m;
     }
     warp_add_counters(counters, rays, amb, retests, overflow);
 }
@@ -1254,10 +1260,10 @@ __global__ void k_frame_init(FrameArgs a, FrameDev* d)
 
 // Frame axes, frame matrix (FP64) and the vertices' frame bounding box, all
 // on the device; the frame travels as a kernel argument (no host copy).
-rc_status frame_setup(rc_bvh h, const rc_params* p, FrameDev* d, cudaStream_t s)
+rc_status frame_setup_f(rc_bvh h, const float* f9, FrameDev* d, cudaStream_t s)
 {
     FrameArgs a;
-    for (int k = 0; k < 9; ++k) a.f[k] = p->frame[k];
+    for (int k = 0; k < 9; ++k) a.f[k] = f9[k];
     k_frame_init<<<1, 32, 0, s>>>(a, d);
     RC_LAUNCHED();
     const int64_t fb = std::min<int64_t>((h->nV + 255) / 256, (int64_t)sm_count() * 4);
@@ -1268,13 +1274,17 @@ rc_status frame_setup(rc_bvh h, const rc_params* p, FrameDev* d, cudaStream_t s)
     return RC_OK;
 }
 
-rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
-                            uint8_t* mask, float* travel, unsigned long long* counters, cudaStream_t s)
+rc_status frame_setup(rc_bvh h, const rc_params* p, FrameDev* d, cudaStream_t s)
 {
-    FrameDev* fd = nullptr;
-    RC_CUDA(cudaMallocAsync(&fd, sizeof(FrameDev), s));
-    rc_status st = frame_setup(h, p, fd, s);
-    if (st != RC_OK) return st;
+    return frame_setup_f(h, p->frame, d, s);
+}
+
+// Orthogonal cast of n points in nf frames (fds: device array of nf set-up
+// frames); mask [nf][n], travel [nf][n][6].
+rc_status launch_orthogonal_frames(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
+                                   const FrameDev* fds, int nf, uint8_t* mask, float* travel,
+                                   unsigned long long* counters, cudaStream_t s)
+{
     int32_t* order = nullptr;
     if (p->point_order == 0 && n > 1) {
         RC_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * n, s));
@@ -1287,16 +1297,26 @@ rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n,
     if (blocks < 1) blocks = 1;
     if (use_wide(p))
         k_orthogonal<true><<<(unsigned)blocks, 128, 0, s>>>(h->wnodes, h->tris, max_steps(h), h->scene_maxabs, P, N,
-                                                           n, order, fd->axes, fd->frame, fd->fbox, p->origin_offset,
+                                                           n, order, fds, nf, p->origin_offset, p->parallel_tol,
                                                            mask, travel, counters);
     else
         k_orthogonal<false><<<(unsigned)blocks, 128, 0, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N,
-                                                            n, order, fd->axes, fd->frame, fd->fbox, p->origin_offset,
+                                                            n, order, fds, nf, p->origin_offset, p->parallel_tol,
                                                             mask, travel, counters);
     RC_LAUNCHED();
-    RC_CUDA(cudaFreeAsync(fd, s));
     if (order) RC_CUDA(cudaFreeAsync(order, s));
     return RC_OK;
+}
+
+rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
+                            uint8_t* mask, float* travel, unsigned long long* counters, cudaStream_t s)
+{
+    FrameDev* fd = nullptr;
+    RC_CUDA(cudaMallocAsync(&fd, sizeof(FrameDev), s));
+    rc_status st = frame_setup(h, p, fd, s);
+    if (st == RC_OK) st = launch_orthogonal_frames(h, P, N, n, p, fd, 1, mask, travel, counters, s);
+    cudaFreeAsync(fd, s);
+    return st;
 }
 
 rc_status launch_batch(const BatchPart* d_parts, int n_parts, long long n_items, int ppi, const float4* tdirs,

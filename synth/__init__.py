@@ -25,6 +25,9 @@ Generators
   void's surface is blocked).
 - :func:`deep_hole` -- block with one narrow deep square hole.
 - :func:`rotate90` -- exact 90-degree rotation / axis permutation of a mesh.
+- :func:`rotation`, :func:`rotate` -- a rotation matrix from Euler angles and
+  a mesh turned by it (vertices rounded to fp32): parts that do not sit in
+  their machining frame.
 """
 from __future__ import annotations
 
@@ -35,7 +38,7 @@ import numpy as np
 __all__ = [
     "pocket_block", "prismatic", "impeller", "cube", "icosphere", "cavity_box",
     "deep_hole", "box_with_pockets", "rotate90", "subdivide", "marching_tets",
-    "part_family", "perturbed_part",
+    "part_family", "perturbed_part", "rotation", "rotate",
 ]
 
 
@@ -245,6 +248,24 @@ def rotate90(V, axis, k=1):
         va, vb = V[:, a].copy(), V[:, b].copy()
         V[:, a], V[:, b] = -vb, va
     return V
+
+
+def rotation(rx_deg=0.0, ry_deg=0.0, rz_deg=0.0):
+    """FP64 rotation matrix Rz @ Ry @ Rx (angles in degrees)."""
+    ax, ay, az = (math.radians(x) for x in (rx_deg, ry_deg, rz_deg))
+    Rx = np.array([[1, 0, 0], [0, math.cos(ax), -math.sin(ax)], [0, math.sin(ax), math.cos(ax)]])
+    Ry = np.array([[math.cos(ay), 0, math.sin(ay)], [0, 1, 0], [-math.sin(ay), 0, math.cos(ay)]])
+    Rz = np.array([[math.cos(az), -math.sin(az), 0], [math.sin(az), math.cos(az), 0], [0, 0, 1]])
+    return Rz @ Ry @ Rx
+
+
+def rotate(V, R, centre=None):
+    """Vertices turned by the 3x3 matrix ``R`` about ``centre`` (default: the
+    bounding-box midpoint), computed in FP64 and rounded to fp32.  The
+    triangle list is unchanged, so the winding stays outward."""
+    V64 = np.asarray(V, np.float64)
+    c = 0.5 * (V64.min(0) + V64.max(0)) if centre is None else np.asarray(centre, np.float64)
+    return ((V64 - c) @ np.asarray(R, np.float64).T + c).astype(np.float32)
 
 
 # ---------------------------------------------------------------------------

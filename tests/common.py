@@ -45,3 +45,41 @@ def compare_bits(gbits, gcnt, obits, oamb, ocnt, N):
     assert np.array_equal(gcnt[clean], ocnt[clean])
     assert np.array_equal(g.sum(1), gcnt)
     return int((~a).sum()), int(a.sum())
+
+
+def setup_outcomes(om, oam, trav, face, fixture, tool_length, max_amb=10):
+    """Every (class counts, mask histogram, exact cover, greedy cover) the
+    oracle allows: its own masks ``om`` with each of its ambiguous axis rays
+    (``oam`` bits) taken either way.  Returns (set of outcomes, per-point
+    classes of the points without ambiguous rays, mask of those points), or
+    None for the set when there are more than ``max_amb`` ambiguous rays."""
+    om = np.asarray(om, np.uint8)
+    oam = np.asarray(oam, np.uint8)
+    pts = np.flatnonzero(oam)
+    bits = [(i, a) for i in pts for a in range(6) if (oam[i] >> a) & 1]
+    clean = oam == 0
+    cls0, _ = oracle.face_classes(om, trav, face, fixture, tool_length)
+    if len(bits) > max_amb:
+        return None, cls0[clean], clean
+    outs = set()
+    for c in range(1 << len(bits)):
+        m = om.copy()
+        for b, (i, a) in enumerate(bits):
+            if (c >> b) & 1:
+                m[i] |= np.uint8(1 << a)
+            else:
+                m[i] &= np.uint8(~(1 << a) & 0xFF)
+        cls, reach = oracle.face_classes(m, trav, face, fixture, tool_length)
+        viable = reach[cls == 0]
+        hist = tuple(int((viable == k).sum()) for k in range(64))
+        counts = tuple(int((cls == k).sum()) for k in range(4))
+        outs.add((counts, hist) + oracle.setups_exact(viable) + oracle.setups_greedy(viable))
+    return outs, cls0[clean], clean
+
+
+def gpu_outcome(su):
+    """The same tuple from a library ``Setups``."""
+    hist = list(su.mask_hist)
+    hist[0] = 0
+    return (tuple(int(x) for x in su.class_counts), tuple(int(x) for x in hist), su.setups_exact,
+            su.chosen_exact, su.setups_greedy, su.chosen_greedy)

@@ -55,10 +55,10 @@ def test_header_compiles_as_c(tmp_path):
 
 def test_struct_layouts_match_header(rc, tmp_path):
     src = tmp_path / "s.c"
-    src.write_text('#include <stdio.h>\n#include "rc.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu", '
+    src.write_text('#include <stdio.h>\n#include "rc.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu", '
                    'sizeof(rc_params), sizeof(rc_summary), sizeof(rc_setups), sizeof(rc_bvh_info), '
                    'sizeof(rc_part_result), sizeof(rc_server_config), sizeof(rc_request_result), '
-                   'sizeof(rc_server_stats));}\n')
+                   'sizeof(rc_server_stats), sizeof(rc_frames));}\n')
     import subprocess
     exe = tmp_path / "s"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
@@ -66,13 +66,15 @@ def test_struct_layouts_match_header(rc, tmp_path):
     assert [int(x) for x in out] == [ctypes.sizeof(rc.Params), ctypes.sizeof(rc.Summary),
                                      ctypes.sizeof(rc.Setups), ctypes.sizeof(rc.BvhInfo),
                                      ctypes.sizeof(rc.PartResult), ctypes.sizeof(rc.ServerConfig),
-                                     ctypes.sizeof(rc.RequestResult), ctypes.sizeof(rc.ServerStats)]
+                                     ctypes.sizeof(rc.RequestResult), ctypes.sizeof(rc.ServerStats),
+                                     ctypes.sizeof(rc.Frames)]
 
 
 def test_params_default(rc):
     p = rc.rc_params_default()
     assert p.n_dirs == 256 and p.origin_offset == 1e-4 and list(p.frame) == [1, 0, 0, 0, 1, 0, 0, 0, 1]
     assert (p.t_acc, p.t_share, p.t_conc) == (0.60, 0.45, 0.41)
+    assert p.parallel_tol == oracle.PARALLEL_TOL
 
 
 def test_direction_table_bit_equal_to_oracle(rc):
@@ -134,6 +136,20 @@ def test_argument_validation_needs_no_gpu(rc):
     assert L.rc_hemisphere_cast(ctypes.c_void_p(16), None, None, 1, ctypes.byref(p), None, None, None,
                                 None) == 1
     assert L.rc_classify(None, None, None) == 1
+    q = rc.rc_params_default(parallel_tol=-1e-3)
+    assert L.rc_hemisphere_cast(ctypes.c_void_p(16), None, None, 1, ctypes.byref(q), None, None, None,
+                                None) == 1 and b"parallel_tol" in L.rc_last_error()
+    fr = rc.Frames()
+    ok = rc.rc_params_default()
+    assert L.rc_frame_candidates(None, ctypes.byref(ok), ctypes.byref(fr), None) == 1
+    for k in (0, rc.RC_MAX_FRAMES + 1):
+        fr.k = k
+        assert L.rc_frame_select(ctypes.c_void_p(16), None, None, None, 0, ctypes.byref(ok), ctypes.byref(fr),
+                                 None, None) == 1 and b"frames.k" in L.rc_last_error()
+    fr.k = 1
+    fr.frame[0][4] = float("nan")
+    assert L.rc_frame_select(ctypes.c_void_p(16), None, None, None, 0, ctypes.byref(ok), ctypes.byref(fr),
+                             None, None) == 1 and b"finite" in L.rc_last_error()
     assert rc.rc_launch_count() == 0
 
 
