@@ -77,7 +77,7 @@ typedef struct {
     double t_conc;           /* ... or the mean axis concentration > t_conc */
     int32_t block_threads;   /* traversal kernel: threads per block (0 = default; only 128 is supported) */
     int32_t blocks_per_sm;   /* traversal kernel: resident blocks per SM (0 = tuned default) */
-    int32_t collect_stats;   /* 1: hemispherical cast runs the instrumented traversal (counters[4..5]) */
+    int32_t collect_stats;   /* 1: casts run the instrumented traversal (counters[4..5]) */
     int32_t always_setups;   /* rc_analyze_part: 1 = orthogonal cast and setups for every part, 0 = 3-axis parts only */
     int32_t point_order;     /* hemispherical cast: 0 = cast points in Morton order (default), 1 = in index order */
     int32_t tile_mode;       /* hemispherical cast: 0 = directions in coherent tiles of 32 (default), 1 = index order */
@@ -219,8 +219,9 @@ rc_status rc_direction_table(int32_t n_dirs, float* h_dirs);
  *   NULL): rays cast, rays decided by an ambiguous pair, ray/triangle pairs
  *   re-tested in FP64, internal errors (must be 0).  With p->collect_stats
  *   the counters array must hold 8 entries and [4] receives the interior
- *   nodes fetched (64 B each) and [5] the triangles tested (48 B each) over
- *   all rays, from an instrumented copy of the same traversal.
+ *   nodes fetched (112 B each on the 4-wide tree, 64 B on the binary tree)
+ *   and [5] the triangles tested (48 B each) over all rays, from an
+ *   instrumented copy of the same traversal.
  * n == 0 is a no-op.  Asynchronous.  Errors: RC_E_ARG, RC_E_CUDA. */
 rc_status rc_hemisphere_cast(rc_bvh h, const float* d_P, const float* d_N, int64_t n,
                              const rc_params* p, uint32_t* d_bits, int32_t* d_count,
@@ -293,7 +294,8 @@ rc_status rc_classify(const rc_summary* s, const rc_params* p, int32_t* label);
  * Travel (Section 3.3, tool travel distance) = distance from p to the
  * part's bounding box (in frame coordinates) along a.
  *   d_mask [n] uint8 (bit a = accessible), d_travel [n][6] float32,
- *   d_counters int64[4] as for rc_hemisphere_cast (may be NULL).
+ *   d_counters int64[4] as for rc_hemisphere_cast (may be NULL; 8 entries
+ *   with node and triangle counts when p->collect_stats is set).
  * Asynchronous.  Errors: RC_E_ARG, RC_E_CUDA. */
 rc_status rc_orthogonal_cast(rc_bvh h, const float* d_P, const float* d_N, int64_t n,
                              const rc_params* p, uint8_t* d_mask, float* d_travel,
@@ -524,7 +526,8 @@ rc_status rc_frame_candidates(rc_bvh h, const rc_params* p, rc_frames* out, void
  * volume, then the lowest index.  Fills io->setups, io->volume, io->best.
  *   d_P, d_N [n][3], d_face [n] (device, as from rc_sample_points);
  *   d_counters int64[4] (rays, ambiguous, FP64 re-tests, overflow; may be
- *   NULL).  The frames may come from rc_frame_candidates or the caller.
+ *   NULL; 8 entries with node and triangle counts when p->collect_stats is
+ *   set).  The frames may come from rc_frame_candidates or the caller.
  * Synchronises `stream`.  Errors: RC_E_ARG (k outside 1..RC_MAX_FRAMES,
  * non-finite frame), RC_E_CUDA. */
 rc_status rc_frame_select(rc_bvh h, const float* d_P, const float* d_N, const int32_t* d_face, int64_t n,

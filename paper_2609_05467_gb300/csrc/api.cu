@@ -423,7 +423,9 @@ rc_status rc_orthogonal_cast(rc_bvh h, const float* d_P, const float* d_N, int64
     if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = use_device_of(h)) != RC_OK) return st;
-    if (d_counters) RC_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(int64_t) * 4, s));
+    const bool stats = p->collect_stats != 0;
+    if (stats && !d_counters) return set_error(RC_E_ARG, "collect_stats needs the counters array");
+    if (d_counters) RC_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(int64_t) * (stats ? 8 : 4), s));
     if (n == 0) return RC_OK;
     if (!d_P || !d_N || !d_mask || !d_travel) return set_error(RC_E_ARG, "array pointer is NULL");
     return launch_orthogonal(h, d_P, d_N, n, p, d_mask, d_travel, (unsigned long long*)d_counters, s);

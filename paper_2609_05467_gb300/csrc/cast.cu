@@ -1049,7 +1049,7 @@ k_batch(const BatchPart* __restrict__ parts, int n_parts, long long n_items, int
 // lane keeps its point's six-bit mask in a register.  Travel to the frame
 // bounding box is FP64.  Frame f writes mask[f n + i] and travel[f n + i][6].
 // ---------------------------------------------------------------------------
-template <bool kWide>
+template <bool kStats, bool kWide>
 __global__ void __launch_bounds__(128, RC_BATCH_MIN_BLOCKS)
 k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
              const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
@@ -1058,7 +1058,7 @@ k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
 {
     const int lane = threadIdx.x & 31;
     int amb = 0, retests = 0, overflow = 0;
-    long long rays = 0;
+    long long rays = 0, nvis = 0, ntri = 0;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t wv = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wv * 32 < n; wv += nwarps) {
         const int64_t k = wv * 32 + lane;
@@ -1086,18 +1086,19 @@ k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
                 if (nd >= -par_tol) {
                     Ray r;
                     setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-                    const TraceOut t = trace_any<false, kWide>(nodes, tris, r, max_steps);
+                    const TraceOut t = trace_any<kStats, kWide>(nodes, tris, r, max_steps);
                     retests += t.retests;
                     overflow += t.overflow;
                     amb += (t.flags >> 1) & 1;
                     if ((t.flags & 1) == 0) m |= 1u << a;
                     rays += 1;
+                    if (kStats) { nvis += t.nodes; ntri += t.tris; }
                 }
             }
             mask[row] = (uint8_t)m;
         }
     }
-    warp_add_counters(counters, rays, amb, retests, overflow);
+    warp_add_counters(counters, rays, amb, retests, overflow, nvis, ntri);
 }
 
 // FP64 bounding box of the vertices in frame coordinates: per-thread
@@ -1295,14 +1296,17 @@ rc_status launch_orthogonal_frames(rc_bvh h, const float* P, const float* N, int
     const int64_t cap = (int64_t)sm_count() * RC_BATCH_MIN_BLOCKS;
     if (blocks > cap && p->launch_mode == 0) blocks = cap;
     if (blocks < 1) blocks = 1;
-    if (use_wide(p))
-        k_orthogonal<true><<<(unsigned)blocks, 128, 0, s>>>(h->wnodes, h->tris, max_steps(h), h->scene_maxabs, P, N,
-                                                           n, order, fds, nf, p->origin_offset, p->parallel_tol,
-                                                           mask, travel, counters);
-    else
-        k_orthogonal<false><<<(unsigned)blocks, 128, 0, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P, N,
-                                                            n, order, fds, nf, p->origin_offset, p->parallel_tol,
-                                                            mask, travel, counters);
+    const float4* tree = use_wide(p) ? h->wnodes : h->nodes;
+#define RC_ORTHO(ST, WD)                                                                                          \
+    k_orthogonal<ST, WD><<<(unsigned)blocks, 128, 0, s>>>(tree, h->tris, max_steps(h), h->scene_maxabs, P, N, n,  \
+                                                          order, fds, nf, p->origin_offset, p->parallel_tol, mask, \
+                                                          travel, counters)
+    const bool stats = p->collect_stats != 0;
+    if (stats && use_wide(p)) RC_ORTHO(true, true);
+    else if (stats) RC_ORTHO(true, false);
+    else if (use_wide(p)) RC_ORTHO(false, true);
+    else RC_ORTHO(false, false);
+#undef RC_ORTHO
     RC_LAUNCHED();
     if (order) RC_CUDA(cudaFreeAsync(order, s));
     return RC_OK;

@@ -7,8 +7,8 @@
 // orthogonal-cast launch.
 //
 // Device: FP64 surface moments (fixed-order block reduction), the
-// cube-map histogram of face-normal lines, the bounding boxes of 384
-// rotations per base frame.  Host: 3x3 eigen-decomposition (cyclic Jacobi),
+// cube-map histogram of face-normal lines, the exact FP64 bounding boxes of
+// 384 rotations per base frame (with an fp32 pre-pass).  Host: 3x3 eigen-decomposition (cyclic Jacobi),
 // snapping and Gram-Schmidt, the choice.  Host code is compiled without
 // floating-point contraction, so every FP64 expression is rounded operation
 // by operation, left to right.
@@ -129,38 +129,103 @@ __global__ void k_normal_cells(const float* __restrict__ fnorm, const long long*
 }
 
 // ---------------------------------------------------------------------------
-// device: bounding boxes of the vertices in many FP64 frames.  Block
-// (x, g) reduces a chunk of vertices for frame g: q_k = (x G0k + y G1k) +
-// z G2k, min/max per column (exact, order-free), one atomic per block and
-// column on order-preserving integers.
+// device: bounding boxes of the vertices in many FP64 frames G (columns).
+// The defined coordinate is Q64 = fl64((x G0k + y G1k) + z G2k), its min and
+// max over the vertices exact.  FP64 is slow on this part, so two passes:
+//   A (fp32): Q32 with the fp32-rounded frame, per column its min and max
+//     and the largest S32 = |x||g0k| + |y||g1k| + |z||g2k|;
+//   B: vertices whose Q32 lies within W = 2^-19 max S32 of an fp32 extreme
+//     get Q64, and only those enter the FP64 min / max.
+// |Q32 - Q64| <= e = 4.1 * 2^-24 * S32 (rounding of the frame to fp32, two
+// three-term dot products), so the vertex holding the FP64 extreme has Q32
+// within 2 max e of the fp32 extreme; W = 2^-19 max S32 covers that twice,
+// including the rounding of the threshold itself.  The result is exactly the
+// one-pass FP64 result.  Block (x, g) handles a chunk of vertices for frame g;
+// per block and column one atomic on order-preserving integers.
 // ---------------------------------------------------------------------------
 constexpr int kBoxThreads = 256;
 constexpr int kBoxChunk = 8192;
 
-__global__ void k_box_init(long long* box, int nf)
+__global__ void k_box_init(long long* box, int* box32, int nf)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nf * 6) return;
-    box[i] = (i % 6) < 3 ? 0x7FFFFFFFFFFFFFFFLL : (long long)0x8000000000000000ULL;
+    if (i < nf * 6) box[i] = (i % 6) < 3 ? 0x7FFFFFFFFFFFFFFFLL : (long long)0x8000000000000000ULL;
+    if (i < nf * 9) {
+        const int c = i % 9;   // lo xyz, hi xyz, max S xyz
+        box32[i] = c < 3 ? 0x7FFFFFFF : (c < 6 ? (int)0x80000000 : 0);
+    }
+}
+
+__device__ __forceinline__ float dot32(float x, float y, float z, float g0, float g1, float g2)
+{
+    return __fadd_rn(__fadd_rn(__fmul_rn(x, g0), __fmul_rn(y, g1)), __fmul_rn(z, g2));
 }
 
 __global__ void __launch_bounds__(kBoxThreads)
-k_box_search(const float* __restrict__ V, int64_t nV, const double* __restrict__ G /*[nf][9]*/,
-             long long* __restrict__ box /*[nf][6]*/)
+k_box_pass32(const float* __restrict__ V, int64_t nV, const double* __restrict__ G /*[nf][9]*/,
+             int* __restrict__ box32 /*[nf][9]*/)
 {
     const int g = blockIdx.y;
-    double gm[9];
-    for (int k = 0; k < 9; ++k) gm[k] = G[9 * g + k];
+    float gm[9];
+    for (int k = 0; k < 9; ++k) gm[k] = __double2float_rn(G[9 * g + k]);
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, sm[3] = {0, 0, 0};
+    const int64_t v0 = (int64_t)blockIdx.x * kBoxChunk;
+    const int64_t v1 = min64(v0 + kBoxChunk, nV);
+    for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        const float x = V[3 * v], y = V[3 * v + 1], z = V[3 * v + 2];
+        for (int k = 0; k < 3; ++k) {
+            const float q = dot32(x, y, z, gm[k], gm[3 + k], gm[6 + k]);
+            lo[k] = fminf(lo[k], q);
+            hi[k] = fmaxf(hi[k], q);
+            sm[k] = fmaxf(sm[k], dot32(fabsf(x), fabsf(y), fabsf(z), fabsf(gm[k]), fabsf(gm[3 + k]),
+                                       fabsf(gm[6 + k])));
+        }
+    }
+    for (int off = 16; off; off >>= 1)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xFFFFFFFFu, lo[k], off));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xFFFFFFFFu, hi[k], off));
+            sm[k] = fmaxf(sm[k], __shfl_xor_sync(0xFFFFFFFFu, sm[k], off));
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 3; ++k)
+            if (lo[k] <= hi[k]) {
+                atomicMin(&box32[9 * g + k], float_to_ordered(lo[k]));
+                atomicMax(&box32[9 * g + 3 + k], float_to_ordered(hi[k]));
+                atomicMax(&box32[9 * g + 6 + k], float_to_ordered(sm[k]));
+            }
+}
+
+__global__ void __launch_bounds__(kBoxThreads)
+k_box_pass64(const float* __restrict__ V, int64_t nV, const double* __restrict__ G /*[nf][9]*/,
+             const int* __restrict__ box32 /*[nf][9]*/, long long* __restrict__ box /*[nf][6]*/)
+{
+    const int g = blockIdx.y;
+    double gd[9];
+    float gm[9];
+    for (int k = 0; k < 9; ++k) {
+        gd[k] = G[9 * g + k];
+        gm[k] = __double2float_rn(gd[k]);
+    }
+    float tlo[3], thi[3];
+    for (int k = 0; k < 3; ++k) {
+        const float w = ordered_to_float(box32[9 * g + 6 + k]) * 1.9073486328125e-06f;   // 2^-19
+        tlo[k] = __fadd_rn(ordered_to_float(box32[9 * g + k]), w);
+        thi[k] = __fsub_rn(ordered_to_float(box32[9 * g + 3 + k]), w);
+    }
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     const int64_t v0 = (int64_t)blockIdx.x * kBoxChunk;
     const int64_t v1 = min64(v0 + kBoxChunk, nV);
     for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-        const double x = V[3 * v], y = V[3 * v + 1], z = V[3 * v + 2];
+        const float x = V[3 * v], y = V[3 * v + 1], z = V[3 * v + 2];
         for (int k = 0; k < 3; ++k) {
-            double q = __dadd_rn(__dmul_rn(x, gm[k]), __dmul_rn(y, gm[3 + k]));
-            q = __dadd_rn(q, __dmul_rn(z, gm[6 + k]));
-            lo[k] = fmin(lo[k], q);
-            hi[k] = fmax(hi[k], q);
+            const float q32 = dot32(x, y, z, gm[k], gm[3 + k], gm[6 + k]);
+            if (q32 <= tlo[k] || q32 >= thi[k]) {
+                double q = __dadd_rn(__dmul_rn((double)x, gd[k]), __dmul_rn((double)y, gd[3 + k]));
+                q = __dadd_rn(q, __dmul_rn((double)z, gd[6 + k]));
+                lo[k] = fmin(lo[k], q);
+                hi[k] = fmax(hi[k], q);
+            }
         }
     }
     for (int off = 16; off; off >>= 1)
@@ -168,20 +233,11 @@ k_box_search(const float* __restrict__ V, int64_t nV, const double* __restrict__
             lo[k] = fmin(lo[k], __shfl_xor_sync(0xFFFFFFFFu, lo[k], off));
             hi[k] = fmax(hi[k], __shfl_xor_sync(0xFFFFFFFFu, hi[k], off));
         }
-    __shared__ double sl[kBoxThreads / 32][3], shh[kBoxThreads / 32][3];
-    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0)
-        for (int k = 0; k < 3; ++k) { sl[w][k] = lo[k]; shh[w][k] = hi[k]; }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-        const int k = threadIdx.x;
-        double a = INFINITY, b = -INFINITY;
-        for (int i = 0; i < kBoxThreads / 32; ++i) { a = fmin(a, sl[i][k]); b = fmax(b, shh[i][k]); }
-        if (a <= b) {
-            atomicMin(&box[6 * g + k], double_to_ordered(a));
-            atomicMax(&box[6 * g + 3 + k], double_to_ordered(b));
+        for (int k = 0; k < 3; ++k) {
+            if (lo[k] <= hi[k]) atomicMin(&box[6 * g + k], double_to_ordered(lo[k]));
+            if (lo[k] <= hi[k]) atomicMax(&box[6 * g + 3 + k], double_to_ordered(hi[k]));
         }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -447,19 +503,24 @@ rc_status rc_frame_candidates(rc_bvh h, const rc_params* p, rc_frames* out, void
     const int nf = (int)(G.size() / 9);
     double* dG = nullptr;
     long long* dbox = nullptr;
+    int* dbox32 = nullptr;
     RC_CUDA(cudaMallocAsync(&dG, sizeof(double) * G.size(), s));
     RC_CUDA(cudaMallocAsync(&dbox, sizeof(long long) * 6 * nf, s));
+    RC_CUDA(cudaMallocAsync(&dbox32, sizeof(int) * 9 * nf, s));
     RC_CUDA(cudaMemcpyAsync(dG, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice, s));
-    k_box_init<<<(6 * nf + 255) / 256, 256, 0, s>>>(dbox, nf);
+    k_box_init<<<(9 * nf + 255) / 256, 256, 0, s>>>(dbox, dbox32, nf);
     RC_LAUNCHED();
     const int64_t chunks = std::max<int64_t>(1, (h->nV + kBoxChunk - 1) / kBoxChunk);
     if (chunks > 0x7FFFFFFF) return set_error(RC_E_UNSUPPORTED, "too many vertices");
-    k_box_search<<<dim3((unsigned)chunks, (unsigned)nf), kBoxThreads, 0, s>>>(h->V, h->nV, dG, dbox);
+    k_box_pass32<<<dim3((unsigned)chunks, (unsigned)nf), kBoxThreads, 0, s>>>(h->V, h->nV, dG, dbox32);
+    RC_LAUNCHED();
+    k_box_pass64<<<dim3((unsigned)chunks, (unsigned)nf), kBoxThreads, 0, s>>>(h->V, h->nV, dG, dbox32, dbox);
     RC_LAUNCHED();
     std::vector<long long> box(6 * (size_t)nf);
     RC_CUDA(cudaMemcpyAsync(box.data(), dbox, sizeof(long long) * 6 * nf, cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaFreeAsync(dG, s));
     RC_CUDA(cudaFreeAsync(dbox, s));
+    RC_CUDA(cudaFreeAsync(dbox32, s));
     RC_CUDA(cudaStreamSynchronize(s));
     // candidates: each base, then its best rotation, negative zeros made
     // positive; a frame whose axes are (up to sign and order) those of an
@@ -530,6 +591,7 @@ rc_status rc_frame_select(rc_bvh h, const float* d_P, const float* d_N, const in
             if (!isfinite(io->frame[c][k])) return set_error(RC_E_ARG, "frame must be finite");
     if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
     if (n > 0 && (!d_P || !d_N || !d_face)) return set_error(RC_E_ARG, "array pointer is NULL");
+    if (p->collect_stats && !d_counters) return set_error(RC_E_ARG, "collect_stats needs the counters array");
     if ((st = on_device(h)) != RC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int K = io->k;
@@ -552,7 +614,8 @@ rc_status rc_frame_select(rc_bvh h, const float* d_P, const float* d_N, const in
             st = set_error(RC_E_CUDA, "memset failed");
             break;
         }
-        if (d_counters && cudaMemsetAsync(d_counters, 0, sizeof(int64_t) * 4, s) != cudaSuccess) {
+        if (d_counters && cudaMemsetAsync(d_counters, 0, sizeof(int64_t) * (p->collect_stats ? 8 : 4), s) !=
+                              cudaSuccess) {
             st = set_error(RC_E_CUDA, "memset failed");
             break;
         }

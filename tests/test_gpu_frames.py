@@ -148,6 +148,33 @@ def test_auto_frame_end_to_end_undoes_a_rotation(rc):
     bvh.close()
 
 
+def test_instrumented_orthogonal_cast_changes_nothing(rc):
+    V, F = PARTS["prismatic_rot"]()
+    Vt, Ft = gpu_mesh(V, F)
+    bvh = rc.Bvh(Vt, Ft)
+    P, Nn, f, _ = oracle.sample_area(V, F, 3000, seed=1)
+    Pt, Nt, ft = torch.from_numpy(P).cuda(), torch.from_numpy(Nn).cuda(), torch.from_numpy(f).cuda()
+    out = []
+    for stats in (0, 1):
+        p = rc.rc_params_default(collect_stats=stats)
+        fr = rc.rc_frame_candidates(bvh.h, p)
+        ctr = torch.zeros(8, dtype=torch.int64, device="cuda")
+        rc.rc_frame_select(bvh.h, Pt, Nt, ft, p, fr, ctr)
+        mask = torch.zeros(len(P), dtype=torch.uint8, device="cuda")
+        trav = torch.zeros((len(P), 6), dtype=torch.float32, device="cuda")
+        c2 = torch.zeros(8, dtype=torch.int64, device="cuda")
+        rc.rc_orthogonal_cast(bvh.h, Pt, Nt, p, mask, trav, c2)
+        out.append((fr.best, [gpu_outcome(fr.setups[k]) for k in range(fr.k)], mask.cpu().numpy(),
+                    ctr.cpu().numpy(), c2.cpu().numpy()))
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1] and np.array_equal(out[0][2], out[1][2])
+    c, c2 = out[1][3], out[1][4]
+    assert np.array_equal(c[:4], out[0][3][:4]) and c[4] >= c[0] and c[5] > 0
+    assert out[0][3][4] == 0 and c2[4] >= c2[0] > 0
+    with pytest.raises(rc.RcError):
+        rc.rc_orthogonal_cast(bvh.h, Pt, Nt, rc.rc_params_default(collect_stats=1), mask, trav, None)
+    bvh.close()
+
+
 def test_frame_select_edge_cases(rc):
     V, F = synth.cube(20.0, 0)
     Vt, Ft = gpu_mesh(V, F)
