@@ -261,7 +261,7 @@ def run_gpu(args, wl, V, F):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     n, N = wl["n"], wl["n_dirs"]
-    W = N // 32
+    W = (N + 31) // 32
     p = rc.rc_params_default(n_dirs=N, seed=rank, tool_length=60.0, always_setups=1)
 
     Vh = torch.from_numpy(V).pin_memory()
@@ -616,7 +616,7 @@ def run_batched(args):
         Nn = torch.empty_like(P)
         f = torch.empty(n, dtype=torch.int32, device="cuda")
         rc.rc_sample_points(bvh.h, n, p, P, Nn, f)
-        bits = torch.empty((n, N // 32), dtype=torch.int32, device="cuda")
+        bits = torch.empty((n, (N + 31) // 32), dtype=torch.int32, device="cuda")
         cnt = torch.empty(n, dtype=torch.int32, device="cuda")
         ctr = torch.zeros(4, dtype=torch.int64, device="cuda")
         items.append(dict(bvh=bvh, P=P, N=Nn, bits=bits, cnt=cnt, ctr=ctr, n=n))
@@ -787,13 +787,99 @@ def run_autoframe(args):
     bvh.close()
 
 
+def run_facelevel(args):
+    """The paper's face-level analysis of an STL file: the prismatic part
+    written as binary STL, one point per face centroid, 150 directions,
+    area-weighted score, orthogonal cast and setups -- rc_analyze_stl, file
+    to result, each step."""
+    import tempfile
+    import struct
+    import torch
+    import synth
+    import paper_2609_05467_gb300 as rc
+    rc.load()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    V, F = synth.prismatic()
+    tmp = tempfile.mkdtemp(prefix="rc_stl_")
+    path = os.path.join(tmp, "prismatic.stl")
+    tri = V[F.astype(np.int64)].reshape(len(F), 9)
+    rec = np.zeros(len(F), dtype=np.dtype([("n", "<f4", 3), ("v", "<f4", 9), ("a", "<u2")]))
+    rec["v"] = tri
+    with open(path, "wb") as f:
+        f.write(b"prismatic part".ljust(80, b" "))
+        f.write(struct.pack("<I", len(F)))
+        f.write(rec.tobytes())
+    N = 150
+    p = rc.rc_params_default(n_dirs=N, sample_mode=rc.RC_SAMPLE_FACE_CENTROID, always_setups=1, tool_length=60.0)
+    for _ in range(args.warmup):
+        r = rc.rc_analyze_stl(path, 0, p, stream)
+    torch.cuda.synchronize()
+    uuid = str(getattr(torch.cuda.get_device_properties(0), "uuid", "") or "")
+    if uuid and not uuid.startswith("GPU-"):
+        uuid = "GPU-" + uuid
+    clk = ClockSampler(uuid)
+    clk.start()
+    launches0 = rc.rc_launch_count()
+    ev_ms, wall = [], []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        r = rc.rc_analyze_stl(path, 0, p, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall.append(time.perf_counter() - t0)
+        ev_ms.append(e0.elapsed_time(e1))
+    launches = rc.rc_launch_count() - launches0
+    clocks = clk.stop()
+    rays = float(r.cast_counters[0] + r.ortho_counters[0])
+    out = {
+        "metric": METRIC, "value": rays / (float(np.mean(ev_ms)) / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ev_ms)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "facelevel: prismatic part (%d triangles) as a binary STL file, one point per face "
+                               "centroid (area-weighted score), %d directions, six-axis cast and setups; "
+                               "rc_analyze_stl from the file each step" % (len(F), N),
+                   "tris": int(len(F)), "points": int(len(F)), "dirs": N,
+                   "l2": "not flushed: each step re-reads the file and rebuilds everything"},
+        "e2e": {"value": rays / float(np.mean(wall)), "unit": UNIT, "file_bytes": os.path.getsize(path),
+                "h2d_bytes_per_step": int(V.nbytes + F.nbytes), "d2h_bytes_per_step": 0,
+                "api": "rc_analyze_stl (file read, merge, upload, build, cast, summary, setups)"},
+        "summary": {"overall_access": r.summary.overall_access,
+                    "overall_access_unweighted": r.summary.overall_access_unweighted,
+                    "axis_share": list(r.summary.axis_share), "mean_conc": r.summary.mean_conc,
+                    "label": ["3-axis", "multi-axis"][r.label], "setups_exact": r.setups.setups_exact,
+                    "setups_greedy": r.setups.setups_greedy},
+        "gpu_launches": int(launches), "clocks": clocks,
+        "quality": {"ambiguous_rays": int(r.cast_counters[1] + r.ortho_counters[1]),
+                    "errors": int(r.cast_counters[3] + r.ortho_counters[3])},
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        P, Nn, fc, w = oracle.sample_centroid(V, F)
+        m = oracle.Mesh(V, F)
+        k = 20000
+        t0 = time.perf_counter()
+        m.hemisphere(P[:k], Nn[:k], N)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": k * N / dt, "unit": UNIT, "cores": oracle.num_cores(), "kind": "oracle",
+                               "sample": "the first %d face centroids x %d directions, FP64 CPU BVH cast, %.1f s"
+                                         % (k, N, dt)}
+    os.remove(path)
+    os.rmdir(tmp)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="prismatic", choices=list(WORKLOADS) + ["served", "batched", "autoframe"])
+    ap.add_argument("--workload", default="prismatic", choices=list(WORKLOADS) + ["served", "batched", "autoframe", "facelevel"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--points", type=int, default=0, help="override the workload's point count (profiling runs)")
@@ -814,6 +900,9 @@ def main():
         return
     if args.workload == "autoframe":
         run_autoframe(args)
+        return
+    if args.workload == "facelevel":
+        run_facelevel(args)
         return
     wl = dict(WORKLOADS[args.workload])
     if args.points > 0:

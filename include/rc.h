@@ -27,9 +27,9 @@
  *  - Layouts: points, normals and vertices are row-major float32 xyz
  *    ([n][3]); faces are int32 vertex indices ([T][3]), wound
  *    counter-clockwise seen from outside (the normal is the right-hand rule
- *    on the stored winding).  Visibility bits: row i has W = n_dirs/32
+ *    on the stored winding).  Visibility bits: row i has W = ceil(n_dirs/32)
  *    uint32 words; bit (j & 31) of word (j >> 5) is 1 iff hemisphere
- *    direction j of point i is unobstructed.
+ *    direction j of point i is unobstructed; bits j >= n_dirs are 0.
  *  - Precision: traversal and intersection run in FP32 with a forward error
  *    bound per ray/triangle test; tests whose FP32 outcome is not certain
  *    are re-decided in FP64 (Section 3.1's intersection test made exact
@@ -65,7 +65,7 @@ enum { RC_SAMPLE_AREA_RANDOM = 0, RC_SAMPLE_FACE_CENTROID = 1 };
 
 /* Analysis parameters.  Fill with rc_params_default() and override. */
 typedef struct {
-    int32_t n_dirs;          /* N: hemisphere directions per point; multiple of 32, 32..65536 */
+    int32_t n_dirs;          /* N: hemisphere directions per point, 1..65536 (the paper uses 150) */
     int32_t sample_mode;     /* RC_SAMPLE_* */
     double origin_offset;    /* mm; rays start at fl32(p + origin_offset * n) (Section 3.1) */
     uint64_t seed;           /* area-random sampling seed */
@@ -214,7 +214,7 @@ rc_status rc_direction_table(int32_t n_dirs, float* h_dirs);
  * d_ij = (t1*hx + t2*hy) + n*hz in float32 with (t1, t2) the orthonormal
  * basis of Duff et al. (2017); it is obstructed iff some triangle meets it
  * at t > 0.
- *   d_P, d_N [n][3]; d_bits [n][n_dirs/32] uint32 (written); d_count [n]
+ *   d_P, d_N [n][3]; d_bits [n][W] uint32, W = ceil(n_dirs/32), (written); d_count [n]
  *   int32 unobstructed counts (written); d_counters int64[4] (written, may be
  *   NULL): rays cast, rays decided by an ambiguous pair, ray/triangle pairs
  *   re-tested in FP64, internal errors (must be 0).  With p->collect_stats
@@ -238,7 +238,7 @@ rc_status rc_hemisphere_cast(rc_bvh h, const float* d_P, const float* d_N, int64
  * dom = argmax_k |M_k| (ties to the lower axis; -1 if nothing is visible);
  * conc (conc_mode 0) = share of visible rays whose largest |component| is
  * axis dom, (conc_mode 1) = |M_dom| / (2^40 count).
- *   d_bits [n][N/32], d_N [n][3]; d_weight [n] (NULL = unit weights);
+ *   d_bits [n][W], d_N [n][3]; d_weight [n] (NULL = unit weights);
  *   outputs (each may be NULL): d_acc [n] float32, d_dom [n] int8,
  *   d_conc [n] float32, d_dir_area [N] double (sum over points of weight
  *   times visibility of direction j, weights in 2^-24 fixed point of max w);
@@ -379,7 +379,7 @@ typedef struct {
  * p->always_setups -- cast the six axes and search the setups; then copy
  * the requested per-point results back.
  *   h_V [nV][3], h_F [T][3] (host; pinned memory makes the copies
- *   asynchronous); outputs h_bits [n][N/32], h_count [n], h_mask [n],
+ *   asynchronous); outputs h_bits [n][W], h_count [n], h_mask [n],
  *   h_class [n] are host arrays and may each be NULL; h_out receives the
  *   part-level result.
  * Device memory is allocated on `stream` and released before returning.
@@ -449,7 +449,7 @@ rc_status rc_server_submit(rc_server s, uint64_t part_key, const float* h_V, int
  * queued; the request stays known), RC_E_ARG (unknown id). */
 rc_status rc_server_wait(rc_server s, int64_t req_id, double timeout_s, rc_request_result* out);
 
-/* Copy a resident part's visibility bits [n][N/32] and counts [n] to host
+/* Copy a resident part's visibility bits [n][W] and counts [n] to host
  * arrays (either may be NULL).  Errors: RC_E_ARG (not resident, in use, or
  * n differs). */
 rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, int32_t* h_count, int64_t n);
@@ -467,6 +467,34 @@ rc_status rc_server_destroy(rc_server s);
  * chosen_* of *out; other fields are left unchanged.  Host only, no GPU.
  * Errors: RC_E_ARG (NULL, negative count). */
 rc_status rc_setup_cover(const int64_t* h_mask_hist, rc_setups* out);
+
+/* ---------------------------------------------------------------------- */
+/* STL import and the paper's face-level analysis                         */
+/* ---------------------------------------------------------------------- */
+
+/* Read an STL file (binary, or ASCII "solid ... endsolid") into the mesh
+ * layout of rc_build_bvh.  A file is binary when its size is 84 + 50 *
+ * (facet count at byte 80); otherwise it must be ASCII.  Facet vertices are
+ * taken in stored order (counter-clockwise seen from outside); the stored
+ * normal is ignored.  Vertices with identical coordinates (bit for bit, -0
+ * read as +0) are merged in order of first appearance.
+ *   Size query: h_V = h_F = NULL fills *nV, *T only.
+ *   Otherwise h_V [cap_V][3] float32 and h_F [cap_F][3] int32 (host,
+ *   caller-owned) receive the mesh if cap_V >= *nV and cap_F >= *T.
+ * Host only.  Errors: RC_E_ARG (cannot open, malformed or truncated file,
+ * non-finite vertex, arrays too small -- *nV and *T are still set). */
+rc_status rc_stl_read(const char* path, float* h_V, int64_t cap_V, int32_t* h_F, int64_t cap_F, int64_t* nV,
+                      int64_t* T);
+
+/* The paper's per-part analysis of an STL file (Section 3.1 casts from
+ * every face centroid; Sections 3.2-3.3 give the summary of Tables 1-2):
+ * rc_stl_read, then rc_analyze_part.  With p->sample_mode ==
+ * RC_SAMPLE_FACE_CENTROID the points are the face centroids (n is ignored
+ * and set to T) and the overall accessibility is area-weighted; with area
+ * sampling n points are drawn.  p->n_dirs may be any value in 1..65536 (the
+ * paper uses 150).  Per-point outputs are not returned.  Synchronises
+ * `stream`.  Errors: those of rc_stl_read and rc_analyze_part. */
+rc_status rc_analyze_stl(const char* path, int64_t n, const rc_params* p, rc_part_result* h_out, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Automatic machining frame (Section 3.2 assumes the part sits in a      */

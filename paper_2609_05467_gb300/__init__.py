@@ -191,6 +191,10 @@ def load(build_if_missing=True):
             "rc_server_destroy": ([P], st),
             "rc_analyze_part": ([P, i64, P, i64, i64, ctypes.POINTER(Params), P, P, P, P,
                                  ctypes.POINTER(PartResult), P], st),
+            "rc_frame_candidates": ([P, ctypes.POINTER(Params), ctypes.POINTER(Frames), P], st),
+            "rc_frame_select": ([P, P, P, P, i64, ctypes.POINTER(Params), ctypes.POINTER(Frames), P, P], st),
+            "rc_stl_read": ([ctypes.c_char_p, P, i64, P, i64, ctypes.POINTER(i64), ctypes.POINTER(i64)], st),
+            "rc_analyze_stl": ([ctypes.c_char_p, i64, ctypes.POINTER(Params), ctypes.POINTER(PartResult), P], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -345,6 +349,27 @@ def rc_frame_select(h, P, N, face, params, frames, counters=None, stream=None):
     _check(load().rc_frame_select(ctypes.c_void_p(h), _ptr(P), _ptr(N), _ptr(face), P.shape[0],
                                   ctypes.byref(params), ctypes.byref(frames), _ptr(counters), _stream(stream)))
     return frames
+
+
+def rc_stl_read(path):
+    """Read an STL file (binary or ASCII): returns (V float32 [nV,3], F
+    int32 [T,3]) as numpy arrays, vertices merged as include/rc.h says."""
+    import numpy as np
+    b = os.fsencode(path)
+    nV, T = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().rc_stl_read(b, None, 0, None, 0, ctypes.byref(nV), ctypes.byref(T)))
+    V = np.zeros((nV.value, 3), np.float32)
+    F = np.zeros((T.value, 3), np.int32)
+    _check(load().rc_stl_read(b, V.ctypes.data_as(ctypes.c_void_p), nV.value, F.ctypes.data_as(ctypes.c_void_p),
+                              T.value, ctypes.byref(nV), ctypes.byref(T)))
+    return V, F
+
+
+def rc_analyze_stl(path, n, params, stream=None):
+    """The paper's per-part analysis of an STL file: returns a PartResult."""
+    out = PartResult()
+    _check(load().rc_analyze_stl(os.fsencode(path), n, ctypes.byref(params), ctypes.byref(out), _stream(stream)))
+    return out
 
 
 def _hptr(a):

@@ -1,7 +1,8 @@
 """Build ``librc.so`` (the sm_103a ray-casting library) in-tree with nvcc.
 
-Each ``csrc/*.cu`` is compiled to an object in parallel, then linked into a
-shared library with the static CUDA runtime.  Host code is compiled with
+Each ``csrc/*.cu`` (nvcc) and ``csrc/*.cpp`` (host-only, g++) is compiled to an
+object in parallel, then linked into a shared library with the static CUDA
+runtime.  Host code is compiled with
 ``-ffp-contract=off`` so that the host-side direction table is evaluated
 with separately rounded operations on every platform.
 """
@@ -45,12 +46,15 @@ def build(force=False, verbose=False, extra=()):
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     cc = nvcc()
 
     def one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *_flags(extra), "-c", src, "-o", obj]
+        obj = os.path.join(BUILD, os.path.splitext(os.path.basename(src))[0] + ".o")
+        if src.endswith(".cpp"):      # host-only sources: the host compiler, same flags
+            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", "-c", src, "-o", obj]
+        else:
+            cmd = [cc, *_flags(extra), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))

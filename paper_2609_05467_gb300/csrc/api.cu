@@ -103,10 +103,17 @@ static rc_status device_dirs(int32_t N, const float4** canon, const float4** til
     std::lock_guard<std::mutex> lk(g_dir_mu);
     auto it = g_dirs.find({dev, N});
     if (it == g_dirs.end()) {
+        // both tables hold 32 * ceil(N / 32) entries; the entries past N
+        // (canonical index -1, zero direction) pad the last tile and are
+        // never cast
+        const int32_t N32 = (N + 31) / 32 * 32;
         std::vector<float> h(3 * (size_t)N);
         fibonacci_hemisphere(N, h.data());
         const std::vector<int32_t> ord = tile_order(N, h.data());
-        std::vector<float4> h4(2 * (size_t)N);
+        float pad_w;
+        const int32_t minus1 = -1;
+        memcpy(&pad_w, &minus1, sizeof pad_w);
+        std::vector<float4> h4(2 * (size_t)N32, make_float4(0.0f, 0.0f, 0.0f, pad_w));
         for (int32_t j = 0; j < N; ++j) {
             float w;
             memcpy(&w, &j, sizeof w);
@@ -116,12 +123,12 @@ static rc_status device_dirs(int32_t N, const float4** canon, const float4** til
             const int32_t j = ord[k];
             float w;
             memcpy(&w, &j, sizeof w);
-            h4[N + k] = make_float4(h[3 * j], h[3 * j + 1], h[3 * j + 2], w);
+            h4[N32 + k] = make_float4(h[3 * j], h[3 * j + 1], h[3 * j + 2], w);
         }
         float4* d = nullptr;
-        RC_CUDA(cudaMalloc(&d, sizeof(float4) * 2 * N));
-        RC_CUDA(cudaMemcpy(d, h4.data(), sizeof(float4) * 2 * N, cudaMemcpyHostToDevice));
-        it = g_dirs.emplace(std::make_pair(dev, N), DirTables{d, d + N}).first;
+        RC_CUDA(cudaMalloc(&d, sizeof(float4) * 2 * N32));
+        RC_CUDA(cudaMemcpy(d, h4.data(), sizeof(float4) * 2 * N32, cudaMemcpyHostToDevice));
+        it = g_dirs.emplace(std::make_pair(dev, N), DirTables{d, d + N32}).first;
     }
     *canon = it->second.canon;
     if (tiled) *tiled = it->second.tiled;
@@ -131,8 +138,7 @@ static rc_status device_dirs(int32_t N, const float4** canon, const float4** til
 static rc_status check_params(const rc_params* p)
 {
     if (!p) return set_error(RC_E_ARG, "params is NULL");
-    if (p->n_dirs < 32 || p->n_dirs > kMaxDirs || p->n_dirs % 32)
-        return set_error(RC_E_ARG, "n_dirs must be a multiple of 32 in [32, 65536]");
+    if (p->n_dirs < 1 || p->n_dirs > kMaxDirs) return set_error(RC_E_ARG, "n_dirs must be in [1, 65536]");
     if (!(p->origin_offset >= 0.0) || !isfinite(p->origin_offset))
         return set_error(RC_E_ARG, "origin_offset must be finite and >= 0");
     if (p->sample_mode != RC_SAMPLE_AREA_RANDOM && p->sample_mode != RC_SAMPLE_FACE_CENTROID)
@@ -478,7 +484,7 @@ rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int6
     if (nV < 3 || T < 1) return set_error(RC_E_ARG, "empty mesh");
     cudaStream_t s = (cudaStream_t)stream;
     memset(h_out, 0, sizeof *h_out);
-    const int W = p->n_dirs / 32;
+    const int W = (p->n_dirs + 31) / 32;
     const bool centroid = p->sample_mode == RC_SAMPLE_FACE_CENTROID;
     // one device block for everything, carved into aligned pieces
     size_t off = 0;

@@ -600,25 +600,28 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
     int cnt = 0;
     for (int t = 0; t < W; ++t) {
         const float4 h = __ldg(&tdirs[32 * t + lane]);
-        const int j = __float_as_int(h.w);
-        float dx, dy, dz;
-        local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
-        Ray r;
-        setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-        const TraceOut tr = trace_any<kStats, kWide>(nodes, tris, r, max_steps);
-        acc.retests += tr.retests;
-        acc.overflow += tr.overflow;
-        acc.amb += (tr.flags >> 1) & 1;
-        if (kStats) { acc.nvis += tr.nodes; acc.ntri += tr.tris; }
-        const bool visible = (tr.flags & 1) == 0;
-        if (visible) atomicOr(&row[j >> 5], 1u << (j & 31));
+        const int j = __float_as_int(h.w);      // canonical index; -1 pads the last tile when 32 does not divide N
+        bool visible = false;
+        if (j >= 0) {
+            float dx, dy, dz;
+            local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
+            Ray r;
+            setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
+            const TraceOut tr = trace_any<kStats, kWide>(nodes, tris, r, max_steps);
+            acc.retests += tr.retests;
+            acc.overflow += tr.overflow;
+            acc.amb += (tr.flags >> 1) & 1;
+            if (kStats) { acc.nvis += tr.nodes; acc.ntri += tr.tris; }
+            visible = (tr.flags & 1) == 0;
+            if (visible) atomicOr(&row[j >> 5], 1u << (j & 31));
+            acc.rays += 1;
+        }
         cnt += __popc(__ballot_sync(0xFFFFFFFFu, visible));
     }
     __syncwarp();
     for (int w = lane; w < W; w += 32) bits[i * W + w] = row[w];
     __syncwarp();
     if (lane == 0) count[i] = cnt;
-    acc.rays += W;   // per lane
 }
 
 // The hemispherical cast of one point with each lane walking its own list
@@ -651,6 +654,8 @@ __device__ __forceinline__ void cast_point_flat(const float4* __restrict__ nodes
             const float4 h = __ldg(&tdirs[32 * m + lane]);
             ++m;
             j = __float_as_int(h.w);
+            if (j < 0) continue;                 // pad of the last tile
+            ++acc.rays;
             float dx, dy, dz;
             local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
             setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
@@ -675,7 +680,6 @@ __device__ __forceinline__ void cast_point_flat(const float4* __restrict__ nodes
     for (int w = lane; w < W; w += 32) bits[i * W + w] = row[w];
     __syncwarp();
     if (lane == 0) count[i] = cnt;
-    acc.rays += W;   // per lane
 }
 
 #ifndef RC_FLAT_MIN_BLOCKS
@@ -691,7 +695,7 @@ k_hemisphere_flat(const float4* __restrict__ nodes, const float4* __restrict__ t
 {
     extern __shared__ uint32_t s_rows[];
     const int lane = threadIdx.x & 31;
-    const int W = n_dirs >> 5;
+    const int W = (n_dirs + 31) >> 5;
     uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
     CastAcc acc;
     for (;;) {
@@ -720,7 +724,7 @@ k_hemisphere_pkt(const float4* __restrict__ nodes, const float4* __restrict__ tr
                  unsigned long long* work)
 {
     const int lane = threadIdx.x & 31;
-    const int W = n_dirs >> 5;
+    const int W = (n_dirs + 31) >> 5;
     const unsigned long long chunks = (unsigned long long)((n + 31) / 32);
     CastAcc acc;
     // work item = (chunk of 32 points, word of 32 directions)
@@ -742,7 +746,8 @@ k_hemisphere_pkt(const float4* __restrict__ nodes, const float4* __restrict__ tr
         const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
         const Onb b = make_onb(nx, ny, nz);
         uint32_t word = 0;
-        for (int bit = 0; bit < 32; ++bit) {
+        const int nbits = min(32, n_dirs - 32 * w);
+        for (int bit = 0; bit < nbits; ++bit) {
             if (!valid) break;
             const float4 h = __ldg(&dirs[32 * w + bit]);
             float dx, dy, dz;
@@ -758,7 +763,7 @@ k_hemisphere_pkt(const float4* __restrict__ nodes, const float4* __restrict__ tr
         if (valid) {
             bits[i * W + w] = word;
             atomicAdd(&count[i], __popc(word));
-            acc.rays += 32;
+            acc.rays += nbits;
         }
     }
     warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow);
@@ -774,7 +779,7 @@ k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
 {
     extern __shared__ uint32_t s_rows[];
     const int lane = threadIdx.x & 31;
-    const int W = n_dirs >> 5;
+    const int W = (n_dirs + 31) >> 5;
     uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
     CastAcc acc;
     // with a work counter the warps take points until none are left; without
@@ -833,7 +838,7 @@ k_hemisphere_dyn(const float4* __restrict__ nodes, const float4* __restrict__ tr
     __shared__ SlotInfo s_slot[4][2];
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int W = n_dirs >> 5;
+    const int W = (n_dirs + 31) >> 5;
     uint32_t* rows = s_mem + wid * (2 * W);
     SlotInfo* si = s_slot[wid];
 
@@ -1012,7 +1017,7 @@ k_batch(const BatchPart* __restrict__ parts, int n_parts, long long n_items, int
 {
     extern __shared__ uint32_t s_rows[];
     const int lane = threadIdx.x & 31;
-    const int W = n_dirs >> 5;
+    const int W = (n_dirs + 31) >> 5;
     uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
     CastAcc acc;
     int cur = -1;
@@ -1182,7 +1187,7 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
     if (blocks < 1) blocks = 1;
     if (blocks > 0x7FFFFFFF) return set_error(RC_E_UNSUPPORTED, "too many points for one launch");
     if (p->launch_mode == 1) work = nullptr;
-    const size_t smem = (size_t)(threads / 32) * (p->n_dirs / 32) * sizeof(uint32_t);
+    const size_t smem = (size_t)(threads / 32) * ((p->n_dirs + 31) / 32) * sizeof(uint32_t);
     const bool wide = use_wide(p);
     if (smem > 48 * 1024) {
         RC_CUDA(cudaFuncSetAttribute(k_hemisphere<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1195,7 +1200,7 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
         RC_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * n, s));
         const int64_t chunks = (n + 31) / 32;
         int64_t pblocks = (int64_t)sm_count() * (p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_HEMI_MIN_BLOCKS);
-        const int64_t pneed = (chunks * (p->n_dirs / 32) * 32 + threads - 1) / threads;
+        const int64_t pneed = (chunks * ((p->n_dirs + 31) / 32) * 32 + threads - 1) / threads;
         if (pblocks > pneed) pblocks = pneed;
         if (pblocks < 1) pblocks = 1;
         if (wide)
@@ -1327,7 +1332,7 @@ rc_status launch_batch(const BatchPart* d_parts, int n_parts, long long n_items,
                        const rc_params* p, unsigned long long* work, cudaStream_t s)
 {
     const int threads = 128;
-    const size_t smem = (size_t)(threads / 32) * (p->n_dirs / 32) * sizeof(uint32_t);
+    const size_t smem = (size_t)(threads / 32) * ((p->n_dirs + 31) / 32) * sizeof(uint32_t);
     const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_HEMI_MIN_BLOCKS;
     int64_t blocks = (int64_t)sm_count() * per_sm;
     const int64_t need = (n_items * 32 + threads - 1) / threads;
@@ -1345,7 +1350,7 @@ rc_status launch_batch(const BatchPart* d_parts, int n_parts, long long n_items,
 
 rc_status prepare_batch_kernel(int n_dirs)
 {
-    const size_t smem = (size_t)4 * (n_dirs / 32) * sizeof(uint32_t);
+    const size_t smem = (size_t)4 * ((n_dirs + 31) / 32) * sizeof(uint32_t);
     if (smem > 48 * 1024) {
         RC_CUDA(cudaFuncSetAttribute(k_batch<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         RC_CUDA(cudaFuncSetAttribute(k_batch<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

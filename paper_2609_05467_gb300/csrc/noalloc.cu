@@ -51,7 +51,7 @@ extern "C" rc_status rc_direction_variability_noalloc(const uint32_t* d_bits, co
                                                       double* d_dir_area, rc_summary* h_summary, void* stream)
 {
     if (!p) return set_error(RC_E_ARG, "params is NULL");
-    if (p->n_dirs < 32 || p->n_dirs % 32) return set_error(RC_E_ARG, "n_dirs must be a positive multiple of 32");
+    if (p->n_dirs < 1) return set_error(RC_E_ARG, "n_dirs must be >= 1");
     if (p->n_dirs > kNoAllocMaxDirs)
         return set_error(RC_E_UNSUPPORTED, "rc_direction_variability_noalloc supports at most 8192 directions "
                                            "(its static scratch is 196,864 bytes per device)");

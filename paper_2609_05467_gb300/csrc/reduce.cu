@@ -54,7 +54,7 @@ k_variability(const uint32_t* __restrict__ bits, const float* __restrict__ Nrm,
     if (threadIdx.x < S_N) blk[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int W = n_dirs >> 5;
+    const int W = (n_dirs + 31) >> 5;
     const double wmax = weight ? *wmax_p : 1.0;
     long long loc[S_N] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -250,7 +250,7 @@ rc_status launch_variability(const uint32_t* bits, const float* N, const double*
         RC_LAUNCHED();
     }
     if (dir_area) {
-        const int W = nd / 32;
+        const int W = (nd + 31) / 32;
         const int64_t warps = ((n + kDirChunk - 1) / kDirChunk) * W;
         if (warps > 0) {
             k_dir_hist<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(bits, n, W, weight, wmax_p, dirq);

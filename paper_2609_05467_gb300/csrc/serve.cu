@@ -233,7 +233,7 @@ static rc_status run_request(rc_server s, SrvRequest* r, SrvEntry* e, cudaStream
         SRV_CUDA(cudaMallocAsync(&e->P, sizeof(float) * 3 * c, st));
         SRV_CUDA(cudaMallocAsync(&e->Nn, sizeof(float) * 3 * c, st));
         SRV_CUDA(cudaMallocAsync(&e->face, sizeof(int32_t) * c, st));
-        SRV_CUDA(cudaMallocAsync(&e->bits, sizeof(uint32_t) * (N / 32) * c, st));
+        SRV_CUDA(cudaMallocAsync(&e->bits, sizeof(uint32_t) * ((N + 31) / 32) * c, st));
         SRV_CUDA(cudaMallocAsync(&e->count, sizeof(int32_t) * c, st));
         SRV_CUDA(cudaMallocAsync(&e->mask, c, st));
         SRV_CUDA(cudaMallocAsync(&e->travel, sizeof(float) * 6 * c, st));
@@ -413,7 +413,7 @@ rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, 
     SrvEntry* e = it->second;
     if (e->busy) return set_error(RC_E_ARG, "part is being analysed");
     if (n != e->n) return set_error(RC_E_ARG, "n differs from the resident part's point count");
-    if (h_bits && n) RC_CUDA(cudaMemcpy(h_bits, e->bits, sizeof(uint32_t) * (e->N / 32) * n, cudaMemcpyDeviceToHost));
+    if (h_bits && n) RC_CUDA(cudaMemcpy(h_bits, e->bits, sizeof(uint32_t) * ((e->N + 31) / 32) * n, cudaMemcpyDeviceToHost));
     if (h_count && n) RC_CUDA(cudaMemcpy(h_count, e->count, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
     return RC_OK;
 }

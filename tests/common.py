@@ -1,5 +1,7 @@
 """Shared helpers for the GPU tests: run the library through the binding and
 compare with the oracle.  Imports torch lazily."""
+import struct
+
 import numpy as np
 
 import oracle
@@ -20,7 +22,7 @@ def gpu_mesh(V, F):
 def gpu_cast(rc, h, P, Nn, params):
     import torch
     n = len(P)
-    W = params.n_dirs // 32
+    W = (params.n_dirs + 31) // 32
     Pt = torch.from_numpy(np.ascontiguousarray(P, np.float32)).cuda()
     Nt = torch.from_numpy(np.ascontiguousarray(Nn, np.float32)).cuda()
     bits = torch.zeros((n, W), dtype=torch.int32, device="cuda")
@@ -83,3 +85,31 @@ def gpu_outcome(su):
     hist[0] = 0
     return (tuple(int(x) for x in su.class_counts), tuple(int(x) for x in hist), su.setups_exact,
             su.chosen_exact, su.setups_greedy, su.chosen_greedy)
+
+
+def stl_facets(V, F):
+    """Triangle corners [T, 3, 3] of a mesh."""
+    return np.asarray(V, np.float32)[np.asarray(F, np.int64)]          # [T, 3, 3]
+
+
+def write_stl_binary(path, V, F, header=b"binary test part"):
+    tri = stl_facets(V, F)
+    with open(path, "wb") as f:
+        f.write(header.ljust(80, b" ")[:80])
+        f.write(struct.pack("<I", len(tri)))
+        for t in tri:
+            f.write(struct.pack("<3f", 0.0, 0.0, 0.0))                  # stored normal: ignored
+            f.write(struct.pack("<9f", *t.reshape(9).tolist()))
+            f.write(b"\0\0")
+
+
+def write_stl_ascii(path, V, F, name="part"):
+    tri = stl_facets(V, F)
+    with open(path, "w") as f:
+        f.write("solid %s\n" % name)
+        for t in tri:
+            f.write("  facet normal 0 0 0\n    outer loop\n")
+            for v in t:
+                f.write("      vertex %s %s %s\n" % tuple(repr(float(x)) for x in v))
+            f.write("    endloop\n  endfacet\n")
+        f.write("endsolid %s\n" % name)

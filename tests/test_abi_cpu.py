@@ -45,6 +45,21 @@ def test_library_exports_every_declared_symbol(rc):
     assert not missing, missing
 
 
+def test_binding_declares_every_argument_type(rc):
+    """Each entry point's ctypes prototype is set, with as many arguments
+    as the header declares (so 64-bit sizes are never passed as C int)."""
+    L = rc.load()
+    txt = open(os.path.join(ROOT, "include", "rc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    for m in re.finditer(r"\b(rc_\w+)\s*\(([^)]*)\);", txt):
+        name, args = m.group(1), m.group(2).strip()
+        if name not in declared_symbols():
+            continue
+        n_args = 0 if args in ("", "void") else args.count(",") + 1
+        fn = getattr(L, name)
+        assert fn.argtypes is not None and len(fn.argtypes) == n_args, name
+
+
 def test_header_compiles_as_c(tmp_path):
     src = tmp_path / "t.c"
     src.write_text('#include "rc.h"\nint main(void){rc_params p; return rc_params_default(&p);}\n')
@@ -132,7 +147,7 @@ def test_argument_validation_needs_no_gpu(rc):
     assert b"NULL" in L.rc_last_error()
     assert L.rc_build_bvh(ctypes.c_void_p(16), 2, ctypes.c_void_p(16), 1, None, ctypes.byref(h)) == 1
     assert L.rc_build_bvh(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 0, None, ctypes.byref(h)) == 1
-    p = rc.rc_params_default(n_dirs=100)
+    p = rc.rc_params_default(n_dirs=0)
     assert L.rc_hemisphere_cast(ctypes.c_void_p(16), None, None, 1, ctypes.byref(p), None, None, None,
                                 None) == 1
     assert L.rc_classify(None, None, None) == 1

@@ -35,7 +35,7 @@ def _setup(rc, N, counts):
         Nn = torch.zeros_like(P)
         f = torch.zeros(n, dtype=torch.int32, device="cuda")
         rc.rc_sample_points(bvh.h, n, p, P, Nn, f)
-        ref_b = torch.zeros((n, N // 32), dtype=torch.int32, device="cuda")
+        ref_b = torch.zeros((n, (N + 31) // 32), dtype=torch.int32, device="cuda")
         ref_c = torch.zeros(n, dtype=torch.int32, device="cuda")
         rc.rc_hemisphere_cast(bvh.h, P, Nn, p, ref_b, ref_c)
         out.append(dict(bvh=bvh, P=P, N=Nn, ref_b=ref_b, ref_c=ref_c,
@@ -53,7 +53,7 @@ def _check(parts, N):
         assert c[0] == q["P"].shape[0] * N and c[3] == 0
 
 
-@pytest.mark.parametrize("N", [64, 512])
+@pytest.mark.parametrize("N", [64, 512, 150])
 def test_batch_equals_single_part(rc, N):
     counts = [1000, 777, 1500, 1, 333, 64]
     parts = _setup(rc, N, counts)
@@ -116,7 +116,7 @@ def test_single_part_knobs_do_not_change_results(rc):
                                                  (0, 0, 1, 0), (0, 0, 0, 2), (0, 0, 1, 2)):
                 q = rc.rc_params_default(n_dirs=N, point_order=order, tile_mode=tile, blocks_per_sm=per_sm,
                                          fetch_mode=fetch, launch_mode=launch, tree_width=width)
-                bits = torch.zeros((n, N // 32), dtype=torch.int32, device="cuda")
+                bits = torch.zeros((n, (N + 31) // 32), dtype=torch.int32, device="cuda")
                 cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
                 rc.rc_hemisphere_cast(bvh.h, P, Nn, q, bits, cnt)
                 res.append((bits, cnt))

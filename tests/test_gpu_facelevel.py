@@ -1,0 +1,101 @@
+"""The paper's face-level analysis (one point per face centroid, 150
+directions, area-weighted score) of STL files, through rc_analyze_stl,
+against rc_analyze_part on the same mesh and against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+from common import gpu_outcome, setup_outcomes, write_stl_ascii as _write_ascii, write_stl_binary as _write_binary
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2609_05467_gb300 as rc
+    rc.load()
+    return rc
+
+
+PARTS = {
+    "pocket": lambda: synth.pocket_block(2),
+    "multi_pocket": lambda: synth.box_with_pockets((100.0, 60.0, 40.0), (
+        ("+z", (35.0, 65.0), (15.0, 45.0), 15.0), ("+x", (10.0, 50.0), (10.0, 30.0), 10.0)), subdiv=1),
+    "prismatic_coarse": lambda: synth.prismatic(h=6.0),
+    "impeller_coarse": lambda: synth.impeller(h=4.0),
+}
+
+
+@pytest.mark.parametrize("name", list(PARTS))
+@pytest.mark.parametrize("N", [150, 64])
+def test_face_level_stl_matches_oracle(rc, tmp_path, name, N):
+    V0, F0 = PARTS[name]()
+    path = str(tmp_path / "part.stl")
+    (_write_ascii if name == "pocket" else _write_binary)(path, V0, F0)
+    V, F = rc.rc_stl_read(path)
+    L = 40.0
+    p = rc.rc_params_default(n_dirs=N, sample_mode=rc.RC_SAMPLE_FACE_CENTROID, always_setups=1, tool_length=L)
+    r = rc.rc_analyze_stl(path, 0, p)
+    # the same as rc_analyze_part on the mesh read back
+    W = (N + 31) // 32
+    bits = np.zeros((len(F), W), np.uint32)
+    cnt = np.zeros(len(F), np.int32)
+    mask = np.zeros(len(F), np.uint8)
+    r2 = rc.rc_analyze_part(V, F, len(F), p, bits=bits, count=cnt, mask=mask)
+    for k in ("overall_access", "overall_access_unweighted", "mean_conc", "n_points", "n_counted", "count_sum"):
+        assert getattr(r.summary, k) == getattr(r2.summary, k), k
+    assert list(r.summary.axis_share) == list(r2.summary.axis_share) and r.label == r2.label
+    assert gpu_outcome(r.setups) == gpu_outcome(r2.setups)
+    assert r.summary.n_points == len(F) and r.cast_counters[0] == len(F) * N
+    # the oracle: centroids, area weights, its own casts
+    P, Nn, f, w = oracle.sample_centroid(V, F)
+    m = oracle.Mesh(V, F)
+    ob, oa, oc = m.hemisphere(P, Nn, N)
+    amb = int(np.unpackbits(oa.view(np.uint8)).sum())
+    M, ac, dom, conc, c2 = oracle.variability(ob, Nn, N)
+    s = oracle.summary(c2, dom, conc, N, weight=w)
+    if amb == 0:
+        assert np.array_equal(bits, ob) and r.summary.overall_access == s["overall_access"]
+        assert list(r.summary.axis_share) == s["axis_share"] and r.summary.mean_conc == s["mean_conc"]
+        assert r.label == oracle.classify(s)
+    else:
+        # centroid rays on these meshes can meet other faces' edges exactly
+        assert abs(r.summary.overall_access - s["overall_access"]) <= max(1e-4, amb / (len(F) * N))
+    assert abs(r.summary.overall_access_unweighted - s["overall_access_unweighted"]) <= max(1e-4, amb / (len(F) * N))
+    om, oam = m.orthogonal(P, Nn)
+    tr = oracle.travel(V, P)
+    fx = oracle.fixture_faces(V, F)
+    outs, ocls, clean = setup_outcomes(om, oam, tr, f, fx, L)
+    if outs is not None:
+        assert gpu_outcome(r.setups) in outs
+    elif np.array_equal(mask, om):
+        ocls, oreach = oracle.face_classes(om, tr, f, fx, L)
+        assert r.setups.setups_exact == oracle.setups_exact(oreach[ocls == 0])[0]
+
+
+def test_face_level_paper_example_labels(rc, tmp_path):
+    """A block with one top pocket is a 3-axis part needing one setup once the
+    stock faces are excluded (the semantic expectation for this shape)."""
+    V, F = synth.pocket_block(2)
+    path = str(tmp_path / "block.stl")
+    _write_binary(path, V, F)
+    p = rc.rc_params_default(n_dirs=150, sample_mode=rc.RC_SAMPLE_FACE_CENTROID, always_setups=1, tool_length=40.0)
+    r = rc.rc_analyze_stl(path, 0, p)
+    assert r.setups_ran == 1 and r.setups.setups_exact == 1
+    assert r.summary.axis_share[2] == max(r.summary.axis_share)
+
+
+def test_analyze_stl_errors(rc, tmp_path):
+    p = rc.rc_params_default(n_dirs=150, sample_mode=rc.RC_SAMPLE_FACE_CENTROID)
+    with pytest.raises(rc.RcError):
+        rc.rc_analyze_stl(str(tmp_path / "missing.stl"), 0, p)
+    empty = str(tmp_path / "empty.stl")
+    _write_binary(empty, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32))
+    with pytest.raises(rc.RcError):
+        rc.rc_analyze_stl(empty, 0, p)

@@ -32,6 +32,15 @@ def _build(rc, V, F):
     return rc.Bvh(Vt, Ft)
 
 
+def _points(V, F, n, params):
+    """Sample points from the oracle's sampler (the library's own sampler is
+    compared with it bit for bit in test_sampling_bit_exact), so that no
+    GPU output is an input of the oracle's casts."""
+    if params.sample_mode == 1:
+        return oracle.sample_centroid(V, F)
+    return oracle.sample_area(V, F, n, seed=params.seed)
+
+
 def _sample(rc, bvh, n, params):
     P = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
     N = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
@@ -92,6 +101,11 @@ def test_direction_table_matches_oracle(rc):
 @pytest.mark.parametrize("name,n,N", [
     ("pocket", 1000, 256),          # configuration-1 geometry and sizes
     ("pocket", 37, 32),
+    ("pocket", 300, 150),           # the paper's 150 directions (last word padded)
+    ("prismatic_coarse", 333, 150),
+    ("cube", 50, 1),
+    ("cavity", 100, 7),
+    ("impeller_coarse", 120, 1000),
     ("cube", 200, 64),
     ("icosphere", 300, 96),
     ("cavity", 300, 64),
@@ -103,7 +117,7 @@ def test_hemisphere_parity(rc, name, n, N):
     V, F = PARTS[name]()
     bvh = _build(rc, V, F)
     p = rc.rc_params_default(n_dirs=N)
-    P, Nn, f, w = _sample(rc, bvh, n, p)
+    P, Nn, f, w = _points(V, F, n, p)
     gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
     ob, oa, oc = oracle.Mesh(V, F).hemisphere(P, Nn, N)
     cmp_, amb = compare_bits(gb, gc, ob, oa, oc, N)
@@ -117,7 +131,8 @@ def test_hemisphere_parity(rc, name, n, N):
 
 @pytest.mark.parametrize("mode", ["binary", "dynamic_fetch", "lane_lists", "packets", "packets_binary"])
 @pytest.mark.parametrize("name,n,N", [("pocket", 1000, 256), ("prismatic_coarse", 777, 160),
-                                       ("impeller_coarse", 500, 128), ("cavity", 300, 64)])
+                                       ("impeller_coarse", 500, 128), ("cavity", 300, 64),
+                                       ("prismatic_coarse", 333, 150), ("pocket", 90, 13)])
 def test_hemisphere_parity_other_traversals(rc, name, n, N, mode):
     """The binary-tree and dynamic-fetch traversals give the oracle's bits too."""
     V, F = PARTS[name]()
@@ -128,7 +143,7 @@ def test_hemisphere_parity_other_traversals(rc, name, n, N, mode):
         p = rc.rc_params_default(n_dirs=N, tree_width=2 if mode.endswith("binary") else 4, fetch_mode=3)
     else:
         p = rc.rc_params_default(n_dirs=N, tree_width=2, fetch_mode=1 if mode == "dynamic_fetch" else 0)
-    P, Nn, f, w = _sample(rc, bvh, n, p)
+    P, Nn, f, w = _points(V, F, n, p)
     gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
     ob, oa, oc = oracle.Mesh(V, F).hemisphere(P, Nn, N)
     compare_bits(gb, gc, ob, oa, oc, N)
@@ -141,14 +156,14 @@ def test_hemisphere_closed_forms_on_gpu(rc):
     for V, F, expect in ((*synth.cube(20.0, 2), 1), (*synth.icosphere(10.0, 3), 1)):
         bvh = _build(rc, V, F)
         p = rc.rc_params_default(n_dirs=128)
-        P, Nn, f, w = _sample(rc, bvh, 500, p)
+        P, Nn, f, w = _points(V, F, 500, p)
         gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
         assert (gc == 128).all()
         bvh.close()
     V, F = synth.cavity_box(subdiv=1)
     bvh = _build(rc, V, F)
     p = rc.rc_params_default(n_dirs=64)
-    P, Nn, f, w = _sample(rc, bvh, 600, p)
+    P, Nn, f, w = _points(V, F, 600, p)
     inner = (P.min(1) > 5) & (P.max(1) < 35)
     gb, gc, ctr = gpu_cast(rc, bvh.h, P[inner], Nn[inner], p)
     assert (gc == 0).all()
@@ -172,7 +187,7 @@ def test_cast_is_deterministic(rc):
     V, F = PARTS["prismatic_coarse"]()
     bvh = _build(rc, V, F)
     p = rc.rc_params_default(n_dirs=256)
-    P, Nn, f, w = _sample(rc, bvh, 2000, p)
+    P, Nn, f, w = _points(V, F, 2000, p)
     a = gpu_cast(rc, bvh.h, P, Nn, p)
     b = gpu_cast(rc, bvh.h, P, Nn, p)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
@@ -183,31 +198,33 @@ def test_cast_is_deterministic(rc):
 # Section 3.3 variability, classification
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("N", [256, 150])
 @pytest.mark.parametrize("conc_mode", [0, 1])
 @pytest.mark.parametrize("mode", ["area", "centroid"])
-def test_variability_parity(rc, conc_mode, mode):
+def test_variability_parity(rc, conc_mode, mode, N):
     V, F = PARTS["multi_pocket"]()
     bvh = _build(rc, V, F)
-    N = 256
     if mode == "area":
         p = rc.rc_params_default(n_dirs=N, conc_mode=conc_mode)
-        P, Nn, f, w = _sample(rc, bvh, 3000, p)
+        P, Nn, f, w = _points(V, F, 3000, p)
         wt = None
     else:
         p = rc.rc_params_default(n_dirs=N, conc_mode=conc_mode, sample_mode=rc.RC_SAMPLE_FACE_CENTROID)
-        P, Nn, f, w = _sample(rc, bvh, len(F), p)
+        P, Nn, f, w = _points(V, F, len(F), p)
         wt = torch.from_numpy(w).cuda()
     gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
+    ob, oa, oc = oracle.Mesh(V, F).hemisphere(P, Nn, N)
+    compare_bits(gb, gc, ob, oa, oc, N)
     n = len(P)
-    bits = torch.from_numpy(gb.view(np.int32).copy()).cuda()
+    # both sides reduce the oracle's bits (its ambiguous rays as it took them)
+    bits = torch.from_numpy(ob.view(np.int32).copy()).cuda()
     Nt = torch.from_numpy(Nn).cuda()
     acc = torch.zeros(n, dtype=torch.float32, device="cuda")
     dom = torch.zeros(n, dtype=torch.int8, device="cuda")
     conc = torch.zeros(n, dtype=torch.float32, device="cuda")
     dira = torch.zeros(N, dtype=torch.float64, device="cuda")
     s = rc.rc_direction_variability(bits, Nt, p, weight=wt, acc=acc, dom=dom, conc=conc, dir_area=dira)
-    # the oracle on the same bits
-    M, ac, odom, oconc, ocnt = oracle.variability(gb, Nn, N, conc_mode=conc_mode)
+    M, ac, odom, oconc, ocnt = oracle.variability(ob, Nn, N, conc_mode=conc_mode)
     assert np.array_equal(dom.cpu().numpy(), odom)
     assert np.array_equal(conc.cpu().numpy(), oconc.astype(np.float32))
     assert np.array_equal(acc.cpu().numpy(), (ocnt / N).astype(np.float32))
@@ -221,7 +238,7 @@ def test_variability_parity(rc, conc_mode, mode):
     # per-direction visible weight
     wq = oracle.quantised_weights(np.ones(n) if wt is None else w)
     scale = 1.0 if wt is None else w.max() / 16777216.0
-    expect = (unpack(gb, N) * wq[:, None]).sum(0).astype(np.float64) * scale
+    expect = (unpack(ob, N) * wq[:, None]).sum(0).astype(np.float64) * scale
     assert np.array_equal(dira.cpu().numpy(), expect)
     bvh.close()
 
@@ -247,7 +264,7 @@ def test_orthogonal_and_setups_parity(rc, name, frame):
     for mode in (rc.RC_SAMPLE_FACE_CENTROID, rc.RC_SAMPLE_AREA_RANDOM):
         p = rc.rc_params_default(sample_mode=mode, tool_length=30.0, **kw)
         n = len(F) if mode == rc.RC_SAMPLE_FACE_CENTROID else 2500
-        P, Nn, f, w = _sample(rc, bvh, n, p)
+        P, Nn, f, w = _points(V, F, n, p)
         Pt, Nt = torch.from_numpy(P).cuda(), torch.from_numpy(Nn).cuda()
         mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
         trav = torch.zeros((n, 6), dtype=torch.float32, device="cuda")
@@ -298,7 +315,7 @@ def test_edge_cases(rc):
         F = F[:T]
         bvh = _build(rc, V, F)
         p = rc.rc_params_default(n_dirs=64)
-        P, Nn, f, w = _sample(rc, bvh, 50, p)
+        P, Nn, f, w = _points(V, F, 50, p)
         gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
         ob, oa, oc = oracle.Mesh(V, F).hemisphere(P, Nn, 64)
         compare_bits(gb, gc, ob, oa, oc, 64)
@@ -311,9 +328,10 @@ def test_edge_cases(rc):
     rc.rc_hemisphere_cast(bvh.h, e, e, p, torch.zeros((0, 2), dtype=torch.int32, device="cuda"),
                           torch.zeros(0, dtype=torch.int32, device="cuda"))
     # bad n_dirs
-    with pytest.raises(rc.RcError) as ei:
-        rc.rc_hemisphere_cast(bvh.h, e, e, rc.rc_params_default(n_dirs=100), e, e)
-    assert ei.value.status == 1
+    for bad_n in (0, -3, 65537):
+        with pytest.raises(rc.RcError) as ei:
+            rc.rc_hemisphere_cast(bvh.h, e, e, rc.rc_params_default(n_dirs=bad_n), e, e)
+        assert ei.value.status == 1
     bvh.close()
     # invalid meshes are rejected
     Vt, Ft = gpu_mesh(V, F)
@@ -363,7 +381,7 @@ def test_refit_matches_rebuild(rc):
 def _full_size(rc, V, F, n, N, n_check, seed=0):
     bvh = _build(rc, V, F)
     p = rc.rc_params_default(n_dirs=N, seed=seed)
-    P, Nn, f, w = _sample(rc, bvh, n, p)
+    P, Nn, f, w = _points(V, F, n, p)
     gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
     assert ctr[0] == n * N and ctr[3] == 0
     rng = np.random.default_rng(seed + 1)

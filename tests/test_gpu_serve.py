@@ -22,7 +22,7 @@ def rc():
 
 
 def _alone(rc, V, F, n, p):
-    W = p.n_dirs // 32
+    W = (p.n_dirs + 31) // 32
     bits = np.zeros((n, W), np.uint32)
     cnt = np.zeros(n, np.int32)
     r = rc.rc_analyze_part(V, F, n, p, bits=bits, count=cnt)

@@ -58,7 +58,7 @@ def test_noalloc_variability_matches_allocating_entry_point():
         face = torch.zeros(n, dtype=torch.int32, device="cuda")
         w = torch.zeros(n, dtype=torch.float64, device="cuda")
         rc.rc_sample_points(bvh.h, n, p, P, Nn, face, w)
-        bits = torch.zeros((n, N // 32), dtype=torch.int32, device="cuda")
+        bits = torch.zeros((n, (N + 31) // 32), dtype=torch.int32, device="cuda")
         cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
         rc.rc_hemisphere_cast(bvh.h, P, Nn, p, bits, cnt)
         wt = w if mode == rc.RC_SAMPLE_FACE_CENTROID else None
