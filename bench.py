@@ -873,13 +873,121 @@ def run_facelevel(args):
     print(json.dumps(out), flush=True)
 
 
+def run_incremental(args):
+    """Re-analysis after an edit that keeps the triangle list: a local bump on
+    an impeller blade (default; 200,000 points), or the pocket block refined
+    to 458,752 triangles with its pocket deepened or moved (100,000 points);
+    1,024 directions.  One step = changed faces + points kept on their faces
+    + the update cast; compared with a full re-cast of the edited part at
+    the same points."""
+    import torch
+    import synth
+    import paper_2609_05467_gb300 as rc
+    rc.load()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    if args.edit == "bump":
+        V0, F = synth.impeller()
+        # a 0.3 mm bump of 4 mm radius on a blade, mid-span
+        r = np.hypot(V0[:, 0], V0[:, 1])
+        c = V0[np.argmin(np.abs(r - 55.0) + np.abs(V0[:, 2] - 25.0))].astype(np.float64)
+        V1 = synth.bump(V0, c, 4.0, 0.3, direction=(-c[1], c[0], 0.0))
+        edit = "a 0.3 mm bump of 4 mm radius on a blade"
+        name = "impeller (%d triangles)" % len(F)
+        default_n = 200_000
+    else:
+        V0, F = synth.perturbed_part(7, 0.0)
+        V1, _ = (synth.perturbed_part(7, 0.0, deepen_mm=2.0) if args.edit == "deepen" else synth.perturbed_part(7, 2.5))
+        edit = "pocket 2 mm deeper" if args.edit == "deepen" else "pocket moved 2.5 mm"
+        name = "pocket block refined to %d triangles" % len(F)
+        default_n = 100_000
+    n = args.points if args.points > 0 else default_n
+    N = 1024
+    p = rc.rc_params_default(n_dirs=N, seed=0)
+    Vt0, Vt1, Ft = (torch.from_numpy(V0).to(dev), torch.from_numpy(V1).to(dev), torch.from_numpy(F).to(dev))
+    b0, b1 = rc.Bvh(Vt0, Ft), rc.Bvh(Vt1, Ft)
+    P0 = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    N0 = torch.empty_like(P0)
+    f = torch.empty(n, dtype=torch.int32, device=dev)
+    rc.rc_sample_points(b0.h, n, p, P0, N0, f, None, stream)
+    W = (N + 31) // 32
+    bits0 = torch.empty((n, W), dtype=torch.int32, device=dev)
+    cnt0 = torch.empty(n, dtype=torch.int32, device=dev)
+    rc.rc_hemisphere_cast(b0.h, P0, N0, p, bits0, cnt0, None, stream)
+    P1, N1 = torch.empty_like(P0), torch.empty_like(P0)
+    changed = torch.empty(len(F), dtype=torch.uint8, device=dev)
+    bits, cnt = torch.empty_like(bits0), torch.empty_like(cnt0)
+    fb, fc = torch.empty_like(bits0), torch.empty_like(cnt0)
+    ctr = torch.zeros(4, dtype=torch.int64, device=dev)
+    fctr = torch.zeros(4, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def update():
+        bits.copy_(bits0)
+        cnt.copy_(cnt0)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nc, box = rc.rc_changed_faces(Vt0, Vt1, Ft, changed, stream)
+        rc.rc_sample_points_on_faces(b1.h, p, f, P1, N1, stream)
+        rc.rc_hemisphere_update(b1.h, P1, N1, f, changed, box, p, bits, cnt, ctr, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), nc
+
+    def full():
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc.rc_hemisphere_cast(b1.h, P1, N1, p, fb, fc, fctr, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        update()
+        full()
+    uuid = str(getattr(torch.cuda.get_device_properties(0), "uuid", "") or "")
+    if uuid and not uuid.startswith("GPU-"):
+        uuid = "GPU-" + uuid
+    clk = ClockSampler(uuid)
+    clk.start()
+    launches0 = rc.rc_launch_count()
+    tu, nc = zip(*[update() for _ in range(args.steps)])
+    launches = rc.rc_launch_count() - launches0
+    tf = [full() for _ in range(args.steps)]
+    clocks = clk.stop()
+    same = bool(torch.equal(bits, fb))
+    c, fcn = ctr.cpu().numpy(), fctr.cpu().numpy()
+    ms = float(np.mean(tu))
+    out = {
+        "metric": METRIC, "value": n * N / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "incremental: %s, %s (same triangle list, %d faces changed); %d points kept on "
+                               "their faces x %d directions; value = rays of the full result per second of update"
+                               % (name, edit, nc[0], n, N),
+                   "tris": int(len(F)), "points": n, "dirs": N, "l2": "flushed between steps (256 MB write)"},
+        "rays_cast_again": int(c[0]), "rays_total": n * N, "fraction_cast_again": float(c[0]) / (n * N),
+        "full_recast_ms": float(np.mean(tf)), "speedup_vs_full_recast": float(np.mean(tf)) / ms,
+        "same_bits_as_full_recast": same,
+        "quality": {"ambiguous_rays": int(c[1]), "full_ambiguous_rays": int(fcn[1]), "errors": int(c[3])},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+    b0.close()
+    b1.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="prismatic", choices=list(WORKLOADS) + ["served", "batched", "autoframe", "facelevel"])
+    ap.add_argument("--workload", default="prismatic", choices=list(WORKLOADS) + ["served", "batched", "autoframe", "facelevel",
+                                                                 "incremental"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--points", type=int, default=0, help="override the workload's point count (profiling runs)")
@@ -887,6 +995,8 @@ def main():
     ap.add_argument("--rate", type=float, default=20.0, help="served workload: arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="served workload: server slots")
     ap.add_argument("--parts", type=int, default=64, help="batched workload: number of parts")
+    ap.add_argument("--edit", default="bump", choices=["bump", "deepen", "shift"],
+                    help="incremental workload: the edit")
     ap.add_argument("--small-rays", type=float, default=4e6,
                     help="served workload: rays up to which a request runs at the highest priority")
     args = ap.parse_args()
@@ -903,6 +1013,9 @@ def main():
         return
     if args.workload == "facelevel":
         run_facelevel(args)
+        return
+    if args.workload == "incremental":
+        run_incremental(args)
         return
     wl = dict(WORKLOADS[args.workload])
     if args.points > 0:

@@ -469,6 +469,45 @@ rc_status rc_server_destroy(rc_server s);
 rc_status rc_setup_cover(const int64_t* h_mask_hist, rc_setups* out);
 
 /* ---------------------------------------------------------------------- */
+/* Re-analysis after an edit that keeps the triangle list                 */
+/* (interactive design, Sections 1 and 5; not a step of the paper)        */
+/* ---------------------------------------------------------------------- */
+
+/* Sample points kept on given faces: point i lies on d_face[i] of the
+ * part in h (typically edited since the points were drawn).  Area mode:
+ * at (1 - s) A + s (1 - u2) B + s u2 C, s = sqrt(u1), with point i's own
+ * counter-based u1, u2 (p->seed) -- on an unedited part exactly the point
+ * rc_sample_points drew; centroid mode: at the face centroid.  d_N gets
+ * the face normals.  Synchronises `stream`.  Errors: RC_E_ARG (a face id
+ * outside [0, T)), RC_E_CUDA. */
+rc_status rc_sample_points_on_faces(rc_bvh h, int64_t n, const rc_params* p, const int32_t* d_face, float* d_P,
+                                    float* d_N, void* stream);
+
+/* Faces whose vertices moved between d_V_old and d_V_new (bit-for-bit
+ * comparison, same triangle list d_F [T][3]): d_changed [T] = 1 / 0,
+ * *h_n_changed their number, h_box [6] (lo xyz, hi xyz) the bounding box
+ * of their old and new triangles (an empty box, lo > hi, when none moved).
+ * Synchronises `stream`.  Errors: RC_E_ARG (a vertex index outside
+ * [0, nV)), RC_E_CUDA. */
+rc_status rc_changed_faces(const float* d_V_old, const float* d_V_new, int64_t nV, const int32_t* d_F, int64_t T,
+                           uint8_t* d_changed, float* h_box, int64_t* h_n_changed, void* stream);
+
+/* Hemispherical cast of the edited part h, re-using the results of the
+ * unedited part: d_bits / d_count hold the old results of the same points
+ * (rc_sample_points_on_faces) on entry and the new ones on return.  Points
+ * on changed faces are cast in full; for the others only rays that can
+ * enter h_box (the conservative slab test of the traversal) are cast again,
+ * and a point whose tangent plane has the whole box behind it is skipped.
+ * The result equals rc_hemisphere_cast of the edited part at these points
+ * (rays decided by FP64-ambiguous pairs may differ, as between any two
+ * trees).  d_counters int64[4]: rays cast again, ambiguous, FP64
+ * re-tests, errors (may be NULL).  Asynchronous.  Errors: RC_E_ARG,
+ * RC_E_CUDA. */
+rc_status rc_hemisphere_update(rc_bvh h, const float* d_P, const float* d_N, const int32_t* d_face, int64_t n,
+                               const uint8_t* d_changed, const float* h_box, const rc_params* p, uint32_t* d_bits,
+                               int32_t* d_count, int64_t* d_counters, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* STL import and the paper's face-level analysis                         */
 /* ---------------------------------------------------------------------- */
 

@@ -59,6 +59,8 @@ def _L():
             lib.or_face_prep.argtypes = [P, P, i64, P, P, P]
             lib.or_sample_area.argtypes = [P, P, i64, i64, ctypes.c_uint64, P, P, P]
             lib.or_sample_area.restype = ctypes.c_int
+            lib.or_sample_on_faces.argtypes = [P, P, i64, i64, ctypes.c_uint64, ctypes.c_int, P, P, P]
+            lib.or_sample_on_faces.restype = i64
             lib.or_direction_table.argtypes = [i32, P, P]
             lib.or_ray_dirs.argtypes = [P, P, i32, P]
             lib.or_ray_origin.argtypes = [P, P, f64, P]
@@ -128,6 +130,22 @@ def sample_area(V, F, n, seed=0):
     if rc != 0:
         raise ValueError("part has no positive-area face")
     return P, Nn, fc, np.ones(n, np.float64)
+
+
+def sample_on_faces(V, F, face, seed=0, centroid=False):
+    """Points kept on the given faces (reading R9 of ``oracle.c``): point i
+    on face[i] at the position its own counter-based u1, u2 give (area
+    mode), or at the face centroid; with the face normals."""
+    V, F = _c(V, np.float32), _c(F, np.int32)
+    face = _c(face, np.int32)
+    n = len(face)
+    P = np.zeros((n, 3), np.float32)
+    Nn = np.zeros((n, 3), np.float32)
+    bad = _L().or_sample_on_faces(_p(V), _p(F), len(F), n, ctypes.c_uint64(seed), int(bool(centroid)), _p(face),
+                                  _p(P), _p(Nn))
+    if bad >= 0:
+        raise ValueError("face of point %d out of range" % bad)
+    return P, Nn
 
 
 def direction_table(N):

@@ -41,6 +41,11 @@
  *      otherwise AMBIGUOUS if some pair is ambiguous, otherwise MISS.
  *   R7 area sampling: splitmix64 counter stream; triangle chosen by an
  *      integer (2^32-quantised) area CDF; point by Osada et al. (2002).
+ *   R9 re-analysis of an edited part (same triangle list, moved vertices):
+ *      every sample point stays on its face -- in area mode at the position
+ *      its own u1, u2 give on the moved triangle, in centroid mode at the
+ *      moved centroid -- and the result is the full analysis of the edited
+ *      part at those points.
  *   R8 orthogonal eligibility: axis a is eligible for a point with normal n
  *      when n.a >= -parallel_tol (FP64, x, y, z order); a face parallel to
  *      the axis is side-milled, and the tolerance absorbs the tilt that fp32
@@ -124,6 +129,45 @@ void or_face_prep(const float* V, const int32_t* F, int64_t T, float* nrm, doubl
 /* ------------------------------------------------------------------------ */
 /* Sample points (Section 3.1 uses face centroids; the area-weighted random */
 /* mode is reading R7).                                                     */
+/* ------------------------------------------------------------------------ */
+/* Points kept on given faces (re-analysis of an edited part whose triangle  */
+/* list is unchanged, reading R9): point i lies on face[i] at the barycentric */
+/* position its own u1, u2 give in area mode; in centroid mode at the face   */
+/* centroid.  Returns the first out-of-range face position, or -1.          */
+/* ------------------------------------------------------------------------ */
+int64_t or_sample_on_faces(const float* V, const int32_t* F, int64_t T, int64_t n, uint64_t seed,
+                           int centroid, const int32_t* face, float* P, float* Nout)
+{
+    float* nrm = (float*)malloc(sizeof(float) * 3 * (size_t)(T > 0 ? T : 1));
+    float* cen = (float*)malloc(sizeof(float) * 3 * (size_t)(T > 0 ? T : 1));
+    double* area = (double*)malloc(sizeof(double) * (size_t)(T > 0 ? T : 1));
+    or_face_prep(V, F, T, nrm, area, cen);
+    int64_t bad = -1;
+    for (int64_t i = 0; i < n && bad < 0; ++i) {
+        const int64_t f = face[i];
+        if (f < 0 || f >= T) { bad = i; break; }
+        if (centroid) {
+            for (int k = 0; k < 3; ++k) { P[3 * i + k] = cen[3 * f + k]; Nout[3 * i + k] = nrm[3 * f + k]; }
+            continue;
+        }
+        double u1 = or_uniform(seed, i, 1), u2 = or_uniform(seed, i, 2);
+        double A[3], B[3], C[3];
+        load_vert(V, F[3 * f + 0], A);
+        load_vert(V, F[3 * f + 1], B);
+        load_vert(V, F[3 * f + 2], C);
+        double s = sqrt(u1);
+        double wa = 1.0 - s, wb = s * (1.0 - u2), wc = s * u2;
+        for (int k = 0; k < 3; ++k) {
+            double p = wa * A[k] + wb * B[k];
+            p = p + wc * C[k];
+            P[3 * i + k] = (float)p;
+            Nout[3 * i + k] = nrm[3 * f + k];
+        }
+    }
+    free(nrm); free(cen); free(area);
+    return bad;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Area mode.  Returns 0 on success, -1 when the part has no positive area. */
 int or_sample_area(const float* V, const int32_t* F, int64_t T, int64_t n, uint64_t seed,

@@ -192,6 +192,9 @@ def load(build_if_missing=True):
             "rc_analyze_part": ([P, i64, P, i64, i64, ctypes.POINTER(Params), P, P, P, P,
                                  ctypes.POINTER(PartResult), P], st),
             "rc_frame_candidates": ([P, ctypes.POINTER(Params), ctypes.POINTER(Frames), P], st),
+            "rc_sample_points_on_faces": ([P, i64, ctypes.POINTER(Params), P, P, P, P], st),
+            "rc_changed_faces": ([P, P, i64, P, i64, P, P, ctypes.POINTER(i64), P], st),
+            "rc_hemisphere_update": ([P, P, P, P, i64, P, P, ctypes.POINTER(Params), P, P, P, P], st),
             "rc_frame_select": ([P, P, P, P, i64, ctypes.POINTER(Params), ctypes.POINTER(Frames), P, P], st),
             "rc_stl_read": ([ctypes.c_char_p, P, i64, P, i64, ctypes.POINTER(i64), ctypes.POINTER(i64)], st),
             "rc_analyze_stl": ([ctypes.c_char_p, i64, ctypes.POINTER(Params), ctypes.POINTER(PartResult), P], st),
@@ -349,6 +352,27 @@ def rc_frame_select(h, P, N, face, params, frames, counters=None, stream=None):
     _check(load().rc_frame_select(ctypes.c_void_p(h), _ptr(P), _ptr(N), _ptr(face), P.shape[0],
                                   ctypes.byref(params), ctypes.byref(frames), _ptr(counters), _stream(stream)))
     return frames
+
+
+def rc_sample_points_on_faces(h, params, face, P, N, stream=None):
+    _check(load().rc_sample_points_on_faces(ctypes.c_void_p(h), face.shape[0], ctypes.byref(params), _ptr(face),
+                                            _ptr(P), _ptr(N), _stream(stream)))
+
+
+def rc_changed_faces(V_old, V_new, F, changed, stream=None):
+    """Returns (number of changed faces, box as a list lo xyz + hi xyz)."""
+    box = (ctypes.c_float * 6)()
+    nc = ctypes.c_int64()
+    _check(load().rc_changed_faces(_ptr(V_old), _ptr(V_new), V_old.shape[0], _ptr(F), F.shape[0], _ptr(changed),
+                                   box, ctypes.byref(nc), _stream(stream)))
+    return nc.value, list(box)
+
+
+def rc_hemisphere_update(h, P, N, face, changed, box, params, bits, count, counters=None, stream=None):
+    b = (ctypes.c_float * 6)(*[float(x) for x in box])
+    _check(load().rc_hemisphere_update(ctypes.c_void_p(h), _ptr(P), _ptr(N), _ptr(face), P.shape[0], _ptr(changed),
+                                       b, ctypes.byref(params), _ptr(bits), _ptr(count), _ptr(counters),
+                                       _stream(stream)))
 
 
 def rc_stl_read(path):

@@ -803,6 +803,104 @@ k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
 }
 
 // ---------------------------------------------------------------------------
+// Re-analysis after an edit that keeps the triangle list (reading: every
+// sample point stays on its face).  The result of a ray depends only on the
+// triangles it can meet; the edited triangles lie in the box [blo, bhi] in
+// both the old and the new part, so a ray from an unmoved point that cannot
+// enter that box (the conservative slab test of the traversal, monotone in
+// the box) keeps its old bit.  Points on moved faces are cast in full; an
+// unmoved point whose tangent plane has the whole box behind it (every
+// hemisphere direction has d.n > 0) is skipped outright.  Rays whose old
+// and new decisions are both made only by FP64-ambiguous pairs may differ
+// from a full re-cast; they are counted as ambiguous like any other.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool ray_enters_box(const Ray& r, const float4 lo, const float4 hi)
+{
+    const float rob = 1.0f + 2.0f * 1.7881394e-7f;
+    const bool sx = signbit(r.ix), sy = signbit(r.iy), sz = signbit(r.iz);
+    const float nx = ((sx ? hi.x : lo.x) - r.ox) * r.ix, fx = ((sx ? lo.x : hi.x) - r.ox) * r.ix;
+    const float ny = ((sy ? hi.y : lo.y) - r.oy) * r.iy, fy = ((sy ? lo.y : hi.y) - r.oy) * r.iy;
+    const float nz = ((sz ? hi.z : lo.z) - r.oz) * r.iz, fz = ((sz ? lo.z : hi.z) - r.oz) * r.iz;
+    const float tn = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.0f));
+    const float tf = fminf(fminf(fx, fy), fz) * rob;
+    return tn <= tf;
+}
+
+// max over the box corners of (c - o).n in FP64, with its rounding bound
+__device__ __forceinline__ bool box_in_front(const float4 lo, const float4 hi, float ox, float oy, float oz, float nx,
+                                             float ny, float nz)
+{
+    double best = -INFINITY, mag = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        const double x = __dsub_rn((double)((c & 1) ? hi.x : lo.x), (double)ox);
+        const double y = __dsub_rn((double)((c & 2) ? hi.y : lo.y), (double)oy);
+        const double z = __dsub_rn((double)((c & 4) ? hi.z : lo.z), (double)oz);
+        const double a = __dmul_rn(x, (double)nx), b = __dmul_rn(y, (double)ny), e = __dmul_rn(z, (double)nz);
+        best = fmax(best, __dadd_rn(__dadd_rn(a, b), e));
+        mag = fmax(mag, __dadd_rn(__dadd_rn(fabs(a), fabs(b)), fabs(e)));
+    }
+    return best > -1e-12 * mag;
+}
+
+template <bool kWide>
+__global__ void __launch_bounds__(128, RC_HEMI_MIN_BLOCKS)
+k_hemisphere_update(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps,
+                    float scene_maxabs, const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
+                    const int32_t* __restrict__ order, const int32_t* __restrict__ face,
+                    const uint8_t* __restrict__ changed, float4 blo, float4 bhi, const float4* __restrict__ tdirs,
+                    int n_dirs, double eps, uint32_t* __restrict__ bits, int32_t* __restrict__ count,
+                    unsigned long long* counters, unsigned long long* work)
+{
+    extern __shared__ uint32_t s_rows[];
+    const int lane = threadIdx.x & 31;
+    const int W = (n_dirs + 31) >> 5;
+    uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
+    CastAcc acc;
+    for (;;) {
+        unsigned long long k = 0;
+        if (lane == 0) k = atomicAdd(work, 1ULL);
+        k = __shfl_sync(0xFFFFFFFFu, k, 0);
+        if (k >= (unsigned long long)n) break;
+        const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
+        const bool moved = changed[face[i]] != 0;
+        const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
+        const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
+        const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
+        if (!moved && !box_in_front(blo, bhi, ox, oy, oz, nx, ny, nz)) continue;   // nothing can change
+        for (int w = lane; w < W; w += 32) row[w] = moved ? 0u : bits[i * W + w];
+        __syncwarp();
+        const Onb b = make_onb(nx, ny, nz);
+        for (int t = 0; t < W; ++t) {
+            const float4 h = __ldg(&tdirs[32 * t + lane]);
+            const int j = __float_as_int(h.w);
+            if (j < 0) continue;
+            float dx, dy, dz;
+            local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
+            Ray r;
+            setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
+            if (!moved && !ray_enters_box(r, blo, bhi)) continue;              // keeps its old bit
+            const TraceOut tr = trace_any<false, kWide>(nodes, tris, r, max_steps);
+            acc.retests += tr.retests;
+            acc.overflow += tr.overflow;
+            acc.amb += (tr.flags >> 1) & 1;
+            acc.rays += 1;
+            if ((tr.flags & 1) == 0) atomicOr(&row[j >> 5], 1u << (j & 31));
+            else atomicAnd(&row[j >> 5], ~(1u << (j & 31)));
+        }
+        __syncwarp();
+        int cnt = 0;
+        for (int w = lane; w < W; w += 32) {
+            bits[i * W + w] = row[w];
+            cnt += __popc(row[w]);
+        }
+        for (int off = 16; off; off >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, off);
+        if (lane == 0) count[i] = cnt;
+        __syncwarp();
+    }
+    warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow);
+}
+
+// ---------------------------------------------------------------------------
 // Hemispherical cast with dynamic ray fetch (after Aila and Laine, HPG 2009):
 // the same rays and decisions as k_hemisphere, but a lane whose ray has
 // finished takes the next ray at once instead of waiting for the rest of its
@@ -1245,6 +1343,52 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
     }
     RC_LAUNCHED();
     if (work_alloc) RC_CUDA(cudaFreeAsync(work_alloc, s));
+    if (order) RC_CUDA(cudaFreeAsync(order, s));
+    return RC_OK;
+}
+
+// Re-analysis of the points after an edit (see k_hemisphere_update); bits
+// and count hold the old results on entry.
+rc_status launch_hemisphere_update(rc_bvh h, const float* P, const float* N, int64_t n, const int32_t* face,
+                                   const uint8_t* changed, const float box[6], const float4* tdirs,
+                                   const rc_params* p, uint32_t* bits, int32_t* count, unsigned long long* counters,
+                                   cudaStream_t s)
+{
+    unsigned long long* work = nullptr;
+    RC_CUDA(cudaMallocAsync(&work, sizeof(unsigned long long), s));
+    RC_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
+    int32_t* order = nullptr;
+    if (p->point_order == 0 && n > 1) {
+        RC_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * n, s));
+        rc_status st = point_order(h, P, n, order, s);
+        if (st != RC_OK) return st;
+    }
+    const int threads = 128;
+    const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_HEMI_MIN_BLOCKS;
+    int64_t blocks = (int64_t)sm_count() * per_sm;
+    const int64_t need = (n * 32 + threads - 1) / threads;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    const size_t smem = (size_t)(threads / 32) * ((p->n_dirs + 31) / 32) * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        RC_CUDA(cudaFuncSetAttribute(k_hemisphere_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RC_CUDA(cudaFuncSetAttribute(k_hemisphere_update<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    const float4 lo = make_float4(box[0], box[1], box[2], 0.0f), hi = make_float4(box[3], box[4], box[5], 0.0f);
+    if (use_wide(p))
+        k_hemisphere_update<true><<<(unsigned)blocks, threads, smem, s>>>(h->wnodes, h->tris, max_steps(h),
+                                                                         h->scene_maxabs, P, N, n, order, face,
+                                                                         changed, lo, hi, tdirs, p->n_dirs,
+                                                                         p->origin_offset, bits, count, counters,
+                                                                         work);
+    else
+        k_hemisphere_update<false><<<(unsigned)blocks, threads, smem, s>>>(h->nodes, h->tris, max_steps(h),
+                                                                          h->scene_maxabs, P, N, n, order, face,
+                                                                          changed, lo, hi, tdirs, p->n_dirs,
+                                                                          p->origin_offset, bits, count, counters,
+                                                                          work);
+    RC_LAUNCHED();
+    RC_CUDA(cudaFreeAsync(work, s));
     if (order) RC_CUDA(cudaFreeAsync(order, s));
     return RC_OK;
 }

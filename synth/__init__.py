@@ -25,6 +25,8 @@ Generators
   void's surface is blocked).
 - :func:`deep_hole` -- block with one narrow deep square hole.
 - :func:`rotate90` -- exact 90-degree rotation / axis permutation of a mesh.
+- :func:`bump` -- a local smooth bump of a mesh (vertices within a radius
+  pushed along a direction; the triangle list is unchanged): a local edit.
 - :func:`rotation`, :func:`rotate` -- a rotation matrix from Euler angles and
   a mesh turned by it (vertices rounded to fp32): parts that do not sit in
   their machining frame.
@@ -38,7 +40,7 @@ import numpy as np
 __all__ = [
     "pocket_block", "prismatic", "impeller", "cube", "icosphere", "cavity_box",
     "deep_hole", "box_with_pockets", "rotate90", "subdivide", "marching_tets",
-    "part_family", "perturbed_part", "rotation", "rotate",
+    "part_family", "perturbed_part", "rotation", "rotate", "bump",
 ]
 
 
@@ -248,6 +250,21 @@ def rotate90(V, axis, k=1):
         va, vb = V[:, a].copy(), V[:, b].copy()
         V[:, a], V[:, b] = -vb, va
     return V
+
+
+def bump(V, centre, radius, height, direction=(0.0, 0.0, 1.0)):
+    """Vertices within ``radius`` of ``centre`` moved by height * (1 -
+    (d / radius)^2)^2 along ``direction`` (FP64, rounded to fp32); the others
+    are unchanged bit for bit."""
+    V64 = np.asarray(V, np.float64)
+    d = np.linalg.norm(V64 - np.asarray(centre, np.float64), axis=1)
+    w = np.where(d < radius, (1.0 - (d / radius) ** 2) ** 2, 0.0)
+    u = np.asarray(direction, np.float64)
+    u = u / np.linalg.norm(u)
+    out = np.asarray(V, np.float32).copy()
+    sel = w > 0
+    out[sel] = (V64[sel] + height * w[sel, None] * u).astype(np.float32)
+    return out
 
 
 def rotation(rx_deg=0.0, ry_deg=0.0, rz_deg=0.0):
@@ -492,10 +509,12 @@ def part_family(family, target_tris, rng):
     return impeller(h=0.69 * sc * math.sqrt(1.93e6 / max(target_tris, 1000)), scale=sc)
 
 
-def perturbed_part(subdiv, shift_mm, size=(100.0, 60.0, 40.0), width=30.0, depth=15.0):
-    """Pocket block whose pocket is moved ``shift_mm`` along x.  The mesh has
-    the same triangle list ``F`` as the unshifted block, so a BVH built for
-    one can be refitted to the other."""
+def perturbed_part(subdiv, shift_mm, size=(100.0, 60.0, 40.0), width=30.0, depth=15.0, deepen_mm=0.0):
+    """Pocket block whose pocket is moved ``shift_mm`` along x and sunk
+    ``deepen_mm`` deeper.  The mesh has the same triangle list ``F`` as the
+    unedited block, so a BVH built for one can be refitted to the other.
+    Moving the pocket moves every vertex of the top face's ring around it;
+    deepening moves only the pocket's walls and floor."""
     cx, cy = size[0] / 2 + shift_mm, size[1] / 2
     h = width / 2
-    return box_with_pockets(size, (("+z", (cx - h, cx + h), (cy - h, cy + h), depth),), subdiv)
+    return box_with_pockets(size, (("+z", (cx - h, cx + h), (cy - h, cy + h), depth + deepen_mm),), subdiv)

@@ -466,3 +466,38 @@ def test_accessibility_rotation_invariant(orc):
         _, _, cnt = orc.Mesh(VV, F).hemisphere(P, Nn, 1024)
         out.append(orc.summary(cnt, np.zeros(len(cnt), np.int8), np.zeros(len(cnt)), 1024, w))
     assert abs(out[0]["overall_access"] - out[1]["overall_access"]) < 5e-3
+
+
+# ---------------------------------------------------------------------------
+# points kept on their faces (re-analysis of an edited part)
+# ---------------------------------------------------------------------------
+
+def test_points_on_faces_reproduce_sampling_and_follow_the_edit(orc):
+    V0, F = synth.perturbed_part(2, 0.0)
+    V1, F1 = synth.perturbed_part(2, 3.0)
+    assert np.array_equal(F, F1) and not np.array_equal(V0, V1)
+    P, Nn, f, _ = orc.sample_area(V0, F, 3000, seed=7)
+    # on the unedited part: exactly the sampler's points
+    Q, Qn = orc.sample_on_faces(V0, F, f, seed=7)
+    assert np.array_equal(Q, P) and np.array_equal(Qn, Nn)
+    # on the edited part: same barycentric position on the moved triangle
+    R, Rn = orc.sample_on_faces(V1, F, f, seed=7)
+    tri = V1.astype(np.float64)[F[f]]
+    e1, e2, d = tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0], R.astype(np.float64) - tri[:, 0]
+    # barycentrics by least squares: both within [0, 1] and summing to <= 1
+    G = np.stack([e1, e2], axis=2)
+    lam = np.linalg.lstsq(G[0], d[0], rcond=None)[0]
+    for k in range(0, len(f), 97):
+        lam = np.linalg.lstsq(G[k], d[k], rcond=None)[0]
+        assert lam.min() >= -1e-5 and lam.sum() <= 1 + 1e-5
+    moved = (V0[F[f]] != V1[F[f]]).any(axis=(1, 2))
+    assert moved.any() and (~moved).any()
+    assert np.array_equal(R[~moved], P[~moved]) and not np.array_equal(R[moved], P[moved])
+    n1, _, _ = orc.face_prep(V1, F)
+    assert np.array_equal(Rn, n1[f])
+    # centroid mode: the moved centroids
+    C, Cn = orc.sample_on_faces(V1, F, np.arange(len(F), dtype=np.int32), centroid=True)
+    c1, cn1, _, _ = orc.sample_centroid(V1, F)
+    assert np.array_equal(C, c1) and np.array_equal(Cn, cn1)
+    with pytest.raises(ValueError):
+        orc.sample_on_faces(V1, F, np.array([0, len(F)], np.int32))
