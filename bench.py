@@ -510,7 +510,8 @@ def run_served(args):
         return out, time.perf_counter() - t0
 
     # continuous batching through the server
-    srv = rc.rc_server_create(ps, slots=args.slots, hbm_budget_bytes=120 << 30, small_rays=int(args.small_rays))
+    srv = rc.rc_server_create(ps, slots=args.slots, hbm_budget_bytes=120 << 30, small_rays=int(args.small_rays),
+                              incremental=int(args.incremental))
     lat_holder = {}
 
     def s_submit(r, t0):
@@ -521,7 +522,8 @@ def run_served(args):
         res = rc.rc_server_wait(srv, rid, timeout_s=600.0)
         return dict(lat=res.t_end - res.t_submit, rays=res.result.cast_counters[0] + res.result.ortho_counters[0],
                     rebuilt=res.rebuilt, status=res.status, wait=res.t_start - res.t_submit,
-                    level=res.priority_level, tris=len(r["F"]), n=r["n"], arrival=r["t"])
+                    level=res.priority_level, tris=len(r["F"]), n=r["n"], arrival=r["t"], updated=res.updated,
+                    resub=r["resub"])
     # warm-up pass over a few requests (module load, tables, pools)
     for r in reqs[:3]:
         rc.rc_server_wait(srv, rc.rc_server_submit(srv, 10**9 + r["key"], r["V"], r["F"], r["n"]), 600.0)
@@ -543,7 +545,8 @@ def run_served(args):
             res = rc.rc_analyze_part(r["V"], r["F"], r["n"], p)
         t_end = time.perf_counter()
         return dict(lat=t_end - tsub, rays=res.cast_counters[0] + res.ortho_counters[0],
-                    rebuilt=1, status=0, wait=t_run - tsub, level=0, tris=len(r["F"]), n=r["n"], arrival=r["t"])
+                    rebuilt=1, status=0, wait=t_run - tsub, level=0, tris=len(r["F"]), n=r["n"], arrival=r["t"],
+                    resub=r["resub"])
     plain, wall_p = replay(p_submit, p_collect)
 
     def summ(x, wall):
@@ -561,6 +564,10 @@ def run_served(args):
                            "tris": int(x[k]["tris"]), "points": int(x[k]["n"]), "level": int(x[k]["level"]),
                            "rebuilt": int(x[k]["rebuilt"]), "arrival_s": round(float(x[k]["arrival"]), 3)}
                           for k in slow]
+        rs = np.array([bool(d["resub"]) for d in x])
+        if rs.any():
+            out["resubmissions"] = {"requests": int(rs.sum()), "p50_ms": float(np.percentile(lat[rs], 50)),
+                                    "p99_ms": float(np.percentile(lat[rs], 99))}
         for name, lo, hi in (("lt_50k", 0, 5e4), ("100k_400k", 1e5, 4e5), ("gt_400k", 4e5, 1e12)):
             sel = lat[(tr >= lo) & (tr < hi)]
             if len(sel):
@@ -579,10 +586,14 @@ def run_served(args):
                                                                               int(np.median(tris))),
                    "slots": args.slots, "hbm_budget_gb": 120, "small_rays": args.small_rays,
                    "server_cast": "one warp per point (short blocks), small requests on high-priority streams",
-                   "plain": "rc_analyze_part per request, FIFO, one at a time, persistent grid"},
+                   "plain": "rc_analyze_part per request, FIFO, one at a time, persistent grid",
+                   "incremental": "re-submissions with the same triangle list keep their points on their faces "
+                                  "and cast only what the edit can change" if args.incremental else "off"},
         "served": sv, "plain_one_at_a_time": pl,
         "server_stats": {k: getattr(stats, k) for k in ("completed", "failed", "rejected", "evicted")},
         "refits": int(sum(1 for d in served if d["rebuilt"] == 0)),
+        "incremental": bool(args.incremental),
+        "incremental_updates": int(sum(1 for d in served if d.get("updated"))),
         "requests": len(reqs),
     }
     print(json.dumps(out), flush=True)
@@ -995,6 +1006,7 @@ def main():
     ap.add_argument("--rate", type=float, default=20.0, help="served workload: arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="served workload: server slots")
     ap.add_argument("--parts", type=int, default=64, help="batched workload: number of parts")
+    ap.add_argument("--incremental", action="store_true", help="served workload: incremental re-analysis")
     ap.add_argument("--edit", default="bump", choices=["bump", "deepen", "shift"],
                     help="incremental workload: the edit")
     ap.add_argument("--small-rays", type=float, default=4e6,

@@ -414,6 +414,12 @@ typedef struct {
     int64_t hbm_budget_bytes;   /* admission budget for resident parts plus running requests */
     int64_t small_rays;         /* requests with at most this many hemisphere rays run at the highest
                                    stream priority, each doubling one level lower (0 = all at the lowest) */
+    int32_t incremental;        /* 1: a re-submission with the same triangle list and point count keeps the
+                                   part's sample points on their faces (rc_sample_points_on_faces) and casts
+                                   again only what the edit can change (rc_changed_faces +
+                                   rc_hemisphere_update); its result is the analysis of the edited part at
+                                   those points.  0: every request samples afresh */
+    int32_t pad;
 } rc_server_config;
 
 typedef struct {
@@ -423,6 +429,8 @@ typedef struct {
     int32_t slot;               /* worker slot that ran it */
     int32_t rebuilt;            /* 1 = BVH built, 0 = refitted */
     int32_t priority_level;     /* stream priority level it ran at (0 = highest) */
+    int32_t updated;            /* 1 = incremental re-analysis (cfg.incremental), 0 = full analysis */
+    int32_t pad;
     double t_submit, t_admit, t_start, t_end;   /* steady-clock seconds */
     int64_t resident_bytes;     /* device bytes the part keeps resident */
     rc_part_result result;

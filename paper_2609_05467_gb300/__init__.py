@@ -112,14 +112,15 @@ class PartResult(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("cast_blocks_per_sm", ctypes.c_int32),
-                ("hbm_budget_bytes", ctypes.c_int64), ("small_rays", ctypes.c_int64)]
+                ("hbm_budget_bytes", ctypes.c_int64), ("small_rays", ctypes.c_int64),
+                ("incremental", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class RequestResult(ctypes.Structure):
     _fields_ = [
         ("request_id", ctypes.c_int64), ("part_key", ctypes.c_uint64), ("status", ctypes.c_int),
         ("slot", ctypes.c_int32), ("rebuilt", ctypes.c_int32), ("priority_level", ctypes.c_int32),
-        ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_start", ctypes.c_double),
+        ("updated", ctypes.c_int32), ("pad", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_start", ctypes.c_double),
         ("t_end", ctypes.c_double), ("resident_bytes", ctypes.c_int64), ("result", PartResult),
         ("message", ctypes.c_char * 128),
     ]
@@ -454,8 +455,9 @@ def rc_batch_destroy(b):
     _check(load().rc_batch_destroy(ctypes.c_void_p(b)))
 
 
-def rc_server_create(params, slots=4, hbm_budget_bytes=120 << 30, cast_blocks_per_sm=0, small_rays=0):
-    cfg = ServerConfig(slots, cast_blocks_per_sm, hbm_budget_bytes, small_rays)
+def rc_server_create(params, slots=4, hbm_budget_bytes=120 << 30, cast_blocks_per_sm=0, small_rays=0,
+                     incremental=0):
+    cfg = ServerConfig(slots, cast_blocks_per_sm, hbm_budget_bytes, small_rays, incremental, 0)
     s = ctypes.c_void_p()
     _check(load().rc_server_create(ctypes.byref(params), ctypes.byref(cfg), ctypes.byref(s)))
     return s.value

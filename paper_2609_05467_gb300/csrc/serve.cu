@@ -4,7 +4,8 @@
 // concurrently on the slots' streams, so their work overlaps on the GPU.
 // Each part's BVH, sample points and visibility maps stay resident, keyed by
 // the caller's part key; a re-submission with the same triangle list is
-// refitted instead of rebuilt.
+// refitted instead of rebuilt, and with cfg.incremental its points stay on
+// their faces and only the rays the edit can change are cast again.
 #include <string.h>
 
 #include <chrono>
@@ -208,7 +209,24 @@ static rc_status run_request(rc_server s, SrvRequest* r, SrvEntry* e, cudaStream
     SRV_CUDA(cudaMallocAsync(&dV, sizeof(float) * 3 * r->nV, st));
     SRV_CUDA(cudaMemcpyAsync(dV, r->V.data(), sizeof(float) * 3 * r->nV, cudaMemcpyHostToDevice, st));
     rc_status rs;
-    if (e->h && e->T == r->T && e->nV == r->nV && e->fhash == fh) {
+    const bool same_topology = e->h && e->T == r->T && e->nV == r->nV && e->fhash == fh;
+    // incremental re-analysis: same triangle list, point count and directions,
+    // and the resident results of the previous request on this key
+    const bool incremental = s->cfg.incremental && same_topology && e->P && e->n == r->n && e->N == N && r->n > 0;
+    uint8_t* changed = nullptr;
+    float box[6];
+    int64_t n_changed = 0;
+    if (incremental) {
+        // compare with the resident vertices before the refit replaces them
+        SRV_CUDA(cudaMallocAsync(&changed, (size_t)r->T, st));
+        rs = rc_changed_faces(e->h->V, dV, r->nV, e->h->F, r->T, changed, box, &n_changed, st);
+        if (rs != RC_OK) {
+            cudaFreeAsync(changed, st);
+            cudaFreeAsync(dV, st);
+            return rs;
+        }
+    }
+    if (same_topology) {
         rs = rc_refit_bvh(e->h, dV, st);
         r->res.rebuilt = 0;
     } else {
@@ -221,7 +239,10 @@ static rc_status run_request(rc_server s, SrvRequest* r, SrvEntry* e, cudaStream
     }
     cudaFreeAsync(dV, st);
     if (dF) cudaFreeAsync(dF, st);
-    if (rs != RC_OK) return rs;
+    if (rs != RC_OK) {
+        if (changed) cudaFreeAsync(changed, st);
+        return rs;
+    }
     e->T = r->T;
     e->nV = r->nV;
     e->fhash = fh;
@@ -244,8 +265,18 @@ static rc_status run_request(rc_server s, SrvRequest* r, SrvEntry* e, cudaStream
     }
     e->n = n;
     rc_part_result& o = r->res.result;
-    SRV_TRY(rc_sample_points(e->h, n, &p, e->P, e->Nn, e->face, nullptr, st));
-    SRV_TRY(rc_hemisphere_cast(e->h, e->P, e->Nn, n, &p, e->bits, e->count, e->ctr, st));
+    if (incremental) {
+        rs = rc_sample_points_on_faces(e->h, n, &p, e->face, e->P, e->Nn, st);
+        if (rs == RC_OK)
+            rs = rc_hemisphere_update(e->h, e->P, e->Nn, e->face, n, changed, box, &p, e->bits, e->count, e->ctr,
+                                      st);
+        cudaFreeAsync(changed, st);
+        if (rs != RC_OK) return rs;
+        r->res.updated = 1;
+    } else {
+        SRV_TRY(rc_sample_points(e->h, n, &p, e->P, e->Nn, e->face, nullptr, st));
+        SRV_TRY(rc_hemisphere_cast(e->h, e->P, e->Nn, n, &p, e->bits, e->count, e->ctr, st));
+    }
     SRV_TRY(rc_direction_variability(e->bits, e->Nn, nullptr, n, &p, nullptr, nullptr, nullptr, nullptr, &o.summary,
                                      st));
     SRV_TRY(rc_classify(&o.summary, &p, &o.label));
@@ -331,6 +362,7 @@ rc_status rc_server_create(const rc_params* p, const rc_server_config* cfg, rc_s
     if (st != RC_OK) return st;
     if (cfg->slots < 1 || cfg->slots > 64) return set_error(RC_E_ARG, "slots must be in [1, 64]");
     if (cfg->hbm_budget_bytes <= 0) return set_error(RC_E_ARG, "hbm_budget_bytes must be positive");
+    if (cfg->incremental != 0 && cfg->incremental != 1) return set_error(RC_E_ARG, "incremental must be 0 or 1");
     rc_server s = new rc_server_s();
     s->p = *p;
     s->cfg = *cfg;

@@ -93,3 +93,50 @@ def test_budget_rejection_and_failure_isolation(rc):
     with pytest.raises(rc.RcError):
         rc.rc_server_wait(srv, 12345, timeout_s=0.1)            # unknown id
     rc.rc_server_destroy(srv)
+
+
+def test_incremental_resubmission_equals_the_standalone_chain(rc):
+    """With cfg.incremental a re-submission with the same triangle list keeps
+    the points on their faces and casts only what the edit can change; its
+    bits and summary equal a full cast of the edited part at those points."""
+    p = rc.rc_params_default(n_dirs=256, always_setups=1, tool_length=40.0, seed=4)
+    V0, F = synth.perturbed_part(3, 0.0)
+    V1, _ = synth.perturbed_part(3, 2.0, deepen_mm=1.5)
+    n = 3000
+    srv = rc.rc_server_create(p, slots=2, hbm_budget_bytes=4 << 30, incremental=1)
+    a = rc.rc_server_wait(srv, rc.rc_server_submit(srv, 7, V0, F, n), timeout_s=120.0)
+    b = rc.rc_server_wait(srv, rc.rc_server_submit(srv, 7, V1, F, n), timeout_s=120.0)
+    c = rc.rc_server_wait(srv, rc.rc_server_submit(srv, 7, V1, F, n + 1), timeout_s=120.0)   # other n: full
+    assert a.status == b.status == c.status == 0
+    assert (a.updated, b.updated, c.updated) == (0, 1, 0) and b.rebuilt == 0
+    assert 0 < b.result.cast_counters[0] < n * 256
+    rb, rcnt = rc.rc_server_read_bits(srv, 7, n + 1, 256)
+    rc.rc_server_destroy(srv)
+    # standalone chain on the GPU: sample on the unedited part, keep the
+    # points on their faces on the edited one, cast in full
+    srv = rc.rc_server_create(p, slots=1, hbm_budget_bytes=4 << 30, incremental=1)
+    rc.rc_server_wait(srv, rc.rc_server_submit(srv, 8, V0, F, n), timeout_s=120.0)
+    b2 = rc.rc_server_wait(srv, rc.rc_server_submit(srv, 8, V1, F, n), timeout_s=120.0)
+    ub, ucnt = rc.rc_server_read_bits(srv, 8, n, 256)
+    rc.rc_server_destroy(srv)
+    b0 = rc.Bvh(torch.from_numpy(V0).cuda(), torch.from_numpy(F).cuda())
+    b1 = rc.Bvh(torch.from_numpy(V1).cuda(), torch.from_numpy(F).cuda())
+    P = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    Nn = torch.zeros_like(P)
+    f = torch.zeros(n, dtype=torch.int32, device="cuda")
+    rc.rc_sample_points(b0.h, n, p, P, Nn, f)
+    rc.rc_sample_points_on_faces(b1.h, p, f, P, Nn)
+    bits = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    rc.rc_hemisphere_cast(b1.h, P, Nn, p, bits, cnt)
+    s = rc.rc_direction_variability(bits, Nn, p)
+    torch.cuda.synchronize()
+    assert np.array_equal(ub, bits.cpu().numpy().view(np.uint32)) and np.array_equal(ucnt, cnt.cpu().numpy())
+    assert b2.result.summary.overall_access == s.overall_access and b2.result.summary.mean_conc == s.mean_conc
+    assert b.result.summary.overall_access == s.overall_access
+    # the full request that followed (other n) is the ordinary analysis
+    alone, bits_a, cnt_a = _alone(rc, V1, F, n + 1, p)
+    _same(c.result, alone)
+    assert np.array_equal(rb, bits_a)
+    b0.close()
+    b1.close()
