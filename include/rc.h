@@ -168,6 +168,20 @@ int64_t rc_launch_count(void);
 rc_status rc_build_bvh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t T, void* stream,
                        rc_bvh* out);
 
+/* Binary-tree builders for rc_build_bvh_ex. */
+enum { RC_BUILDER_KARRAS = 0, RC_BUILDER_PLOC = 1 };
+
+/* rc_build_bvh with a choice of the binary tree under the 4-wide tree:
+ * RC_BUILDER_KARRAS (rc_build_bvh's: the binary radix tree of the sorted
+ * Morton codes, Karras 2012) or RC_BUILDER_PLOC (parallel locally-ordered
+ * clustering, Meister and Bittner 2018: mutual nearest neighbours by merged
+ * surface area within 16 positions of the Morton order, merged round by
+ * round; fewer node visits per ray, a slower build).  Both give the same
+ * casts' results (up to rays decided by FP64-ambiguous pairs).  Errors: as
+ * rc_build_bvh, and RC_E_ARG for an unknown builder. */
+rc_status rc_build_bvh_ex(const float* d_V, int64_t nV, const int32_t* d_F, int64_t T, int32_t builder,
+                          void* stream, rc_bvh* out);
+
 /* Refit an existing handle to moved vertices of the same triangle list
  * (same F, same nV): recomputes face data, leaf and node boxes bottom-up
  * and the area CDF; the tree topology is kept.  Synchronises `stream`.

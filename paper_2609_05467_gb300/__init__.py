@@ -163,6 +163,7 @@ def load(build_if_missing=True):
             "rc_last_error": ([], ctypes.c_char_p),
             "rc_launch_count": ([], i64),
             "rc_build_bvh": ([P, i64, P, i64, P, ctypes.POINTER(P)], st),
+            "rc_build_bvh_ex": ([P, i64, P, i64, i32, P, ctypes.POINTER(P)], st),
             "rc_refit_bvh": ([P, P, P], st),
             "rc_destroy_bvh": ([P], st),
             "rc_bvh_get_info": ([P, ctypes.POINTER(BvhInfo)], st),
@@ -254,6 +255,17 @@ def rc_build_bvh(V, F, stream=None):
     (int32 [T,3] CUDA); returns an opaque handle (int)."""
     h = ctypes.c_void_p()
     _check(load().rc_build_bvh(_ptr(V), V.shape[0], _ptr(F), F.shape[0], _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+RC_BUILDER_KARRAS, RC_BUILDER_PLOC = 0, 1
+
+
+def rc_build_bvh_ex(V, F, builder, stream=None):
+    """rc_build_bvh with a choice of binary builder (RC_BUILDER_*)."""
+    h = ctypes.c_void_p()
+    _check(load().rc_build_bvh_ex(_ptr(V), V.shape[0], _ptr(F), F.shape[0], builder, _stream(stream),
+                                  ctypes.byref(h)))
     return h.value
 
 
@@ -505,8 +517,8 @@ def rc_launch_count():
 class Bvh:
     """Owning wrapper of an ``rc_bvh`` handle (destroyed on ``close``)."""
 
-    def __init__(self, V, F, stream=None):
-        self.h = rc_build_bvh(V, F, stream)
+    def __init__(self, V, F, stream=None, builder=None):
+        self.h = rc_build_bvh(V, F, stream) if builder is None else rc_build_bvh_ex(V, F, builder, stream)
         self.T = F.shape[0]
 
     def close(self):

@@ -104,8 +104,8 @@ static rc_status device_dirs(int32_t N, const float4** canon, const float4** til
     auto it = g_dirs.find({dev, N});
     if (it == g_dirs.end()) {
         // both tables hold 32 * ceil(N / 32) entries; the entries past N
-        // (canonical index -1, zero direction) pad the last tile and are
-        // never cast
+        // pad the last tile: canonical index -1 and the direction of entry
+        // 0 (a real direction, so a cast may trace them and discard them)
         const int32_t N32 = (N + 31) / 32 * 32;
         std::vector<float> h(3 * (size_t)N);
         fibonacci_hemisphere(N, h.data());
@@ -113,7 +113,7 @@ static rc_status device_dirs(int32_t N, const float4** canon, const float4** til
         float pad_w;
         const int32_t minus1 = -1;
         memcpy(&pad_w, &minus1, sizeof pad_w);
-        std::vector<float4> h4(2 * (size_t)N32, make_float4(0.0f, 0.0f, 0.0f, pad_w));
+        std::vector<float4> h4(2 * (size_t)N32, make_float4(h[0], h[1], h[2], pad_w));
         for (int32_t j = 0; j < N; ++j) {
             float w;
             memcpy(&w, &j, sizeof w);
@@ -247,7 +247,15 @@ int64_t rc_launch_count(void) { return g_launches.load(std::memory_order_relaxed
 
 rc_status rc_build_bvh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t T, void* stream, rc_bvh* out)
 {
+    return rc_build_bvh_ex(d_V, nV, d_F, T, RC_BUILDER_KARRAS, stream, out);
+}
+
+rc_status rc_build_bvh_ex(const float* d_V, int64_t nV, const int32_t* d_F, int64_t T, int32_t builder, void* stream,
+                          rc_bvh* out)
+{
     if (!out) return set_error(RC_E_ARG, "out is NULL");
+    if (builder != RC_BUILDER_KARRAS && builder != RC_BUILDER_PLOC)
+        return set_error(RC_E_ARG, "builder must be RC_BUILDER_KARRAS or RC_BUILDER_PLOC");
     *out = nullptr;
     if (!d_V || !d_F) return set_error(RC_E_ARG, "vertex or face pointer is NULL");
     if (nV < 3) return set_error(RC_E_ARG, "need at least 3 vertices");
@@ -260,6 +268,7 @@ rc_status rc_build_bvh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t
     keep_pool_memory();
     h->nV = nV;
     h->T = T;
+    h->builder = builder;
 #define RC_TRY(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) return fail(cuda_error(_e, #call)); } while (0)
     RC_TRY(cudaMallocAsync(&h->V, sizeof(float) * 3 * nV, s));
     RC_TRY(cudaMallocAsync(&h->F, sizeof(int32_t) * 3 * T, s));

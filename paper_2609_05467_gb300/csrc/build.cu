@@ -261,6 +261,234 @@ __global__ void k_karras(const unsigned long long* __restrict__ keys, int64_t T,
 }
 
 // ---------------------------------------------------------------------------
+// PLOC (Meister and Bittner, "Parallel Locally-Ordered Clustering for
+// Bounding Volume Hierarchy Construction", IEEE TVCG 2018): clusters start as
+// the Morton-ordered leaves; each round every cluster finds, within kPlocR
+// positions, the cluster whose merged box has the smallest surface area;
+// mutual nearest neighbours merge into a new interior node (at the lower
+// position) and the array is compacted in order.  Raw interior ids come from
+// an atomic counter; the tree is then renumbered in depth-first order (root
+// 0, each subtree's leaves contiguous) so that packing, the 4-wide collapse
+// and refit work on it as on the Karras tree.
+// ---------------------------------------------------------------------------
+constexpr int kPlocR = 16;
+constexpr int kPlocThreads = 256;
+
+__device__ __forceinline__ float merged_area(const float* a, const float* b)
+{
+    const float dx = fmaxf(a[3], b[3]) - fminf(a[0], b[0]);
+    const float dy = fmaxf(a[4], b[4]) - fminf(a[1], b[1]);
+    const float dz = fmaxf(a[5], b[5]) - fminf(a[2], b[2]);
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void k_ploc_init(const float* __restrict__ tbox, const int32_t* __restrict__ order, int64_t T,
+                            int64_t n_int, int32_t* cl, float* cb, int* n_ptr)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k == 0) *n_ptr = (int)T;
+    if (k >= T) return;
+    cl[k] = (int32_t)(n_int + k);
+    const int32_t f = order[k];
+    for (int c = 0; c < 6; ++c) cb[6 * k + c] = tbox[6 * (int64_t)f + c];
+}
+
+__global__ void __launch_bounds__(kPlocThreads)
+k_ploc_nn(const int* __restrict__ n_ptr, const float* __restrict__ cb, int32_t* __restrict__ nn)
+{
+    __shared__ float sb[kPlocThreads + 2 * kPlocR][6];
+    const int n = *n_ptr;
+    const int base = blockIdx.x * kPlocThreads;
+    if (base >= n) return;
+    for (int t = threadIdx.x; t < kPlocThreads + 2 * kPlocR; t += blockDim.x) {
+        const int j = base - kPlocR + t;
+        if (j >= 0 && j < n)
+            for (int c = 0; c < 6; ++c) sb[t][c] = cb[6 * (int64_t)j + c];
+    }
+    __syncthreads();
+    const int i = base + threadIdx.x;
+    if (i >= n) return;
+    const float* bi = sb[threadIdx.x + kPlocR];
+    int best = -1;
+    float ba = INFINITY;
+    const int j0 = max(0, i - kPlocR), j1 = min(n - 1, i + kPlocR);
+    for (int j = j0; j <= j1; ++j) {
+        if (j == i) continue;
+        const float a = merged_area(bi, sb[j - base + kPlocR]);
+        if (a < ba) { ba = a; best = j; }          // ascending j: ties go to the lower position
+    }
+    nn[i] = best;
+}
+
+__global__ void k_ploc_merge(const int* __restrict__ n_ptr, const int32_t* __restrict__ nn,
+                             const int32_t* __restrict__ cl, const float* __restrict__ cb, int32_t* cl_tmp,
+                             float* cb_tmp, int* keep, int32_t* child_raw, int32_t* parent_raw, int* counter,
+                             int64_t n_int)
+{
+    const int n = *n_ptr;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int j = nn[i];
+    if (j >= 0 && nn[j] == i) {
+        if (i > j) { keep[i] = 0; return; }        // merged into its partner
+        const int id = atomicAdd(counter, 1);
+        if (id >= n_int) { keep[i] = 0; return; }  // cannot happen for a valid cluster array
+        const int32_t a = cl[i], b = cl[j];
+        child_raw[2 * id] = a;
+        child_raw[2 * id + 1] = b;
+        parent_raw[a] = id;
+        parent_raw[b] = id;
+        for (int c = 0; c < 3; ++c) {
+            cb_tmp[6 * (int64_t)i + c] = fminf(cb[6 * (int64_t)i + c], cb[6 * (int64_t)j + c]);
+            cb_tmp[6 * (int64_t)i + 3 + c] = fmaxf(cb[6 * (int64_t)i + 3 + c], cb[6 * (int64_t)j + 3 + c]);
+        }
+        cl_tmp[i] = id;
+    } else {
+        cl_tmp[i] = cl[i];
+        for (int c = 0; c < 6; ++c) cb_tmp[6 * (int64_t)i + c] = cb[6 * (int64_t)i + c];
+    }
+    keep[i] = 1;
+}
+
+// order-preserving compaction of the kept clusters: per-block counts, one
+// block scanning them (it also writes the new count), then the scatter
+constexpr int kCompact = 1024;
+
+__global__ void k_ploc_count(const int* __restrict__ n_ptr, const int* __restrict__ keep, int* bsum)
+{
+    __shared__ int warp_tot[kCompact / 32];
+    const int n = *n_ptr;
+    const int i = blockIdx.x * kCompact + threadIdx.x;
+    const int v = i < n ? keep[i] : 0;
+    const int c = __popc(__ballot_sync(0xFFFFFFFFu, v));
+    if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kCompact / 32; ++w) t += warp_tot[w];
+        bsum[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_ploc_scan(int* bsum, int nb, const int* __restrict__ n_ptr, int* n_next)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int n = *n_ptr;
+    const int used = (n + kCompact - 1) / kCompact;
+    int run = 0;
+    for (int b = 0; b < nb && b < used; ++b) {
+        const int v = bsum[b];
+        bsum[b] = run;
+        run += v;
+    }
+    *n_next = run;
+}
+
+__global__ void k_ploc_scatter(const int* __restrict__ n_ptr, const int* __restrict__ keep,
+                               const int* __restrict__ bsum, const int32_t* __restrict__ cl_tmp,
+                               const float* __restrict__ cb_tmp, int32_t* cl_out, float* cb_out)
+{
+    __shared__ int warp_pre[kCompact / 32];
+    const int n = *n_ptr;
+    const int i = blockIdx.x * kCompact + threadIdx.x;
+    const int v = i < n ? keep[i] : 0;
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) warp_pre[w] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < kCompact / 32; ++k) {
+            const int c = warp_pre[k];
+            warp_pre[k] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    if (!v) return;
+    const int pos = bsum[blockIdx.x] + warp_pre[w] + __popc(bal & ((1u << lane) - 1u));
+    cl_out[pos] = cl_tmp[i];
+    for (int c = 0; c < 6; ++c) cb_out[6 * (int64_t)pos + c] = cb_tmp[6 * (int64_t)i + c];
+}
+
+// subtree sizes (leaves, interior nodes) bottom-up with arrival counters;
+// sizes of raw interior id p at sz_leaf[p], sz_int[p]
+__global__ void k_ploc_sizes(int64_t T, int64_t n_int, const int32_t* __restrict__ parent_raw,
+                             const int32_t* __restrict__ child_raw, int32_t* sz_leaf, int32_t* sz_int, int32_t* visits,
+                             int* err)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= T) return;
+    int32_t p = parent_raw[n_int + k];
+    for (int steps = 0; p >= 0; ++steps) {
+        if (steps > kMaxWalk) { atomicExch(err, 1); return; }
+        __threadfence();
+        if (atomicAdd(&visits[p], 1) == 0) return;
+        const int32_t a = child_raw[2 * p], b = child_raw[2 * p + 1];
+        const int la = a >= n_int ? 1 : __ldcg(&sz_leaf[a]), lb = b >= n_int ? 1 : __ldcg(&sz_leaf[b]);
+        const int ia = a >= n_int ? 0 : __ldcg(&sz_int[a]), ib = b >= n_int ? 0 : __ldcg(&sz_int[b]);
+        __stcg(&sz_leaf[p], la + lb);
+        __stcg(&sz_int[p], ia + ib + 1);
+        p = parent_raw[p];
+    }
+}
+
+// depth-first numbering: every node walks to the root adding, for each
+// ancestor whose right subtree it is in, the sizes of the left sibling
+// subtree.  Interior raw id p -> preorder index newid[p]; leaf k -> leaf
+// position pos[k] (a subtree's leaves are contiguous in that order).
+__global__ void k_ploc_number(int64_t T, int64_t n_int, const int32_t* __restrict__ parent_raw,
+                              const int32_t* __restrict__ child_raw, const int32_t* __restrict__ sz_leaf,
+                              const int32_t* __restrict__ sz_int, int32_t* newid, int32_t* leafstart,
+                              int32_t* pos, int* err)
+{
+    const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (x >= n_int + T) return;
+    int pre = x < n_int ? 0 : 0, lstart = 0;
+    int32_t cur = (int32_t)x;
+    int steps = 0;
+    for (int32_t p = parent_raw[cur]; p >= 0; cur = p, p = parent_raw[p]) {
+        if (++steps > kMaxWalk) { atomicExch(err, 1); return; }
+        const int32_t left = child_raw[2 * p];
+        pre += 1;                                   // the parent comes first
+        if (cur != left) {
+            pre += left >= n_int ? 0 : sz_int[left];
+            lstart += left >= n_int ? 1 : sz_leaf[left];
+        }
+    }
+    if (x < n_int) {
+        newid[x] = pre;
+        leafstart[x] = lstart;
+    } else {
+        pos[x - n_int] = lstart;
+    }
+}
+
+// the renumbered tree: child / parent in combined indexing (interior
+// preorder ids, leaf n_int + position), ranges, and the leaf order
+__global__ void k_ploc_emit(int64_t T, int64_t n_int, const int32_t* __restrict__ parent_raw,
+                            const int32_t* __restrict__ child_raw, const int32_t* __restrict__ newid,
+                            const int32_t* __restrict__ leafstart, const int32_t* __restrict__ sz_leaf,
+                            const int32_t* __restrict__ pos, const int32_t* __restrict__ order_in, int32_t* child,
+                            int32_t* range, int32_t* parent, int32_t* order_out)
+{
+    const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (x >= n_int + T) return;
+    auto map = [&](int32_t c) -> int32_t { return c >= n_int ? (int32_t)(n_int + pos[c - n_int]) : newid[c]; };
+    const int32_t p = parent_raw[x];
+    const int32_t me = map((int32_t)x);
+    parent[me] = p >= 0 ? newid[p] : -1;
+    if (x < n_int) {
+        child[2 * me] = map(child_raw[2 * x]);
+        child[2 * me + 1] = map(child_raw[2 * x + 1]);
+        range[2 * me] = leafstart[x];
+        range[2 * me + 1] = leafstart[x] + sz_leaf[x] - 1;
+    } else {
+        order_out[pos[x - n_int]] = order_in[x - n_int];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // bottom-up refit
 // ---------------------------------------------------------------------------
 __global__ void k_leaf_boxes(const float* __restrict__ tbox, const int32_t* __restrict__ order,
@@ -723,6 +951,97 @@ static rc_status check_scalars(rc_bvh h, cudaStream_t s)
     return RC_OK;
 }
 
+// PLOC build of the binary tree over the Morton-sorted leaves (h->order);
+// writes h->child, h->range, h->parent in the Karras layout and replaces
+// h->order by the depth-first leaf order.
+static rc_status build_ploc(rc_bvh h, const float* tbox, cudaStream_t s)
+{
+    const int64_t T = h->T, n_int = h->n_int;
+    if (T > 0x7FFFFFFF / 2) return set_error(RC_E_UNSUPPORTED, "too many triangles for the PLOC build");
+    const int64_t nb_max = (T + kCompact - 1) / kCompact;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+    const size_t o_cla = take(4 * T), o_clt = take(4 * T), o_cba = take(24 * T), o_cbt = take(24 * T);
+    const size_t o_nn = take(4 * T), o_keep = take(4 * T), o_bsum = take(4 * nb_max), o_n = take(16);
+    const size_t o_craw = take(8 * n_int), o_praw = take(4 * (n_int + T)), o_szl = take(4 * n_int);
+    const size_t o_szi = take(4 * n_int), o_nid = take(4 * n_int), o_ls = take(4 * n_int), o_pos = take(4 * T);
+    const size_t o_ord = take(4 * T);
+    char* base = nullptr;
+    RC_CUDA(cudaMallocAsync((void**)&base, off, s));
+    int32_t* cl_a = (int32_t*)(base + o_cla);
+    int32_t* cl_t = (int32_t*)(base + o_clt);
+    float* cb_a = (float*)(base + o_cba);
+    float* cb_t = (float*)(base + o_cbt);
+    int32_t* nn = (int32_t*)(base + o_nn);
+    int* keep = (int*)(base + o_keep);
+    int* bsum = (int*)(base + o_bsum);
+    int* dn = (int*)(base + o_n);          // [0], [1]: cluster counts (ping-pong), [2]: node counter, [3]: error
+    int32_t* child_raw = (int32_t*)(base + o_craw);
+    int32_t* parent_raw = (int32_t*)(base + o_praw);
+    int32_t* sz_leaf = (int32_t*)(base + o_szl);
+    int32_t* sz_int = (int32_t*)(base + o_szi);
+    int32_t* newid = (int32_t*)(base + o_nid);
+    int32_t* lstart = (int32_t*)(base + o_ls);
+    int32_t* pos = (int32_t*)(base + o_pos);
+    int32_t* order_out = (int32_t*)(base + o_ord);
+    RC_CUDA(cudaMemsetAsync(dn, 0, 16, s));
+    RC_CUDA(cudaMemsetAsync(parent_raw, 0xFF, 4 * (n_int + T), s));
+    k_ploc_init<<<nblocks(T, 256), 256, 0, s>>>(tbox, h->order, T, n_int, cl_a, cb_a, dn);
+    RC_LAUNCHED();
+    int cur = 0;
+    int64_t n_host = T;
+    const int kRoundsPerCheck = 8;
+    int rounds = 0;
+    while (n_host > 1) {
+        if (rounds > 64 + 8 * 64) {
+            cudaFreeAsync(base, s);
+            return set_error(RC_E_DEVICE, "PLOC build did not converge");
+        }
+        const unsigned g_nn = (unsigned)((n_host + kPlocThreads - 1) / kPlocThreads);
+        const unsigned g_c = (unsigned)((n_host + kCompact - 1) / kCompact);
+        for (int r = 0; r < kRoundsPerCheck; ++r, ++rounds) {
+            k_ploc_nn<<<g_nn, kPlocThreads, 0, s>>>(dn + cur, cb_a, nn);
+            RC_LAUNCHED();
+            k_ploc_merge<<<g_nn, kPlocThreads, 0, s>>>(dn + cur, nn, cl_a, cb_a, cl_t, cb_t, keep, child_raw,
+                                                       parent_raw, dn + 2, n_int);
+            RC_LAUNCHED();
+            k_ploc_count<<<g_c, kCompact, 0, s>>>(dn + cur, keep, bsum);
+            RC_LAUNCHED();
+            k_ploc_scan<<<1, 32, 0, s>>>(bsum, (int)g_c, dn + cur, dn + 1 - cur);
+            RC_LAUNCHED();
+            k_ploc_scatter<<<g_c, kCompact, 0, s>>>(dn + cur, keep, bsum, cl_t, cb_t, cl_a, cb_a);
+            RC_LAUNCHED();
+            cur = 1 - cur;
+        }
+        int hn[3];
+        RC_CUDA(cudaMemcpyAsync(hn, dn, sizeof hn, cudaMemcpyDeviceToHost, s));
+        RC_CUDA(cudaStreamSynchronize(s));
+        n_host = hn[cur];
+        if (n_host == 1 && hn[2] != n_int) {
+            cudaFreeAsync(base, s);
+            return set_error(RC_E_DEVICE, "PLOC build made a wrong number of interior nodes");
+        }
+    }
+    // depth-first renumbering into the Karras layout
+    RC_CUDA(cudaMemsetAsync(h->visits, 0, sizeof(int32_t) * n_int, s));
+    k_ploc_sizes<<<nblocks(T, 256), 256, 0, s>>>(T, n_int, parent_raw, child_raw, sz_leaf, sz_int, h->visits,
+                                                 dn + 3);
+    RC_LAUNCHED();
+    k_ploc_number<<<nblocks(n_int + T, 256), 256, 0, s>>>(T, n_int, parent_raw, child_raw, sz_leaf, sz_int, newid,
+                                                          lstart, pos, dn + 3);
+    RC_LAUNCHED();
+    k_ploc_emit<<<nblocks(n_int + T, 256), 256, 0, s>>>(T, n_int, parent_raw, child_raw, newid, lstart, sz_leaf, pos,
+                                                        h->order, h->child, h->range, h->parent, order_out);
+    RC_LAUNCHED();
+    RC_CUDA(cudaMemcpyAsync(h->order, order_out, sizeof(int32_t) * T, cudaMemcpyDeviceToDevice, s));
+    int herr = 0;
+    RC_CUDA(cudaMemcpyAsync(&herr, dn + 3, sizeof herr, cudaMemcpyDeviceToHost, s));
+    RC_CUDA(cudaFreeAsync(base, s));
+    RC_CUDA(cudaStreamSynchronize(s));
+    if (herr) return set_error(RC_E_DEVICE, "PLOC tree walk exceeded its bound");
+    return RC_OK;
+}
+
 // Collapse the binary tree into the 4-wide layout (wnodes), or make the
 // one-leaf wide root for tiny parts.  Needs the binary tree and its boxes.
 static rc_status build_wide(rc_bvh h, const float* tbox, cudaStream_t s)
@@ -796,8 +1115,13 @@ rc_status build_bvh(rc_bvh h, cudaStream_t s)
         RC_CUDA(cudaMallocAsync(&h->range, sizeof(int32_t) * 2 * n_int, s));
         RC_CUDA(cudaMallocAsync(&h->nbox, sizeof(float) * 6 * (n_int + T), s));
         RC_CUDA(cudaMallocAsync(&h->visits, sizeof(int32_t) * n_int, s));
-        k_karras<<<nblocks(n_int, 256), 256, 0, s>>>(k0, T, h->child, h->range, h->parent);
-        RC_LAUNCHED();
+        if (h->builder == RC_BUILDER_PLOC) {
+            rc_status pst = build_ploc(h, tbox, s);
+            if (pst != RC_OK) return pst;
+        } else {
+            k_karras<<<nblocks(n_int, 256), 256, 0, s>>>(k0, T, h->child, h->range, h->parent);
+            RC_LAUNCHED();
+        }
         RC_CUDA(cudaMemsetAsync(h->visits, 0, sizeof(int32_t) * n_int, s));
         k_leaf_boxes<<<nblocks(T, 256), 256, 0, s>>>(tbox, h->order, T, n_int, h->nbox);
         RC_LAUNCHED();

@@ -599,29 +599,30 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
     const Onb b = make_onb(nx, ny, nz);
     int cnt = 0;
     for (int t = 0; t < W; ++t) {
+        // canonical index j; when 32 does not divide N the last tile is
+        // padded with entries j = -1 that carry a real direction: they are
+        // cast like the others (no branch in the loop) and then discarded
         const float4 h = __ldg(&tdirs[32 * t + lane]);
-        const int j = __float_as_int(h.w);      // canonical index; -1 pads the last tile when 32 does not divide N
-        bool visible = false;
-        if (j >= 0) {
-            float dx, dy, dz;
-            local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
-            Ray r;
-            setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-            const TraceOut tr = trace_any<kStats, kWide>(nodes, tris, r, max_steps);
-            acc.retests += tr.retests;
-            acc.overflow += tr.overflow;
-            acc.amb += (tr.flags >> 1) & 1;
-            if (kStats) { acc.nvis += tr.nodes; acc.ntri += tr.tris; }
-            visible = (tr.flags & 1) == 0;
-            if (visible) atomicOr(&row[j >> 5], 1u << (j & 31));
-            acc.rays += 1;
-        }
+        const int j = __float_as_int(h.w);
+        float dx, dy, dz;
+        local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
+        Ray r;
+        setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
+        const TraceOut tr = trace_any<kStats, kWide>(nodes, tris, r, max_steps);
+        acc.retests += tr.retests;
+        acc.overflow += tr.overflow;
+        acc.amb += (j >= 0) & ((tr.flags >> 1) & 1);
+        if (kStats) { acc.nvis += tr.nodes; acc.ntri += tr.tris; }
+        const bool visible = (tr.flags & 1) == 0 && j >= 0;
+        if (visible) atomicOr(&row[j >> 5], 1u << (j & 31));
         cnt += __popc(__ballot_sync(0xFFFFFFFFu, visible));
     }
     __syncwarp();
     for (int w = lane; w < W; w += 32) bits[i * W + w] = row[w];
     __syncwarp();
     if (lane == 0) count[i] = cnt;
+    // rays per lane: W, less the pad of the last tile if this lane has one
+    acc.rays += W - (__float_as_int(__ldg(&tdirs[32 * (W - 1) + lane]).w) < 0 ? 1 : 0);
 }
 
 // The hemispherical cast of one point with each lane walking its own list

@@ -90,6 +90,7 @@ struct BatchPart {
 
 struct rc_bvh_s {
     int device = 0;
+    int builder = 0;               // RC_BUILDER_KARRAS or RC_BUILDER_PLOC
     int64_t nV = 0, T = 0;
     float* V = nullptr;            // [nV][3] copy of the vertices
     int32_t* F = nullptr;          // [T][3] copy of the faces

@@ -407,3 +407,51 @@ def test_full_size_impeller(rc):
     """Freeform impeller: ~2M triangles, 1M points x 2,048 directions."""
     V, F = synth.impeller()
     _full_size(rc, V, F, 1_000_000, 2048, 60)
+
+
+# ---------------------------------------------------------------------------
+# the PLOC binary tree (rc_build_bvh_ex): same results as the Karras tree
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,n,N", [("pocket", 500, 256), ("prismatic_coarse", 600, 150),
+                                       ("impeller_coarse", 300, 128), ("cavity", 200, 64), ("cube", 3, 32)])
+def test_ploc_tree_parity(rc, name, n, N):
+    V, F = PARTS[name]()
+    Vt, Ft = gpu_mesh(V, F)
+    bvh = rc.Bvh(Vt, Ft, builder=rc.RC_BUILDER_PLOC)
+    info = rc.rc_bvh_get_info(bvh.h)
+    assert info.n_tris == len(F)
+    for width in (4, 2):
+        p = rc.rc_params_default(n_dirs=N, tree_width=width)
+        P, Nn, f, w = _points(V, F, n, p)
+        gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
+        ob, oa, oc = oracle.Mesh(V, F).hemisphere(P, Nn, N)
+        compare_bits(gb, gc, ob, oa, oc, N)
+        assert ctr[0] == n * N and ctr[3] == 0
+    bvh.close()
+
+
+def test_ploc_tree_refit_and_tiny_parts(rc):
+    V0, F = synth.perturbed_part(2, 0.0)
+    V1, _ = synth.perturbed_part(2, 3.5)
+    Vt0, Ft = gpu_mesh(V0, F)
+    Vt1, _ = gpu_mesh(V1, F)
+    a = rc.Bvh(Vt0, Ft, builder=rc.RC_BUILDER_PLOC)
+    rc.rc_refit_bvh(a.h, Vt1)
+    b = rc.Bvh(Vt1, Ft, builder=rc.RC_BUILDER_PLOC)
+    p = rc.rc_params_default(n_dirs=128)
+    P, Nn, f, w = _points(V1, F, 700, p)
+    assert np.array_equal(gpu_cast(rc, a.h, P, Nn, p)[0], gpu_cast(rc, b.h, P, Nn, p)[0])
+    a.close()
+    b.close()
+    for T in (1, 2, 3, 5):
+        V, F = synth.cube(10.0, 0)
+        bvh = rc.Bvh(*gpu_mesh(V, F[:T]), builder=rc.RC_BUILDER_PLOC)
+        p = rc.rc_params_default(n_dirs=64)
+        P, Nn, f, w = _points(V, F[:T], 40, p)
+        gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
+        ob, oa, oc = oracle.Mesh(V, F[:T]).hemisphere(P, Nn, 64)
+        compare_bits(gb, gc, ob, oa, oc, 64)
+        bvh.close()
+    with pytest.raises(rc.RcError):
+        rc.rc_build_bvh_ex(*gpu_mesh(V, F), 7)
