@@ -315,6 +315,23 @@ rc_status rc_orthogonal_cast(rc_bvh h, const float* d_P, const float* d_N, int64
                              const rc_params* p, uint8_t* d_mask, float* d_travel,
                              int64_t* d_counters, void* stream);
 
+/* Tool-aware accessibility along the six axes of the frame (a variant the
+ * paper does not run: its rays are thin; the accessibility cones of the
+ * prior art it cites account for the tool).  A ball-end tool of radius r
+ * touches point p: centre c = p + (r + origin_offset) n.  Along axis a its
+ * shank is sampled by the ray from c and ring_rays parallel rays from
+ * c + r (cos t_k u + sin t_k v), t_k = 2 pi k / ring_rays, (u, v) the
+ * branchless orthonormal basis of a (Duff et al. 2017), all in FP64 with
+ * origins rounded to fp32.  Bit a of d_mask[i] is set iff a is eligible
+ * (n.a >= -parallel_tol) and none of those rays is obstructed.  With r = 0
+ * and ring_rays = 0 this is the mask of rc_orthogonal_cast.
+ *   d_P, d_N [n][3]; d_mask [n] uint8 (written); d_counters int64[4] as
+ *   for rc_orthogonal_cast (may be NULL).  Synchronises `stream`.
+ * Errors: RC_E_ARG (tool_radius outside [0, 1e4] mm, ring_rays outside
+ * [0, 64]), RC_E_CUDA. */
+rc_status rc_tool_cast(rc_bvh h, const float* d_P, const float* d_N, int64_t n, const rc_params* p,
+                       double tool_radius, int32_t ring_rays, uint8_t* d_mask, int64_t* d_counters, void* stream);
+
 /* Reachability, fixture exclusion, face classes and setup count (Section
  * 3.3: directions whose travel exceeds the tool length are discarded,
  * bounding-box faces are excluded as fixture surfaces, faces are viable /

@@ -198,6 +198,7 @@ def load(build_if_missing=True):
             "rc_changed_faces": ([P, P, i64, P, i64, P, P, ctypes.POINTER(i64), P], st),
             "rc_hemisphere_update": ([P, P, P, P, i64, P, P, ctypes.POINTER(Params), P, P, P, P], st),
             "rc_frame_select": ([P, P, P, P, i64, ctypes.POINTER(Params), ctypes.POINTER(Frames), P, P], st),
+            "rc_tool_cast": ([P, P, P, i64, ctypes.POINTER(Params), ctypes.c_double, i32, P, P, P], st),
             "rc_stl_read": ([ctypes.c_char_p, P, i64, P, i64, ctypes.POINTER(i64), ctypes.POINTER(i64)], st),
             "rc_analyze_stl": ([ctypes.c_char_p, i64, ctypes.POINTER(Params), ctypes.POINTER(PartResult), P], st),
         }
@@ -331,6 +332,11 @@ def rc_classify(summary, params):
 def rc_orthogonal_cast(h, P, N, params, mask, travel, counters=None, stream=None):
     _check(load().rc_orthogonal_cast(ctypes.c_void_p(h), _ptr(P), _ptr(N), P.shape[0], ctypes.byref(params),
                                      _ptr(mask), _ptr(travel), _ptr(counters), _stream(stream)))
+
+
+def rc_tool_cast(h, P, N, params, tool_radius, ring_rays, mask, counters=None, stream=None):
+    _check(load().rc_tool_cast(ctypes.c_void_p(h), _ptr(P), _ptr(N), P.shape[0], ctypes.byref(params),
+                               float(tool_radius), int(ring_rays), _ptr(mask), _ptr(counters), _stream(stream)))
 
 
 def rc_min_setups(h, mask, travel, face, params, cls=None, stream=None):

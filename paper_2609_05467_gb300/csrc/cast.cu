@@ -1205,6 +1205,81 @@ k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
     warp_add_counters(counters, rays, amb, retests, overflow, nvis, ntri);
 }
 
+// ---------------------------------------------------------------------------
+// Tool-aware accessibility (a reading of the accessibility cones of the prior
+// art the paper cites; the paper itself casts thin rays).  A ball-end tool of
+// radius r touches the point: centre c = p + (r + eps) n (FP64).  Along axis
+// a its shank is sampled by the ray from c and K rays from the ring
+// c + r (cos t_k u + sin t_k v), (u, v) the branchless orthonormal basis of
+// a (Duff et al. 2017) in FP64; origins are rounded to fp32, every ray goes
+// along a.  The axis is tool-accessible iff it is eligible (n.a >=
+// -parallel_tol) and none of the 1 + K rays is obstructed.
+// ---------------------------------------------------------------------------
+template <bool kWide>
+__global__ void __launch_bounds__(128, RC_BATCH_MIN_BLOCKS)
+k_tool_cast(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
+            const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n, const int32_t* __restrict__ order,
+            const FrameDev* __restrict__ fd, double eps, double par_tol, double radius,
+            const double2* __restrict__ ring /*cos, sin*/, int K, uint8_t* __restrict__ mask,
+            unsigned long long* counters)
+{
+    const int lane = threadIdx.x & 31;
+    int amb = 0, retests = 0, overflow = 0;
+    long long rays = 0;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t wv = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wv * 32 < n; wv += nwarps) {
+        const int64_t k = wv * 32 + lane;
+        if (k >= n) continue;
+        const int64_t i = order ? (int64_t)__ldg(&order[k]) : k;
+        const double px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
+        const float nxf = Nrm[3 * i], nyf = Nrm[3 * i + 1], nzf = Nrm[3 * i + 2];
+        const double nx = nxf, ny = nyf, nz = nzf;
+        const double h = __dadd_rn(radius, eps);
+        const double cx = __dadd_rn(px, __dmul_rn(h, nx)), cy = __dadd_rn(py, __dmul_rn(h, ny)),
+                     cz = __dadd_rn(pz, __dmul_rn(h, nz));
+        unsigned m = 0;
+        for (int a = 0; a < 6; ++a) {
+            const float dx = fd->axes[3 * a], dy = fd->axes[3 * a + 1], dz = fd->axes[3 * a + 2];
+            double nd = __dadd_rn(__dmul_rn(nx, (double)dx), __dmul_rn(ny, (double)dy));
+            nd = __dadd_rn(nd, __dmul_rn(nz, (double)dz));
+            if (!(nd >= -par_tol)) continue;
+            // orthonormal basis (u, v) of the axis, FP64
+            const double ax = dx, ay = dy, az = dz;
+            const double sg = az >= 0.0 ? 1.0 : -1.0;
+            const double q = __ddiv_rn(-1.0, __dadd_rn(sg, az));
+            const double bb = __dmul_rn(__dmul_rn(ax, ay), q);
+            const double ux = __dadd_rn(1.0, __dmul_rn(__dmul_rn(__dmul_rn(sg, ax), ax), q));
+            const double uy = __dmul_rn(sg, bb), uz = __dmul_rn(-sg, ax);
+            const double vx = bb, vy = __dadd_rn(sg, __dmul_rn(__dmul_rn(ay, ay), q)), vz = -ay;
+            bool open = true;
+            for (int r = -1; r < K && open; ++r) {
+                float ox, oy, oz;
+                if (r < 0) {
+                    ox = __double2float_rn(cx);
+                    oy = __double2float_rn(cy);
+                    oz = __double2float_rn(cz);
+                } else {
+                    const double rc = __dmul_rn(radius, ring[r].x), rs = __dmul_rn(radius, ring[r].y);
+                    ox = __double2float_rn(__dadd_rn(__dadd_rn(cx, __dmul_rn(rc, ux)), __dmul_rn(rs, vx)));
+                    oy = __double2float_rn(__dadd_rn(__dadd_rn(cy, __dmul_rn(rc, uy)), __dmul_rn(rs, vy)));
+                    oz = __double2float_rn(__dadd_rn(__dadd_rn(cz, __dmul_rn(rc, uz)), __dmul_rn(rs, vz)));
+                }
+                Ray ray;
+                setup_ray(ray, ox, oy, oz, dx, dy, dz, scene_maxabs);
+                const TraceOut t = trace_any<false, kWide>(nodes, tris, ray, max_steps);
+                retests += t.retests;
+                overflow += t.overflow;
+                amb += (t.flags >> 1) & 1;
+                rays += 1;
+                open = (t.flags & 1) == 0;
+            }
+            if (open) m |= 1u << a;
+        }
+        mask[i] = (uint8_t)m;
+    }
+    warp_add_counters(counters, rays, amb, retests, overflow);
+}
+
 // FP64 bounding box of the vertices in frame coordinates: per-thread
 // min/max over a grid-stride range, warp reduction, one atomic per warp.
 __global__ void k_frame_box(const float* __restrict__ V, int64_t nV, const double* __restrict__ frame,
@@ -1470,6 +1545,37 @@ rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n,
     rc_status st = frame_setup(h, p, fd, s);
     if (st == RC_OK) st = launch_orthogonal_frames(h, P, N, n, p, fd, 1, mask, travel, counters, s);
     cudaFreeAsync(fd, s);
+    return st;
+}
+
+rc_status launch_tool_cast(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p, double radius,
+                          const double2* ring, int K, uint8_t* mask, unsigned long long* counters, cudaStream_t s)
+{
+    FrameDev* fd = nullptr;
+    RC_CUDA(cudaMallocAsync(&fd, sizeof(FrameDev), s));
+    rc_status st = frame_setup(h, p, fd, s);
+    int32_t* order = nullptr;
+    if (st == RC_OK && p->point_order == 0 && n > 1) {
+        RC_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * n, s));
+        st = point_order(h, P, n, order, s);
+    }
+    if (st == RC_OK) {
+        int64_t blocks = (n + 127) / 128;
+        const int64_t cap = (int64_t)sm_count() * RC_BATCH_MIN_BLOCKS;
+        if (blocks > cap) blocks = cap;
+        if (blocks < 1) blocks = 1;
+        if (use_wide(p))
+            k_tool_cast<true><<<(unsigned)blocks, 128, 0, s>>>(h->wnodes, h->tris, max_steps(h), h->scene_maxabs, P,
+                                                              N, n, order, fd, p->origin_offset, p->parallel_tol,
+                                                              radius, ring, K, mask, counters);
+        else
+            k_tool_cast<false><<<(unsigned)blocks, 128, 0, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P,
+                                                               N, n, order, fd, p->origin_offset, p->parallel_tol,
+                                                               radius, ring, K, mask, counters);
+        RC_LAUNCHED();
+    }
+    cudaFreeAsync(fd, s);
+    if (order) cudaFreeAsync(order, s);
     return st;
 }
 
