@@ -486,7 +486,7 @@ def run_served(args):
     torch.cuda.set_device(0)
     reqs = served_trace(args.duration, args.rate)
     p = rc.rc_params_default(n_dirs=512, tool_length=60.0)
-    ps = rc.rc_params_default(n_dirs=512, tool_length=60.0, launch_mode=1)
+    ps = rc.rc_params_default(n_dirs=512, tool_length=60.0, launch_mode=0 if args.server_persistent else 1)
 
     def replay(submit, collect):
         import queue as _q
@@ -585,7 +585,8 @@ def run_served(args):
                                "re-submissions with a feature moved 1-5 mm" % (args.rate, args.duration,
                                                                               int(np.median(tris))),
                    "slots": args.slots, "hbm_budget_gb": 120, "small_rays": args.small_rays,
-                   "server_cast": "one warp per point (short blocks), small requests on high-priority streams",
+                   "server_cast": ("persistent grid" if args.server_persistent else "one warp per point (short blocks)")
+                                  + ", small requests on high-priority streams",
                    "plain": "rc_analyze_part per request, FIFO, one at a time, persistent grid",
                    "incremental": "re-submissions with the same triangle list keep their points on their faces "
                                   "and cast only what the edit can change" if args.incremental else "off"},
@@ -1069,6 +1070,8 @@ def main():
     ap.add_argument("--slots", type=int, default=4, help="served workload: server slots")
     ap.add_argument("--parts", type=int, default=64, help="batched workload: number of parts")
     ap.add_argument("--incremental", action="store_true", help="served workload: incremental re-analysis")
+    ap.add_argument("--server-persistent", action="store_true",
+                    help="served workload: the server's casts use the persistent grid (launch_mode 0)")
     ap.add_argument("--edit", default="bump", choices=["bump", "deepen", "shift"],
                     help="incremental workload: the edit")
     ap.add_argument("--small-rays", type=float, default=4e6,

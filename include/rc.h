@@ -489,8 +489,9 @@ rc_status rc_server_submit(rc_server s, uint64_t part_key, const float* h_V, int
 rc_status rc_server_wait(rc_server s, int64_t req_id, double timeout_s, rc_request_result* out);
 
 /* Copy a resident part's visibility bits [n][W] and counts [n] to host
- * arrays (either may be NULL).  Errors: RC_E_ARG (not resident, in use, or
- * n differs). */
+ * arrays (either may be NULL).  A part in use is read once it is idle
+ * again (waiting at most 60 s).  Errors: RC_E_ARG (not resident, or n
+ * differs), RC_E_TIMEOUT. */
 rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, int32_t* h_count, int64_t n);
 
 /* Counters of the server (host struct). */

@@ -63,6 +63,7 @@ struct SrvEntry {
     int64_t nV = 0, T = 0, n = 0, cap_n = 0;
     int32_t N = 0;
     uint64_t fhash = 0;
+    bool fhash_valid = false;      // false: fhash is computed after the result is delivered
     float* P = nullptr;
     float* Nn = nullptr;
     int32_t* face = nullptr;
@@ -202,14 +203,18 @@ static rc_status run_request(rc_server s, SrvRequest* r, SrvEntry* e, cudaStream
     rc_params p = s->p;
     if (s->cfg.cast_blocks_per_sm > 0) p.blocks_per_sm = s->cfg.cast_blocks_per_sm;
     const int32_t N = p.n_dirs;
-    const uint64_t fh = hash_faces(r->F.data(), r->T * 3);
+    // the triangle-list hash decides refit vs rebuild; it is needed now only
+    // when a resident part of the same size exists (otherwise the worker
+    // computes it after delivering the result, before the part is released)
+    const bool candidate = e->h && e->T == r->T && e->nV == r->nV;
+    const uint64_t fh = candidate ? hash_faces(r->F.data(), r->T * 3) : 0;
     // geometry: refit when the triangle list is unchanged, else (re)build
     float* dV = nullptr;
     int32_t* dF = nullptr;
     SRV_CUDA(cudaMallocAsync(&dV, sizeof(float) * 3 * r->nV, st));
     SRV_CUDA(cudaMemcpyAsync(dV, r->V.data(), sizeof(float) * 3 * r->nV, cudaMemcpyHostToDevice, st));
     rc_status rs;
-    const bool same_topology = e->h && e->T == r->T && e->nV == r->nV && e->fhash == fh;
+    const bool same_topology = candidate && e->fhash_valid && e->fhash == fh;
     // incremental re-analysis: same triangle list, point count and directions,
     // and the resident results of the previous request on this key
     const bool incremental = s->cfg.incremental && same_topology && e->P && e->n == r->n && e->N == N && r->n > 0;
@@ -246,6 +251,7 @@ static rc_status run_request(rc_server s, SrvRequest* r, SrvEntry* e, cudaStream
     e->T = r->T;
     e->nV = r->nV;
     e->fhash = fh;
+    e->fhash_valid = candidate;
     // resident per-point arrays
     const int64_t n = r->n;
     if (n > e->cap_n || N != e->N) {
@@ -324,6 +330,11 @@ static void worker(rc_server s, int slot)
         r->res.priority_level = level;
         const rc_status rs = run_request(s, r, e, st);
         const double t_end = now_s();
+        // a new part's triangle-list hash is computed after its result is
+        // delivered; the part stays busy (not re-used or evicted) until then
+        const bool hash_later = rs == RC_OK && !e->fhash_valid;
+        std::vector<int32_t> faces;
+        if (hash_later) faces = std::move(r->F);
         {
             std::lock_guard<std::mutex> lk(s->mu);
             r->res.status = rs;
@@ -339,8 +350,10 @@ static void worker(rc_server s, int slot)
                 const int64_t actual = r->res.resident_bytes;
                 s->used += actual - e->bytes;
                 e->bytes = actual;
-                e->busy = false;
-                e->last_use = ++s->tick;
+                if (!hash_later) {
+                    e->busy = false;
+                    e->last_use = ++s->tick;
+                }
                 s->st.completed++;
             }
             r->res.t_end = t_end;
@@ -348,6 +361,16 @@ static void worker(rc_server s, int slot)
             s->st.running--;
             s->cv_done.notify_all();
             s->cv_work.notify_all();
+        }
+        if (hash_later) {
+            const uint64_t fh = hash_faces(faces.data(), (int64_t)faces.size());
+            std::lock_guard<std::mutex> lk(s->mu);
+            e->fhash = fh;
+            e->fhash_valid = true;
+            e->busy = false;
+            e->last_use = ++s->tick;
+            s->cv_work.notify_all();
+            s->cv_done.notify_all();
         }
     }
 }
@@ -439,11 +462,19 @@ rc_status rc_server_wait(rc_server s, int64_t req_id, double timeout_s, rc_reque
 rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, int32_t* h_count, int64_t n)
 {
     if (!s) return set_error(RC_E_ARG, "server is NULL");
-    std::lock_guard<std::mutex> lk(s->mu);
+    std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->cache.find(part_key);
     if (it == s->cache.end()) return set_error(RC_E_ARG, "part is not resident");
+    // a part in use (being analysed, or finishing its bookkeeping) is read
+    // once it is idle again; the wait is bounded
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::seconds(60);
+    while (it->second->busy) {
+        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && it->second->busy)
+            return set_error(RC_E_TIMEOUT, "part stayed busy for 60 s");
+        it = s->cache.find(part_key);
+        if (it == s->cache.end()) return set_error(RC_E_ARG, "part is not resident");
+    }
     SrvEntry* e = it->second;
-    if (e->busy) return set_error(RC_E_ARG, "part is being analysed");
     if (n != e->n) return set_error(RC_E_ARG, "n differs from the resident part's point count");
     if (h_bits && n) RC_CUDA(cudaMemcpy(h_bits, e->bits, sizeof(uint32_t) * ((e->N + 31) / 32) * n, cudaMemcpyDeviceToHost));
     if (h_count && n) RC_CUDA(cudaMemcpy(h_count, e->count, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
