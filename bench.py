@@ -383,6 +383,14 @@ def run_gpu(args, wl, V, F):
     alg_bytes = bytes_per_ray * rays_cast_step
     achieved = alg_bytes / cast_s / 1e9
     traffic, tsrc = committed_traffic(args.workload)
+    # the ceilings of a traversal whose tree stays in L2: random node-sized
+    # (128-byte) reads from a 64 MiB L2-resident buffer and FP32 FMA issue
+    # (our probe kernels, run after the timed region)
+    l2_gbs = rc.rc_probe_l2(64 << 20, 128, 256, stream)
+    l2_16 = rc.rc_probe_l2(64 << 20, 16, 256, stream)
+    fp32_tf = rc.rc_probe_fp32(4096, stream)
+    ops_per_ray = 14.0 * (4.0 if ps.tree_width != 2 else 2.0) * nodes_per_ray + 35.0 * tris_per_ray
+    fp32_ach = ops_per_ray * rays_cast_step / cast_s / 1e12
 
     if rank != 0:
         return
@@ -408,7 +416,17 @@ def run_gpu(args, wl, V, F):
                      "kernel": "k_hemisphere", "kernel_ms": 1e3 * cast_s,
                      "bytes_per_ray": bytes_per_ray, "nodes_per_ray": nodes_per_ray, "tris_per_ray": tris_per_ray,
                      "node_bytes": node_bytes, "tree": "4-wide" if ps.tree_width != 2 else "binary",
-                     "traffic_source": tsrc},
+                     "traffic_source": tsrc,
+                     "ceilings": {
+                         "l2_random_128B_gbs": l2_gbs, "l2_random_16B_gbs": l2_16,
+                         "l2_note": "rc_probe_l2, random records from a 64 MiB L2-resident buffer, measured in this "
+                                    "run; the traversal's fetches hit L1 for most sectors, so its algorithmic "
+                                    "bytes per second can exceed these",
+                         "fp32": {"achieved": fp32_ach, "peak": fp32_tf, "unit": "TFLOP/s",
+                                  "frac": fp32_ach / fp32_tf, "ops_per_ray": ops_per_ray,
+                                  "ops_source": "14 per box test, 35 per triangle test (slab and watertight "
+                                                "formulas)",
+                                  "peak_source": "measured in this run: rc_probe_fp32, 8 FMA chains per thread"}}},
         "quality": {"ambiguous_rays": amb_rays, "fp64_retests": retests, "errors": errors,
                     "rays_per_step": float(np.mean(rays_per_step)), "wall_s": wall,
                     "overall_access": s.overall_access, "label": label, "setups_exact": su.setups_exact,

@@ -640,6 +640,25 @@ rc_status rc_frame_candidates(rc_bvh h, const rc_params* p, rc_frames* out, void
 rc_status rc_frame_select(rc_bvh h, const float* d_P, const float* d_N, const int32_t* d_face, int64_t n,
                           const rc_params* p, rc_frames* io, int64_t* d_counters, void* stream);
 
+/* ---------------------------------------------------------------------- */
+/* Measurement probes (no counterpart in the paper): the ceilings of a    */
+/* traversal whose tree stays in L2                                       */
+/* ---------------------------------------------------------------------- */
+
+/* Random reads of record_bytes (16, 32, 64 or 128: 128 is the size of a
+ * 4-wide node) from an L2-resident buffer of buffer_bytes (a power of two
+ * in [1 MiB, 1 GiB]; records picked by splitmix64 of a counter),
+ * reads_per_thread records per thread over 8 blocks of 256 threads per SM:
+ * *h_gbs receives the read bandwidth in GB/s (one timed launch after a
+ * warm-up).  Synchronises `stream`.  Errors: RC_E_ARG, RC_E_CUDA. */
+rc_status rc_probe_l2(int64_t buffer_bytes, int32_t record_bytes, int32_t reads_per_thread, double* h_gbs,
+                      void* stream);
+
+/* FP32 fused multiply-add throughput: eight independent chains of iters
+ * FMAs per thread over 8 blocks of 256 threads per SM; *h_tflops receives
+ * TFLOP/s (2 per FMA).  Synchronises `stream`.  Errors: RC_E_ARG, RC_E_CUDA. */
+rc_status rc_probe_fp32(int32_t iters, double* h_tflops, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -198,6 +198,8 @@ def load(build_if_missing=True):
             "rc_changed_faces": ([P, P, i64, P, i64, P, P, ctypes.POINTER(i64), P], st),
             "rc_hemisphere_update": ([P, P, P, P, i64, P, P, ctypes.POINTER(Params), P, P, P, P], st),
             "rc_frame_select": ([P, P, P, P, i64, ctypes.POINTER(Params), ctypes.POINTER(Frames), P, P], st),
+            "rc_probe_l2": ([i64, i32, i32, ctypes.POINTER(ctypes.c_double), P], st),
+            "rc_probe_fp32": ([i32, ctypes.POINTER(ctypes.c_double), P], st),
             "rc_tool_cast": ([P, P, P, i64, ctypes.POINTER(Params), ctypes.c_double, i32, P, P, P], st),
             "rc_stl_read": ([ctypes.c_char_p, P, i64, P, i64, ctypes.POINTER(i64), ctypes.POINTER(i64)], st),
             "rc_analyze_stl": ([ctypes.c_char_p, i64, ctypes.POINTER(Params), ctypes.POINTER(PartResult), P], st),
@@ -337,6 +339,20 @@ def rc_orthogonal_cast(h, P, N, params, mask, travel, counters=None, stream=None
 def rc_tool_cast(h, P, N, params, tool_radius, ring_rays, mask, counters=None, stream=None):
     _check(load().rc_tool_cast(ctypes.c_void_p(h), _ptr(P), _ptr(N), P.shape[0], ctypes.byref(params),
                                float(tool_radius), int(ring_rays), _ptr(mask), _ptr(counters), _stream(stream)))
+
+
+def rc_probe_l2(buffer_bytes=64 << 20, record_bytes=128, reads_per_thread=256, stream=None):
+    """Random-record read bandwidth of an L2-resident buffer (GB/s)."""
+    g = ctypes.c_double()
+    _check(load().rc_probe_l2(buffer_bytes, record_bytes, reads_per_thread, ctypes.byref(g), _stream(stream)))
+    return g.value
+
+
+def rc_probe_fp32(iters=4096, stream=None):
+    """FP32 FMA throughput (TFLOP/s)."""
+    t = ctypes.c_double()
+    _check(load().rc_probe_fp32(iters, ctypes.byref(t), _stream(stream)))
+    return t.value
 
 
 def rc_min_setups(h, mask, travel, face, params, cls=None, stream=None):
