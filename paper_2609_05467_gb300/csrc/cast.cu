@@ -43,9 +43,14 @@ __device__ __forceinline__ void setup_ray(Ray& r, float ox, float oy, float oz, 
 {
     r.ox = ox; r.oy = oy; r.oz = oz;
     r.dx = dx; r.dy = dy; r.dz = dz;
+    // reciprocals; a zero (or denormal) component gets +-1e30 instead of
+    // +-inf, so slab products stay finite (no inf * 0 = NaN)
     r.ix = __frcp_rn(dx);
     r.iy = __frcp_rn(dy);
     r.iz = __frcp_rn(dz);
+    if (!(fabsf(r.ix) <= 1e30f)) r.ix = copysignf(1e30f, dx);
+    if (!(fabsf(r.iy) <= 1e30f)) r.iy = copysignf(1e30f, dy);
+    if (!(fabsf(r.iz) <= 1e30f)) r.iz = copysignf(1e30f, dz);
     const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
     int kz = ax >= ay ? (ax >= az ? 0 : 2) : (ay >= az ? 1 : 2);
     int kx = kz == 2 ? 0 : kz + 1;
@@ -289,6 +294,66 @@ __device__ __forceinline__ TraceOut trace(const float4* __restrict__ nodes, cons
 // Any-hit walk of the 4-wide tree: the same ray, box and triangle decisions
 // as trace(); per node the four child boxes are tested together, the
 // nearest hit child is visited next and the others are pushed far-to-near.
+// Per-ray constants of the 4-wide slab test.  A slab distance is one FMA,
+// t = b * i - o * i, with the near / far bound of each axis picked by the
+// load address (the node stores lo and hi of an axis in adjacent float4s).
+// Conservative: with u = 2^-24, i = fl(1/d), M >= |every box coordinate|,
+// the computed b*i - fl(o*i) differs from (b - o)/d by at most
+// 2u|t| + 2u|o i| (+ lower-order terms) <= 4.01 u (M + |o|) |i|; every near
+// distance is lowered and every far distance raised by E = 5 u (M + |o|) |i|
+// (folded into the subtracted constant, its rounding included), so a box
+// the exact ray enters is never rejected.
+struct SlabRay {
+    float ix, iy, iz;
+    float nox, noy, noz;    // o * i + E  (subtracted for near distances)
+    float fox, foy, foz;    // o * i - E  (subtracted for far distances)
+    int offx, offy, offz;   // 1 when the axis runs backwards: near = hi
+};
+
+__device__ __forceinline__ SlabRay make_slab_ray(const Ray& r, float M)
+{
+    const float u = 5.9604644775390625e-8f;
+    SlabRay s;
+    s.ix = r.ix; s.iy = r.iy; s.iz = r.iz;
+    const float ex = 5.0f * u * ((M + fabsf(r.ox)) * fabsf(r.ix));
+    const float ey = 5.0f * u * ((M + fabsf(r.oy)) * fabsf(r.iy));
+    const float ez = 5.0f * u * ((M + fabsf(r.oz)) * fabsf(r.iz));
+    const float oix = r.ox * r.ix, oiy = r.oy * r.iy, oiz = r.oz * r.iz;
+    s.nox = oix + ex; s.noy = oiy + ey; s.noz = oiz + ez;
+    s.fox = oix - ex; s.foy = oiy - ey; s.foz = oiz - ez;
+    s.offx = signbit(r.ix) ? 1 : 0;
+    s.offy = signbit(r.iy) ? 1 : 0;
+    s.offz = signbit(r.iz) ? 1 : 0;
+    return s;
+}
+
+// Slab test of the four children of wide node nd: d[k] = entry distance of a
+// hit child (else +inf), c[k] = child index; returns the number of hits.
+__device__ __forceinline__ int slab4(const float4* __restrict__ nd, const SlabRay& s, float d[4], int c[4])
+{
+    const float4 nxv = __ldg(nd + 0 + s.offx), fxv = __ldg(nd + 1 - s.offx);
+    const float4 nyv = __ldg(nd + 2 + s.offy), fyv = __ldg(nd + 3 - s.offy);
+    const float4 nzv = __ldg(nd + 4 + s.offz), fzv = __ldg(nd + 5 - s.offz);
+    const float4 ci = __ldg(nd + 6);
+    const float nx[4] = {nxv.x, nxv.y, nxv.z, nxv.w}, fx[4] = {fxv.x, fxv.y, fxv.z, fxv.w};
+    const float ny[4] = {nyv.x, nyv.y, nyv.z, nyv.w}, fy[4] = {fyv.x, fyv.y, fyv.z, fyv.w};
+    const float nz[4] = {nzv.x, nzv.y, nzv.z, nzv.w}, fz[4] = {fzv.x, fzv.y, fzv.z, fzv.w};
+    const int cc[4] = {__float_as_int(ci.x), __float_as_int(ci.y), __float_as_int(ci.z), __float_as_int(ci.w)};
+    int nh = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float tn = fmaxf(fmaxf(fmaf(nx[k], s.ix, -s.nox), fmaf(ny[k], s.iy, -s.noy)),
+                               fmaxf(fmaf(nz[k], s.iz, -s.noz), 0.0f));
+        const float tf = fminf(fminf(fmaf(fx[k], s.ix, -s.fox), fmaf(fy[k], s.iy, -s.foy)),
+                               fmaf(fz[k], s.iz, -s.foz));
+        const bool hit = tn <= tf;
+        d[k] = hit ? tn : INFINITY;
+        c[k] = cc[k];
+        nh += hit;
+    }
+    return nh;
+}
+
 template <bool kStats>
 __device__ __forceinline__ TraceOut trace4_ifif(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
                                            const Ray& r, int max_steps)
@@ -298,34 +363,14 @@ __device__ __forceinline__ TraceOut trace4_ifif(const float4* __restrict__ wnode
     int sp = 0;
     int cur = 0;
     bool amb = false, ambhit = false;
-    const float rob = 1.0f + 2.0f * 1.7881394e-7f;
-    const bool sx = signbit(r.ix), sy = signbit(r.iy), sz = signbit(r.iz);
+    const SlabRay sr = make_slab_ray(r, r.rs);
     for (int steps = 0;; ++steps) {
         if (steps > max_steps) { out.overflow = 1; out.flags = 1; return out; }
         if (cur >= 0) {
             if (kStats) ++out.nodes;
-            const float4* nd = wnodes + 8 * cur;
-            const float4 lox = __ldg(nd + 0), hix = __ldg(nd + 1), loy = __ldg(nd + 2), hiy = __ldg(nd + 3);
-            const float4 loz = __ldg(nd + 4), hiz = __ldg(nd + 5), ci = __ldg(nd + 6);
             float d[4];
             int c[4];
-            const float lx[4] = {lox.x, lox.y, lox.z, lox.w}, hx[4] = {hix.x, hix.y, hix.z, hix.w};
-            const float ly[4] = {loy.x, loy.y, loy.z, loy.w}, hy[4] = {hiy.x, hiy.y, hiy.z, hiy.w};
-            const float lz[4] = {loz.x, loz.y, loz.z, loz.w}, hz[4] = {hiz.x, hiz.y, hiz.z, hiz.w};
-            const int cc[4] = {__float_as_int(ci.x), __float_as_int(ci.y), __float_as_int(ci.z), __float_as_int(ci.w)};
-            int nh = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float nx = ((sx ? hx[k] : lx[k]) - r.ox) * r.ix, fx = ((sx ? lx[k] : hx[k]) - r.ox) * r.ix;
-                const float ny = ((sy ? hy[k] : ly[k]) - r.oy) * r.iy, fy = ((sy ? ly[k] : hy[k]) - r.oy) * r.iy;
-                const float nz = ((sz ? hz[k] : lz[k]) - r.oz) * r.iz, fz = ((sz ? lz[k] : hz[k]) - r.oz) * r.iz;
-                const float tn = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.0f));
-                const float tf = fminf(fminf(fx, fy), fz) * rob;
-                const bool hit = tn <= tf;
-                d[k] = hit ? tn : INFINITY;
-                c[k] = cc[k];
-                nh += hit;
-            }
+            const int nh = slab4(wnodes + 8 * cur, sr, d, c);
             if (nh == 0) {
                 if (sp == 0) break;
                 cur = stack[--sp];
@@ -382,8 +427,7 @@ __device__ __forceinline__ TraceOut trace4(const float4* __restrict__ wnodes, co
     int sp = 0;
     int cur = 0;
     bool amb = false, ambhit = false;
-    const float rob = 1.0f + 2.0f * 1.7881394e-7f;
-    const bool sx = signbit(r.ix), sy = signbit(r.iy), sz = signbit(r.iz);
+    const SlabRay sr = make_slab_ray(r, r.rs);
     int steps = 0;
     for (;;) {
         // descend through interior nodes until a leaf is current (or the
@@ -391,28 +435,9 @@ __device__ __forceinline__ TraceOut trace4(const float4* __restrict__ wnodes, co
         while (cur >= 0) {
             if (++steps > max_steps) { out.overflow = 1; out.flags = 1; return out; }
             if (kStats) ++out.nodes;
-            const float4* nd = wnodes + 8 * cur;
-            const float4 lox = __ldg(nd + 0), hix = __ldg(nd + 1), loy = __ldg(nd + 2), hiy = __ldg(nd + 3);
-            const float4 loz = __ldg(nd + 4), hiz = __ldg(nd + 5), ci = __ldg(nd + 6);
             float d[4];
             int c[4];
-            const float lx[4] = {lox.x, lox.y, lox.z, lox.w}, hx[4] = {hix.x, hix.y, hix.z, hix.w};
-            const float ly[4] = {loy.x, loy.y, loy.z, loy.w}, hy[4] = {hiy.x, hiy.y, hiy.z, hiy.w};
-            const float lz[4] = {loz.x, loz.y, loz.z, loz.w}, hz[4] = {hiz.x, hiz.y, hiz.z, hiz.w};
-            const int cc[4] = {__float_as_int(ci.x), __float_as_int(ci.y), __float_as_int(ci.z), __float_as_int(ci.w)};
-            int nh = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float nx = ((sx ? hx[k] : lx[k]) - r.ox) * r.ix, fx = ((sx ? lx[k] : hx[k]) - r.ox) * r.ix;
-                const float ny = ((sy ? hy[k] : ly[k]) - r.oy) * r.iy, fy = ((sy ? ly[k] : hy[k]) - r.oy) * r.iy;
-                const float nz = ((sz ? hz[k] : lz[k]) - r.oz) * r.iz, fz = ((sz ? lz[k] : hz[k]) - r.oz) * r.iz;
-                const float tn = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.0f));
-                const float tf = fminf(fminf(fx, fy), fz) * rob;
-                const bool hit = tn <= tf;
-                d[k] = hit ? tn : INFINITY;
-                c[k] = cc[k];
-                nh += hit;
-            }
+            const int nh = slab4(wnodes + 8 * cur, sr, d, c);
             if (nh == 0) {
                 if (sp == 0) {
                     out.flags = (ambhit ? 1 : 0) | (amb ? 2 : 0);
