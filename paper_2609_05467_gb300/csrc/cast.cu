@@ -43,14 +43,16 @@ __device__ __forceinline__ void setup_ray(Ray& r, float ox, float oy, float oz, 
 {
     r.ox = ox; r.oy = oy; r.oz = oz;
     r.dx = dx; r.dy = dy; r.dz = dz;
-    // reciprocals; a zero (or denormal) component gets +-1e30 instead of
-    // +-inf, so slab products stay finite (no inf * 0 = NaN)
+    // reciprocals; a zero (or tiny) component gets +-2^100 instead of
+    // +-inf, so slab products stay finite (no inf * 0 = NaN) and, 2^100
+    // being a power of two, exact: such a slab is decided by the sign of
+    // b - o alone
     r.ix = __frcp_rn(dx);
     r.iy = __frcp_rn(dy);
     r.iz = __frcp_rn(dz);
-    if (!(fabsf(r.ix) <= 1e30f)) r.ix = copysignf(1e30f, dx);
-    if (!(fabsf(r.iy) <= 1e30f)) r.iy = copysignf(1e30f, dy);
-    if (!(fabsf(r.iz) <= 1e30f)) r.iz = copysignf(1e30f, dz);
+    if (!(fabsf(r.ix) <= 0x1p100f)) r.ix = copysignf(0x1p100f, dx);
+    if (!(fabsf(r.iy) <= 0x1p100f)) r.iy = copysignf(0x1p100f, dy);
+    if (!(fabsf(r.iz) <= 0x1p100f)) r.iz = copysignf(0x1p100f, dz);
     const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
     int kz = ax >= ay ? (ax >= az ? 0 : 2) : (ay >= az ? 1 : 2);
     int kx = kz == 2 ? 0 : kz + 1;
@@ -302,7 +304,8 @@ __device__ __forceinline__ TraceOut trace(const float4* __restrict__ nodes, cons
 // 2u|t| + 2u|o i| (+ lower-order terms) <= 4.01 u (M + |o|) |i|; every near
 // distance is lowered and every far distance raised by E = 5 u (M + |o|) |i|
 // (folded into the subtracted constant, its rounding included), so a box
-// the exact ray enters is never rejected.
+// the exact ray enters is never rejected.  An axis with i = +-2^100 (the
+// direction has no component along it) needs no margin: see setup_ray.
 struct SlabRay {
     float ix, iy, iz;
     float nox, noy, noz;    // o * i + E  (subtracted for near distances)
@@ -315,9 +318,11 @@ __device__ __forceinline__ SlabRay make_slab_ray(const Ray& r, float M)
     const float u = 5.9604644775390625e-8f;
     SlabRay s;
     s.ix = r.ix; s.iy = r.iy; s.iz = r.iz;
-    const float ex = 5.0f * u * ((M + fabsf(r.ox)) * fabsf(r.ix));
-    const float ey = 5.0f * u * ((M + fabsf(r.oy)) * fabsf(r.iy));
-    const float ez = 5.0f * u * ((M + fabsf(r.oz)) * fabsf(r.iz));
+    // a +-2^100 reciprocal (axis parallel to the slab) makes b*i and o*i
+    // exact, so only the sign-preserving final rounding remains: no margin
+    const float ex = fabsf(r.ix) == 0x1p100f ? 0.0f : 5.0f * u * ((M + fabsf(r.ox)) * fabsf(r.ix));
+    const float ey = fabsf(r.iy) == 0x1p100f ? 0.0f : 5.0f * u * ((M + fabsf(r.oy)) * fabsf(r.iy));
+    const float ez = fabsf(r.iz) == 0x1p100f ? 0.0f : 5.0f * u * ((M + fabsf(r.oz)) * fabsf(r.iz));
     const float oix = r.ox * r.ix, oiy = r.oy * r.iy, oiz = r.oz * r.iz;
     s.nox = oix + ex; s.noy = oiy + ey; s.noz = oiz + ez;
     s.fox = oix - ex; s.foy = oiy - ey; s.foz = oiz - ez;
