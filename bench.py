@@ -280,15 +280,22 @@ def run_gpu(args, wl, V, F):
     total_steps = args.warmup + args.steps
     ctr = torch.zeros((total_steps, 2, 4), dtype=torch.int64, device=dev)
 
+    side = torch.cuda.Stream(device=dev)
+
     def step(k, ev):
         h = rc.rc_build_bvh(Vd, Fd, stream)
         rc.rc_sample_points(h, n, p, P, Nn, face, None, stream)
         ev[0].record(stream)
         rc.rc_hemisphere_cast(h, P, Nn, p, bits, cnt, ctr[k, 0], stream)
         ev[1].record(stream)
+        # the orthogonal cast needs only the points: it runs on a side stream
+        # while the variability reduction runs on the main one
+        side.wait_event(ev[1])
+        rc.rc_orthogonal_cast(h, P, Nn, p, mask, trav, ctr[k, 1], side)
+        ev[2].record(side)
         s = rc.rc_direction_variability(bits, Nn, p, stream=stream)
         label = rc.rc_classify(s, p)
-        rc.rc_orthogonal_cast(h, P, Nn, p, mask, trav, ctr[k, 1], stream)
+        stream.wait_event(ev[2])
         su = rc.rc_min_setups(h, mask, trav, face, p, cls, stream)
         rc.rc_destroy_bvh(h)
         return s, label, su
@@ -311,7 +318,7 @@ def run_gpu(args, wl, V, F):
     bytes_per_ray = node_bytes * nodes_per_ray + 48.0 * tris_per_ray + 24.0 / N + 1.0 / 8.0
 
     # warm-up
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(total_steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(total_steps)]
     for k in range(args.warmup):
         step(k, evs[k][2:])
     torch.cuda.synchronize()

@@ -480,6 +480,25 @@ rc_status rc_min_setups(rc_bvh h, const uint8_t* d_mask, const float* d_travel, 
     return rc_setup_cover(h_out->mask_hist, h_out);
 }
 
+// A non-blocking side stream and two events per host thread and device,
+// created on first use and kept for the life of the thread.
+struct SideStream { cudaStream_t s = nullptr; cudaEvent_t fork = nullptr, join = nullptr; };
+
+static rc_status side_stream(SideStream** out)
+{
+    static thread_local std::map<int, SideStream> per_device;
+    int dev = 0;
+    RC_CUDA(cudaGetDevice(&dev));
+    SideStream& ss = per_device[dev];
+    if (!ss.s) {
+        RC_CUDA(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+        RC_CUDA(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
+        RC_CUDA(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming));
+    }
+    *out = &ss;
+    return RC_OK;
+}
+
 rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int64_t T, int64_t n,
                           const rc_params* p, uint32_t* h_bits, int32_t* h_count, uint8_t* h_mask,
                           uint8_t* h_class, rc_part_result* h_out, void* stream)
@@ -519,8 +538,14 @@ rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int6
     float* dtrav = (float*)(base + otrav);
     uint8_t* dcls = (uint8_t*)(base + ocls);
     rc_bvh h = nullptr;
+    // with always_setups the orthogonal cast (it needs only the points) runs
+    // on a side stream while the hemispherical cast and the reduction run on
+    // `s`; the side stream joins `s` before the setups
+    SideStream* side = nullptr;
+    bool forked = false;
     auto done = [&](rc_status r) {
         std::string m = t_err;
+        if (forked) cudaStreamSynchronize(side->s);
         cudaFreeAsync(base, s);
         cudaStreamSynchronize(s);
         if (h) rc_destroy_bvh(h);
@@ -533,6 +558,14 @@ rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int6
     RC_CSTEP(cudaMemcpyAsync(dF, h_F, sizeof(int32_t) * 3 * T, cudaMemcpyHostToDevice, s));
     RC_STEP(rc_build_bvh(dV, nV, dF, T, stream, &h));
     RC_STEP(rc_sample_points(h, n, p, dP, dN, dface, dw, stream));
+    if (p->always_setups && n > 0) {
+        RC_STEP(side_stream(&side));
+        RC_CSTEP(cudaEventRecord(side->fork, s));
+        RC_CSTEP(cudaStreamWaitEvent(side->s, side->fork, 0));
+        forked = true;
+        RC_STEP(rc_orthogonal_cast(h, dP, dN, n, p, dmask, dtrav, dctr + 4, side->s));
+        RC_CSTEP(cudaEventRecord(side->join, side->s));
+    }
     RC_STEP(rc_hemisphere_cast(h, dP, dN, n, p, dbits, dcnt, dctr, stream));
     RC_CSTEP(cudaMemcpyAsync(h_out->cast_counters, dctr, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost, s));
     RC_STEP(rc_direction_variability(dbits, dN, dw, n, p, nullptr, nullptr, nullptr, nullptr, &h_out->summary, stream));
@@ -540,7 +573,8 @@ rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int6
     if (h_bits && n) RC_CSTEP(cudaMemcpyAsync(h_bits, dbits, sizeof(uint32_t) * W * n, cudaMemcpyDeviceToHost, s));
     if (h_count && n) RC_CSTEP(cudaMemcpyAsync(h_count, dcnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
     if (p->always_setups || h_out->label == 0) {
-        RC_STEP(rc_orthogonal_cast(h, dP, dN, n, p, dmask, dtrav, dctr + 4, stream));
+        if (forked) RC_CSTEP(cudaStreamWaitEvent(s, side->join, 0));
+        else RC_STEP(rc_orthogonal_cast(h, dP, dN, n, p, dmask, dtrav, dctr + 4, stream));
         RC_CSTEP(cudaMemcpyAsync(h_out->ortho_counters, dctr + 4, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost, s));
         RC_STEP(rc_min_setups(h, dmask, dtrav, dface, n, p, dcls, &h_out->setups, stream));
         h_out->setups_ran = 1;
