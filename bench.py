@@ -396,7 +396,7 @@ def run_gpu(args, wl, V, F):
     l2_gbs = rc.rc_probe_l2(64 << 20, 128, 256, stream)
     l2_16 = rc.rc_probe_l2(64 << 20, 16, 256, stream)
     fp32_tf = rc.rc_probe_fp32(4096, stream)
-    ops_per_ray = 14.0 * (4.0 if ps.tree_width != 2 else 2.0) * nodes_per_ray + 35.0 * tris_per_ray
+    ops_per_ray = 18.0 * (4.0 if ps.tree_width != 2 else 2.0) * nodes_per_ray + 35.0 * tris_per_ray
     fp32_ach = ops_per_ray * rays_cast_step / cast_s / 1e12
 
     if rank != 0:
@@ -431,8 +431,8 @@ def run_gpu(args, wl, V, F):
                                     "bytes per second can exceed these",
                          "fp32": {"achieved": fp32_ach, "peak": fp32_tf, "unit": "TFLOP/s",
                                   "frac": fp32_ach / fp32_tf, "ops_per_ray": ops_per_ray,
-                                  "ops_source": "14 per box test, 35 per triangle test (slab and watertight "
-                                                "formulas)",
+                                  "ops_source": "18 per box test (6 FMA counted as 2 each, 5 min/max, 1 "
+                                                "compare), 35 per triangle test (watertight formulas)",
                                   "peak_source": "measured in this run: rc_probe_fp32, 8 FMA chains per thread"}}},
         "quality": {"ambiguous_rays": amb_rays, "fp64_retests": retests, "errors": errors,
                     "rays_per_step": float(np.mean(rays_per_step)), "wall_s": wall,
