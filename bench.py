@@ -288,9 +288,11 @@ def run_gpu(args, wl, V, F):
         ev[0].record(stream)
         rc.rc_hemisphere_cast(h, P, Nn, p, bits, cnt, ctr[k, 0], stream)
         ev[1].record(stream)
-        # the orthogonal cast needs only the points: it runs on a side stream
-        # while the variability reduction runs on the main one
-        side.wait_event(ev[1])
+        # the orthogonal cast needs only the points: as in rc_analyze_part it
+        # runs on a side stream beside the hemispherical cast, issued after
+        # it so that the persistent kernel holds the SMs first and the
+        # orthogonal cast fills them as it drains
+        side.wait_event(ev[0])
         rc.rc_orthogonal_cast(h, P, Nn, p, mask, trav, ctr[k, 1], side)
         ev[2].record(side)
         s = rc.rc_direction_variability(bits, Nn, p, stream=stream)

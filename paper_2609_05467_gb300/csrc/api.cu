@@ -539,7 +539,7 @@ rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int6
     uint8_t* dcls = (uint8_t*)(base + ocls);
     rc_bvh h = nullptr;
     // with always_setups the orthogonal cast (it needs only the points) runs
-    // on a side stream while the hemispherical cast and the reduction run on
+    // on a side stream beside the hemispherical cast and the reduction on
     // `s`; the side stream joins `s` before the setups
     SideStream* side = nullptr;
     bool forked = false;
@@ -561,12 +561,16 @@ rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int6
     if (p->always_setups && n > 0) {
         RC_STEP(side_stream(&side));
         RC_CSTEP(cudaEventRecord(side->fork, s));
+    }
+    RC_STEP(rc_hemisphere_cast(h, dP, dN, n, p, dbits, dcnt, dctr, stream));
+    if (side) {
+        // issued after the hemispherical cast, whose persistent kernel then
+        // holds the SMs first; the orthogonal cast fills them as it drains
         RC_CSTEP(cudaStreamWaitEvent(side->s, side->fork, 0));
         forked = true;
         RC_STEP(rc_orthogonal_cast(h, dP, dN, n, p, dmask, dtrav, dctr + 4, side->s));
         RC_CSTEP(cudaEventRecord(side->join, side->s));
     }
-    RC_STEP(rc_hemisphere_cast(h, dP, dN, n, p, dbits, dcnt, dctr, stream));
     RC_CSTEP(cudaMemcpyAsync(h_out->cast_counters, dctr, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost, s));
     RC_STEP(rc_direction_variability(dbits, dN, dw, n, p, nullptr, nullptr, nullptr, nullptr, &h_out->summary, stream));
     RC_STEP(rc_classify(&h_out->summary, p, &h_out->label));

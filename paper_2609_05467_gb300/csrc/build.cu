@@ -4,12 +4,14 @@
 // Pipeline (one stream):
 //   face_prep   : FP64 normal / area / centroid per face, fp32 face boxes,
 //                 mesh validation, scene bounds (atomics)
-//   morton      : 63-bit Morton code of each face-box centre
-//   radix sort  : 8 passes of 8-bit LSD (histogram / scan / stable scatter)
+//   morton      : 48-bit Morton code of each face-box centre (16 bits per axis)
+//   radix sort  : 6 passes of 8-bit LSD (histogram / scan / stable scatter)
 //   karras      : binary radix tree over the sorted codes (Karras, HPG 2012)
 //   refit       : bottom-up boxes with arrival counters
 //   pack        : BVH2 nodes holding both child boxes (64 B), leaves of up
 //                 to kLeafMax consecutive triangles, triangle records 48 B
+//   wide        : top-down collapse into 4-wide nodes (128 B): the top
+//                 levels one launch each, the subtrees below depth-first
 //   area cdf    : 2^32-quantised face areas, inclusive int64 prefix
 #include <math.h>
 #include <stdio.h>
@@ -105,6 +107,16 @@ __device__ __forceinline__ unsigned long long spread21(unsigned long long x)
     return x;
 }
 
+// Morton code of each face-box centre, kMortonBits per axis (interleaved
+// x, y, z from the top); the radix sort then needs kMortonPasses byte passes
+#ifndef RC_MORTON_BITS
+#define RC_MORTON_BITS 16
+#endif
+constexpr int kMortonBits = RC_MORTON_BITS;
+constexpr int kMortonPasses = (3 * kMortonBits + 7) / 8;
+static_assert(kMortonBits >= 8 && kMortonBits <= 21, "Morton bits per axis out of range");
+static_assert(kMortonPasses % 2 == 0, "an even number of sort passes leaves the result in place");
+
 __global__ void k_morton(const float* __restrict__ tbox, int64_t T, const DevScalars* sc,
                          unsigned long long* keys, int32_t* vals)
 {
@@ -118,7 +130,8 @@ __global__ void k_morton(const float* __restrict__ tbox, int64_t T, const DevSca
         float ext = hi - lo;
         float u = ext > 0.0f ? (c - lo) / ext : 0.0f;
         u = fminf(fmaxf(u, 0.0f), 1.0f);
-        unsigned long long q = (unsigned long long)fminf(u * 2097152.0f, 2097151.0f);
+        const float cells = (float)(1 << kMortonBits);
+        unsigned long long q = (unsigned long long)fminf(u * cells, cells - 1.0f);
         code |= spread21(q) << (2 - k);
     }
     keys[f] = code;
@@ -577,16 +590,13 @@ __device__ __forceinline__ float half_area(const float* b)
     return dx * dy + dy * dz + dz * dx;
 }
 
-__global__ void k_wide_level(int64_t n_int, const int32_t* __restrict__ child, const int32_t* __restrict__ range,
-                             const float* __restrict__ nbox, const int32_t* __restrict__ qin_bin,
-                             const int32_t* __restrict__ qin_wide, const int* __restrict__ qin_count,
-                             int32_t* qout_bin, int32_t* qout_wide, int* qout_count, int* wide_count,
-                             float4* wnodes, DevScalars* sc, int level)
+// the children of the wide node made from binary interior node b: start
+// from b's two children and keep replacing the interior child of largest box
+// surface area by its two children until there are four or only leaves
+__device__ __forceinline__ int wide_children(int32_t b, int64_t n_int, const int32_t* __restrict__ child,
+                                             const int32_t* __restrict__ range, const float* __restrict__ nbox,
+                                             int32_t ch[4])
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= *qin_count) return;
-    const int32_t b = qin_bin[t], w = qin_wide[t];
-    int32_t ch[4];
     int nch = 2;
     ch[0] = child[2 * b];
     ch[1] = child[2 * b + 1];
@@ -603,24 +613,24 @@ __global__ void k_wide_level(int64_t n_int, const int32_t* __restrict__ child, c
         ch[best] = child[2 * c];
         ch[nch++] = child[2 * c + 1];
     }
+    return nch;
+}
+
+// write wide node w: the boxes of its nch children and their indices idx
+// (wide node >= 0, leaf < 0); empty slots get an empty box and index -1
+__device__ __forceinline__ void wide_write(float4* wnodes, int32_t w, const float* __restrict__ nbox,
+                                           const int32_t ch[4], const int32_t idx[4], int nch)
+{
     float lo[3][4], hi[3][4];
-    int32_t idx[4];
+    int32_t ix[4];
     for (int k = 0; k < 4; ++k) {
         if (k < nch) {
             const float* bb = nbox + 6 * (int64_t)ch[k];
             for (int a = 0; a < 3; ++a) { lo[a][k] = bb[a]; hi[a][k] = bb[3 + a]; }
-            if (bin_is_leaf(ch[k], n_int, range)) {
-                idx[k] = encode_child(ch[k], n_int, range);
-            } else {
-                const int nw = atomicAdd(wide_count, 1);
-                const int q = atomicAdd(qout_count, 1);
-                qout_bin[q] = ch[k];
-                qout_wide[q] = nw;
-                idx[k] = nw;
-            }
+            ix[k] = idx[k];
         } else {
             for (int a = 0; a < 3; ++a) { lo[a][k] = INFINITY; hi[a][k] = -INFINITY; }
-            idx[k] = -1;
+            ix[k] = -1;
         }
     }
     float4* nd = wnodes + 8 * (int64_t)w;
@@ -630,9 +640,86 @@ __global__ void k_wide_level(int64_t n_int, const int32_t* __restrict__ child, c
     nd[3] = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
     nd[4] = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
     nd[5] = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
-    nd[6] = make_float4(__int_as_float(idx[0]), __int_as_float(idx[1]), __int_as_float(idx[2]), __int_as_float(idx[3]));
+    nd[6] = make_float4(__int_as_float(ix[0]), __int_as_float(ix[1]), __int_as_float(ix[2]), __int_as_float(ix[3]));
     nd[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+// one level of the top of the tree: each queued binary node becomes a wide
+// node; its interior children go to the next level's queue
+__global__ void k_wide_level(int64_t n_int, const int32_t* __restrict__ child, const int32_t* __restrict__ range,
+                             const float* __restrict__ nbox, const int32_t* __restrict__ qin_bin,
+                             const int32_t* __restrict__ qin_wide, const int* __restrict__ qin_count,
+                             int32_t* qout_bin, int32_t* qout_wide, int* qout_count, int* wide_count,
+                             float4* wnodes, DevScalars* sc, int level)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *qin_count) return;
+    const int32_t b = qin_bin[t], w = qin_wide[t];
+    int32_t ch[4], idx[4];
+    const int nch = wide_children(b, n_int, child, range, nbox, ch);
+    for (int k = 0; k < nch; ++k) {
+        if (bin_is_leaf(ch[k], n_int, range)) {
+            idx[k] = encode_child(ch[k], n_int, range);
+        } else {
+            const int nw = atomicAdd(wide_count, 1);
+            const int q = atomicAdd(qout_count, 1);
+            qout_bin[q] = ch[k];
+            qout_wide[q] = nw;
+            idx[k] = nw;
+        }
+    }
+    wide_write(wnodes, w, nbox, ch, idx, nch);
     atomicMax(&sc->wide_depth, level + 1);
+}
+
+// the rest of the tree: each thread finishes the subtree below one queued
+// binary node depth-first, so a subtree's wide nodes are made by one thread
+// (numbered with the siblings of a node consecutive).  A subtree deeper than
+// the stack reports a wide depth that the host rejects.
+constexpr int kWideDfs = 96;
+#ifndef RC_WIDE_SUBTREE
+#define RC_WIDE_SUBTREE 16.0     // binary nodes per subtree thread (0: one launch per level throughout)
+#endif
+
+__global__ void k_wide_subtrees(int64_t n_int, const int32_t* __restrict__ child, const int32_t* __restrict__ range,
+                                const float* __restrict__ nbox, const int32_t* __restrict__ qin_bin,
+                                const int32_t* __restrict__ qin_wide, const int* __restrict__ qin_count,
+                                int* wide_count, float4* wnodes, DevScalars* sc, int level)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *qin_count) return;
+    int32_t sb[kWideDfs], sw[kWideDfs];
+    uint8_t sd[kWideDfs];
+    sb[0] = qin_bin[t];
+    sw[0] = qin_wide[t];
+    sd[0] = 0;
+    int sp = 1, maxd = 0;
+    while (sp > 0) {
+        --sp;
+        const int32_t b = sb[sp], w = sw[sp];
+        const int d = sd[sp];
+        int32_t ch[4], idx[4];
+        const int nch = wide_children(b, n_int, child, range, nbox, ch);
+        int ni = 0;
+        for (int k = 0; k < nch; ++k) ni += bin_is_leaf(ch[k], n_int, range) ? 0 : 1;
+        if (sp + ni > kWideDfs || d + 1 > 250) {
+            atomicMax(&sc->wide_depth, kStack4);
+            return;
+        }
+        int nw = ni ? atomicAdd(wide_count, ni) : 0;
+        for (int k = 0; k < nch; ++k) idx[k] = bin_is_leaf(ch[k], n_int, range) ? encode_child(ch[k], n_int, range)
+                                                                                 : nw++;
+        wide_write(wnodes, w, nbox, ch, idx, nch);
+        maxd = max(maxd, d + 1);
+        for (int k = nch - 1; k >= 0; --k) {     // the first child is taken next
+            if (idx[k] < 0) continue;
+            sb[sp] = ch[k];
+            sw[sp] = idx[k];
+            sd[sp] = (uint8_t)(d + 1);
+            ++sp;
+        }
+    }
+    atomicMax(&sc->wide_depth, level + maxd);
 }
 
 // wide root for parts with at most kLeafMax triangles: one leaf child
@@ -1062,8 +1149,16 @@ static rc_status build_wide(rc_bvh h, const float* tbox, cudaStream_t s)
     int *ca = counts, *cb = counts + 1;
     k_wide_init<<<1, 32, 0, s>>>(qa_bin, qa_wide, counts);
     RC_LAUNCHED();
-    // a wide level consumes at least one binary level: max_depth + 1 launches suffice
-    for (int level = 0; level <= h->max_depth; ++level) {
+    // The top `split` levels take one launch each (a level's queue is at most
+    // 4^level long); then one launch finishes every queued subtree, a thread
+    // each, once the queue holds about n_int / RC_WIDE_SUBTREE nodes.  A wide level
+    // consumes at least one binary level, so max_depth + 1 levels finish the
+    // tree if the split is never reached.
+    int split = 0;
+    while (split < 30 && std::pow(4.0, (double)split) * RC_WIDE_SUBTREE < (double)n_int) ++split;
+    split = RC_WIDE_SUBTREE > 0 ? std::min(split, h->max_depth + 1) : h->max_depth + 1;
+    int level = 0;
+    for (; level < split; ++level) {
         const double cap = std::min((double)n_int, std::pow(4.0, (double)std::min(level, 30)));
         const unsigned grid = (unsigned)std::max(1.0, std::ceil(cap / 256.0));
         RC_CUDA(cudaMemsetAsync(cb, 0, sizeof(int), s));
@@ -1073,6 +1168,13 @@ static rc_status build_wide(rc_bvh h, const float* tbox, cudaStream_t s)
         std::swap(qa_bin, qb_bin);
         std::swap(qa_wide, qb_wide);
         std::swap(ca, cb);
+    }
+    {
+        const double cap = std::min((double)n_int, std::pow(4.0, (double)std::min(level, 30)));
+        const unsigned grid = (unsigned)std::max(1.0, std::ceil(cap / 256.0));
+        k_wide_subtrees<<<grid, 256, 0, s>>>(n_int, h->child, h->range, h->nbox, qa_bin, qa_wide, ca, counts + 2,
+                                             h->wnodes, h->sc, level);
+        RC_LAUNCHED();
     }
     RC_CUDA(cudaFreeAsync(q, s));
     RC_CUDA(cudaFreeAsync(counts, s));
@@ -1106,9 +1208,9 @@ rc_status build_bvh(rc_bvh h, cudaStream_t s)
         RC_CUDA(cudaMallocAsync(&k0, sizeof(unsigned long long) * T, s));
         k_morton<<<nblocks(T, 256), 256, 0, s>>>(tbox, T, h->sc, k0, h->order);
         RC_LAUNCHED();
-        rc_status sst = sort_pairs(k0, h->order, T, 8, (unsigned int*)&h->sc->pad, s);
+        rc_status sst = sort_pairs(k0, h->order, T, kMortonPasses, (unsigned int*)&h->sc->pad, s);
         if (sst != RC_OK) return sst;
-        // after 8 passes the sorted data is back in (k0, h->order)
+        // after an even number of passes the sorted data is back in (k0, h->order)
         const int64_t n_int = h->n_int;
         RC_CUDA(cudaMallocAsync(&h->parent, sizeof(int32_t) * (n_int + T), s));
         RC_CUDA(cudaMallocAsync(&h->child, sizeof(int32_t) * 2 * n_int, s));

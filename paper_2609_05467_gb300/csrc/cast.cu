@@ -1177,62 +1177,75 @@ k_batch(const BatchPart* __restrict__ parts, int n_parts, long long n_items, int
 }
 
 // ---------------------------------------------------------------------------
-// Section 3.2: orthogonal cast.  A warp holds 32 points (Morton order) and
-// casts, frame after frame, the six axes (+X', -X', +Y', -Y', +Z', -Z') one
-// after the other, so all lanes follow the same direction at a time; each
-// lane keeps its point's six-bit mask in a register.  Travel to the frame
-// bounding box is FP64.  Frame f writes mask[f n + i] and travel[f n + i][6].
+// Section 3.2: orthogonal cast along the six frame axes (+X', -X', +Y', -Y',
+// +Z', -Z').  A work item (frame f, axis a, group g) is 32 consecutive points
+// of the Morton processing order cast along one axis, one ray per lane --
+// parallel rays from neighbouring origins.  Warps take items one at a time
+// from a counter, because a few rays that graze a surface parallel to an axis
+// (along a fillet or a bore) take far longer than the rest.  Travel to the
+// frame bounding box is FP64.  Frame f writes travel[f n + i][6]; reachable
+// bits gather in mbits[f n + i] (zeroed by the caller) and are packed into
+// mask[f n + i] afterwards.
 // ---------------------------------------------------------------------------
 template <bool kStats, bool kWide>
 __global__ void __launch_bounds__(128, RC_BATCH_MIN_BLOCKS)
-k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
-             const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
-             const int32_t* __restrict__ order, const FrameDev* __restrict__ fds, int nf, double eps,
-             double par_tol, uint8_t* __restrict__ mask, float* __restrict__ travel, unsigned long long* counters)
+k_orthogonal_axis(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps,
+                  float scene_maxabs, const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
+                  const int32_t* __restrict__ order, const FrameDev* __restrict__ fds, int nf, double eps,
+                  double par_tol, uint32_t* __restrict__ mbits, float* __restrict__ travel,
+                  unsigned long long* counters, unsigned long long* work)
 {
     const int lane = threadIdx.x & 31;
     int amb = 0, retests = 0, overflow = 0;
     long long rays = 0, nvis = 0, ntri = 0;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t wv = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wv * 32 < n; wv += nwarps) {
-        const int64_t k = wv * 32 + lane;
+    const int64_t G = (n + 31) >> 5;
+    const int64_t items = (int64_t)nf * 6 * G;
+    for (;;) {
+        unsigned long long w = 0;
+        if (lane == 0) w = atomicAdd(work, 1ULL);
+        const int64_t it = (int64_t)__shfl_sync(0xFFFFFFFFu, w, 0);
+        if (it >= items) break;
+        const int fa = (int)(it / G);
+        const int64_t g = it - (int64_t)fa * G;
+        const int f = fa / 6, a = fa - 6 * f;
+        const int64_t k = g * 32 + lane;
         if (k >= n) continue;
         const int64_t i = order ? (int64_t)__ldg(&order[k]) : k;
         const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
         const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
-        const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
-        for (int f = 0; f < nf; ++f) {
-            const float* axes = fds[f].axes;
-            const double* frame = fds[f].frame;
-            const double* fbox = fds[f].fbox;
-            const int64_t row = (int64_t)f * n + i;
-            unsigned m = 0;
-            for (int a = 0; a < 6; ++a) {
-                const float dx = axes[3 * a], dy = axes[3 * a + 1], dz = axes[3 * a + 2];
-                const int kk = a >> 1;
-                double q = __dadd_rn(__dmul_rn((double)px, frame[kk]), __dmul_rn((double)py, frame[3 + kk]));
-                q = __dadd_rn(q, __dmul_rn((double)pz, frame[6 + kk]));
-                const double tv = (a & 1) ? __dsub_rn(q, fbox[kk]) : __dsub_rn(fbox[3 + kk], q);
-                travel[6 * row + a] = __double2float_rn(tv);
-                // eligibility n.a >= -parallel_tol (FP64, x, y, z order)
-                double nd = __dadd_rn(__dmul_rn((double)nx, (double)dx), __dmul_rn((double)ny, (double)dy));
-                nd = __dadd_rn(nd, __dmul_rn((double)nz, (double)dz));
-                if (nd >= -par_tol) {
-                    Ray r;
-                    setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-                    const TraceOut t = trace_any<kStats, kWide>(nodes, tris, r, max_steps);
-                    retests += t.retests;
-                    overflow += t.overflow;
-                    amb += (t.flags >> 1) & 1;
-                    if ((t.flags & 1) == 0) m |= 1u << a;
-                    rays += 1;
-                    if (kStats) { nvis += t.nodes; ntri += t.tris; }
-                }
-            }
-            mask[row] = (uint8_t)m;
+        const float* axes = fds[f].axes;
+        const double* frame = fds[f].frame;
+        const double* fbox = fds[f].fbox;
+        const int64_t row = (int64_t)f * n + i;
+        const float dx = axes[3 * a], dy = axes[3 * a + 1], dz = axes[3 * a + 2];
+        const int kk = a >> 1;
+        double q = __dadd_rn(__dmul_rn((double)px, frame[kk]), __dmul_rn((double)py, frame[3 + kk]));
+        q = __dadd_rn(q, __dmul_rn((double)pz, frame[6 + kk]));
+        const double tv = (a & 1) ? __dsub_rn(q, fbox[kk]) : __dsub_rn(fbox[3 + kk], q);
+        travel[6 * row + a] = __double2float_rn(tv);
+        // eligibility n.a >= -parallel_tol (FP64, x, y, z order)
+        double nd = __dadd_rn(__dmul_rn((double)nx, (double)dx), __dmul_rn((double)ny, (double)dy));
+        nd = __dadd_rn(nd, __dmul_rn((double)nz, (double)dz));
+        if (nd >= -par_tol) {
+            Ray r;
+            setup_ray(r, offset_coord(px, nx, eps), offset_coord(py, ny, eps), offset_coord(pz, nz, eps), dx, dy, dz,
+                      scene_maxabs);
+            const TraceOut t = trace_any<kStats, kWide>(nodes, tris, r, max_steps);
+            retests += t.retests;
+            overflow += t.overflow;
+            amb += (t.flags >> 1) & 1;
+            if ((t.flags & 1) == 0) atomicOr(&mbits[row], 1u << a);
+            rays += 1;
+            if (kStats) { nvis += t.nodes; ntri += t.tris; }
         }
     }
     warp_add_counters(counters, rays, amb, retests, overflow, nvis, ntri);
+}
+
+__global__ void k_mask_pack(const uint32_t* __restrict__ mbits, int64_t m, uint8_t* __restrict__ mask)
+{
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < m) mask[r] = (uint8_t)mbits[r];
 }
 
 // ---------------------------------------------------------------------------
@@ -1243,69 +1256,72 @@ k_orthogonal(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
 // c + r (cos t_k u + sin t_k v), (u, v) the branchless orthonormal basis of
 // a (Duff et al. 2017) in FP64; origins are rounded to fp32, every ray goes
 // along a.  The axis is tool-accessible iff it is eligible (n.a >=
-// -parallel_tol) and none of the 1 + K rays is obstructed.
+// -parallel_tol) and none of the 1 + K rays is obstructed.  Work items are
+// (axis, 32 consecutive points) as in the orthogonal cast; accessible bits
+// gather in mbits[i] (zeroed by the caller).
 // ---------------------------------------------------------------------------
 template <bool kWide>
 __global__ void __launch_bounds__(128, RC_BATCH_MIN_BLOCKS)
-k_tool_cast(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
-            const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n, const int32_t* __restrict__ order,
-            const FrameDev* __restrict__ fd, double eps, double par_tol, double radius,
-            const double2* __restrict__ ring /*cos, sin*/, int K, uint8_t* __restrict__ mask,
-            unsigned long long* counters)
+k_tool_cast_axis(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps,
+                 float scene_maxabs, const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
+                 const int32_t* __restrict__ order, const FrameDev* __restrict__ fd, double eps, double par_tol,
+                 double radius, const double2* __restrict__ ring /*cos, sin*/, int K, uint32_t* __restrict__ mbits,
+                 unsigned long long* counters, unsigned long long* work)
 {
     const int lane = threadIdx.x & 31;
     int amb = 0, retests = 0, overflow = 0;
     long long rays = 0;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t wv = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wv * 32 < n; wv += nwarps) {
-        const int64_t k = wv * 32 + lane;
+    const int64_t G = (n + 31) >> 5;
+    const int64_t items = 6 * G;
+    for (;;) {
+        unsigned long long w = 0;
+        if (lane == 0) w = atomicAdd(work, 1ULL);
+        const int64_t it = (int64_t)__shfl_sync(0xFFFFFFFFu, w, 0);
+        if (it >= items) break;
+        const int a = (int)(it / G);
+        const int64_t k = (it - (int64_t)a * G) * 32 + lane;
         if (k >= n) continue;
         const int64_t i = order ? (int64_t)__ldg(&order[k]) : k;
         const double px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
-        const float nxf = Nrm[3 * i], nyf = Nrm[3 * i + 1], nzf = Nrm[3 * i + 2];
-        const double nx = nxf, ny = nyf, nz = nzf;
+        const double nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
+        const float dx = fd->axes[3 * a], dy = fd->axes[3 * a + 1], dz = fd->axes[3 * a + 2];
+        double nd = __dadd_rn(__dmul_rn(nx, (double)dx), __dmul_rn(ny, (double)dy));
+        nd = __dadd_rn(nd, __dmul_rn(nz, (double)dz));
+        if (!(nd >= -par_tol)) continue;
         const double h = __dadd_rn(radius, eps);
         const double cx = __dadd_rn(px, __dmul_rn(h, nx)), cy = __dadd_rn(py, __dmul_rn(h, ny)),
                      cz = __dadd_rn(pz, __dmul_rn(h, nz));
-        unsigned m = 0;
-        for (int a = 0; a < 6; ++a) {
-            const float dx = fd->axes[3 * a], dy = fd->axes[3 * a + 1], dz = fd->axes[3 * a + 2];
-            double nd = __dadd_rn(__dmul_rn(nx, (double)dx), __dmul_rn(ny, (double)dy));
-            nd = __dadd_rn(nd, __dmul_rn(nz, (double)dz));
-            if (!(nd >= -par_tol)) continue;
-            // orthonormal basis (u, v) of the axis, FP64
-            const double ax = dx, ay = dy, az = dz;
-            const double sg = az >= 0.0 ? 1.0 : -1.0;
-            const double q = __ddiv_rn(-1.0, __dadd_rn(sg, az));
-            const double bb = __dmul_rn(__dmul_rn(ax, ay), q);
-            const double ux = __dadd_rn(1.0, __dmul_rn(__dmul_rn(__dmul_rn(sg, ax), ax), q));
-            const double uy = __dmul_rn(sg, bb), uz = __dmul_rn(-sg, ax);
-            const double vx = bb, vy = __dadd_rn(sg, __dmul_rn(__dmul_rn(ay, ay), q)), vz = -ay;
-            bool open = true;
-            for (int r = -1; r < K && open; ++r) {
-                float ox, oy, oz;
-                if (r < 0) {
-                    ox = __double2float_rn(cx);
-                    oy = __double2float_rn(cy);
-                    oz = __double2float_rn(cz);
-                } else {
-                    const double rc = __dmul_rn(radius, ring[r].x), rs = __dmul_rn(radius, ring[r].y);
-                    ox = __double2float_rn(__dadd_rn(__dadd_rn(cx, __dmul_rn(rc, ux)), __dmul_rn(rs, vx)));
-                    oy = __double2float_rn(__dadd_rn(__dadd_rn(cy, __dmul_rn(rc, uy)), __dmul_rn(rs, vy)));
-                    oz = __double2float_rn(__dadd_rn(__dadd_rn(cz, __dmul_rn(rc, uz)), __dmul_rn(rs, vz)));
-                }
-                Ray ray;
-                setup_ray(ray, ox, oy, oz, dx, dy, dz, scene_maxabs);
-                const TraceOut t = trace_any<false, kWide>(nodes, tris, ray, max_steps);
-                retests += t.retests;
-                overflow += t.overflow;
-                amb += (t.flags >> 1) & 1;
-                rays += 1;
-                open = (t.flags & 1) == 0;
+        // orthonormal basis (u, v) of the axis, FP64
+        const double ax = dx, ay = dy, az = dz;
+        const double sg = az >= 0.0 ? 1.0 : -1.0;
+        const double q = __ddiv_rn(-1.0, __dadd_rn(sg, az));
+        const double bb = __dmul_rn(__dmul_rn(ax, ay), q);
+        const double ux = __dadd_rn(1.0, __dmul_rn(__dmul_rn(__dmul_rn(sg, ax), ax), q));
+        const double uy = __dmul_rn(sg, bb), uz = __dmul_rn(-sg, ax);
+        const double vx = bb, vy = __dadd_rn(sg, __dmul_rn(__dmul_rn(ay, ay), q)), vz = -ay;
+        bool open = true;
+        for (int r = -1; r < K && open; ++r) {
+            float ox, oy, oz;
+            if (r < 0) {
+                ox = __double2float_rn(cx);
+                oy = __double2float_rn(cy);
+                oz = __double2float_rn(cz);
+            } else {
+                const double rc = __dmul_rn(radius, ring[r].x), rs = __dmul_rn(radius, ring[r].y);
+                ox = __double2float_rn(__dadd_rn(__dadd_rn(cx, __dmul_rn(rc, ux)), __dmul_rn(rs, vx)));
+                oy = __double2float_rn(__dadd_rn(__dadd_rn(cy, __dmul_rn(rc, uy)), __dmul_rn(rs, vy)));
+                oz = __double2float_rn(__dadd_rn(__dadd_rn(cz, __dmul_rn(rc, uz)), __dmul_rn(rs, vz)));
             }
-            if (open) m |= 1u << a;
+            Ray ray;
+            setup_ray(ray, ox, oy, oz, dx, dy, dz, scene_maxabs);
+            const TraceOut t = trace_any<false, kWide>(nodes, tris, ray, max_steps);
+            retests += t.retests;
+            overflow += t.overflow;
+            amb += (t.flags >> 1) & 1;
+            rays += 1;
+            open = (t.flags & 1) == 0;
         }
-        mask[i] = (uint8_t)m;
+        if (open) atomicOr(&mbits[i], 1u << a);
     }
     warp_add_counters(counters, rays, amb, retests, overflow);
 }
@@ -1541,21 +1557,28 @@ rc_status launch_orthogonal_frames(rc_bvh h, const float* P, const float* N, int
                                    const FrameDev* fds, int nf, uint8_t* mask, float* travel,
                                    unsigned long long* counters, cudaStream_t s)
 {
+    if (n == 0) return RC_OK;
     int32_t* order = nullptr;
     if (p->point_order == 0 && n > 1) {
         RC_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * n, s));
         rc_status pst = point_order(h, P, n, order, s);
         if (pst != RC_OK) return pst;
     }
-    int64_t blocks = (n + 127) / 128;
+    const int64_t m = (int64_t)nf * n;
+    uint32_t* mbits = nullptr;                 // m words, then the item counter
+    const int64_t mw = (m + 1) & ~(int64_t)1;
+    RC_CUDA(cudaMallocAsync(&mbits, sizeof(uint32_t) * (mw + 2), s));
+    RC_CUDA(cudaMemsetAsync(mbits, 0, sizeof(uint32_t) * (mw + 2), s));
+    unsigned long long* work = (unsigned long long*)(mbits + mw);
+    const int64_t items = (int64_t)nf * 6 * ((n + 31) / 32);
     const int64_t cap = (int64_t)sm_count() * RC_BATCH_MIN_BLOCKS;
+    int64_t blocks = (items + 3) / 4;
     if (blocks > cap && p->launch_mode == 0) blocks = cap;
-    if (blocks < 1) blocks = 1;
     const float4* tree = use_wide(p) ? h->wnodes : h->nodes;
-#define RC_ORTHO(ST, WD)                                                                                          \
-    k_orthogonal<ST, WD><<<(unsigned)blocks, 128, 0, s>>>(tree, h->tris, max_steps(h), h->scene_maxabs, P, N, n,  \
-                                                          order, fds, nf, p->origin_offset, p->parallel_tol, mask, \
-                                                          travel, counters)
+#define RC_ORTHO(ST, WD)                                                                                      \
+    k_orthogonal_axis<ST, WD><<<(unsigned)blocks, 128, 0, s>>>(tree, h->tris, max_steps(h), h->scene_maxabs, \
+                                                               P, N, n, order, fds, nf, p->origin_offset,    \
+                                                               p->parallel_tol, mbits, travel, counters, work)
     const bool stats = p->collect_stats != 0;
     if (stats && use_wide(p)) RC_ORTHO(true, true);
     else if (stats) RC_ORTHO(true, false);
@@ -1563,6 +1586,9 @@ rc_status launch_orthogonal_frames(rc_bvh h, const float* P, const float* N, int
     else RC_ORTHO(false, false);
 #undef RC_ORTHO
     RC_LAUNCHED();
+    k_mask_pack<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(mbits, m, mask);
+    RC_LAUNCHED();
+    RC_CUDA(cudaFreeAsync(mbits, s));
     if (order) RC_CUDA(cudaFreeAsync(order, s));
     return RC_OK;
 }
@@ -1578,34 +1604,53 @@ rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n,
     return st;
 }
 
+// RC_LAUNCHED without the early return
+static rc_status launch_status()
+{
+    count_launch();
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RC_OK : cuda_error(e, "kernel launch");
+}
+
 rc_status launch_tool_cast(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p, double radius,
                           const double2* ring, int K, uint8_t* mask, unsigned long long* counters, cudaStream_t s)
 {
+    if (n == 0) return RC_OK;
     FrameDev* fd = nullptr;
-    RC_CUDA(cudaMallocAsync(&fd, sizeof(FrameDev), s));
-    rc_status st = frame_setup(h, p, fd, s);
     int32_t* order = nullptr;
-    if (st == RC_OK && p->point_order == 0 && n > 1) {
-        RC_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * n, s));
-        st = point_order(h, P, n, order, s);
-    }
+    uint32_t* mbits = nullptr;                     // n words, then the item counter
+    const int64_t mw = (n + 1) & ~(int64_t)1;
+    cudaError_t e = cudaMallocAsync(&fd, sizeof(FrameDev), s);
+    if (e == cudaSuccess && p->point_order == 0 && n > 1) e = cudaMallocAsync(&order, sizeof(int32_t) * n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&mbits, sizeof(uint32_t) * (mw + 2), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mbits, 0, sizeof(uint32_t) * (mw + 2), s);
+    rc_status st = e == cudaSuccess ? RC_OK : cuda_error(e, "tool cast scratch");
+    if (st == RC_OK) st = frame_setup(h, p, fd, s);
+    if (st == RC_OK && order) st = point_order(h, P, n, order, s);
     if (st == RC_OK) {
-        int64_t blocks = (n + 127) / 128;
+        int64_t blocks = (6 * ((n + 31) / 32) + 3) / 4;
         const int64_t cap = (int64_t)sm_count() * RC_BATCH_MIN_BLOCKS;
         if (blocks > cap) blocks = cap;
-        if (blocks < 1) blocks = 1;
+        unsigned long long* work = (unsigned long long*)(mbits + mw);
         if (use_wide(p))
-            k_tool_cast<true><<<(unsigned)blocks, 128, 0, s>>>(h->wnodes, h->tris, max_steps(h), h->scene_maxabs, P,
-                                                              N, n, order, fd, p->origin_offset, p->parallel_tol,
-                                                              radius, ring, K, mask, counters);
+            k_tool_cast_axis<true><<<(unsigned)blocks, 128, 0, s>>>(h->wnodes, h->tris, max_steps(h), h->scene_maxabs,
+                                                                   P, N, n, order, fd, p->origin_offset,
+                                                                   p->parallel_tol, radius, ring, K, mbits, counters,
+                                                                   work);
         else
-            k_tool_cast<false><<<(unsigned)blocks, 128, 0, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs, P,
-                                                               N, n, order, fd, p->origin_offset, p->parallel_tol,
-                                                               radius, ring, K, mask, counters);
-        RC_LAUNCHED();
+            k_tool_cast_axis<false><<<(unsigned)blocks, 128, 0, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs,
+                                                                    P, N, n, order, fd, p->origin_offset,
+                                                                    p->parallel_tol, radius, ring, K, mbits, counters,
+                                                                    work);
+        st = launch_status();
     }
-    cudaFreeAsync(fd, s);
+    if (st == RC_OK) {
+        k_mask_pack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(mbits, n, mask);
+        st = launch_status();
+    }
+    if (mbits) cudaFreeAsync(mbits, s);
     if (order) cudaFreeAsync(order, s);
+    if (fd) cudaFreeAsync(fd, s);
     return st;
 }
 

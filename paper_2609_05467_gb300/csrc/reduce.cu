@@ -43,7 +43,10 @@ __device__ __forceinline__ long long fixed40(float x)
 }
 
 // One warp per point: recompute each visible direction, sum llrint(d*2^40)
-// per axis, count visible rays per largest-|component| axis.
+// per axis, count visible rays per largest-|component| axis.  The point's
+// bit row is read 32 words at a time by the whole warp (one coalesced load)
+// and each word is handed to the lanes by a shuffle, so the loop over the
+// words waits on memory once per 32 words instead of once per word.
 __global__ void __launch_bounds__(256)
 k_variability(const uint32_t* __restrict__ bits, const float* __restrict__ Nrm,
               const double* __restrict__ weight, const double* __restrict__ wmax_p, int64_t n,
@@ -63,23 +66,28 @@ k_variability(const uint32_t* __restrict__ bits, const float* __restrict__ Nrm,
         const Onb b = make_onb(nx, ny, nz);
         long long M0 = 0, M1 = 0, M2 = 0;
         int a0 = 0, a1 = 0, a2 = 0, cnt = 0;
-        for (int w = 0; w < W; ++w) {
-            const uint32_t word = bits[i * W + w];
-            if (!((word >> lane) & 1u)) continue;
-            const float4 h = __ldg(&dirs[32 * w + lane]);
-            float dx, dy, dz;
-            local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
-            M0 += fixed40(dx);
-            M1 += fixed40(dy);
-            M2 += fixed40(dz);
-            int best = 0;
-            float bv = fabsf(dx);
-            if (fabsf(dy) > bv) { best = 1; bv = fabsf(dy); }
-            if (fabsf(dz) > bv) best = 2;
-            a0 += best == 0;
-            a1 += best == 1;
-            a2 += best == 2;
-            ++cnt;
+        for (int w0 = 0; w0 < W; w0 += 32) {
+            const int wn = min(32, W - w0);
+            const uint32_t mine = lane < wn ? __ldg(&bits[i * W + w0 + lane]) : 0u;
+            for (int dw = 0; dw < wn; ++dw) {
+                const int w = w0 + dw;
+                const uint32_t word = __shfl_sync(0xFFFFFFFFu, mine, dw);
+                if (!((word >> lane) & 1u)) continue;
+                const float4 h = __ldg(&dirs[32 * w + lane]);
+                float dx, dy, dz;
+                local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
+                M0 += fixed40(dx);
+                M1 += fixed40(dy);
+                M2 += fixed40(dz);
+                int best = 0;
+                float bv = fabsf(dx);
+                if (fabsf(dy) > bv) { best = 1; bv = fabsf(dy); }
+                if (fabsf(dz) > bv) best = 2;
+                a0 += best == 0;
+                a1 += best == 1;
+                a2 += best == 2;
+                ++cnt;
+            }
         }
         for (int off = 16; off; off >>= 1) {
             M0 += __shfl_xor_sync(0xFFFFFFFFu, M0, off);
