@@ -678,7 +678,7 @@ __global__ void k_wide_level(int64_t n_int, const int32_t* __restrict__ child, c
 // the stack reports a wide depth that the host rejects.
 constexpr int kWideDfs = 96;
 #ifndef RC_WIDE_SUBTREE
-#define RC_WIDE_SUBTREE 16.0     // binary nodes per subtree thread (0: one launch per level throughout)
+#define RC_WIDE_SUBTREE 4.0      // binary nodes per subtree thread (0: one launch per level throughout)
 #endif
 
 __global__ void k_wide_subtrees(int64_t n_int, const int32_t* __restrict__ child, const int32_t* __restrict__ range,
