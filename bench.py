@@ -800,7 +800,7 @@ def run_autoframe(args):
         "gpu_launches": int(launches), "clocks": clocks,
         "roofline": {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
                      "frac": ach / pk, "traffic": None, "peak_source": pk_src + " (MEASURED_PEAKS.json hbm_gbs)",
-                     "kernel": "k_orthogonal (all candidate frames in one launch)",
+                     "kernel": "k_orthogonal_axis (all candidate frames in one launch)",
                      "kernel_ms": float(np.mean(t_s)),
                      "kernel_ms_note": "rc_frame_select as a whole (the cast is ~90% of it): achieved is a lower bound",
                      "bytes_per_ray": bpr, "nodes_per_ray": nodes_pr, "tris_per_ray": tris_pr},
