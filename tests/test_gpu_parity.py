@@ -304,6 +304,30 @@ def test_orthogonal_and_setups_parity(rc, name, frame):
     bvh.close()
 
 
+@pytest.mark.parametrize("point_order", [0, 1])
+def test_orthogonal_small_counts(rc, point_order):
+    # work items are (axis, 32 points): counts below, at and just past a
+    # multiple of 32, in Morton and in index order
+    V, F = PARTS["multi_pocket"]()
+    bvh = _build(rc, V, F)
+    p = rc.rc_params_default(tool_length=30.0, point_order=point_order)
+    Pall, Nall, _, _ = _points(V, F, 97, p)
+    om_all, oam_all = oracle.Mesh(V, F).orthogonal(Pall, Nall)
+    ot_all = oracle.travel(V, Pall)
+    for n in (1, 31, 32, 33, 97):
+        Pt, Nt = torch.from_numpy(Pall[:n].copy()).cuda(), torch.from_numpy(Nall[:n].copy()).cuda()
+        mask = torch.full((n,), 0xFF, dtype=torch.uint8, device="cuda")
+        trav = torch.zeros((n, 6), dtype=torch.float32, device="cuda")
+        ctr = torch.zeros(4, dtype=torch.int64, device="cuda")
+        rc.rc_orthogonal_cast(bvh.h, Pt, Nt, p, mask, trav, ctr)
+        clean = oam_all[:n] == 0
+        assert np.array_equal(mask.cpu().numpy()[clean], om_all[:n][clean])
+        assert np.array_equal(trav.cpu().numpy().view(np.uint32), ot_all[:n].view(np.uint32))
+        c = ctr.cpu().numpy()
+        assert c[3] == 0 and 0 < c[0] <= 6 * n
+    bvh.close()
+
+
 # ---------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------
