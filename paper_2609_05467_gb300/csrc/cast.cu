@@ -1200,10 +1200,18 @@ k_orthogonal_axis(const float4* __restrict__ nodes, const float4* __restrict__ t
     long long rays = 0, nvis = 0, ntri = 0;
     const int64_t G = (n + 31) >> 5;
     const int64_t items = (int64_t)nf * 6 * G;
-    for (;;) {
-        unsigned long long w = 0;
-        if (lane == 0) w = atomicAdd(work, 1ULL);
-        const int64_t it = (int64_t)__shfl_sync(0xFFFFFFFFu, w, 0);
+    // without a work counter (grid sized to the work) each warp casts only
+    // its own item, so blocks stay short and concurrent requests interleave
+    const unsigned long long own = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (bool first = true;; first = false) {
+        unsigned long long w = (unsigned long long)items;
+        if (work) {
+            if (lane == 0) w = atomicAdd(work, 1ULL);
+            w = __shfl_sync(0xFFFFFFFFu, w, 0);
+        } else if (first) {
+            w = own;
+        }
+        const int64_t it = (int64_t)w;
         if (it >= items) break;
         const int fa = (int)(it / G);
         const int64_t g = it - (int64_t)fa * G;
@@ -1574,6 +1582,7 @@ rc_status launch_orthogonal_frames(rc_bvh h, const float* P, const float* N, int
     const int64_t cap = (int64_t)sm_count() * RC_BATCH_MIN_BLOCKS;
     int64_t blocks = (items + 3) / 4;
     if (blocks > cap && p->launch_mode == 0) blocks = cap;
+    if (p->launch_mode == 1) work = nullptr;
     const float4* tree = use_wide(p) ? h->wnodes : h->nodes;
 #define RC_ORTHO(ST, WD)                                                                                      \
     k_orthogonal_axis<ST, WD><<<(unsigned)blocks, 128, 0, s>>>(tree, h->tris, max_steps(h), h->scene_maxabs, \
