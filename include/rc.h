@@ -87,7 +87,9 @@ typedef struct {
     int32_t fetch_mode;      /* hemispherical cast, persistent grid: 0 = lanes wait for their tile of 32 rays;
                                 1 (binary tree) = a lane takes the next ray of the warp's points as soon as its
                                 ray finishes; 2 (4-wide tree) = each lane walks its own list of the point's rays;
-                                3 = a warp casts one direction at a time from 32 Morton-adjacent points */
+                                3 = a warp casts one direction at a time from 32 Morton-adjacent points;
+                                4 (4-wide tree) = the warp walks each tile's 32 rays together over one shared
+                                stack whose entries carry the mask of lanes that entered the node */
     int32_t tree_width;      /* casts: 0 or 4 = 4-wide tree (default), 2 = binary tree */
     double parallel_tol;     /* orthogonal cast: axis a is eligible when n.a >= -parallel_tol (FP64); a face
                                 parallel to the axis is side-milled, and the tolerance absorbs the tilt that

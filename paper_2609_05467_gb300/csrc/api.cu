@@ -153,7 +153,7 @@ static rc_status check_params(const rc_params* p)
     if (p->points_per_item < 0 || p->points_per_item > 64)
         return set_error(RC_E_ARG, "points_per_item must be in [0, 64]");
     if (p->launch_mode != 0 && p->launch_mode != 1) return set_error(RC_E_ARG, "launch_mode must be 0 or 1");
-    if (p->fetch_mode < 0 || p->fetch_mode > 3) return set_error(RC_E_ARG, "fetch_mode must be in [0, 3]");
+    if (p->fetch_mode < 0 || p->fetch_mode > 4) return set_error(RC_E_ARG, "fetch_mode must be in [0, 4]");
     if (p->tree_width != 0 && p->tree_width != 2 && p->tree_width != 4)
         return set_error(RC_E_ARG, "tree_width must be 0 (default), 2 or 4");
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return set_error(RC_E_ARG, "blocks_per_sm out of range");

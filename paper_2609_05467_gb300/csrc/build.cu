@@ -144,49 +144,62 @@ __global__ void k_morton(const float* __restrict__ tbox, int64_t T, const DevSca
 constexpr int kMaxWalk = 4096;   // bound on leaf-to-root walks
 constexpr int kMaxWalkHost = kMaxWalk;
 constexpr int kSortThreads = 256;
-constexpr int kSortTile = 4096;   // keys per block
+constexpr int kSortTile = 4096;   // most keys per block
 
-__global__ void k_sort_hist(const unsigned long long* __restrict__ keys, int64_t T, int shift,
+__global__ void k_sort_hist(const unsigned long long* __restrict__ keys, int64_t T, int shift, int tile,
                             int nblk, unsigned int* __restrict__ counts)
 {
     __shared__ unsigned int h[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * kSortTile;
-    int64_t end = min64(T, base + kSortTile);
+    int64_t base = (int64_t)blockIdx.x * tile;
+    int64_t end = min64(T, base + tile);
     for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x)
         atomicAdd(&h[(keys[i] >> shift) & 255], 1u);
     __syncthreads();
     for (int i = threadIdx.x; i < 256; i += blockDim.x) counts[(int64_t)i * nblk + blockIdx.x] = h[i];
 }
 
-// exclusive scan of m uint32 counts (digit-major) in one block
-__global__ void k_sort_scan(unsigned int* __restrict__ counts, int64_t m)
+// exclusive scan of m uint32 counts (digit-major) in one block of 1024
+// threads: each warp owns a contiguous segment, read 32 entries at a time
+// (coalesced) -- once for its total, once to write the prefixes
+__device__ __forceinline__ unsigned int warp_incl_scan(unsigned int v, int lane)
 {
-    __shared__ unsigned int part[1024];
-    const int t = threadIdx.x;
-    const int64_t per = (m + blockDim.x - 1) / blockDim.x;
-    const int64_t b = t * per, e = min64(m, b + per);
-    unsigned int s = 0;
-    for (int64_t i = b; i < e; ++i) s += counts[i];
-    part[t] = s;
-    __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        unsigned int v = t >= off ? part[t - off] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned int u = __shfl_up_sync(0xFFFFFFFFu, v, off);
+        if (lane >= off) v += u;
     }
-    unsigned int run = part[t] - s;
-    for (int64_t i = b; i < e; ++i) {
-        unsigned int c = counts[i];
-        counts[i] = run;
-        run += c;
+    return v;
+}
+
+__global__ void __launch_bounds__(1024) k_sort_scan(unsigned int* __restrict__ counts, int64_t m)
+{
+    __shared__ unsigned int wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t seg = ((m + 31) / 32 + 31) / 32 * 32;       // entries per warp, a multiple of 32
+    const int64_t b = warp * seg, e = min64(m, b + seg);
+    unsigned int tot = 0;
+    for (int64_t i = b + lane; i < e; i += 32) tot += counts[i];
+    for (int off = 16; off; off >>= 1) tot += __shfl_xor_sync(0xFFFFFFFFu, tot, off);
+    if (lane == 0) wsum[warp] = tot;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned int v = wsum[lane];
+        wsum[lane] = warp_incl_scan(v, lane) - v;
+    }
+    __syncthreads();
+    unsigned int carry = wsum[warp];
+    for (int64_t c = b; c < e; c += 32) {
+        const int64_t i = c + lane;
+        const unsigned int v = i < e ? counts[i] : 0u;
+        const unsigned int inc = warp_incl_scan(v, lane);
+        if (i < e) counts[i] = carry + inc - v;
+        carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
     }
 }
 
 __global__ void k_sort_scatter(const unsigned long long* __restrict__ kin, const int32_t* __restrict__ vin,
-                               int64_t T, int shift, int nblk, const unsigned int* __restrict__ offs,
+                               int64_t T, int shift, int tile, int nblk, const unsigned int* __restrict__ offs,
                                unsigned long long* __restrict__ kout, int32_t* __restrict__ vout,
                                unsigned int* err)
 {
@@ -195,8 +208,8 @@ __global__ void k_sort_scatter(const unsigned long long* __restrict__ kin, const
     __shared__ unsigned int wcnt[W][256];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < 256; i += blockDim.x) base[i] = offs[(int64_t)i * nblk + blockIdx.x];
-    const int64_t b0 = (int64_t)blockIdx.x * kSortTile;
-    const int64_t e0 = min64(T, b0 + kSortTile);
+    const int64_t b0 = (int64_t)blockIdx.x * tile;
+    const int64_t e0 = min64(T, b0 + tile);
     for (int64_t c0 = b0; c0 < e0; c0 += kSortThreads) {
         for (int i = threadIdx.x; i < W * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
         __syncthreads();
@@ -946,7 +959,14 @@ static rc_status sort_pairs(unsigned long long* keys, int32_t* vals, int64_t n, 
     unsigned long long* k1 = nullptr;
     int32_t* v1 = nullptr;
     unsigned int* counts = nullptr;
-    const int nblk = (int)((n + kSortTile - 1) / kSortTile);
+    // about two tiles per SM (a multiple of the block size, 512 to 4096 keys):
+    // small sorts spread over the GPU, large ones keep the count table short
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    int64_t tile = (n + 2 * sms - 1) / (2 * sms);
+    tile = std::min<int64_t>(kSortTile, std::max<int64_t>(512, (tile + kSortThreads - 1) / kSortThreads * kSortThreads));
+    const int nblk = (int)((n + tile - 1) / tile);
     RC_CUDA(cudaMallocAsync(&k1, sizeof(unsigned long long) * n, s));
     RC_CUDA(cudaMallocAsync(&v1, sizeof(int32_t) * n, s));
     RC_CUDA(cudaMallocAsync(&counts, sizeof(unsigned int) * 256 * nblk, s));
@@ -954,11 +974,11 @@ static rc_status sort_pairs(unsigned long long* keys, int32_t* vals, int64_t n, 
     int32_t *vin = vals, *vout = v1;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
-        k_sort_hist<<<nblk, kSortThreads, 0, s>>>(kin, n, shift, nblk, counts);
+        k_sort_hist<<<nblk, kSortThreads, 0, s>>>(kin, n, shift, (int)tile, nblk, counts);
         RC_LAUNCHED();
         k_sort_scan<<<1, 1024, 0, s>>>(counts, (int64_t)256 * nblk);
         RC_LAUNCHED();
-        k_sort_scatter<<<nblk, kSortThreads, 0, s>>>(kin, vin, n, shift, nblk, counts, kout, vout, err);
+        k_sort_scatter<<<nblk, kSortThreads, 0, s>>>(kin, vin, n, shift, (int)tile, nblk, counts, kout, vout, err);
         RC_LAUNCHED();
         std::swap(kin, kout);
         std::swap(vin, vout);

@@ -564,6 +564,103 @@ __device__ __forceinline__ int step4(const float4* __restrict__ wnodes, const fl
     return 0;
 }
 
+// Any-hit walk of the 4-wide tree by a whole warp over one shared stack
+// (fetch_mode 4).  The 32 lanes hold the rays of one direction tile (one
+// origin).  A stack entry is a node and the mask of lanes whose rays entered
+// its box at the parent, so every lane takes part in exactly the nodes and
+// leaves its own walk would visit -- the same pairs are tested and the same
+// decisions made -- while the warp steps through their union with uniform
+// control flow and one (broadcast) fetch per node.  Children are ordered by
+// the entry distances of the lowest participating lane.  `stk` is the warp's
+// shared-memory stack of kStack4 entries.
+__device__ __forceinline__ TraceOut trace4_warp(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
+                                                const Ray& r, int max_steps, int2* stk)
+{
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    TraceOut out = {0, 0, 0, 0, 0};
+    bool amb = false, ambhit = false, blocked = false;
+    const SlabRay sr = make_slab_ray(r, r.rs);
+    unsigned active = FULL;          // lanes without a certain hit yet
+    int cur = 0;
+    unsigned cmask = FULL;
+    int sp = 0;
+    for (int steps = 0;; ++steps) {
+        if (steps > max_steps) {
+            if ((active >> lane) & 1u) { out.overflow = 1; blocked = true; }
+            break;
+        }
+        const unsigned m = cmask & active;
+        const bool in = (m >> lane) & 1u;
+        if (m != 0u && cur >= 0) {
+            float d[4];
+            int c[4];
+            slab4(wnodes + 8 * cur, sr, d, c);
+            unsigned cm[4];
+            float dl[4];
+            const int leader = __ffs(m) - 1;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                cm[k] = __ballot_sync(FULL, in && d[k] != INFINITY);
+                dl[k] = __shfl_sync(FULL, d[k], leader);
+                if (cm[k] == 0u) dl[k] = INFINITY;
+            }
+            // sort (distance, child, mask) of the leader: misses go last
+#define RC_WSWAP(a, b)                                                                      \
+    if (dl[b] < dl[a] || (cm[a] == 0u && cm[b] != 0u)) {                                     \
+        const float td = dl[a]; dl[a] = dl[b]; dl[b] = td;                                  \
+        const int tc = c[a]; c[a] = c[b]; c[b] = tc;                                        \
+        const unsigned tm = cm[a]; cm[a] = cm[b]; cm[b] = tm;                               \
+    }
+            RC_WSWAP(0, 1) RC_WSWAP(2, 3) RC_WSWAP(0, 2) RC_WSWAP(1, 3) RC_WSWAP(1, 2)
+#undef RC_WSWAP
+            const int nh = (cm[0] != 0u) + (cm[1] != 0u) + (cm[2] != 0u) + (cm[3] != 0u);
+            if (nh > 0) {
+                if (sp + nh - 1 > kStack4) {
+                    if ((active >> lane) & 1u) { out.overflow = 1; blocked = true; }
+                    break;
+                }
+                if (lane == 0) {
+                    if (nh > 3) stk[sp] = make_int2(c[3], (int)cm[3]);
+                    if (nh > 2) stk[sp + (nh > 3)] = make_int2(c[2], (int)cm[2]);
+                    if (nh > 1) stk[sp + (nh > 3) + (nh > 2)] = make_int2(c[1], (int)cm[1]);
+                }
+                sp += nh - 1;
+                cur = c[0];
+                cmask = cm[0];
+                __syncwarp();
+                continue;
+            }
+        } else if (m != 0u) {
+            if (in) {
+                const int v = -1 - cur;
+                const int first = v >> 3, cnt = (v & 7) + 1;
+                for (int k = 0; k < cnt; ++k) {
+                    const float4* t = tris + 3 * (first + k);
+                    const float4 v0 = __ldg(t), v1 = __ldg(t + 1), v2 = __ldg(t + 2);
+                    const int st = tri_test32(r, v0, v1, v2);
+                    if (st == kHit) { blocked = true; break; }
+                    if (st == kUnsure) {
+                        ++out.retests;
+                        const Pair64 pr = retest64(r, v0, v1, v2);
+                        if (pr.state == kHit) { blocked = true; break; }
+                        if (pr.state == kUnsure) { amb = true; ambhit |= pr.hit64; }
+                    }
+                }
+            }
+            active &= ~__ballot_sync(FULL, blocked);
+        }
+        if (sp == 0 || active == 0u) break;
+        --sp;
+        const int2 e = stk[sp];
+        cur = e.x;
+        cmask = (unsigned)e.y;
+    }
+    __syncwarp();
+    out.flags = blocked ? 1 : ((ambhit ? 1 : 0) | (amb ? 2 : 0));
+    return out;
+}
+
 template <bool kStats, bool kWide>
 __device__ __forceinline__ TraceOut trace_any(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                               const Ray& r, int max_steps)
@@ -653,6 +750,76 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
     if (lane == 0) count[i] = cnt;
     // rays per lane: W, less the pad of the last tile if this lane has one
     acc.rays += W - (__float_as_int(__ldg(&tdirs[32 * (W - 1) + lane]).w) < 0 ? 1 : 0);
+}
+
+// The hemispherical cast of one point by one warp walking each tile's rays
+// together over a shared stack (trace4_warp); otherwise as cast_point.
+__device__ __forceinline__ void cast_point_wp(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
+                                              int max_steps, float scene_maxabs, const float* __restrict__ P,
+                                              const float* __restrict__ Nrm, int64_t i,
+                                              const float4* __restrict__ tdirs, int W, double eps, uint32_t* row,
+                                              int2* stk, uint32_t* __restrict__ bits, int32_t* __restrict__ count,
+                                              CastAcc& acc)
+{
+    const int lane = threadIdx.x & 31;
+    for (int w = lane; w < W; w += 32) row[w] = 0u;
+    __syncwarp();
+    const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
+    const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
+    const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
+    const Onb b = make_onb(nx, ny, nz);
+    int cnt = 0;
+    for (int t = 0; t < W; ++t) {
+        const float4 h = __ldg(&tdirs[32 * t + lane]);
+        const int j = __float_as_int(h.w);
+        float dx, dy, dz;
+        local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
+        Ray r;
+        setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
+        const TraceOut tr = trace4_warp(wnodes, tris, r, max_steps, stk);
+        acc.retests += tr.retests;
+        acc.overflow += tr.overflow;
+        acc.amb += (j >= 0) & ((tr.flags >> 1) & 1);
+        const bool visible = (tr.flags & 1) == 0 && j >= 0;
+        if (visible) atomicOr(&row[j >> 5], 1u << (j & 31));
+        cnt += __popc(__ballot_sync(0xFFFFFFFFu, visible));
+    }
+    __syncwarp();
+    for (int w = lane; w < W; w += 32) bits[i * W + w] = row[w];
+    __syncwarp();
+    if (lane == 0) count[i] = cnt;
+    acc.rays += W - (__float_as_int(__ldg(&tdirs[32 * (W - 1) + lane]).w) < 0 ? 1 : 0);
+}
+
+#ifndef RC_WP_MIN_BLOCKS
+#define RC_WP_MIN_BLOCKS 6
+#endif
+
+// Hemispherical cast with warp-shared walks (fetch_mode 4, 4-wide tree):
+// persistent warps take points from the work counter; dynamic shared memory
+// holds each warp's bit row (W words) and then its stack (kStack4 int2).
+__global__ void __launch_bounds__(128, RC_WP_MIN_BLOCKS)
+k_hemisphere_wp(const float4* __restrict__ wnodes, const float4* __restrict__ tris, int max_steps,
+                float scene_maxabs, const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
+                const int32_t* __restrict__ order, const float4* __restrict__ tdirs, int n_dirs, double eps,
+                uint32_t* __restrict__ bits, int32_t* __restrict__ count, unsigned long long* counters,
+                unsigned long long* work)
+{
+    extern __shared__ uint32_t s_mem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int W = (n_dirs + 31) >> 5;
+    uint32_t* row = s_mem + wid * W;
+    int2* stk = reinterpret_cast<int2*>(s_mem + (blockDim.x >> 5) * ((W + 1) & ~1)) + wid * kStack4;
+    CastAcc acc;
+    for (;;) {
+        unsigned long long k = 0;
+        if (lane == 0) k = atomicAdd(work, 1ULL);
+        k = __shfl_sync(0xFFFFFFFFu, k, 0);
+        if (k >= (unsigned long long)n) break;
+        const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
+        cast_point_wp(wnodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, stk, bits, count, acc);
+    }
+    warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow);
 }
 
 // The hemispherical cast of one point with each lane walking its own list
@@ -1424,7 +1591,18 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
         RC_CUDA(cudaFuncSetAttribute(k_hemisphere<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     const float4* tree = wide ? h->wnodes : h->nodes;
-    if (p->fetch_mode == 3 && !stats && work) {
+    if (p->fetch_mode == 4 && !stats && work && wide) {
+        const size_t wsmem = (size_t)(threads / 32) * ((((p->n_dirs + 31) / 32) + 1) & ~1) * sizeof(uint32_t) +
+                             (size_t)(threads / 32) * kStack4 * sizeof(int2);
+        if (wsmem > 48 * 1024)
+            RC_CUDA(cudaFuncSetAttribute(k_hemisphere_wp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem));
+        int64_t wblocks = (int64_t)sm_count() * (p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_WP_MIN_BLOCKS);
+        if (wblocks > need) wblocks = need;
+        if (wblocks < 1) wblocks = 1;
+        k_hemisphere_wp<<<(unsigned)wblocks, threads, wsmem, s>>>(h->wnodes, h->tris, max_steps(h), h->scene_maxabs,
+                                                                 P, N, n, order, h->tdirs, p->n_dirs,
+                                                                 p->origin_offset, bits, count, counters, work);
+    } else if (p->fetch_mode == 3 && !stats && work) {
         RC_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * n, s));
         const int64_t chunks = (n + 31) / 32;
         int64_t pblocks = (int64_t)sm_count() * (p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_HEMI_MIN_BLOCKS);

@@ -129,7 +129,7 @@ def test_hemisphere_parity(rc, name, n, N):
     bvh.close()
 
 
-@pytest.mark.parametrize("mode", ["binary", "dynamic_fetch", "lane_lists", "packets", "packets_binary"])
+@pytest.mark.parametrize("mode", ["binary", "dynamic_fetch", "lane_lists", "packets", "packets_binary", "warp_stack"])
 @pytest.mark.parametrize("name,n,N", [("pocket", 1000, 256), ("prismatic_coarse", 777, 160),
                                        ("impeller_coarse", 500, 128), ("cavity", 300, 64),
                                        ("prismatic_coarse", 333, 150), ("pocket", 90, 13)])
@@ -139,6 +139,8 @@ def test_hemisphere_parity_other_traversals(rc, name, n, N, mode):
     bvh = _build(rc, V, F)
     if mode == "lane_lists":
         p = rc.rc_params_default(n_dirs=N, tree_width=4, fetch_mode=2)
+    elif mode == "warp_stack":
+        p = rc.rc_params_default(n_dirs=N, tree_width=4, fetch_mode=4)
     elif mode.startswith("packets"):
         p = rc.rc_params_default(n_dirs=N, tree_width=2 if mode.endswith("binary") else 4, fetch_mode=3)
     else:
