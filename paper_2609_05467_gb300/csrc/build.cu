@@ -142,7 +142,6 @@ __global__ void k_morton(const float* __restrict__ tbox, int64_t T, const DevSca
 // LSD radix sort of (uint64 key, int32 value), 8-bit digits, stable
 // ---------------------------------------------------------------------------
 constexpr int kMaxWalk = 4096;   // bound on leaf-to-root walks
-constexpr int kMaxWalkHost = kMaxWalk;
 constexpr int kSortThreads = 256;
 constexpr int kSortTile = 4096;   // most keys per block
 
@@ -523,7 +522,7 @@ __global__ void k_leaf_boxes(const float* __restrict__ tbox, const int32_t* __re
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= T) return;
     const int32_t f = order[k];
-    for (int c = 0; c < 6; ++c) nbox[6 * (n_int + k) + c] = tbox[6 * (int64_t)f + c];
+    for (int c = 0; c < 6; ++c) nbox[6 * (n_int + k) + c] = f >= 0 && f < T ? tbox[6 * (int64_t)f + c] : 0.0f;
 }
 
 __global__ void k_refit(int64_t T, int64_t n_int, const int32_t* __restrict__ parent,
@@ -785,15 +784,21 @@ __global__ void k_pack_small(int64_t T, const float* __restrict__ tbox, float4* 
     nodes[3] = make_float4(__int_as_float(-1 - (0 * 8 + (int)(T - 1))), __int_as_float(-1), 0.0f, 0.0f);
 }
 
-__global__ void k_tri_records(const float* __restrict__ V, const int32_t* __restrict__ F,
+__global__ void k_tri_records(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ F,
                               const int32_t* __restrict__ order, int64_t T, float4* tris)
 {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= T) return;
     const int32_t f = order[k];
-    float v[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 3; ++c) v[a][c] = V[3 * (int64_t)F[3 * (int64_t)f + a] + c];
+    float v[3][3] = {};
+    // a bad mesh (reported by the build) must not be gathered out of range
+    if (f >= 0 && f < T) {
+        for (int a = 0; a < 3; ++a) {
+            const int64_t vi = F[3 * (int64_t)f + a];
+            if (vi >= 0 && vi < nV)
+                for (int c = 0; c < 3; ++c) v[a][c] = V[3 * vi + c];
+        }
+    }
     float le = 0.0f;
     for (int c = 0; c < 3; ++c) {
         le = fmaxf(le, fabsf(v[1][c] - v[0][c]));
@@ -1009,21 +1014,25 @@ rc_status point_order(rc_bvh h, const float* P, int64_t n, int32_t* order, cudaS
     return RC_OK;
 }
 
+__global__ void k_init_scalars(DevScalars* sc)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    sc->amax_bits = 0;
+    sc->total = 0;
+    for (int k = 0; k < 3; ++k) { sc->cmin[k] = 0x7FFFFFFF; sc->cmax[k] = (int)0x80000000; }
+    sc->vmaxabs = 0;
+    sc->err_index = 0x7FFFFFFF;
+    sc->err_vertex = 0x7FFFFFFF;
+    sc->max_depth = 0;
+    sc->pad = 0;
+    sc->wide_depth = 0;
+    sc->pad2 = 0;
+}
+
 static rc_status init_scalars(DevScalars* sc, cudaStream_t s)
 {
-    DevScalars h;
-    h.amax_bits = 0;
-    h.total = 0;
-    for (int k = 0; k < 3; ++k) { h.cmin[k] = 0x7FFFFFFF; h.cmax[k] = (int)0x80000000; }
-    h.vmaxabs = 0;
-    h.err_index = 0x7FFFFFFF;
-    h.err_vertex = 0x7FFFFFFF;
-    h.max_depth = 0;
-    h.pad = 0;
-    h.wide_depth = 0;
-    h.pad2 = 0;
-    RC_CUDA(cudaMemcpyAsync(sc, &h, sizeof h, cudaMemcpyHostToDevice, s));
-    RC_CUDA(cudaStreamSynchronize(s));
+    k_init_scalars<<<1, 32, 0, s>>>(sc);
+    RC_LAUNCHED();
     return RC_OK;
 }
 
@@ -1043,10 +1052,9 @@ static rc_status face_data(rc_bvh h, float* tbox, cudaStream_t s)
     return RC_OK;
 }
 
-static rc_status check_scalars(rc_bvh h, cudaStream_t s)
+// mesh validity and scene bounds from the scalars already read back
+static rc_status checked_scalars(rc_bvh h)
 {
-    RC_CUDA(cudaMemcpyAsync(&h->host_sc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
-    RC_CUDA(cudaStreamSynchronize(s));
     const DevScalars& d = h->host_sc;
     if (d.err_index != 0x7FFFFFFF)
         return set_error(RC_E_ARG, "face " + std::to_string(d.err_index) + " has a vertex index outside [0, nV)");
@@ -1056,6 +1064,13 @@ static rc_status check_scalars(rc_bvh h, cudaStream_t s)
     // the tree depth is set by the build once the tree exists (a refit keeps
     // the topology and hence the depth)
     return RC_OK;
+}
+
+static rc_status check_scalars(rc_bvh h, cudaStream_t s)
+{
+    RC_CUDA(cudaMemcpyAsync(&h->host_sc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    RC_CUDA(cudaStreamSynchronize(s));
+    return checked_scalars(h);
 }
 
 // PLOC build of the binary tree over the Morton-sorted leaves (h->order);
@@ -1171,12 +1186,11 @@ static rc_status build_wide(rc_bvh h, const float* tbox, cudaStream_t s)
     RC_LAUNCHED();
     // The top `split` levels take one launch each (a level's queue is at most
     // 4^level long); then one launch finishes every queued subtree, a thread
-    // each, once the queue holds about n_int / RC_WIDE_SUBTREE nodes.  A wide level
-    // consumes at least one binary level, so max_depth + 1 levels finish the
-    // tree if the split is never reached.
+    // each, once the queue holds about n_int / RC_WIDE_SUBTREE nodes.  Levels
+    // past the bottom of a shallow tree find an empty queue.
     int split = 0;
     while (split < 30 && std::pow(4.0, (double)split) * RC_WIDE_SUBTREE < (double)n_int) ++split;
-    split = RC_WIDE_SUBTREE > 0 ? std::min(split, h->max_depth + 1) : h->max_depth + 1;
+    if (RC_WIDE_SUBTREE <= 0) split = kStack;      // a deeper tree is rejected anyway
     int level = 0;
     for (; level < split; ++level) {
         const double cap = std::min((double)n_int, std::pow(4.0, (double)std::min(level, 30)));
@@ -1206,10 +1220,10 @@ rc_status build_bvh(rc_bvh h, cudaStream_t s)
     const int64_t T = h->T;
     float* tbox = nullptr;
     RC_CUDA(cudaMallocAsync(&tbox, sizeof(float) * 6 * T, s));
+    // No host synchronisation until the end: a bad mesh is reported from the
+    // one final readback (every kernel in between guards its gathers).
     rc_status st = face_data(h, tbox, s);
     if (st != RC_OK) return st;
-    st = check_scalars(h, s);
-    if (st != RC_OK) { cudaFreeAsync(tbox, s); return st; }
 
     h->n_int = T > kLeafMax ? T - 1 : 1;
     RC_CUDA(cudaMallocAsync(&h->nodes, sizeof(float4) * 4 * h->n_int, s));
@@ -1252,18 +1266,15 @@ rc_status build_bvh(rc_bvh h, cudaStream_t s)
         k_pack<<<nblocks(n_int, 256), 256, 0, s>>>(n_int, h->child, h->range, h->nbox, h->nodes);
         RC_LAUNCHED();
         RC_CUDA(cudaFreeAsync(k0, s));
-        // the collapse needs the depth bound on the host
-        RC_CUDA(cudaMemcpyAsync(&h->host_sc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
-        RC_CUDA(cudaStreamSynchronize(s));
-        h->max_depth = std::min(h->host_sc.max_depth, kMaxWalkHost);
     }
     st = build_wide(h, tbox, s);
     if (st != RC_OK) return st;
-    k_tri_records<<<nblocks(T, 256), 256, 0, s>>>(h->V, h->F, h->order, T, h->tris);
+    k_tri_records<<<nblocks(T, 256), 256, 0, s>>>(h->V, h->nV, h->F, h->order, T, h->tris);
     RC_LAUNCHED();
     RC_CUDA(cudaFreeAsync(tbox, s));
     RC_CUDA(cudaMemcpyAsync(&h->host_sc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaStreamSynchronize(s));
+    if ((st = checked_scalars(h)) != RC_OK) return st;
     if (h->host_sc.pad != 0) return set_error(RC_E_DEVICE, "radix sort produced an out-of-range position");
     if (T > kLeafMax) h->max_depth = h->host_sc.max_depth;
     h->wide_depth = h->host_sc.wide_depth;
@@ -1301,7 +1312,7 @@ rc_status refit_bvh(rc_bvh h, cudaStream_t s)
     }
     st = build_wide(h, tbox, s);
     if (st != RC_OK) return st;
-    k_tri_records<<<nblocks(T, 256), 256, 0, s>>>(h->V, h->F, h->order, T, h->tris);
+    k_tri_records<<<nblocks(T, 256), 256, 0, s>>>(h->V, h->nV, h->F, h->order, T, h->tris);
     RC_LAUNCHED();
     RC_CUDA(cudaFreeAsync(tbox, s));
     RC_CUDA(cudaMemcpyAsync(&h->host_sc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
