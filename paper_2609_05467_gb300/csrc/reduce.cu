@@ -19,27 +19,20 @@ __device__ __forceinline__ long long quant_weight(const double* w, int64_t i, do
     return llround(__dmul_rn(__ddiv_rn(w[i], wmax), 16777216.0));
 }
 
-// round(x * 2^40) to nearest, ties to even, for an fp32 x with |x| <= 2^22,
-// in integer arithmetic (equal to llrint((double)x * 2^40), whose product is
-// exact in FP64)
-__device__ __forceinline__ long long fixed40(float x)
+// round(x * 2^40) to nearest, ties to even, for an fp32 x with |x| < 8, in
+// fp32 arithmetic: x * 2^40 = hi * 2^22 + lo with hi = rint(x * 2^18) and
+// lo = rint((x * 2^18 - hi) * 2^22).  x * 2^18 and its remainder are exact;
+// each rint adds 1.5 * 2^23, whose ulp is 1, and reads the integer from the
+// bits.  hi * 2^22 is even, so rounding the remainder alone makes the same
+// tie decisions as rounding the whole (equal to llrint((double)x * 2^40)).
+__device__ __forceinline__ void fixed40_split(float x, int& hi, int& lo)
 {
-    const unsigned b = __float_as_uint(x);
-    const int e = (int)((b >> 23) & 0xFFu);
-    if (e == 0) return 0;                           // zero or subnormal: |x * 2^40| < 2^-86
-    const long long mant = (long long)((b & 0x7FFFFFu) | 0x800000u);
-    const int sh = e - 110;                         // x * 2^40 = mant * 2^(e - 110)
-    long long q;
-    if (sh >= 0) {
-        q = mant << sh;
-    } else {
-        const int r = -sh;
-        if (r > 24) return 0;                       // mant / 2^r < 1/2
-        q = mant >> r;
-        const long long rem = mant & ((1LL << r) - 1), half = 1LL << (r - 1);
-        if (rem > half || (rem == half && (q & 1))) ++q;
-    }
-    return (b >> 31) ? -q : q;
+    const float C = 12582912.0f;
+    const float t = __fmul_rn(x, 262144.0f);
+    const float a = __fadd_rn(t, C);
+    hi = __float_as_int(a) - __float_as_int(C);
+    const float r = __fsub_rn(t, __fsub_rn(a, C));
+    lo = __float_as_int(__fmaf_rn(r, 4194304.0f, C)) - __float_as_int(C);
 }
 
 // One warp per point: recompute each visible direction, sum llrint(d*2^40)
@@ -69,6 +62,9 @@ k_variability(const uint32_t* __restrict__ bits, const float* __restrict__ Nrm,
         for (int w0 = 0; w0 < W; w0 += 32) {
             const int wn = min(32, W - w0);
             const uint32_t mine = lane < wn ? __ldg(&bits[i * W + w0 + lane]) : 0u;
+            // per 32 words a lane adds at most 32 terms: |sum hi| < 2^24,
+            // |sum lo| < 2^27, so int32 partial sums are exact
+            int h0 = 0, h1 = 0, h2 = 0, l0 = 0, l1 = 0, l2 = 0;
             for (int dw = 0; dw < wn; ++dw) {
                 const int w = w0 + dw;
                 const uint32_t word = __shfl_sync(0xFFFFFFFFu, mine, dw);
@@ -76,9 +72,16 @@ k_variability(const uint32_t* __restrict__ bits, const float* __restrict__ Nrm,
                 const float4 h = __ldg(&dirs[32 * w + lane]);
                 float dx, dy, dz;
                 local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
-                M0 += fixed40(dx);
-                M1 += fixed40(dy);
-                M2 += fixed40(dz);
+                int qh, ql;
+                fixed40_split(dx, qh, ql);
+                h0 += qh;
+                l0 += ql;
+                fixed40_split(dy, qh, ql);
+                h1 += qh;
+                l1 += ql;
+                fixed40_split(dz, qh, ql);
+                h2 += qh;
+                l2 += ql;
                 int best = 0;
                 float bv = fabsf(dx);
                 if (fabsf(dy) > bv) { best = 1; bv = fabsf(dy); }
@@ -88,6 +91,9 @@ k_variability(const uint32_t* __restrict__ bits, const float* __restrict__ Nrm,
                 a2 += best == 2;
                 ++cnt;
             }
+            M0 += (long long)h0 * 4194304LL + l0;
+            M1 += (long long)h1 * 4194304LL + l1;
+            M2 += (long long)h2 * 4194304LL + l2;
         }
         for (int off = 16; off; off >>= 1) {
             M0 += __shfl_xor_sync(0xFFFFFFFFu, M0, off);
