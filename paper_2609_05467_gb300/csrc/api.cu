@@ -480,9 +480,13 @@ rc_status rc_min_setups(rc_bvh h, const uint8_t* d_mask, const float* d_travel, 
     return rc_setup_cover(h_out->mask_hist, h_out);
 }
 
-// A non-blocking side stream and two events per host thread and device,
-// created on first use and kept for the life of the thread.
-struct SideStream { cudaStream_t s = nullptr; cudaEvent_t fork = nullptr, join = nullptr; };
+// Two non-blocking side streams (the orthogonal cast; the copy of the bits
+// back to the host) and their events per host thread and device, created on
+// first use and kept for the life of the thread.
+struct SideStream {
+    cudaStream_t s = nullptr, copy = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, cast_done = nullptr;
+};
 
 static rc_status side_stream(SideStream** out)
 {
@@ -492,8 +496,10 @@ static rc_status side_stream(SideStream** out)
     SideStream& ss = per_device[dev];
     if (!ss.s) {
         RC_CUDA(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+        RC_CUDA(cudaStreamCreateWithFlags(&ss.copy, cudaStreamNonBlocking));
         RC_CUDA(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
         RC_CUDA(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming));
+        RC_CUDA(cudaEventCreateWithFlags(&ss.cast_done, cudaEventDisableTiming));
     }
     *out = &ss;
     return RC_OK;
@@ -542,10 +548,11 @@ rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int6
     // on a side stream beside the hemispherical cast and the reduction on
     // `s`; the side stream joins `s` before the setups
     SideStream* side = nullptr;
-    bool forked = false;
+    bool forked = false, copying = false;
     auto done = [&](rc_status r) {
         std::string m = t_err;
         if (forked) cudaStreamSynchronize(side->s);
+        if (copying) cudaStreamSynchronize(side->copy);
         cudaFreeAsync(base, s);
         cudaStreamSynchronize(s);
         if (h) rc_destroy_bvh(h);
@@ -558,12 +565,21 @@ rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int6
     RC_CSTEP(cudaMemcpyAsync(dF, h_F, sizeof(int32_t) * 3 * T, cudaMemcpyHostToDevice, s));
     RC_STEP(rc_build_bvh(dV, nV, dF, T, stream, &h));
     RC_STEP(rc_sample_points(h, n, p, dP, dN, dface, dw, stream));
-    if (p->always_setups && n > 0) {
-        RC_STEP(side_stream(&side));
-        RC_CSTEP(cudaEventRecord(side->fork, s));
-    }
+    const bool copy_bits = n > 0 && (h_bits || h_count);
+    if ((p->always_setups || copy_bits) && n > 0) RC_STEP(side_stream(&side));
+    if (p->always_setups && n > 0) RC_CSTEP(cudaEventRecord(side->fork, s));
     RC_STEP(rc_hemisphere_cast(h, dP, dN, n, p, dbits, dcnt, dctr, stream));
-    if (side) {
+    if (copy_bits) {
+        // the bits and counts go back to the host beside the reduction
+        RC_CSTEP(cudaEventRecord(side->cast_done, s));
+        RC_CSTEP(cudaStreamWaitEvent(side->copy, side->cast_done, 0));
+        copying = true;
+        if (h_bits)
+            RC_CSTEP(cudaMemcpyAsync(h_bits, dbits, sizeof(uint32_t) * W * n, cudaMemcpyDeviceToHost, side->copy));
+        if (h_count)
+            RC_CSTEP(cudaMemcpyAsync(h_count, dcnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, side->copy));
+    }
+    if (p->always_setups && n > 0) {
         // issued after the hemispherical cast, whose persistent kernel then
         // holds the SMs first; the orthogonal cast fills them as it drains
         RC_CSTEP(cudaStreamWaitEvent(side->s, side->fork, 0));
@@ -574,8 +590,6 @@ rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int6
     RC_CSTEP(cudaMemcpyAsync(h_out->cast_counters, dctr, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost, s));
     RC_STEP(rc_direction_variability(dbits, dN, dw, n, p, nullptr, nullptr, nullptr, nullptr, &h_out->summary, stream));
     RC_STEP(rc_classify(&h_out->summary, p, &h_out->label));
-    if (h_bits && n) RC_CSTEP(cudaMemcpyAsync(h_bits, dbits, sizeof(uint32_t) * W * n, cudaMemcpyDeviceToHost, s));
-    if (h_count && n) RC_CSTEP(cudaMemcpyAsync(h_count, dcnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
     if (p->always_setups || h_out->label == 0) {
         if (forked) RC_CSTEP(cudaStreamWaitEvent(s, side->join, 0));
         else RC_STEP(rc_orthogonal_cast(h, dP, dN, n, p, dmask, dtrav, dctr + 4, stream));
