@@ -159,9 +159,6 @@ __global__ void k_sort_hist(const unsigned long long* __restrict__ keys, int64_t
     for (int i = threadIdx.x; i < 256; i += blockDim.x) counts[(int64_t)i * nblk + blockIdx.x] = h[i];
 }
 
-// exclusive scan of m uint32 counts (digit-major) in one block of 1024
-// threads: each warp owns a contiguous segment, read 32 entries at a time
-// (coalesced) -- once for its total, once to write the prefixes
 __device__ __forceinline__ unsigned int warp_incl_scan(unsigned int v, int lane)
 {
     for (int off = 1; off < 32; off <<= 1) {
@@ -171,42 +168,50 @@ __device__ __forceinline__ unsigned int warp_incl_scan(unsigned int v, int lane)
     return v;
 }
 
-__global__ void __launch_bounds__(1024) k_sort_scan(unsigned int* __restrict__ counts, int64_t m)
+// per digit, the exclusive prefix of its counts over the blocks (in place,
+// digit-major layout counts[d * nblk + b]) and the digit's total; one warp
+// per digit, 32 counts per step
+__global__ void __launch_bounds__(1024) k_sort_scan(unsigned int* __restrict__ counts, int nblk,
+                                                    unsigned int* __restrict__ totals)
 {
-    __shared__ unsigned int wsum[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t seg = ((m + 31) / 32 + 31) / 32 * 32;       // entries per warp, a multiple of 32
-    const int64_t b = warp * seg, e = min64(m, b + seg);
-    unsigned int tot = 0;
-    for (int64_t i = b + lane; i < e; i += 32) tot += counts[i];
-    for (int off = 16; off; off >>= 1) tot += __shfl_xor_sync(0xFFFFFFFFu, tot, off);
-    if (lane == 0) wsum[warp] = tot;
-    __syncthreads();
-    if (warp == 0) {
-        const unsigned int v = wsum[lane];
-        wsum[lane] = warp_incl_scan(v, lane) - v;
-    }
-    __syncthreads();
-    unsigned int carry = wsum[warp];
-    for (int64_t c = b; c < e; c += 32) {
-        const int64_t i = c + lane;
-        const unsigned int v = i < e ? counts[i] : 0u;
+    const int lane = threadIdx.x & 31;
+    const int d = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (d >= 256) return;
+    unsigned int* c = counts + (int64_t)d * nblk;
+    unsigned int carry = 0;
+    for (int b = 0; b < nblk; b += 32) {
+        const int i = b + lane;
+        const unsigned int v = i < nblk ? c[i] : 0u;
         const unsigned int inc = warp_incl_scan(v, lane);
-        if (i < e) counts[i] = carry + inc - v;
+        if (i < nblk) c[i] = carry + inc - v;
         carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
     }
+    if (lane == 0) totals[d] = carry;
 }
 
 __global__ void k_sort_scatter(const unsigned long long* __restrict__ kin, const int32_t* __restrict__ vin,
                                int64_t T, int shift, int tile, int nblk, const unsigned int* __restrict__ offs,
-                               unsigned long long* __restrict__ kout, int32_t* __restrict__ vout,
-                               unsigned int* err)
+                               const unsigned int* __restrict__ totals, unsigned long long* __restrict__ kout,
+                               int32_t* __restrict__ vout, unsigned int* err)
 {
     constexpr int W = kSortThreads / 32;
+    static_assert(kSortThreads == 256, "one thread per digit");
     __shared__ unsigned int base[256];
     __shared__ unsigned int wcnt[W][256];
+    __shared__ unsigned int wsum[W];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) base[i] = offs[(int64_t)i * nblk + blockIdx.x];
+    // the digit's start = the totals of the smaller digits (a block scan of
+    // the 256 totals) + this digit's count in the blocks before this one
+    {
+        const unsigned int t = totals[threadIdx.x];
+        const unsigned int inc = warp_incl_scan(t, lane);
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        unsigned int before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        base[threadIdx.x] = before + inc - t + offs[(int64_t)threadIdx.x * nblk + blockIdx.x];
+    }
+    __syncthreads();
     const int64_t b0 = (int64_t)blockIdx.x * tile;
     const int64_t e0 = min64(T, b0 + tile);
     for (int64_t c0 = b0; c0 < e0; c0 += kSortThreads) {
@@ -974,16 +979,17 @@ static rc_status sort_pairs(unsigned long long* keys, int32_t* vals, int64_t n, 
     const int nblk = (int)((n + tile - 1) / tile);
     RC_CUDA(cudaMallocAsync(&k1, sizeof(unsigned long long) * n, s));
     RC_CUDA(cudaMallocAsync(&v1, sizeof(int32_t) * n, s));
-    RC_CUDA(cudaMallocAsync(&counts, sizeof(unsigned int) * 256 * nblk, s));
+    RC_CUDA(cudaMallocAsync(&counts, sizeof(unsigned int) * (256 * (size_t)nblk + 256), s));   // counts, then digit totals
     unsigned long long *kin = keys, *kout = k1;
     int32_t *vin = vals, *vout = v1;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
         k_sort_hist<<<nblk, kSortThreads, 0, s>>>(kin, n, shift, (int)tile, nblk, counts);
         RC_LAUNCHED();
-        k_sort_scan<<<1, 1024, 0, s>>>(counts, (int64_t)256 * nblk);
+        k_sort_scan<<<8, 1024, 0, s>>>(counts, nblk, counts + (int64_t)256 * nblk);
         RC_LAUNCHED();
-        k_sort_scatter<<<nblk, kSortThreads, 0, s>>>(kin, vin, n, shift, (int)tile, nblk, counts, kout, vout, err);
+        k_sort_scatter<<<nblk, kSortThreads, 0, s>>>(kin, vin, n, shift, (int)tile, nblk, counts,
+                                                     counts + (int64_t)256 * nblk, kout, vout, err);
         RC_LAUNCHED();
         std::swap(kin, kout);
         std::swap(vin, vout);
