@@ -190,7 +190,7 @@ static void free_handle(rc_bvh h)
 {
     if (!h) return;
     void* ptrs[] = {h->V, h->F, h->tris, h->nodes, h->wnodes, h->parent, h->child, h->range, h->order, h->nbox,
-                    h->visits, h->fnorm, h->farea, h->fcent, h->cdf, h->sc};
+                    h->visits, h->fnorm, h->farea, h->cdf, h->sc};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, 0);
     delete h;
@@ -274,7 +274,6 @@ rc_status rc_build_bvh_ex(const float* d_V, int64_t nV, const int32_t* d_F, int6
     RC_TRY(cudaMallocAsync(&h->F, sizeof(int32_t) * 3 * T, s));
     RC_TRY(cudaMallocAsync(&h->fnorm, sizeof(float) * 3 * T, s));
     RC_TRY(cudaMallocAsync(&h->farea, sizeof(double) * T, s));
-    RC_TRY(cudaMallocAsync(&h->fcent, sizeof(float) * 3 * T, s));
     RC_TRY(cudaMallocAsync(&h->cdf, sizeof(long long) * T, s));
     RC_TRY(cudaMallocAsync(&h->sc, sizeof(DevScalars), s));
     RC_TRY(cudaMemcpyAsync(h->V, d_V, sizeof(float) * 3 * nV, cudaMemcpyDeviceToDevice, s));

@@ -28,69 +28,86 @@ namespace rc {
 // face preparation and validation
 // ---------------------------------------------------------------------------
 __global__ void k_face_prep(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ F,
-                            int64_t T, float* fnorm, double* farea, float* fcent, float* tbox,
-                            DevScalars* sc)
+                            int64_t T, float* fnorm, double* farea, float* tbox, DevScalars* sc)
 {
-    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (f >= T) return;
-    int32_t id[3];
-    bool bad = false;
-    for (int k = 0; k < 3; ++k) {
-        id[k] = F[3 * f + k];
-        if (id[k] < 0 || id[k] >= nV) bad = true;
-    }
-    if (bad) {
-        atomicMin(&sc->err_index, (int)f);
-        for (int k = 0; k < 6; ++k) tbox[6 * f + k] = 0.0f;
-        return;
-    }
-    float v[3][3];
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // contributions to the scene bounds, reduced over the warp before the
+    // atomics (one set per warp instead of per face); neutral when absent
+    float cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
     float mabs = 0.0f;
-    for (int a = 0; a < 3; ++a) {
+    double amax = 0.0;
+    if (f < T) {
+        int32_t id[3];
+        bool bad = false;
         for (int k = 0; k < 3; ++k) {
-            v[a][k] = V[3 * (int64_t)id[a] + k];
-            if (!isfinite(v[a][k])) {
-                atomicMin(&sc->err_vertex, id[a]);
-                v[a][k] = 0.0f;
+            id[k] = F[3 * f + k];
+            if (id[k] < 0 || id[k] >= nV) bad = true;
+        }
+        if (bad) {
+            atomicMin(&sc->err_index, (int)f);
+            for (int k = 0; k < 6; ++k) tbox[6 * f + k] = 0.0f;
+        } else {
+            float v[3][3];
+            for (int a = 0; a < 3; ++a) {
+                for (int k = 0; k < 3; ++k) {
+                    v[a][k] = V[3 * (int64_t)id[a] + k];
+                    if (!isfinite(v[a][k])) {
+                        atomicMin(&sc->err_vertex, id[a]);
+                        v[a][k] = 0.0f;
+                    }
+                    mabs = fmaxf(mabs, fabsf(v[a][k]));
+                }
             }
-            mabs = fmaxf(mabs, fabsf(v[a][k]));
+            // c = (B - A) x (C - A) in FP64, each operation rounded separately
+            double e1[3], e2[3];
+            for (int k = 0; k < 3; ++k) {
+                e1[k] = __dsub_rn((double)v[1][k], (double)v[0][k]);
+                e2[k] = __dsub_rn((double)v[2][k], (double)v[0][k]);
+            }
+            const double c0 = __dsub_rn(__dmul_rn(e1[1], e2[2]), __dmul_rn(e1[2], e2[1]));
+            const double c1 = __dsub_rn(__dmul_rn(e1[2], e2[0]), __dmul_rn(e1[0], e2[2]));
+            const double c2 = __dsub_rn(__dmul_rn(e1[0], e2[1]), __dmul_rn(e1[1], e2[0]));
+            const double len =
+                __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(c0, c0), __dmul_rn(c1, c1)), __dmul_rn(c2, c2)));
+            farea[f] = 0.5 * len;
+            amax = 0.5 * len;
+            float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f;
+            if (len > 0.0) {
+                n0 = __double2float_rn(__ddiv_rn(c0, len));
+                n1 = __double2float_rn(__ddiv_rn(c1, len));
+                n2 = __double2float_rn(__ddiv_rn(c2, len));
+            }
+            fnorm[3 * f + 0] = n0;
+            fnorm[3 * f + 1] = n1;
+            fnorm[3 * f + 2] = n2;
+            for (int k = 0; k < 3; ++k) {
+                const float lo = fminf(v[0][k], fminf(v[1][k], v[2][k]));
+                const float hi = fmaxf(v[0][k], fmaxf(v[1][k], v[2][k]));
+                tbox[6 * f + k] = lo;
+                tbox[6 * f + 3 + k] = hi;
+                const float c = 0.5f * (lo + hi);
+                cmin[k] = c;
+                cmax[k] = c;
+            }
         }
     }
-    // c = (B - A) x (C - A) in FP64, each operation rounded separately
-    double e1[3], e2[3];
-    for (int k = 0; k < 3; ++k) {
-        e1[k] = __dsub_rn((double)v[1][k], (double)v[0][k]);
-        e2[k] = __dsub_rn((double)v[2][k], (double)v[0][k]);
+    const unsigned FULL = 0xFFFFFFFFu;
+    for (int off = 16; off; off >>= 1) {
+        for (int k = 0; k < 3; ++k) {
+            cmin[k] = fminf(cmin[k], __shfl_xor_sync(FULL, cmin[k], off));
+            cmax[k] = fmaxf(cmax[k], __shfl_xor_sync(FULL, cmax[k], off));
+        }
+        mabs = fmaxf(mabs, __shfl_xor_sync(FULL, mabs, off));
+        amax = fmax(amax, __shfl_xor_sync(FULL, amax, off));
     }
-    double c0 = __dsub_rn(__dmul_rn(e1[1], e2[2]), __dmul_rn(e1[2], e2[1]));
-    double c1 = __dsub_rn(__dmul_rn(e1[2], e2[0]), __dmul_rn(e1[0], e2[2]));
-    double c2 = __dsub_rn(__dmul_rn(e1[0], e2[1]), __dmul_rn(e1[1], e2[0]));
-    double len = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(c0, c0), __dmul_rn(c1, c1)), __dmul_rn(c2, c2)));
-    farea[f] = 0.5 * len;
-    float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f;
-    if (len > 0.0) {
-        n0 = __double2float_rn(__ddiv_rn(c0, len));
-        n1 = __double2float_rn(__ddiv_rn(c1, len));
-        n2 = __double2float_rn(__ddiv_rn(c2, len));
+    if ((threadIdx.x & 31) == 0 && cmin[0] <= cmax[0]) {
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&sc->cmin[k], float_to_ordered(cmin[k]));
+            atomicMax(&sc->cmax[k], float_to_ordered(cmax[k]));
+        }
+        atomicMax(&sc->vmaxabs, float_to_ordered(mabs));
+        atomicMax(&sc->amax_bits, (unsigned long long)__double_as_longlong(amax));
     }
-    fnorm[3 * f + 0] = n0;
-    fnorm[3 * f + 1] = n1;
-    fnorm[3 * f + 2] = n2;
-    for (int k = 0; k < 3; ++k) {
-        double s = __dadd_rn(__dadd_rn((double)v[0][k], (double)v[1][k]), (double)v[2][k]);
-        fcent[3 * f + k] = __double2float_rn(__ddiv_rn(s, 3.0));
-    }
-    for (int k = 0; k < 3; ++k) {
-        float lo = fminf(v[0][k], fminf(v[1][k], v[2][k]));
-        float hi = fmaxf(v[0][k], fmaxf(v[1][k], v[2][k]));
-        tbox[6 * f + k] = lo;
-        tbox[6 * f + 3 + k] = hi;
-        float c = 0.5f * (lo + hi);
-        atomicMin(&sc->cmin[k], float_to_ordered(c));
-        atomicMax(&sc->cmax[k], float_to_ordered(c));
-    }
-    atomicMax(&sc->vmaxabs, float_to_ordered(mabs));
-    atomicMax(&sc->amax_bits, (unsigned long long)__double_as_longlong(0.5 * len));
 }
 
 // ---------------------------------------------------------------------------
@@ -919,14 +936,15 @@ __global__ void k_sample_area(const float* __restrict__ V, const int32_t* __rest
     if (weight) weight[i] = 1.0;
 }
 
-__global__ void k_sample_centroid(const float* __restrict__ fcent, const float* __restrict__ fnorm,
+__global__ void k_sample_centroid(const float* __restrict__ V, const int32_t* __restrict__ F,
+                                  const float* __restrict__ fnorm,
                                   const double* __restrict__ farea, int64_t T, float* P, float* Nout,
                                   int32_t* face, double* weight)
 {
     int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f >= T) return;
     for (int k = 0; k < 3; ++k) {
-        P[3 * f + k] = fcent[3 * f + k];
+        P[3 * f + k] = face_centroid(V, F, f, k);
         Nout[3 * f + k] = fnorm[3 * f + k];
     }
     face[f] = (int32_t)f;
@@ -1046,8 +1064,7 @@ static rc_status face_data(rc_bvh h, float* tbox, cudaStream_t s)
 {
     rc_status st = init_scalars(h->sc, s);
     if (st != RC_OK) return st;
-    k_face_prep<<<nblocks(h->T, 256), 256, 0, s>>>(h->V, h->nV, h->F, h->T, h->fnorm, h->farea,
-                                                   h->fcent, tbox, h->sc);
+    k_face_prep<<<nblocks(h->T, 256), 256, 0, s>>>(h->V, h->nV, h->F, h->T, h->fnorm, h->farea, tbox, h->sc);
     RC_LAUNCHED();
     k_quant_area<<<nblocks(h->T, 256), 256, 0, s>>>(h->farea, h->T, h->sc, h->cdf);
     RC_LAUNCHED();
@@ -1333,7 +1350,8 @@ rc_status sample_points(rc_bvh h, int64_t n, const rc_params* p, float* P, float
                         double* weight, cudaStream_t s)
 {
     if (p->sample_mode == RC_SAMPLE_FACE_CENTROID) {
-        k_sample_centroid<<<nblocks(h->T, 256), 256, 0, s>>>(h->fcent, h->fnorm, h->farea, h->T, P, N, face, weight);
+        k_sample_centroid<<<nblocks(h->T, 256), 256, 0, s>>>(h->V, h->F, h->fnorm, h->farea, h->T, P, N, face,
+                                                             weight);
         RC_LAUNCHED();
         return RC_OK;
     }

@@ -107,7 +107,6 @@ struct rc_bvh_s {
     int32_t* visits = nullptr;     // [n_int] refit arrival counters
     float* fnorm = nullptr;        // [T][3] fp32 unit normals
     double* farea = nullptr;       // [T] FP64 areas
-    float* fcent = nullptr;        // [T][3] fp32 centroids
     long long* cdf = nullptr;      // [T] inclusive quantised-area prefix
     rc::DevScalars* sc = nullptr;  // device scalars
     rc::DevScalars host_sc;        // copy after build
@@ -196,6 +195,16 @@ __device__ __forceinline__ void local_to_world(const Onb& b, float nx, float ny,
     dx = __fadd_rn(__fadd_rn(__fmul_rn(b.t1x, hx), __fmul_rn(b.t2x, hy)), __fmul_rn(nx, hz));
     dy = __fadd_rn(__fadd_rn(__fmul_rn(b.t1y, hx), __fmul_rn(b.t2y, hy)), __fmul_rn(ny, hz));
     dz = __fadd_rn(__fadd_rn(__fmul_rn(b.t1z, hx), __fmul_rn(b.t2z, hy)), __fmul_rn(nz, hz));
+}
+
+// Coordinate k of the centroid of face f (Section 3.1):
+// fl32((A_k + B_k + C_k) / 3), summed left to right in FP64.
+__device__ __forceinline__ float face_centroid(const float* __restrict__ V, const int32_t* __restrict__ F,
+                                               int64_t f, int k)
+{
+    const double a = V[3 * (int64_t)F[3 * f] + k], b = V[3 * (int64_t)F[3 * f + 1] + k];
+    const double s = __dadd_rn(__dadd_rn(a, b), (double)V[3 * (int64_t)F[3 * f + 2] + k]);
+    return __double2float_rn(__ddiv_rn(s, 3.0));
 }
 
 // Offset origin fl32(p + eps*n), evaluated in FP64 without contraction.

@@ -33,7 +33,7 @@ __device__ __forceinline__ double uniform01_u(unsigned long long seed, long long
 // s = sqrt(u1) (the sampler's formula and numbers), centroid mode at the
 // face centroid; bad[0] receives the first point whose face is out of range
 __global__ void k_sample_on_faces(const float* __restrict__ V, const int32_t* __restrict__ F, int64_t T,
-                                  const float* __restrict__ fnorm, const float* __restrict__ fcent, int64_t n,
+                                  const float* __restrict__ fnorm, int64_t n,
                                   unsigned long long seed, int centroid, const int32_t* __restrict__ face,
                                   float* P, float* Nout, unsigned long long* bad)
 {
@@ -46,7 +46,7 @@ __global__ void k_sample_on_faces(const float* __restrict__ V, const int32_t* __
     }
     if (centroid) {
         for (int k = 0; k < 3; ++k) {
-            P[3 * i + k] = fcent[3 * f + k];
+            P[3 * i + k] = face_centroid(V, F, f, k);
             Nout[3 * i + k] = fnorm[3 * f + k];
         }
         return;
@@ -138,7 +138,7 @@ rc_status rc_sample_points_on_faces(rc_bvh h, int64_t n, const rc_params* p, con
     unsigned long long* bad = nullptr;
     RC_CUDA(cudaMallocAsync(&bad, sizeof(unsigned long long), s));
     RC_CUDA(cudaMemsetAsync(bad, 0xFF, sizeof(unsigned long long), s));
-    k_sample_on_faces<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->V, h->F, h->T, h->fnorm, h->fcent, n, p->seed,
+    k_sample_on_faces<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->V, h->F, h->T, h->fnorm, n, p->seed,
                                                                   p->sample_mode == RC_SAMPLE_FACE_CENTROID, d_face,
                                                                   d_P, d_N, bad);
     RC_LAUNCHED();
