@@ -550,15 +550,17 @@ __global__ void k_leaf_boxes(const float* __restrict__ tbox, const int32_t* __re
 __global__ void k_refit(int64_t T, int64_t n_int, const int32_t* __restrict__ parent,
                         const int32_t* __restrict__ child, float* nbox, int32_t* visits, DevScalars* sc)
 {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= T) return;
-    int32_t cur = (int32_t)(n_int + k);
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int32_t cur = (int32_t)(n_int + k);
     // every chain ends at the root; the caps only guard against a malformed
     // tree (the build then reports an error instead of looping)
     int depth = 0;
-    for (int32_t p = parent[cur]; p >= 0 && depth <= kMaxWalk; p = parent[p]) ++depth;
-    atomicMax(&sc->max_depth, depth);
-    if (depth > kMaxWalk) return;
+    if (k < T)
+        for (int32_t p = parent[cur]; p >= 0 && depth <= kMaxWalk; p = parent[p]) ++depth;
+    int wmax = depth;                               // one atomic per warp
+    for (int off = 16; off; off >>= 1) wmax = max(wmax, __shfl_xor_sync(0xFFFFFFFFu, wmax, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(&sc->max_depth, wmax);
+    if (k >= T || depth > kMaxWalk) return;
     int32_t p = parent[cur];
     for (int steps = 0; p >= 0 && steps <= kMaxWalk; ++steps) {
         __threadfence();

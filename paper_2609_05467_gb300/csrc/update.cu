@@ -66,37 +66,53 @@ __global__ void k_sample_on_faces(const float* __restrict__ V, const int32_t* __
 }
 
 // faces with a moved vertex (bit-for-bit comparison), their count and the box
-// of their old and new triangles (order-preserving integer min / max)
+// of their old and new triangles (order-preserving integer min / max, reduced
+// over the warp before the atomics)
 __global__ void k_changed_faces(const float* __restrict__ V0, const float* __restrict__ V1, int64_t nV,
                                 const int32_t* __restrict__ F, int64_t T, uint8_t* __restrict__ changed,
                                 int* box /*lo xyz, hi xyz*/, unsigned long long* n_changed,
                                 unsigned long long* bad)
 {
     const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (f >= T) return;
-    int64_t v[3];
-    for (int c = 0; c < 3; ++c) {
-        v[c] = F[3 * f + c];
-        if (v[c] < 0 || v[c] >= nV) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool moved = false;
+    if (f < T) {
+        int64_t v[3];
+        bool ok = true;
+        for (int c = 0; c < 3; ++c) {
+            v[c] = F[3 * f + c];
+            if (v[c] < 0 || v[c] >= nV) ok = false;
+        }
+        if (!ok) {
             atomicMin(bad, (unsigned long long)f);
             changed[f] = 0;
-            return;
+        } else {
+            for (int c = 0; c < 3; ++c)
+                for (int k = 0; k < 3; ++k)
+                    moved |= __float_as_uint(V0[3 * v[c] + k]) != __float_as_uint(V1[3 * v[c] + k]);
+            changed[f] = moved ? 1 : 0;
+            if (moved)
+                for (int k = 0; k < 3; ++k)
+                    for (int c = 0; c < 3; ++c) {
+                        lo[k] = fminf(lo[k], fminf(V0[3 * v[c] + k], V1[3 * v[c] + k]));
+                        hi[k] = fmaxf(hi[k], fmaxf(V0[3 * v[c] + k], V1[3 * v[c] + k]));
+                    }
         }
     }
-    bool moved = false;
-    for (int c = 0; c < 3; ++c)
-        for (int k = 0; k < 3; ++k) moved |= __float_as_uint(V0[3 * v[c] + k]) != __float_as_uint(V1[3 * v[c] + k]);
-    changed[f] = moved ? 1 : 0;
-    if (!moved) return;
-    atomicAdd(n_changed, 1ULL);
-    for (int k = 0; k < 3; ++k) {
-        float lo = INFINITY, hi = -INFINITY;
-        for (int c = 0; c < 3; ++c) {
-            lo = fminf(lo, fminf(V0[3 * v[c] + k], V1[3 * v[c] + k]));
-            hi = fmaxf(hi, fmaxf(V0[3 * v[c] + k], V1[3 * v[c] + k]));
+    const unsigned FULL = 0xFFFFFFFFu;
+    const unsigned m = __ballot_sync(FULL, moved);
+    if (m == 0u) return;
+    for (int off = 16; off; off >>= 1)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(FULL, lo[k], off));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(FULL, hi[k], off));
         }
-        atomicMin(&box[k], float_to_ordered(lo));
-        atomicMax(&box[3 + k], float_to_ordered(hi));
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(n_changed, (unsigned long long)__popc(m));
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&box[k], float_to_ordered(lo[k]));
+            atomicMax(&box[3 + k], float_to_ordered(hi[k]));
+        }
     }
 }
 
