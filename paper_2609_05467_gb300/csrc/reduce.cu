@@ -194,8 +194,28 @@ __global__ void k_fixture(const float* __restrict__ V, const int32_t* __restrict
     const double diag = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2)));
     const double tol = __dmul_rn(1e-6, diag);
     const double lim = 1.0 - 1e-6;
+    // fp32 pre-check.  The frame entries are fp32 values, so the fp32 frame
+    // coordinate q of a vertex (three rounded operations) is within 3 u s of
+    // the exact one, s = sum |V_i f_i|, and the fp32 plane within u |plane|
+    // of the FP64 one; a vertex farther than tol + 4 u (s + |plane|) from a
+    // plane in fp32 is farther than tol in FP64 (whose own error is far
+    // smaller), and the FP64 test of that plane is skipped
+    const float u4 = 4.0f * 5.9604644775390625e-8f;
+    const float tolf = (float)tol;
     bool fx = false;
     for (int k = 0; k < 3; ++k) {
+        const float f0 = (float)frame[k], f1 = (float)frame[3 + k], f2 = (float)frame[6 + k];
+        const float blo = (float)fbox[k], bhi = (float)fbox[3 + k];
+        bool near_lo = true, near_hi = true;
+        for (int a = 0; a < 3; ++a) {
+            const int64_t v = F[3 * f + a];
+            const float x = V[3 * v], y = V[3 * v + 1], z = V[3 * v + 2];
+            const float q = fmaf(x, f0, fmaf(y, f1, z * f2));
+            const float sv = (fabsf(x * f0) + fabsf(y * f1) + fabsf(z * f2)) * 1.01f;
+            near_lo &= fabsf(q - blo) <= tolf + u4 * (sv + fabsf(blo));
+            near_hi &= fabsf(q - bhi) <= tolf + u4 * (sv + fabsf(bhi));
+        }
+        if (!near_lo && !near_hi) continue;
         bool hi_all = true, lo_all = true;
         for (int a = 0; a < 3; ++a) {
             const int64_t v = F[3 * f + a];
