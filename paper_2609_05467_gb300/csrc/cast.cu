@@ -705,19 +705,31 @@ __device__ __forceinline__ void warp_add_counters(unsigned long long* counters, 
 #ifndef RC_HEMI_MIN_BLOCKS
 #define RC_HEMI_MIN_BLOCKS 6
 #endif
+#ifndef RC_TAIL_SPLITS
+#define RC_TAIL_SPLITS 4
+#endif
+#ifndef RC_TAIL_POINTS
+#define RC_TAIL_POINTS 2        // points cast in parts, per resident warp
+#endif
 
 using CastAcc = CastAccFwd;
 
 // The hemispherical cast of one point by one warp (see above).  `tdirs` is
 // the tile-ordered table, `row` the warp's shared-memory row of W words.
+// Tiles [t0, t1) are cast; a whole point (0, W) writes its bit row and count,
+// a part of a point ORs its bits into the (zeroed) row in memory and adds
+// its count.
 template <bool kStats, bool kWide>
 __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                            int max_steps, float scene_maxabs, const float* __restrict__ P,
                                            const float* __restrict__ Nrm, int64_t i,
                                            const float4* __restrict__ tdirs, int W, double eps, uint32_t* row,
-                                           uint32_t* __restrict__ bits, int32_t* __restrict__ count, CastAcc& acc)
+                                           uint32_t* __restrict__ bits, int32_t* __restrict__ count, CastAcc& acc,
+                                           int t0 = 0, int t1 = -1)
 {
     const int lane = threadIdx.x & 31;
+    const bool whole = t1 < 0;
+    if (whole) t1 = W;
     for (int w = lane; w < W; w += 32) row[w] = 0u;
     __syncwarp();
     const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
@@ -725,7 +737,7 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
     const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
     const Onb b = make_onb(nx, ny, nz);
     int cnt = 0;
-    for (int t = 0; t < W; ++t) {
+    for (int t = t0; t < t1; ++t) {
         // canonical index j; when 32 does not divide N the last tile is
         // padded with entries j = -1 that carry a real direction: they are
         // cast like the others (no branch in the loop) and then discarded
@@ -745,11 +757,18 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
         cnt += __popc(__ballot_sync(0xFFFFFFFFu, visible));
     }
     __syncwarp();
-    for (int w = lane; w < W; w += 32) bits[i * W + w] = row[w];
+    if (whole) {
+        for (int w = lane; w < W; w += 32) bits[i * W + w] = row[w];
+        if (lane == 0) count[i] = cnt;
+    } else {
+        for (int w = lane; w < W; w += 32)
+            if (row[w]) atomicOr(&bits[i * W + w], row[w]);
+        if (lane == 0) atomicAdd(&count[i], cnt);
+    }
     __syncwarp();
-    if (lane == 0) count[i] = cnt;
-    // rays per lane: W, less the pad of the last tile if this lane has one
-    acc.rays += W - (__float_as_int(__ldg(&tdirs[32 * (W - 1) + lane]).w) < 0 ? 1 : 0);
+    // rays per lane: the tiles cast, less the pad of the last tile if this
+    // lane has one
+    acc.rays += (t1 - t0) - (t1 == W && __float_as_int(__ldg(&tdirs[32 * (W - 1) + lane]).w) < 0 ? 1 : 0);
 }
 
 // The hemispherical cast of one point by one warp walking each tile's rays
@@ -973,31 +992,60 @@ k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
              const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
              const int32_t* __restrict__ order, const float4* __restrict__ tdirs, int n_dirs, double eps,
              uint32_t* __restrict__ bits, int32_t* __restrict__ count, unsigned long long* counters,
-             unsigned long long* work)
+             unsigned long long* work, int64_t n_whole, int splits)
 {
     extern __shared__ uint32_t s_rows[];
     const int lane = threadIdx.x & 31;
     const int W = (n_dirs + 31) >> 5;
     uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
     CastAcc acc;
-    // with a work counter the warps take points until none are left; without
-    // one (grid sized to the work) each warp casts exactly its own point, so
-    // blocks are short-lived and kernels of concurrent requests interleave
+    // With a work counter the warps take work until none is left: the first
+    // n_whole points of the processing order whole, then the last n - n_whole
+    // points in `splits` parts each, so that the launch ends on short items
+    // instead of whole points.  Without a counter (grid sized to the work)
+    // each warp casts exactly its own point, so blocks are short-lived and
+    // kernels of concurrent requests interleave.
     const unsigned long long own = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const unsigned long long items = (unsigned long long)n_whole + (unsigned long long)(n - n_whole) * splits;
+    const int tw = (W + splits - 1) / splits;
     for (bool first = true;; first = false) {
-        unsigned long long k = (unsigned long long)n;
+        unsigned long long k = items;
         if (work) {
             if (lane == 0) k = atomicAdd(work, 1ULL);
             k = __shfl_sync(0xFFFFFFFFu, k, 0);
         } else if (first) {
             k = own;
         }
-        if (k >= (unsigned long long)n) break;
-        const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
-        cast_point<kStats, kWide>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits, count,
-                                  acc);
+        if (k >= items) break;
+        if (k < (unsigned long long)n_whole) {
+            const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
+            cast_point<kStats, kWide>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits,
+                                      count, acc);
+        } else {
+            const unsigned long long q = k - (unsigned long long)n_whole;
+            const int64_t r = n_whole + (int64_t)(q / splits);
+            const int t0 = (int)(q % splits) * tw, t1 = min(W, t0 + tw);
+            if (t0 >= t1) continue;
+            const int64_t i = order ? (int64_t)__ldg(&order[r]) : r;
+            cast_point<kStats, kWide>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits,
+                                      count, acc, t0, t1);
+        }
     }
     warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow, acc.nvis, acc.ntri);
+}
+
+// zero the bit rows and counts of the points cast in parts (positions
+// [n_whole, n) of the processing order)
+__global__ void k_zero_split(const int32_t* __restrict__ order, int64_t n_whole, int64_t n, int W,
+                             uint32_t* __restrict__ bits, int32_t* __restrict__ count)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t r = n_whole + t / W;
+    if (r >= n) return;
+    const int64_t i = order ? (int64_t)order[r] : r;
+    const int w = (int)(t % W);
+    bits[i * W + w] = 0u;
+    if (w == 0) count[i] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1639,10 +1687,19 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
                                                                    P, N, n, order, h->tdirs, p->n_dirs,
                                                                    p->origin_offset, bits, count, counters, work);
     } else {
+        // the last points (RC_TAIL_POINTS per resident warp) are cast in parts
+        const int W = (p->n_dirs + 31) / 32;
+        int splits = work ? std::min(RC_TAIL_SPLITS, W) : 1;
+        int64_t n_split = splits > 1 ? std::min<int64_t>(n, RC_TAIL_POINTS * blocks * (threads / 32)) : 0;
+        if (n_split == 0) splits = 1;
+        if (n_split > 0) {
+            k_zero_split<<<(unsigned)((n_split * W + 255) / 256), 256, 0, s>>>(order, n - n_split, n, W, bits, count);
+            RC_LAUNCHED();
+        }
 #define RC_HEMI(ST, WD)                                                                                            \
     k_hemisphere<ST, WD><<<(unsigned)blocks, threads, smem, s>>>(tree, h->tris, max_steps(h), h->scene_maxabs, P, N, \
                                                                  n, order, h->tdirs, p->n_dirs, p->origin_offset,  \
-                                                                 bits, count, counters, work)
+                                                                 bits, count, counters, work, n - n_split, splits)
         if (stats && wide) RC_HEMI(true, true);
         else if (stats) RC_HEMI(true, false);
         else if (wide) RC_HEMI(false, true);
