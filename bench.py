@@ -206,12 +206,38 @@ def peaks():
 TRAVERSAL_SOURCES = ("cast.cu", "build.cu", "rc_internal.cuh")
 
 
+def _code_only(text):
+    """C/C++ source without comments, trailing blanks and empty lines (string
+    and character literals are kept), so that editing a comment does not
+    change the hash of the code."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = [ln.rstrip() for ln in "".join(out).split("\n")]
+    return "\n".join(ln for ln in lines if ln)
+
+
 def traversal_hash():
-    """sha256 over the sources that define the traversal kernel and the tree
-    layout it walks."""
+    """sha256 over the code (comments removed) of the sources that define the
+    traversal kernel and the tree layout it walks."""
     h = hashlib.sha256()
     for f in TRAVERSAL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2609_05467_gb300", "csrc", f), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, "paper_2609_05467_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()
 
 

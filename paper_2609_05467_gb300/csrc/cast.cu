@@ -10,8 +10,18 @@
 // re-decided in FP64 (retest64), which evaluates the occlusion predicate
 // directly (signed volumes against each edge, plane crossing N.a / N.d) and
 // reports whether the pair lies inside the ambiguity band.  Box tests are
-// conservative (Ize, JCGT 2013: far distance scaled by 1 + 2*gamma_3), so
-// no triangle that can be hit at t > 0 is skipped.
+// conservative, so no triangle that can be hit at t > 0 is skipped: the
+// 4-wide walk computes each slab distance with one FMA and widens it by a
+// proven absolute margin (make_slab_ray), the binary walk scales the far
+// distance by 1 + 2*gamma_3 (Ize, JCGT 2013).
+//
+// Kernels: k_hemisphere (the default cast: persistent warps, one point per
+// warp in tiles of 32 directions, the last points in parts), its measured
+// alternatives k_hemisphere_dyn / _flat / _pkt / _wp (fetch_mode 1-4),
+// k_hemisphere_update (re-cast after an edit), k_batch (many parts in one
+// launch), k_orthogonal_axis (one frame axis for 32 points per work item),
+// k_tool_cast_axis (the sampled ball-end tool), and the frame set-up
+// kernels (k_frame_init, k_frame_box).
 #include <math.h>
 
 #include <algorithm>
