@@ -1697,19 +1697,28 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
                                                                    P, N, n, order, h->tdirs, p->n_dirs,
                                                                    p->origin_offset, bits, count, counters, work);
     } else {
-        // the last points (RC_TAIL_POINTS per resident warp) are cast in parts
+        // the last points (RC_TAIL_POINTS per resident warp) are cast in parts;
+        // with a grid sized to the work (one item per warp) the parts are the
+        // highest blocks, which the block scheduler starts last
         const int W = (p->n_dirs + 31) / 32;
-        int splits = work ? std::min(RC_TAIL_SPLITS, W) : 1;
-        int64_t n_split = splits > 1 ? std::min<int64_t>(n, RC_TAIL_POINTS * blocks * (threads / 32)) : 0;
+        const int64_t resident_warps = (int64_t)sm_count() * per_sm * (threads / 32);
+        int splits = std::min(RC_TAIL_SPLITS, W);
+        int64_t n_split = splits > 1 ? std::min<int64_t>(n, RC_TAIL_POINTS * resident_warps) : 0;
         if (n_split == 0) splits = 1;
+        if (!work) {
+            const int64_t items = (n - n_split) + n_split * splits;
+            blocks = std::max<int64_t>(1, (items * 32 + threads - 1) / threads);
+            if (blocks > 0x7FFFFFFF) return set_error(RC_E_UNSUPPORTED, "too many points for one launch");
+        }
         if (n_split > 0) {
             k_zero_split<<<(unsigned)((n_split * W + 255) / 256), 256, 0, s>>>(order, n - n_split, n, W, bits, count);
             RC_LAUNCHED();
         }
-#define RC_HEMI(ST, WD)                                                                                            \
-    k_hemisphere<ST, WD><<<(unsigned)blocks, threads, smem, s>>>(tree, h->tris, max_steps(h), h->scene_maxabs, P, N, \
-                                                                 n, order, h->tdirs, p->n_dirs, p->origin_offset,  \
-                                                                 bits, count, counters, work, n - n_split, splits)
+#define RC_HEMI(ST, WD)                                                                                    \
+    k_hemisphere<ST, WD><<<(unsigned)blocks, threads, smem, s>>>(tree, h->tris, max_steps(h), h->scene_maxabs, \
+                                                                 P, N, n, order, h->tdirs, p->n_dirs,         \
+                                                                 p->origin_offset, bits, count, counters, work, \
+                                                                 n - n_split, splits)
         if (stats && wide) RC_HEMI(true, true);
         else if (stats) RC_HEMI(true, false);
         else if (wide) RC_HEMI(false, true);
