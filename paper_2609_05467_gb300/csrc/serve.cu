@@ -86,6 +86,7 @@ struct SrvRequest {
     int64_t nV = 0, T = 0, n = 0;
     int64_t est = 0;
     int state = 0;   // 0 queued, 1 running, 2 done
+    bool large = false;   // in the largest size class (admitted one at a time)
     rc_request_result res;
 };
 
@@ -125,6 +126,7 @@ struct rc_server_s {
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;        // [slot * levels + level], level 0 = highest priority
     int levels = 1;
+    int large_running = 0;                    // admitted requests of the largest size class
     int64_t used = 0;              // resident + reserved bytes
     int64_t next_id = 1;
     uint64_t tick = 0;
@@ -137,12 +139,36 @@ using namespace rc;
 // Pick the first queued request that can run now (its part is not in use
 // and its bytes fit, after evicting idle resident parts if needed).
 // Called with the lock held.  Requests that can never fit fail at once.
+// stream priority level of a request: 0 (highest) up to small_rays
+// hemisphere rays, one level lower per doubling
+static int level_of(rc_server s, const SrvRequest* r)
+{
+    int level = s->levels - 1;
+    if (s->cfg.small_rays > 0) {
+        level = 0;
+        for (double lim = (double)s->cfg.small_rays; (double)r->n * s->p.n_dirs > lim && level < s->levels - 1;
+             lim *= 2.0)
+            ++level;
+    }
+    return level;
+}
+
+// Requests of the largest size class (the lowest priority level) are
+// admitted one at a time, in arrival order: one of them fills the GPU alone,
+// and two side by side would only take twice as long each.  Smaller requests
+// are admitted beside them and run on higher-priority streams.
+static bool is_large(rc_server s, const SrvRequest* r)
+{
+    return s->levels > 1 && s->cfg.small_rays > 0 && level_of(s, r) == s->levels - 1;
+}
+
 static SrvRequest* admit(rc_server s)
 {
     for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
         SrvRequest* r = *it;
         auto ce = s->cache.find(r->key);
         if (ce != s->cache.end() && ce->second->busy) continue;
+        if (s->large_running > 0 && is_large(s, r)) continue;
         const int64_t have = ce != s->cache.end() ? ce->second->bytes : 0;
         const int64_t need = r->est - have;
         if (r->est > s->cfg.hbm_budget_bytes) {
@@ -179,6 +205,8 @@ static SrvRequest* admit(rc_server s)
         e->busy = true;
         s->used += need;
         e->bytes = r->est;
+        r->large = is_large(s, r);
+        if (r->large) s->large_running++;
         r->state = 1;
         r->res.t_admit = now_s();
         s->queue.erase(it);
@@ -317,15 +345,8 @@ static void worker(rc_server s, int slot)
         }
         r->res.t_start = now_s();
         r->res.slot = slot;
-        // smaller requests get higher stream priority: level 0 up to
-        // small_rays hemisphere rays, one level lower per doubling
-        int level = s->levels - 1;
-        if (s->cfg.small_rays > 0) {
-            level = 0;
-            for (double lim = (double)s->cfg.small_rays; (double)r->n * s->p.n_dirs > lim && level < s->levels - 1;
-                 lim *= 2.0)
-                ++level;
-        }
+        // smaller requests get higher stream priority
+        const int level = level_of(s, r);
         cudaStream_t st = s->streams[slot * s->levels + level];
         r->res.priority_level = level;
         const rc_status rs = run_request(s, r, e, st);
@@ -358,6 +379,7 @@ static void worker(rc_server s, int slot)
             }
             r->res.t_end = t_end;
             r->state = 2;
+            if (r->large) s->large_running--;
             s->st.running--;
             s->cv_done.notify_all();
             s->cv_work.notify_all();
