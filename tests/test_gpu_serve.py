@@ -140,3 +140,22 @@ def test_incremental_resubmission_equals_the_standalone_chain(rc):
     assert np.array_equal(rb, bits_a)
     b0.close()
     b1.close()
+
+
+def test_largest_requests_run_one_at_a_time(rc):
+    # with small_rays = 500 every request above 500 * 2^(levels-2) rays is in
+    # the largest size class: two of them must not overlap, a small one may
+    p = rc.rc_params_default(n_dirs=256, tool_length=40.0)
+    srv = rc.rc_server_create(p, slots=3, hbm_budget_bytes=8 << 30, small_rays=500)
+    V, F = synth.prismatic(h=3.0)
+    Vc, Fc = synth.cube(20.0, 2)
+    ids = [rc.rc_server_submit(srv, 11, V, F, 4000), rc.rc_server_submit(srv, 12, V, F, 4000),
+           rc.rc_server_submit(srv, 13, Vc, Fc, 1)]
+    r1, r2, r3 = [rc.rc_server_wait(srv, i, timeout_s=300.0) for i in ids]
+    rc.rc_server_destroy(srv)
+    for r in (r1, r2, r3):
+        assert r.status == 0, r.message
+    if r1.priority_level == 0:
+        pytest.skip("the device has a single stream priority level")
+    assert r1.priority_level == r2.priority_level > r3.priority_level == 0
+    assert r2.t_start >= r1.t_end or r1.t_start >= r2.t_end
