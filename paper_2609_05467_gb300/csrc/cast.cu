@@ -1027,19 +1027,19 @@ k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
             k = own;
         }
         if (k >= items) break;
-        if (k < (unsigned long long)n_whole) {
-            const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
-            cast_point<kStats, kWide>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits,
-                                      count, acc);
-        } else {
+        // item k: a whole point (tiles 0..W, t1 = -1) or a part of one
+        int64_t r = (int64_t)k;
+        int t0 = 0, t1 = -1;
+        if (k >= (unsigned long long)n_whole) {
             const unsigned long long q = k - (unsigned long long)n_whole;
-            const int64_t r = n_whole + (int64_t)(q / splits);
-            const int t0 = (int)(q % splits) * tw, t1 = min(W, t0 + tw);
+            r = n_whole + (int64_t)(q / splits);
+            t0 = (int)(q % splits) * tw;
+            t1 = min(W, t0 + tw);
             if (t0 >= t1) continue;
-            const int64_t i = order ? (int64_t)__ldg(&order[r]) : r;
-            cast_point<kStats, kWide>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits,
-                                      count, acc, t0, t1);
         }
+        const int64_t i = order ? (int64_t)__ldg(&order[r]) : r;
+        cast_point<kStats, kWide>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits, count,
+                                  acc, t0, t1);
     }
     warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow, acc.nvis, acc.ntri);
 }
