@@ -305,7 +305,8 @@ __device__ __forceinline__ TraceOut trace(const float4* __restrict__ nodes, cons
 
 // Any-hit walk of the 4-wide tree: the same ray, box and triangle decisions
 // as trace(); per node the four child boxes are tested together, the
-// nearest hit child is visited next and the others are pushed far-to-near.
+// nearest hit child is visited next and the others are pushed (the default
+// walk orders them only partly, the while-while walk fully, far-to-near).
 // Per-ray constants of the 4-wide slab test.  A slab distance is one FMA,
 // t = b * i - o * i, with the near / far bound of each axis picked by the
 // load address (the node stores lo and hi of an axis in adjacent float4s).
@@ -391,18 +392,20 @@ __device__ __forceinline__ TraceOut trace4_ifif(const float4* __restrict__ wnode
                 cur = stack[--sp];
                 continue;
             }
-            // sort the four (distance, child) pairs: misses (inf) go last
 #define RC_CSWAP(a, b)                                              \
     if (d[b] < d[a]) {                                              \
         const float td = d[a]; d[a] = d[b]; d[b] = td;              \
         const int tc = c[a]; c[a] = c[b]; c[b] = tc;                \
     }
-            RC_CSWAP(0, 1) RC_CSWAP(2, 3) RC_CSWAP(0, 2) RC_CSWAP(1, 3) RC_CSWAP(1, 2)
+            // three of the five exchanges of the sorting network: the nearest
+            // child reaches slot 0 and the others stay partly ordered (faster
+            // than the full network, and no more nodes visited)
+            RC_CSWAP(0, 1) RC_CSWAP(2, 3) RC_CSWAP(0, 2)
 #undef RC_CSWAP
             if (sp + nh - 1 > kStack4) { out.overflow = 1; out.flags = 1; return out; }
-            if (nh > 3) stack[sp++] = c[3];
-            if (nh > 2) stack[sp++] = c[2];
-            if (nh > 1) stack[sp++] = c[1];
+            if (d[3] != INFINITY) stack[sp++] = c[3];
+            if (d[2] != INFINITY) stack[sp++] = c[2];
+            if (d[1] != INFINITY) stack[sp++] = c[1];
             cur = c[0];
             continue;
         } else {
