@@ -1,7 +1,7 @@
 // tool.cu -- tool-aware accessibility along the six machining axes: the
 // orthogonal cast of Section 3.2 with the thin ray replaced by a sampled
 // ball-end tool of radius r (centre ray plus a ring of parallel rays); the
-// kernel is k_tool_cast in cast.cu.
+// kernel is k_tool_cast_axis in cast.cu.
 #include <math.h>
 
 #include <vector>
