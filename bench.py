@@ -144,17 +144,19 @@ def oracle_rate(V, F, n_dirs, n_points, seed=0):
     return n_points * n_dirs, t1 - t0, t2 - t1, oracle.num_cores()
 
 
-def cpu_baseline(V, F, n_dirs, target_s=12.0):
-    """The oracle on a bounded sample sized to about target_s seconds of cast."""
+def cpu_baseline(V, F, n_dirs, n_points, target_s=12.0):
+    """The oracle on a bounded sample of the workload: its first points,
+    as many as about target_s seconds of cast take (all of them if fewer)."""
     import oracle
     oracle.build()
-    probe = 500
+    probe = min(500, n_points)
     rays, tb, tc, cores = oracle_rate(V, F, n_dirs, probe)
-    pts = int(max(probe, min(2_000_000, probe * target_s / max(tc, 1e-3))))
+    pts = int(max(probe, min(n_points, probe * target_s / max(tc, 1e-3))))
     rays, tb, tc, cores = oracle_rate(V, F, n_dirs, pts)
     return {"value": rays / (tb + tc), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "first %d of the workload's area-weighted points x %d directions (%d rays): CPU BVH build "
-                      "+ sampling %.2f s + cast %.1f s, FP64, all host cores" % (pts, n_dirs, rays, tb, tc)}
+            "sample": "first %d of the workload's %d area-weighted points x %d directions (%d rays): CPU BVH "
+                      "build + sampling %.2f s + cast %.1f s, FP64, all host cores"
+                      % (pts, n_points, n_dirs, rays, tb, tc)}
 
 
 def run_reference(args, wl, V, F):
@@ -431,7 +433,7 @@ def run_gpu(args, wl, V, F):
         return
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(V, F, N)
+        cpu = cpu_baseline(V, F, N, n)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
