@@ -151,6 +151,13 @@ const char* rc_last_error(void);
  * Used by benchmarks to report launch counts; never fails. */
 int64_t rc_launch_count(void);
 
+/* Waits for the work queued on `stream` (NULL = the legacy default stream)
+ * and reports an error that asynchronous work raised there: RC_OK, or
+ * RC_E_CUDA with the CUDA error text in rc_last_error().  The library's own
+ * device-side failures (a traversal bound exceeded) are reported through
+ * the counters of each call instead. */
+rc_status rc_stream_status(void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Geometry and acceleration structure                                    */
 /* ---------------------------------------------------------------------- */

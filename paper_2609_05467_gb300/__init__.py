@@ -25,7 +25,7 @@ __all__ = [
     "rc_sample_points", "rc_direction_table", "rc_hemisphere_cast", "rc_direction_variability",
     "rc_direction_variability_noalloc",
     "rc_classify", "rc_orthogonal_cast", "rc_min_setups", "rc_setup_cover", "rc_analyze_part",
-    "rc_launch_count", "Bvh", "PartResult", "rc_batch_create", "rc_batch_add_part", "rc_batch_clear",
+    "rc_launch_count", "rc_stream_status", "Bvh", "PartResult", "rc_batch_create", "rc_batch_add_part", "rc_batch_clear",
     "rc_batch_set_params", "rc_batch_launch", "rc_batch_autotune", "rc_batch_destroy", "rc_server_create",
     "rc_server_submit", "rc_server_wait", "rc_server_read_bits", "rc_server_get_stats", "rc_server_destroy",
 ]
@@ -162,6 +162,7 @@ def load(build_if_missing=True):
             "rc_params_default": ([ctypes.POINTER(Params)], st),
             "rc_last_error": ([], ctypes.c_char_p),
             "rc_launch_count": ([], i64),
+            "rc_stream_status": ([P], st),
             "rc_build_bvh": ([P, i64, P, i64, P, ctypes.POINTER(P)], st),
             "rc_build_bvh_ex": ([P, i64, P, i64, i32, P, ctypes.POINTER(P)], st),
             "rc_refit_bvh": ([P, P, P], st),
@@ -534,6 +535,12 @@ def rc_server_destroy(s):
 
 def rc_launch_count():
     return int(load().rc_launch_count())
+
+
+def rc_stream_status(stream=None):
+    """Wait for `stream` (default: the current torch stream) and raise
+    RcError if asynchronous work queued on it failed."""
+    _check(load().rc_stream_status(_stream(stream)))
 
 
 class Bvh:

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "rc_internal.cuh"
+#include "nvtx_range.h"
 
 namespace rc {
 
@@ -245,14 +246,24 @@ const char* rc_last_error(void) { return t_err.c_str(); }
 
 int64_t rc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+rc_status rc_stream_status(void* stream)
+{
+    RC_RANGE();
+    const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_error(e, "work queued on the stream");
+    return RC_OK;
+}
+
 rc_status rc_build_bvh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t T, void* stream, rc_bvh* out)
 {
+    RC_RANGE();
     return rc_build_bvh_ex(d_V, nV, d_F, T, RC_BUILDER_KARRAS, stream, out);
 }
 
 rc_status rc_build_bvh_ex(const float* d_V, int64_t nV, const int32_t* d_F, int64_t T, int32_t builder, void* stream,
                           rc_bvh* out)
 {
+    RC_RANGE();
     if (!out) return set_error(RC_E_ARG, "out is NULL");
     if (builder != RC_BUILDER_KARRAS && builder != RC_BUILDER_PLOC)
         return set_error(RC_E_ARG, "builder must be RC_BUILDER_KARRAS or RC_BUILDER_PLOC");
@@ -294,6 +305,7 @@ rc_status rc_build_bvh_ex(const float* d_V, int64_t nV, const int32_t* d_F, int6
 
 rc_status rc_refit_bvh(rc_bvh h, const float* d_V, void* stream)
 {
+    RC_RANGE();
     if (!h || !d_V) return set_error(RC_E_ARG, "handle or vertex pointer is NULL");
     rc_status st = use_device_of(h);
     if (st != RC_OK) return st;
@@ -304,6 +316,7 @@ rc_status rc_refit_bvh(rc_bvh h, const float* d_V, void* stream)
 
 rc_status rc_destroy_bvh(rc_bvh h)
 {
+    RC_RANGE();
     if (!h) return RC_OK;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -315,6 +328,7 @@ rc_status rc_destroy_bvh(rc_bvh h)
 
 rc_status rc_bvh_get_info(rc_bvh h, rc_bvh_info* out)
 {
+    RC_RANGE();
     if (!h || !out) return set_error(RC_E_ARG, "handle or out is NULL");
     out->n_tris = h->T;
     out->n_nodes = h->n_int;
@@ -329,6 +343,7 @@ rc_status rc_bvh_get_info(rc_bvh h, rc_bvh_info* out)
 rc_status rc_sample_points(rc_bvh h, int64_t n, const rc_params* p, float* d_P, float* d_N, int32_t* d_face,
                            double* d_weight, void* stream)
 {
+    RC_RANGE();
     if (!h) return set_error(RC_E_ARG, "handle is NULL");
     rc_status st = check_params(p);
     if (st != RC_OK) return st;
@@ -345,6 +360,7 @@ rc_status rc_sample_points(rc_bvh h, int64_t n, const rc_params* p, float* d_P, 
 
 rc_status rc_direction_table(int32_t n_dirs, float* h_dirs)
 {
+    RC_RANGE();
     if (!h_dirs) return set_error(RC_E_ARG, "output is NULL");
     if (n_dirs < 1 || n_dirs > kMaxDirs) return set_error(RC_E_ARG, "n_dirs out of range");
     fibonacci_hemisphere(n_dirs, h_dirs);
@@ -354,6 +370,7 @@ rc_status rc_direction_table(int32_t n_dirs, float* h_dirs)
 rc_status rc_hemisphere_cast(rc_bvh h, const float* d_P, const float* d_N, int64_t n, const rc_params* p,
                              uint32_t* d_bits, int32_t* d_count, int64_t* d_counters, void* stream)
 {
+    RC_RANGE();
     if (!h) return set_error(RC_E_ARG, "handle is NULL");
     rc_status st = check_params(p);
     if (st != RC_OK) return st;
@@ -377,6 +394,7 @@ rc_status rc_direction_variability(const uint32_t* d_bits, const float* d_N, con
                                    const rc_params* p, float* d_acc, int8_t* d_dom, float* d_conc,
                                    double* d_dir_area, rc_summary* h_summary, void* stream)
 {
+    RC_RANGE();
     rc_status st = check_params(p);
     if (st != RC_OK) return st;
     if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
@@ -422,6 +440,7 @@ rc_status rc_direction_variability(const uint32_t* d_bits, const float* d_N, con
 
 rc_status rc_classify(const rc_summary* s, const rc_params* p, int32_t* label)
 {
+    RC_RANGE();
     if (!s || !p || !label) return set_error(RC_E_ARG, "NULL argument");
     const double mx = std::max(s->axis_share[0], std::max(s->axis_share[1], s->axis_share[2]));
     *label = (s->overall_access < p->t_acc || mx < p->t_share || s->mean_conc > p->t_conc) ? 1 : 0;
@@ -431,6 +450,7 @@ rc_status rc_classify(const rc_summary* s, const rc_params* p, int32_t* label)
 rc_status rc_orthogonal_cast(rc_bvh h, const float* d_P, const float* d_N, int64_t n, const rc_params* p,
                              uint8_t* d_mask, float* d_travel, int64_t* d_counters, void* stream)
 {
+    RC_RANGE();
     if (!h) return set_error(RC_E_ARG, "handle is NULL");
     rc_status st = check_params(p);
     if (st != RC_OK) return st;
@@ -448,6 +468,7 @@ rc_status rc_orthogonal_cast(rc_bvh h, const float* d_P, const float* d_N, int64
 rc_status rc_min_setups(rc_bvh h, const uint8_t* d_mask, const float* d_travel, const int32_t* d_face, int64_t n,
                         const rc_params* p, uint8_t* d_class, rc_setups* h_out, void* stream)
 {
+    RC_RANGE();
     if (!h || !h_out) return set_error(RC_E_ARG, "handle or output is NULL");
     rc_status st = check_params(p);
     if (st != RC_OK) return st;
@@ -508,6 +529,7 @@ rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int6
                           const rc_params* p, uint32_t* h_bits, int32_t* h_count, uint8_t* h_mask,
                           uint8_t* h_class, rc_part_result* h_out, void* stream)
 {
+    RC_RANGE();
     if (!h_V || !h_F || !h_out) return set_error(RC_E_ARG, "NULL argument");
     rc_status st = check_params(p);
     if (st != RC_OK) return st;
@@ -605,6 +627,7 @@ rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int6
 
 rc_status rc_setup_cover(const int64_t* h_mask_hist, rc_setups* out)
 {
+    RC_RANGE();
     if (!h_mask_hist || !out) return set_error(RC_E_ARG, "NULL argument");
     int64_t hh[64];
     for (int m = 0; m < 64; ++m) {

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "rc_internal.cuh"
+#include "nvtx_range.h"
 
 namespace rc {
 
@@ -120,6 +121,7 @@ extern "C" {
 
 rc_status rc_batch_create(const rc_params* p, rc_batch* out)
 {
+    RC_RANGE();
     if (!out) return set_error(RC_E_ARG, "out is NULL");
     *out = nullptr;
     rc_status st = check_params_public(p);
@@ -140,6 +142,7 @@ rc_status rc_batch_create(const rc_params* p, rc_batch* out)
 rc_status rc_batch_add_part(rc_batch b, rc_bvh h, const float* d_P, const float* d_N, int64_t n, uint32_t* d_bits,
                             int32_t* d_count, int64_t* d_counters, int64_t* part_id)
 {
+    RC_RANGE();
     if (!b || !h) return set_error(RC_E_ARG, "batch or handle is NULL");
     if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
     if (n > 0 && (!d_P || !d_N || !d_bits || !d_count)) return set_error(RC_E_ARG, "array pointer is NULL");
@@ -160,6 +163,7 @@ rc_status rc_batch_add_part(rc_batch b, rc_bvh h, const float* d_P, const float*
 
 rc_status rc_batch_clear(rc_batch b)
 {
+    RC_RANGE();
     if (!b) return set_error(RC_E_ARG, "batch is NULL");
     for (HostPart& q : b->parts)
         if (q.order) cudaFree(q.order);
@@ -171,6 +175,7 @@ rc_status rc_batch_clear(rc_batch b)
 
 rc_status rc_batch_set_params(rc_batch b, const rc_params* p)
 {
+    RC_RANGE();
     if (!b) return set_error(RC_E_ARG, "batch is NULL");
     rc_status st = check_params_public(p);
     if (st != RC_OK) return st;
@@ -181,6 +186,7 @@ rc_status rc_batch_set_params(rc_batch b, const rc_params* p)
 
 rc_status rc_batch_launch(rc_batch b, void* stream)
 {
+    RC_RANGE();
     if (!b) return set_error(RC_E_ARG, "batch is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     if (b->dirty) {
@@ -195,6 +201,7 @@ rc_status rc_batch_launch(rc_batch b, void* stream)
 
 rc_status rc_batch_autotune(rc_batch b, void* stream, int32_t repeats, rc_params* best)
 {
+    RC_RANGE();
     if (!b) return set_error(RC_E_ARG, "batch is NULL");
     if (repeats < 1) repeats = 1;
     cudaStream_t s = (cudaStream_t)stream;
@@ -237,6 +244,7 @@ rc_status rc_batch_autotune(rc_batch b, void* stream, int32_t repeats, rc_params
 
 rc_status rc_batch_destroy(rc_batch b)
 {
+    RC_RANGE();
     if (!b) return RC_OK;
     for (HostPart& q : b->parts)
         if (q.order) cudaFree(q.order);

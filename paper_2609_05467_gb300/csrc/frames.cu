@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "rc_internal.cuh"
+#include "nvtx_range.h"
 
 namespace rc {
 
@@ -473,6 +474,7 @@ extern "C" {
 
 rc_status rc_frame_candidates(rc_bvh h, const rc_params* p, rc_frames* out, void* stream)
 {
+    RC_RANGE();
     if (!h || !out) return set_error(RC_E_ARG, "handle or output is NULL");
     rc_status st = check_params_public(p);
     if (st != RC_OK) return st;
@@ -582,6 +584,7 @@ rc_status rc_frame_candidates(rc_bvh h, const rc_params* p, rc_frames* out, void
 rc_status rc_frame_select(rc_bvh h, const float* d_P, const float* d_N, const int32_t* d_face, int64_t n,
                           const rc_params* p, rc_frames* io, int64_t* d_counters, void* stream)
 {
+    RC_RANGE();
     if (!h || !io) return set_error(RC_E_ARG, "handle or frames is NULL");
     rc_status st = check_params_public(p);
     if (st != RC_OK) return st;

@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "rc_internal.cuh"
+#include "nvtx_range.h"
 
 namespace rc {
 
@@ -50,6 +51,7 @@ extern "C" rc_status rc_direction_variability_noalloc(const uint32_t* d_bits, co
                                                       float* d_acc, int8_t* d_dom, float* d_conc,
                                                       double* d_dir_area, rc_summary* h_summary, void* stream)
 {
+    RC_RANGE();
     if (!p) return set_error(RC_E_ARG, "params is NULL");
     if (p->n_dirs < 1) return set_error(RC_E_ARG, "n_dirs must be >= 1");
     if (p->n_dirs > kNoAllocMaxDirs)

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "rc_internal.cuh"
+#include "nvtx_range.h"
 
 namespace rc {
 
@@ -401,6 +402,7 @@ extern "C" {
 
 rc_status rc_server_create(const rc_params* p, const rc_server_config* cfg, rc_server* out)
 {
+    RC_RANGE();
     if (!out || !cfg) return set_error(RC_E_ARG, "NULL argument");
     *out = nullptr;
     rc_status st = check_params_public(p);
@@ -435,6 +437,7 @@ rc_status rc_server_create(const rc_params* p, const rc_server_config* cfg, rc_s
 rc_status rc_server_submit(rc_server s, uint64_t part_key, const float* h_V, int64_t nV, const int32_t* h_F,
                            int64_t T, int64_t n, int64_t* req_id)
 {
+    RC_RANGE();
     if (!s || !h_V || !h_F || !req_id) return set_error(RC_E_ARG, "NULL argument");
     if (nV < 3 || T < 1 || n < 0) return set_error(RC_E_ARG, "empty mesh or negative n");
     if (s->p.sample_mode == RC_SAMPLE_FACE_CENTROID && n != T)
@@ -465,6 +468,7 @@ rc_status rc_server_submit(rc_server s, uint64_t part_key, const float* h_V, int
 
 rc_status rc_server_wait(rc_server s, int64_t req_id, double timeout_s, rc_request_result* out)
 {
+    RC_RANGE();
     if (!s || !out) return set_error(RC_E_ARG, "NULL argument");
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->reqs.find(req_id);
@@ -483,6 +487,7 @@ rc_status rc_server_wait(rc_server s, int64_t req_id, double timeout_s, rc_reque
 
 rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, int32_t* h_count, int64_t n)
 {
+    RC_RANGE();
     if (!s) return set_error(RC_E_ARG, "server is NULL");
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->cache.find(part_key);
@@ -505,6 +510,7 @@ rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, 
 
 rc_status rc_server_get_stats(rc_server s, rc_server_stats* out)
 {
+    RC_RANGE();
     if (!s || !out) return set_error(RC_E_ARG, "NULL argument");
     std::lock_guard<std::mutex> lk(s->mu);
     *out = s->st;
@@ -516,6 +522,7 @@ rc_status rc_server_get_stats(rc_server s, rc_server_stats* out)
 
 rc_status rc_server_destroy(rc_server s)
 {
+    RC_RANGE();
     if (!s) return RC_OK;
     {
         std::lock_guard<std::mutex> lk(s->mu);

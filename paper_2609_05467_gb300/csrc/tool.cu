@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "rc_internal.cuh"
+#include "nvtx_range.h"
 
 namespace rc {
 rc_status launch_tool_cast(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p, double radius,
@@ -20,6 +21,7 @@ extern "C" rc_status rc_tool_cast(rc_bvh h, const float* d_P, const float* d_N, 
                                   double tool_radius, int32_t ring_rays, uint8_t* d_mask, int64_t* d_counters,
                                   void* stream)
 {
+    RC_RANGE();
     if (!h) return set_error(RC_E_ARG, "handle is NULL");
     rc_status st = check_params_public(p);
     if (st != RC_OK) return st;

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include "rc_internal.cuh"
+#include "nvtx_range.h"
 
 namespace rc {
 
@@ -143,6 +144,7 @@ extern "C" {
 rc_status rc_sample_points_on_faces(rc_bvh h, int64_t n, const rc_params* p, const int32_t* d_face, float* d_P,
                                     float* d_N, void* stream)
 {
+    RC_RANGE();
     if (!h) return set_error(RC_E_ARG, "handle is NULL");
     rc_status st = check_params_public(p);
     if (st != RC_OK) return st;
@@ -169,6 +171,7 @@ rc_status rc_sample_points_on_faces(rc_bvh h, int64_t n, const rc_params* p, con
 rc_status rc_changed_faces(const float* d_V_old, const float* d_V_new, int64_t nV, const int32_t* d_F, int64_t T,
                            uint8_t* d_changed, float* h_box, int64_t* h_n_changed, void* stream)
 {
+    RC_RANGE();
     if (!h_box || !h_n_changed) return set_error(RC_E_ARG, "output is NULL");
     if (nV < 0 || T < 0) return set_error(RC_E_ARG, "sizes must be >= 0");
     if (T > 0 && (!d_V_old || !d_V_new || !d_F || !d_changed)) return set_error(RC_E_ARG, "array pointer is NULL");
@@ -198,6 +201,7 @@ rc_status rc_hemisphere_update(rc_bvh h, const float* d_P, const float* d_N, con
                                const uint8_t* d_changed, const float* h_box, const rc_params* p, uint32_t* d_bits,
                                int32_t* d_count, int64_t* d_counters, void* stream)
 {
+    RC_RANGE();
     if (!h || !h_box) return set_error(RC_E_ARG, "handle or box is NULL");
     rc_status st = check_params_public(p);
     if (st != RC_OK) return st;

@@ -28,3 +28,12 @@ def test_probes(rc):
             rc.rc_probe_l2(*bad)
     with pytest.raises(rc.RcError):
         rc.rc_probe_fp32(0)
+
+
+def test_stream_status_after_work(rc):
+    # a finished stream reports no asynchronous error
+    rc.rc_probe_fp32(64)
+    rc.rc_stream_status()
+    import torch
+    s = torch.cuda.Stream()
+    rc.rc_stream_status(s)
