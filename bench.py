@@ -572,9 +572,23 @@ def run_served(args):
     def s_submit(r, t0):
         return rc.rc_server_submit(srv, r["key"], r["V"], r["F"], r["n"]), time.perf_counter()
 
+    log = open(args.served_log, "w") if args.served_log else None
+
     def s_collect(h, r, t0):
         rid, tsub = h
         res = rc.rc_server_wait(srv, rid, timeout_s=600.0)
+        if log:
+            # one JSON line per request: its timeline on the server and what it cast
+            log.write(json.dumps({
+                "request": int(res.request_id), "part_key": int(res.part_key), "status": int(res.status),
+                "slot": int(res.slot), "priority_level": int(res.priority_level), "rebuilt": int(res.rebuilt),
+                "updated": int(res.updated), "arrival_s": float(r["t"]), "t_submit": res.t_submit,
+                "t_admit": res.t_admit, "t_start": res.t_start, "t_end": res.t_end, "triangles": int(len(r["F"])),
+                "points": int(r["n"]),
+                "rays": int(res.result.cast_counters[0] + res.result.ortho_counters[0]),
+                "ambiguous_rays": int(res.result.cast_counters[1] + res.result.ortho_counters[1]),
+                "retests": int(res.result.cast_counters[2] + res.result.ortho_counters[2]),
+                "resident_bytes": int(res.resident_bytes)}) + "\n")
         return dict(lat=res.t_end - res.t_submit, rays=res.result.cast_counters[0] + res.result.ortho_counters[0],
                     rebuilt=res.rebuilt, status=res.status, wait=res.t_start - res.t_submit,
                     level=res.priority_level, tris=len(r["F"]), n=r["n"], arrival=r["t"], updated=res.updated,
@@ -583,6 +597,8 @@ def run_served(args):
     for r in reqs[:3]:
         rc.rc_server_wait(srv, rc.rc_server_submit(srv, 10**9 + r["key"], r["V"], r["F"], r["n"]), 600.0)
     served, wall_s = replay(s_submit, s_collect)
+    if log:
+        log.close()
     stats = rc.rc_server_get_stats(srv)
     rc.rc_server_destroy(srv)
 
@@ -1125,6 +1141,7 @@ def main():
     ap.add_argument("--slots", type=int, default=4, help="served workload: server slots")
     ap.add_argument("--parts", type=int, default=64, help="batched workload: number of parts")
     ap.add_argument("--incremental", action="store_true", help="served workload: incremental re-analysis")
+    ap.add_argument("--served-log", default="", help="served workload: write one JSON line per request here")
     ap.add_argument("--server-persistent", action="store_true",
                     help="served workload: the server's casts use the persistent grid (launch_mode 0)")
     ap.add_argument("--edit", default="bump", choices=["bump", "deepen", "shift"],
