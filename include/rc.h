@@ -207,6 +207,17 @@ rc_status rc_destroy_bvh(rc_bvh h);
 /* Sizes, depth and scene bounds of a built handle (host struct). */
 rc_status rc_bvh_get_info(rc_bvh h, rc_bvh_info* out);
 
+/* Index checks of a built tree (the device-side bounds checking that stands
+ * in for a memory checker): every interior child of a 4-wide node must be a
+ * node above its parent's number and below n_int (so no walk can cycle),
+ * every leaf's triangle range inside [0, T), every used child box finite
+ * with lo <= hi, every packed binary child inside its range, and every
+ * triangle record's face id inside [0, T).  h_counts[6] receives the
+ * violations of each kind in that order and, last, the number of 4-wide
+ * nodes reached from the root.  Synchronises `stream`.
+ * Errors: RC_E_ARG (NULL), RC_E_CUDA. */
+rc_status rc_bvh_validate(rc_bvh h, int64_t* h_counts, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Section 3.1: sampling, directions, hemispherical cast                  */
 /* ---------------------------------------------------------------------- */

@@ -25,7 +25,7 @@ __all__ = [
     "rc_sample_points", "rc_direction_table", "rc_hemisphere_cast", "rc_direction_variability",
     "rc_direction_variability_noalloc",
     "rc_classify", "rc_orthogonal_cast", "rc_min_setups", "rc_setup_cover", "rc_analyze_part",
-    "rc_launch_count", "rc_stream_status", "Bvh", "PartResult", "rc_batch_create", "rc_batch_add_part", "rc_batch_clear",
+    "rc_launch_count", "rc_stream_status", "rc_bvh_validate", "Bvh", "PartResult", "rc_batch_create", "rc_batch_add_part", "rc_batch_clear",
     "rc_batch_set_params", "rc_batch_launch", "rc_batch_autotune", "rc_batch_destroy", "rc_server_create",
     "rc_server_submit", "rc_server_wait", "rc_server_read_bits", "rc_server_get_stats", "rc_server_destroy",
 ]
@@ -168,6 +168,7 @@ def load(build_if_missing=True):
             "rc_refit_bvh": ([P, P, P], st),
             "rc_destroy_bvh": ([P], st),
             "rc_bvh_get_info": ([P, ctypes.POINTER(BvhInfo)], st),
+            "rc_bvh_validate": ([P, P, P], st),
             "rc_sample_points": ([P, i64, ctypes.POINTER(Params), P, P, P, P, P], st),
             "rc_direction_table": ([i32, P], st),
             "rc_hemisphere_cast": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P], st),
@@ -531,6 +532,16 @@ def rc_server_get_stats(s):
 
 def rc_server_destroy(s):
     _check(load().rc_server_destroy(ctypes.c_void_p(s)))
+
+
+def rc_bvh_validate(h, stream=None):
+    """Index checks of a built tree; returns a dict of violation counts
+    (all zero for a sound tree) and the number of 4-wide nodes reached."""
+    import numpy as np
+    out = np.zeros(6, np.int64)
+    _check(load().rc_bvh_validate(ctypes.c_void_p(h), out.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    keys = ("wide_child", "wide_leaf", "wide_box", "binary_child", "tri_face", "nodes_seen")
+    return {k: int(v) for k, v in zip(keys, out)}
 
 
 def rc_launch_count():

@@ -481,3 +481,37 @@ def test_ploc_tree_refit_and_tiny_parts(rc):
         bvh.close()
     with pytest.raises(rc.RcError):
         rc.rc_build_bvh_ex(*gpu_mesh(V, F), 7)
+
+
+# ---------------------------------------------------------------------------
+# device-side index checks of the built trees (in place of a memory checker)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["pocket", "cube", "prismatic_coarse", "impeller_coarse", "multi_pocket"])
+def test_built_trees_pass_the_index_checks(rc, name):
+    V, F = PARTS[name]()
+    for builder in (0, 1):
+        Vt, Ft = gpu_mesh(V, F)
+        h = rc.rc_build_bvh_ex(Vt, Ft, builder)
+        c = rc.rc_bvh_validate(h)
+        assert c["nodes_seen"] >= 1
+        assert {k: v for k, v in c.items() if k != "nodes_seen"} == dict.fromkeys(
+            ("wide_child", "wide_leaf", "wide_box", "binary_child", "tri_face"), 0), c
+        rc.rc_destroy_bvh(h)
+
+
+def test_tiny_and_refitted_trees_pass_the_index_checks(rc):
+    V, F = synth.cube(10.0, 0)
+    for T in (1, 2, 3, 5):
+        Vt, Ft = gpu_mesh(V, F[:T])
+        h = rc.rc_build_bvh(Vt, Ft)
+        c = rc.rc_bvh_validate(h)
+        assert c["nodes_seen"] >= 1 and sum(v for k, v in c.items() if k != "nodes_seen") == 0, (T, c)
+        rc.rc_destroy_bvh(h)
+    V0, F0 = synth.perturbed_part(2, 0.0)
+    V1, _ = synth.perturbed_part(2, 3.5)
+    bvh = _build(rc, V0, F0)
+    rc.rc_refit_bvh(bvh.h, torch.from_numpy(V1).cuda())
+    c = rc.rc_bvh_validate(bvh.h)
+    assert sum(v for k, v in c.items() if k != "nodes_seen") == 0, c
+    bvh.close()
