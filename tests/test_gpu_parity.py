@@ -515,3 +515,27 @@ def test_tiny_and_refitted_trees_pass_the_index_checks(rc):
     c = rc.rc_bvh_validate(bvh.h)
     assert sum(v for k, v in c.items() if k != "nodes_seen") == 0, c
     bvh.close()
+
+
+def test_translation_by_an_exact_offset(rc):
+    # the pocket block's vertices lie on a dyadic grid, so adding (64, -32, 128)
+    # is exact; the cast of the translated part from the translated centroids
+    # must agree with the original: only the origin offset is rounded at a
+    # different magnitude, which may move a grazing ray across an edge
+    V, F = synth.pocket_block(3)
+    off = np.array([64.0, -32.0, 128.0], np.float32)
+    Vt = (V + off).astype(np.float32)
+    assert np.array_equal((Vt - off).astype(np.float32), V)
+    p = rc.rc_params_default(n_dirs=256)
+    P, Nn, _, _ = oracle.sample_centroid(V, F)
+    Pt, Nt, _, _ = oracle.sample_centroid(Vt, F)
+    assert np.array_equal(Nt, Nn)
+    b0 = _build(rc, V, F)
+    b1 = _build(rc, Vt, F)
+    g0, c0, _ = gpu_cast(rc, b0.h, P, Nn, p)
+    g1, c1, _ = gpu_cast(rc, b1.h, Pt, Nt, p)
+    same = np.unpackbits(g0.view(np.uint8)) == np.unpackbits(g1.view(np.uint8))
+    assert same.mean() > 0.999
+    assert abs(c0.sum() - c1.sum()) <= 1e-3 * c0.sum()
+    b0.close()
+    b1.close()
