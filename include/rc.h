@@ -434,10 +434,10 @@ typedef struct {
  *   h_class [n] are host arrays and may each be NULL; h_out receives the
  *   part-level result.
  * Device memory is allocated on `stream` and released before returning.
- * With p->always_setups the orthogonal cast runs on a second stream of the
- * calling thread beside the hemispherical cast, and the bits and counts are
- * copied back on a third while the reduction and the setups run; both join
- * before the call returns.
+ * Requested bits and counts are copied back on a second stream of the
+ * calling thread while the reduction and the setups run; with
+ * p->always_setups the orthogonal cast runs on a third beside the
+ * hemispherical cast.  Both join before the call returns.
  * Synchronises `stream`.  Errors: as the individual calls. */
 rc_status rc_analyze_part(const float* h_V, int64_t nV, const int32_t* h_F, int64_t T, int64_t n,
                           const rc_params* p, uint32_t* h_bits, int32_t* h_count, uint8_t* h_mask,
