@@ -283,38 +283,23 @@ def variability(bits, Nrm, N, conc_mode=0):
     return M, ac, dom, conc, cnt
 
 
-def quantised_weights(weight):
-    """Fixed-point weights for the part-level average: 1 for unit weights,
-    else llround(w / max(w) * 2^24)."""
-    w = np.asarray(weight, np.float64)
-    if len(w) == 0 or np.all(w == 1.0):
-        return np.ones(len(w), np.int64)
-    wmax = w.max()
-    return np.array([int(round_half_away(x / wmax * 16777216.0)) for x in w], np.int64)
-
-
-def round_half_away(x):
-    """C llround: nearest integer, halves away from zero."""
-    import math
-    return math.floor(x + 0.5) if x >= 0 else -math.floor(-x + 0.5)
-
-
-def summary(cnt, dom, conc, N, weight=None, dir_bits=None):
+def summary(cnt, dom, conc, N, weight=None):
     """Part-level indicators (Sections 3.1 and 3.3).
 
-    - overall accessibility: sum w_i count_i / (N sum w_i) with the
-      fixed-point weights of :func:`quantised_weights` (area-weighted score
-      of Section 3.1; equals the plain mean for unit weights);
+    - overall accessibility: the area-weighted mean of the per-point
+      unobstructed fractions, sum w_i count_i / (N sum w_i), in FP64 with
+      no quantisation (Section 3.1's area-weighted score; unit weights give
+      the plain mean over the points);
     - dominant-axis distribution: share of points with count > 0 whose
       dominant axis is x, y, z (sums to 1);
     - mean axis concentration over the same points, summed as
       round(conc_i * 2^40) in integers."""
     cnt = np.asarray(cnt, np.int64)
     n = len(cnt)
-    wq = quantised_weights(np.ones(n) if weight is None else weight)
-    num = int((wq * cnt).sum())
-    den = int(wq.sum()) * N
-    overall = float(num) / float(den) if den else 0.0
+    w = np.ones(n, np.float64) if weight is None else np.asarray(weight, np.float64)
+    num = float(np.sum(w * cnt.astype(np.float64)))
+    den = float(np.sum(w)) * N
+    overall = num / den if den else 0.0
     ok = cnt > 0
     nc = int(ok.sum())
     share = [float(int((dom[ok] == k).sum())) / nc if nc else 0.0 for k in range(3)]

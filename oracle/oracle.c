@@ -23,7 +23,7 @@
  * implementing the same definitions separately, produces the same bits.
  * Build with -ffp-contract=off: no operation may be fused.
  *
- * Readings where the paper is silent (each also listed in the design notes):
+ * Readings where the paper is silent:
  *   R1 normal orientation: right-hand rule on the stored winding.
  *   R2 direction set: Fibonacci hemisphere z_j = 1-(j+1/2)/N,
  *      phi_j = j*pi*(3-sqrt5), r_j = sqrt(1-z_j^2), in FP64, rounded to fp32.

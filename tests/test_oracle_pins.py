@@ -294,6 +294,53 @@ def test_pocket_block_matches_exact_visibility(orc):
     assert n_cmp > 5000 and n_amb <= 3
 
 
+def test_area_weighted_accessibility_equals_exact_rational(orc):
+    """Section 3.1's area-weighted overall accessibility, pinned on the
+    pocket block in the paper's centroid mode: every face is axis-aligned,
+    so its exact area is |(B-A) x (C-A)| / 2 with one non-zero component,
+    and every ray's visibility is the exact rational test through the
+    opening.  The weighted mean sum A_f c_f / (N sum A_f) is then an exact
+    rational number; the oracle's summary must give it in FP64, and its
+    whole chain (cast + summary) within the 1e-4 accessibility bar.  The
+    unweighted mean and the n*N denominator both miss it by far, so
+    ignoring the weights or the weight sum fails here."""
+    V, F = synth.pocket_block(2)
+    N = 64
+    P, Nn, fc, w = orc.sample_centroid(V, F)
+    O = orc.ray_origins(P, Nn, 1e-4)
+    rect = ((35.0, 65.0), (15.0, 45.0))
+    Vq = [[Fraction(float(x)) for x in v] for v in V]
+    areas, counts = [], []
+    for f in range(len(F)):
+        A, B, C = (Vq[int(k)] for k in F[f])
+        c = _cross(_sub(B, A), _sub(C, A))
+        nz = [x for x in c if x != 0]
+        assert len(nz) == 1
+        areas.append(abs(nz[0]) / 2)
+        assert abs(float(areas[-1]) - w[f]) <= 1e-12 * float(areas[-1])
+        x, y, z = (float(t) for t in P[f])
+        if not (25.0 <= z < 40.0 and 35.0 <= x <= 65.0 and 15.0 <= y <= 45.0):
+            counts.append(N)
+            continue
+        D = orc.ray_dirs(Nn[f], N)
+        ex = [_pocket_expected(O[f], D[j], rect, 40.0) for j in range(N)]
+        assert all(e is not None for e in ex)
+        counts.append(sum(1 for e in ex if e))
+    cnt = np.array(counts, np.int64)
+    assert 0 < (cnt < N).sum() < len(F)
+    exact = sum(a * c for a, c in zip(areas, counts)) / (N * sum(areas))
+    zero = np.zeros(len(F))
+    s = orc.summary(cnt, np.zeros(len(F), np.int8), zero, N, weight=w)
+    assert abs(s["overall_access"] - float(exact)) <= 1e-12
+    # the pin discriminates: no weights, or n*N as the denominator
+    assert abs(float(Fraction(int(cnt.sum()), N * len(F))) - float(exact)) > 1e-2
+    assert abs(float(sum(a * c for a, c in zip(areas, counts)) / (N * len(F))) - float(exact)) > 1e-2
+    # the oracle's own chain: its cast's counts through the same summary
+    _, amb, ocnt = orc.Mesh(V, F).hemisphere(P, Nn, N)
+    so = orc.summary(ocnt, np.zeros(len(F), np.int8), zero, N, weight=w)
+    assert abs(so["overall_access"] - float(exact)) <= 1e-4
+
+
 def test_pocket_floor_centre_cone_fraction(orc):
     """Floor centre of a square pocket of width w and depth D: the visible
     cone has solid angle 4*asin(w^2/(w^2+4D^2)) (the square-pyramid
