@@ -98,7 +98,7 @@ typedef struct {
 
 /* Part-level indicators (Sections 3.1 and 3.3). */
 typedef struct {
-    double overall_access;            /* sum w_i count_i / (N sum w_i), w in 2^-24 fixed point of max w */
+    double overall_access;            /* sum w_i count_i / (N sum w_i) (Section 3.1's area-weighted score) */
     double overall_access_unweighted; /* sum count_i / (N n) */
     double axis_share[3];             /* fraction of counted points whose dominant axis is x, y, z */
     double mean_conc;                 /* mean axis concentration over counted points */
@@ -107,8 +107,8 @@ typedef struct {
     int64_t n_zero_visible;           /* n - n_counted */
     int64_t dom_count[3];             /* counted points per dominant axis */
     int64_t count_sum;                /* sum of unobstructed counts */
-    int64_t weighted_count_q;         /* sum wq_i * count_i (fixed-point weights) */
-    int64_t weight_sum_q;             /* sum wq_i */
+    double weighted_count;            /* sum w_i count_i, FP64 in a fixed order (= count_sum for unit weights) */
+    double weight_sum;                /* sum w_i, FP64 in a fixed order (= n for unit weights) */
     int64_t conc_sum_q;               /* sum llrint(conc_i * 2^40) over counted points */
 } rc_summary;
 
@@ -275,10 +275,14 @@ rc_status rc_hemisphere_cast(rc_bvh h, const float* d_P, const float* d_N, int64
  *   d_bits [n][W], d_N [n][3]; d_weight [n] (NULL = unit weights);
  *   outputs (each may be NULL): d_acc [n] float32, d_dom [n] int8,
  *   d_conc [n] float32, d_dir_area [N] double (sum over points of weight
- *   times visibility of direction j, weights in 2^-24 fixed point of max w);
- *   h_summary (host, may be NULL).
+ *   times visibility of direction j: exact for unit weights; with real
+ *   weights FP64 sums whose order of addition is not fixed); h_summary
+ *   (host, may be NULL).  The part-level weighted sums are FP64 sums in a
+ *   fixed order (per point, per warp, per block, then over the blocks), so
+ *   the summary is the same on every run; it differs from the exact
+ *   weighted mean by a relative error of order 1e-15.
  * Synchronises `stream` when h_summary is not NULL.  Errors: RC_E_ARG,
- * RC_E_UNSUPPORTED (non-unit weights with n > 2^21), RC_E_CUDA. */
+ * RC_E_CUDA. */
 rc_status rc_direction_variability(const uint32_t* d_bits, const float* d_N,
                                    const double* d_weight, int64_t n, const rc_params* p,
                                    float* d_acc, int8_t* d_dom, float* d_conc, double* d_dir_area,
@@ -292,18 +296,22 @@ rc_status rc_direction_variability(const uint32_t* d_bits, const float* d_N,
  * where a cudaMalloc/cudaMallocAsync inside the call would fail or break
  * the caller's accounting.  The call performs no device or host heap
  * allocation (no cudaMalloc, cudaFree or allocating library routine).
- * Its scratch -- the part-level sums, the per-direction counters and the
- * direction table -- lives in one static device array of 196,864 bytes,
- * which every GPU that loads the library holds until the process exits;
- * hence p->n_dirs is limited to 8192 (larger values return
- * RC_E_UNSUPPORTED).  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress, with that device current) and
- * uploads the direction table, so make that first call before any stream
- * capture.  The counters are cleared on `stream` at every call.  All calls
- * on a device share the array and it keeps the last call's contents, so
- * calls whose work overlaps on the GPU (other streams, other host threads)
- * race with each other; serialise them.  Arguments, outputs, limits on
- * weighted inputs, synchronisation and errors are as for
+ * Its scratch -- the part-level sums, the per-block weighted partials and
+ * the direction table -- lives in one static device array of 164,096
+ * bytes, which every GPU that loads the library holds until the process
+ * exits; hence p->n_dirs is limited to 8192 (larger values up to 65536
+ * return RC_E_UNSUPPORTED).  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current)
+ * and uploads the direction table, so make that first call before any
+ * stream capture.  The array holds one direction table: a call whose
+ * n_dirs differs from the last upload's on that device uploads its own
+ * table from host memory on `stream` (refused with RC_E_UNSUPPORTED while
+ * `stream` is being captured), and work already queued reads whichever
+ * table the array holds when it runs.  The sums are cleared on `stream` at
+ * every call.  All calls on a device share the array and it keeps the last
+ * call's contents, so calls whose work overlaps on the GPU (other streams,
+ * other host threads) race with each other; serialise them.  Arguments,
+ * outputs, synchronisation and errors are otherwise as for
  * rc_direction_variability. */
 rc_status rc_direction_variability_noalloc(const uint32_t* d_bits, const float* d_N,
                                            const double* d_weight, int64_t n, const rc_params* p,
@@ -346,7 +354,7 @@ rc_status rc_orthogonal_cast(rc_bvh h, const float* d_P, const float* d_N, int64
  * (n.a >= -parallel_tol) and none of those rays is obstructed.  With r = 0
  * and ring_rays = 0 this is the mask of rc_orthogonal_cast.
  *   d_P, d_N [n][3]; d_mask [n] uint8 (written); d_counters int64[4] as
- *   for rc_orthogonal_cast (may be NULL).  Synchronises `stream`.
+ *   for rc_orthogonal_cast (may be NULL).  Asynchronous.
  * Errors: RC_E_ARG (tool_radius outside [0, 1e4] mm, ring_rays outside
  * [0, 64]), RC_E_CUDA. */
 rc_status rc_tool_cast(rc_bvh h, const float* d_P, const float* d_N, int64_t n, const rc_params* p,
@@ -377,15 +385,19 @@ typedef struct rc_batch_s* rc_batch;
 /* Create an empty batch for the hemispherical cast of many parts with the
  * parameters *p (copied).  The paper casts one part at a time; a batch puts
  * the points of all its parts on one ray-work queue and casts them in one
- * persistent launch, replayed from a CUDA graph.  Errors: RC_E_ARG,
- * RC_E_CUDA. */
-rc_status rc_batch_create(const rc_params* p, rc_batch* out);
+ * persistent launch, replayed from a CUDA graph.  hbm_budget_bytes (0 = no
+ * limit) bounds the device bytes of the parts the batch admits (see
+ * rc_batch_add_part).  Errors: RC_E_ARG, RC_E_CUDA. */
+rc_status rc_batch_create(const rc_params* p, int64_t hbm_budget_bytes, rc_batch* out);
 
 /* Add a part: its handle and the device arrays of rc_hemisphere_cast
  * (points, normals, n, bits, counts, counters int64[4] or NULL).  The batch
  * keeps these pointers until rc_batch_clear/rc_batch_destroy: they must stay
- * valid.  *part_id (may be NULL) receives the part's index.  Errors:
- * RC_E_ARG. */
+ * valid.  *part_id (may be NULL) receives the part's index.  The part's
+ * device bytes -- 12 nV + 260 T for its handle plus n (32 + 4 W) for its
+ * points, normals, bits, counts and the batch's point order, W =
+ * ceil(n_dirs / 32) -- count against the batch's budget.  Errors: RC_E_ARG,
+ * RC_E_OOM (the part would exceed the budget; it is not added). */
 rc_status rc_batch_add_part(rc_batch b, rc_bvh h, const float* d_P, const float* d_N, int64_t n,
                             uint32_t* d_bits, int32_t* d_count, int64_t* d_counters, int64_t* part_id);
 
@@ -402,6 +414,12 @@ rc_status rc_batch_set_params(rc_batch b, const rc_params* p);
  * exactly those of rc_hemisphere_cast.  Asynchronous after the first
  * launch.  Errors: RC_E_ARG, RC_E_CUDA. */
 rc_status rc_batch_launch(rc_batch b, void* stream);
+
+/* *done = 1 once the work of the most recent rc_batch_launch (every part of
+ * the batch, part_id included) has completed on the device, 0 while it is
+ * still running or before the first launch.  Never blocks.  Errors:
+ * RC_E_ARG (part_id outside the batch), RC_E_CUDA (the launch failed). */
+rc_status rc_batch_poll(rc_batch b, int64_t part_id, int32_t* done);
 
 /* Autotuner: time the batch under every combination of point order (Morton
  * / index), direction order (tiles / index), resident blocks per SM (4, 6,
@@ -512,11 +530,14 @@ rc_status rc_server_submit(rc_server s, uint64_t part_key, const float* h_V, int
  * queued; the request stays known), RC_E_ARG (unknown id). */
 rc_status rc_server_wait(rc_server s, int64_t req_id, double timeout_s, rc_request_result* out);
 
-/* Copy a resident part's visibility bits [n][W] and counts [n] to host
- * arrays (either may be NULL).  A part in use is read once it is idle
- * again (waiting at most 60 s).  Errors: RC_E_ARG (not resident, or n
- * differs), RC_E_TIMEOUT. */
-rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, int32_t* h_count, int64_t n);
+/* Copy a resident part's visibility bits [n][W], W = ceil(n_dirs / 32),
+ * and counts [n] to host arrays (either may be NULL).  bits_words is the
+ * capacity of h_bits in uint32 words and must be at least n * W.  A part
+ * in use is read once it is idle again (waiting at most 60 s).
+ * Errors: RC_E_ARG (not resident, n differs, h_bits too small),
+ * RC_E_TIMEOUT. */
+rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, int64_t bits_words,
+                              int32_t* h_count, int64_t n);
 
 /* Counters of the server (host struct). */
 rc_status rc_server_get_stats(rc_server s, rc_server_stats* out);

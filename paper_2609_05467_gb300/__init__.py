@@ -26,7 +26,7 @@ __all__ = [
     "rc_direction_variability_noalloc",
     "rc_classify", "rc_orthogonal_cast", "rc_min_setups", "rc_setup_cover", "rc_analyze_part",
     "rc_launch_count", "rc_stream_status", "rc_bvh_validate", "Bvh", "PartResult", "rc_batch_create", "rc_batch_add_part", "rc_batch_clear",
-    "rc_batch_set_params", "rc_batch_launch", "rc_batch_autotune", "rc_batch_destroy", "rc_server_create",
+    "rc_batch_set_params", "rc_batch_launch", "rc_batch_poll", "rc_batch_autotune", "rc_batch_destroy", "rc_server_create",
     "rc_server_submit", "rc_server_wait", "rc_server_read_bits", "rc_server_get_stats", "rc_server_destroy",
 ]
 
@@ -62,8 +62,8 @@ class Summary(ctypes.Structure):
         ("overall_access", ctypes.c_double), ("overall_access_unweighted", ctypes.c_double),
         ("axis_share", ctypes.c_double * 3), ("mean_conc", ctypes.c_double),
         ("n_points", ctypes.c_int64), ("n_counted", ctypes.c_int64), ("n_zero_visible", ctypes.c_int64),
-        ("dom_count", ctypes.c_int64 * 3), ("count_sum", ctypes.c_int64), ("weighted_count_q", ctypes.c_int64),
-        ("weight_sum_q", ctypes.c_int64), ("conc_sum_q", ctypes.c_int64),
+        ("dom_count", ctypes.c_int64 * 3), ("count_sum", ctypes.c_int64), ("weighted_count", ctypes.c_double),
+        ("weight_sum", ctypes.c_double), ("conc_sum_q", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -180,7 +180,8 @@ def load(build_if_missing=True):
             "rc_orthogonal_cast": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P], st),
             "rc_min_setups": ([P, P, P, P, i64, ctypes.POINTER(Params), P, ctypes.POINTER(Setups), P], st),
             "rc_setup_cover": ([P, ctypes.POINTER(Setups)], st),
-            "rc_batch_create": ([ctypes.POINTER(Params), ctypes.POINTER(P)], st),
+            "rc_batch_create": ([ctypes.POINTER(Params), i64, ctypes.POINTER(P)], st),
+            "rc_batch_poll": ([P, i64, ctypes.POINTER(i32)], st),
             "rc_batch_add_part": ([P, P, P, P, i64, P, P, P, ctypes.POINTER(i64)], st),
             "rc_batch_clear": ([P], st),
             "rc_batch_set_params": ([P, ctypes.POINTER(Params)], st),
@@ -190,7 +191,7 @@ def load(build_if_missing=True):
             "rc_server_create": ([ctypes.POINTER(Params), ctypes.POINTER(ServerConfig), ctypes.POINTER(P)], st),
             "rc_server_submit": ([P, ctypes.c_uint64, P, i64, P, i64, i64, ctypes.POINTER(i64)], st),
             "rc_server_wait": ([P, i64, ctypes.c_double, ctypes.POINTER(RequestResult)], st),
-            "rc_server_read_bits": ([P, ctypes.c_uint64, P, P, i64], st),
+            "rc_server_read_bits": ([P, ctypes.c_uint64, P, i64, P, i64], st),
             "rc_server_get_stats": ([P, ctypes.POINTER(ServerStats)], st),
             "rc_server_destroy": ([P], st),
             "rc_analyze_part": ([P, i64, P, i64, i64, ctypes.POINTER(Params), P, P, P, P,
@@ -456,10 +457,17 @@ def rc_analyze_part(V, F, n, params, bits=None, count=None, mask=None, cls=None,
     return out
 
 
-def rc_batch_create(params):
+def rc_batch_create(params, hbm_budget_bytes=0):
     b = ctypes.c_void_p()
-    _check(load().rc_batch_create(ctypes.byref(params), ctypes.byref(b)))
+    _check(load().rc_batch_create(ctypes.byref(params), int(hbm_budget_bytes), ctypes.byref(b)))
     return b.value
+
+
+def rc_batch_poll(b, part_id):
+    """1 once the last launch of the batch (this part included) has completed, else 0."""
+    done = ctypes.c_int32()
+    _check(load().rc_batch_poll(ctypes.c_void_p(b), int(part_id), ctypes.byref(done)))
+    return done.value
 
 
 def rc_batch_add_part(b, h, P, N, bits, count, counters=None):
@@ -518,9 +526,10 @@ def rc_server_wait(s, req_id, timeout_s=60.0):
 
 def rc_server_read_bits(s, part_key, n, n_dirs):
     import numpy as np
-    bits = np.zeros((n, n_dirs // 32), np.uint32)
+    bits = np.zeros((n, (n_dirs + 31) // 32), np.uint32)
     cnt = np.zeros(n, np.int32)
-    _check(load().rc_server_read_bits(ctypes.c_void_p(s), ctypes.c_uint64(part_key), _hptr(bits), _hptr(cnt), n))
+    _check(load().rc_server_read_bits(ctypes.c_void_p(s), ctypes.c_uint64(part_key), _hptr(bits), bits.size,
+                                      _hptr(cnt), n))
     return bits, cnt
 
 

@@ -26,9 +26,6 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
 rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
                             uint8_t* mask, float* travel, unsigned long long* counters, cudaStream_t s);
 rc_status frame_setup(rc_bvh h, const rc_params* p, FrameDev* d, cudaStream_t s);
-rc_status launch_variability(const uint32_t* bits, const float* N, const double* weight, int64_t n,
-                             const float4* dirs, const rc_params* p, float* acc, int8_t* dom, float* conc,
-                             double* dir_area, unsigned long long* scratch, cudaStream_t s);
 rc_status launch_classes(rc_bvh h, const uint8_t* mask, const float* travel, const int32_t* face, int64_t n,
                          const rc_params* p, uint8_t* cls, const double* frame_d, const double* fbox_d,
                          uint8_t* fixture, unsigned long long* hist, cudaStream_t s);
@@ -399,42 +396,22 @@ rc_status rc_direction_variability(const uint32_t* d_bits, const float* d_N, con
     if (st != RC_OK) return st;
     if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
     if (n > 0 && (!d_bits || !d_N)) return set_error(RC_E_ARG, "bits or normals pointer is NULL");
-    if (d_weight && n > (1LL << 21))
-        return set_error(RC_E_UNSUPPORTED, "weighted summaries support at most 2^21 points");
     cudaStream_t s = (cudaStream_t)stream;
     const float4* dirs = nullptr;
     if ((st = device_dirs(p->n_dirs, &dirs)) != RC_OK) return st;
-    const size_t words = 8 + 1 + (size_t)p->n_dirs;
-    unsigned long long* scratch = nullptr;
-    RC_CUDA(cudaMallocAsync(&scratch, sizeof(unsigned long long) * words, s));
-    RC_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * words, s));
+    void* scratch = nullptr;
+    RC_CUDA(cudaMallocAsync(&scratch, kVarScratchBytes, s));
     st = launch_variability(d_bits, d_N, d_weight, n, dirs, p, d_acc, d_dom, d_conc, d_dir_area, scratch, s);
     if (st != RC_OK) { cudaFreeAsync(scratch, s); return st; }
-    long long sums[8] = {0};
+    unsigned char back[kVarPartOffset];
     if (h_summary) {
-        RC_CUDA(cudaMemcpyAsync(sums, scratch, sizeof sums, cudaMemcpyDeviceToHost, s));
+        RC_CUDA(cudaMemcpyAsync(back, scratch, sizeof back, cudaMemcpyDeviceToHost, s));
     }
     RC_CUDA(cudaFreeAsync(scratch, s));
     if (!h_summary) return RC_OK;
     RC_CUDA(cudaStreamSynchronize(s));
-    rc_summary& o = *h_summary;
-    memset(&o, 0, sizeof o);
-    const long long counted = sums[0];
-    o.n_points = n;
-    o.n_counted = counted;
-    o.n_zero_visible = n - counted;
-    for (int k = 0; k < 3; ++k) {
-        o.dom_count[k] = sums[1 + k];
-        o.axis_share[k] = counted ? (double)sums[1 + k] / (double)counted : 0.0;
-    }
-    o.count_sum = sums[4];
-    o.weighted_count_q = sums[5];
-    o.weight_sum_q = sums[6];
-    o.conc_sum_q = sums[7];
-    const long long den = sums[6] * (long long)p->n_dirs;
-    o.overall_access = den ? (double)sums[5] / (double)den : 0.0;
-    o.overall_access_unweighted = n ? (double)sums[4] / ((double)n * (double)p->n_dirs) : 0.0;
-    o.mean_conc = counted ? (double)sums[7] / (1099511627776.0 * (double)counted) : 0.0;
+    fill_summary((const long long*)back, (const double*)(back + kVarWsumOffset), n, p->n_dirs, d_weight != nullptr,
+                 h_summary);
     return RC_OK;
 }
 

@@ -34,7 +34,12 @@ struct HostPart {
 struct rc_batch_s {
     rc_params p;
     int device = 0;
+    int64_t budget = 0;            // admission budget in device bytes (0 = none)
+    int64_t used = 0;              // device bytes of the parts admitted so far
     std::vector<rc::HostPart> parts;
+    std::vector<int64_t> part_bytes;
+    cudaEvent_t done = nullptr;    // recorded after the last launch's work
+    bool launched = false;
     rc::BatchPart* d_parts = nullptr;
     unsigned long long* d_work = nullptr;
     int cap = 0;
@@ -119,19 +124,23 @@ static rc_status prepare(rc_batch b, cudaStream_t s)
 
 extern "C" {
 
-rc_status rc_batch_create(const rc_params* p, rc_batch* out)
+rc_status rc_batch_create(const rc_params* p, int64_t hbm_budget_bytes, rc_batch* out)
 {
     RC_RANGE();
     if (!out) return set_error(RC_E_ARG, "out is NULL");
     *out = nullptr;
     rc_status st = check_params_public(p);
     if (st != RC_OK) return st;
+    if (hbm_budget_bytes < 0) return set_error(RC_E_ARG, "hbm_budget_bytes must be >= 0");
     rc_batch b = new rc_batch_s();
     b->p = *p;
+    b->budget = hbm_budget_bytes;
     if (cudaGetDevice(&b->device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&b->d_work, sizeof(unsigned long long)) != cudaSuccess) {
         if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+        if (b->done) cudaEventDestroy(b->done);
         delete b;
         return set_error(RC_E_CUDA, "batch set-up failed");
     }
@@ -147,6 +156,13 @@ rc_status rc_batch_add_part(rc_batch b, rc_bvh h, const float* d_P, const float*
     if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
     if (n > 0 && (!d_P || !d_N || !d_bits || !d_count)) return set_error(RC_E_ARG, "array pointer is NULL");
     if (h->device != b->device) return set_error(RC_E_ARG, "handle and batch are on different devices");
+    // the part's device bytes: its handle (vertices, faces, trees, face
+    // data), its caller-owned points, normals, bits and counts, and the
+    // batch's own point order
+    const int64_t W = (b->p.n_dirs + 31) / 32;
+    const int64_t bytes = 12 * h->nV + 260 * h->T + n * (24 + 4 * W + 4 + 4) + 64;
+    if (b->budget > 0 && b->used + bytes > b->budget)
+        return set_error(RC_E_OOM, "the part does not fit into the batch's HBM budget");
     HostPart q;
     q.h = h;
     q.P = d_P;
@@ -156,6 +172,8 @@ rc_status rc_batch_add_part(rc_batch b, rc_bvh h, const float* d_P, const float*
     q.count = d_count;
     q.counters = d_counters;
     b->parts.push_back(q);
+    b->part_bytes.push_back(bytes);
+    b->used += bytes;
     b->dirty = true;
     if (part_id) *part_id = (int64_t)b->parts.size() - 1;
     return RC_OK;
@@ -168,6 +186,9 @@ rc_status rc_batch_clear(rc_batch b)
     for (HostPart& q : b->parts)
         if (q.order) cudaFree(q.order);
     b->parts.clear();
+    b->part_bytes.clear();
+    b->used = 0;
+    b->launched = false;
     drop_graph(b);
     b->dirty = true;
     return RC_OK;
@@ -196,6 +217,22 @@ rc_status rc_batch_launch(rc_batch b, void* stream)
     if (!b->exec) return RC_OK;   // no parts
     RC_CUDA(cudaGraphLaunch(b->exec, s));
     count_launch();
+    RC_CUDA(cudaEventRecord(b->done, s));
+    b->launched = true;
+    return RC_OK;
+}
+
+rc_status rc_batch_poll(rc_batch b, int64_t part_id, int32_t* done)
+{
+    RC_RANGE();
+    if (!b || !done) return set_error(RC_E_ARG, "batch or done is NULL");
+    if (part_id < 0 || part_id >= (int64_t)b->parts.size()) return set_error(RC_E_ARG, "part_id out of range");
+    *done = 0;
+    if (!b->launched) return RC_OK;
+    const cudaError_t e = cudaEventQuery(b->done);
+    if (e == cudaErrorNotReady) return RC_OK;
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventQuery");
+    *done = 1;
     return RC_OK;
 }
 
@@ -252,6 +289,7 @@ rc_status rc_batch_destroy(rc_batch b)
     if (b->d_parts) cudaFree(b->d_parts);
     if (b->d_work) cudaFree(b->d_work);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->done) cudaEventDestroy(b->done);
     delete b;
     return RC_OK;
 }

@@ -18,15 +18,14 @@
 
 namespace rc {
 
-rc_status launch_variability(const uint32_t* bits, const float* N, const double* weight, int64_t n,
-                             const float4* dirs, const rc_params* p, float* acc, int8_t* dom, float* conc,
-                             double* dir_area, unsigned long long* scratch, cudaStream_t s);
-rc_status set_error(rc_status st, const std::string& msg);
+rc_status check_params_public(const rc_params* p);
 
-// Layout: [ 9 + kNoAllocMaxDirs uint64 accumulators | kNoAllocMaxDirs float4 directions ]
+// Layout: [ the reduction's scratch (kVarScratchBytes, rounded up to 256) |
+//           32 * ceil(kNoAllocMaxDirs / 32) float4 directions ]
 constexpr int kNoAllocMaxDirs = 8192;
-constexpr size_t kNoAllocAccBytes = ((9 + (size_t)kNoAllocMaxDirs) * 8 + 255) / 256 * 256;
-constexpr size_t kNoAllocBytes = kNoAllocAccBytes + (size_t)kNoAllocMaxDirs * 16;   // 196,864 bytes
+constexpr size_t kNoAllocAccBytes = (kVarScratchBytes + 255) / 256 * 256;
+constexpr size_t kNoAllocBytes = kNoAllocAccBytes + (size_t)kNoAllocMaxDirs * 16;   // 164,096 bytes
+static_assert(kNoAllocBytes == 164096, "size stated in rc.h");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -52,16 +51,13 @@ extern "C" rc_status rc_direction_variability_noalloc(const uint32_t* d_bits, co
                                                       double* d_dir_area, rc_summary* h_summary, void* stream)
 {
     RC_RANGE();
-    if (!p) return set_error(RC_E_ARG, "params is NULL");
-    if (p->n_dirs < 1) return set_error(RC_E_ARG, "n_dirs must be >= 1");
+    rc_status st = check_params_public(p);
+    if (st != RC_OK) return st;
     if (p->n_dirs > kNoAllocMaxDirs)
         return set_error(RC_E_UNSUPPORTED, "rc_direction_variability_noalloc supports at most 8192 directions "
-                                           "(its static scratch is 196,864 bytes per device)");
-    if (p->conc_mode != 0 && p->conc_mode != 1) return set_error(RC_E_ARG, "conc_mode must be 0 or 1");
+                                           "(its static scratch is 164,096 bytes per device)");
     if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
     if (n > 0 && (!d_bits || !d_N)) return set_error(RC_E_ARG, "bits or normals pointer is NULL");
-    if (d_weight && n > (1LL << 21))
-        return set_error(RC_E_UNSUPPORTED, "weighted summaries support at most 2^21 points");
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0;
     RC_CUDA(cudaGetDevice(&dev));
@@ -76,41 +72,41 @@ extern "C" rc_status rc_direction_variability_noalloc(const uint32_t* d_bits, co
         RC_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
         d.base = (unsigned char*)ptr;
     }
-    unsigned long long* acc = (unsigned long long*)d.base;
+    void* acc = d.base;
     float4* dirs = (float4*)(d.base + kNoAllocAccBytes);
     if (d.dirs_n != p->n_dirs) {
-        rc_status st = rc_direction_table(p->n_dirs, g_noalloc_h3);
+        // the table is rewritten from host memory; a stream that is being
+        // captured would record that copy instead of running it now
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        RC_CUDA(cudaStreamIsCapturing(s, &cap));
+        if (cap != cudaStreamCaptureStatusNone)
+            return set_error(RC_E_UNSUPPORTED, "rc_direction_variability_noalloc: the direction table for this "
+                                               "n_dirs is uploaded by a call outside stream capture");
+        st = rc_direction_table(p->n_dirs, g_noalloc_h3);
         if (st != RC_OK) return st;
-        for (int32_t j = 0; j < p->n_dirs; ++j)
-            g_noalloc_h4[j] = make_float4(g_noalloc_h3[3 * j], g_noalloc_h3[3 * j + 1], g_noalloc_h3[3 * j + 2], 0.0f);
-        RC_CUDA(cudaMemcpyAsync(dirs, g_noalloc_h4, sizeof(float4) * p->n_dirs, cudaMemcpyHostToDevice, s));
-        d.dirs_n = p->n_dirs;
+        // as the allocating call's table: entry j carries index j in w, and
+        // the last tile is padded with entry 0's direction and index -1
+        const int32_t N = p->n_dirs, N32 = (N + 31) / 32 * 32;
+        float pad_w;
+        const int32_t minus1 = -1;
+        memcpy(&pad_w, &minus1, sizeof pad_w);
+        for (int32_t j = 0; j < N32; ++j) {
+            const int32_t k = j < N ? j : 0;
+            float w = pad_w;
+            if (j < N) memcpy(&w, &j, sizeof w);
+            g_noalloc_h4[j] = make_float4(g_noalloc_h3[3 * k], g_noalloc_h3[3 * k + 1], g_noalloc_h3[3 * k + 2], w);
+        }
+        RC_CUDA(cudaMemcpyAsync(dirs, g_noalloc_h4, sizeof(float4) * N32, cudaMemcpyHostToDevice, s));
+        d.dirs_n = N;
     }
-    // the sums, the max weight and the per-direction counters start at zero
-    RC_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (9 + (size_t)p->n_dirs), s));
-    rc_status st = launch_variability(d_bits, d_N, d_weight, n, dirs, p, d_acc, d_dom, d_conc, d_dir_area, acc, s);
+    // launch_variability clears the sums it accumulates into on `stream`
+    st = launch_variability(d_bits, d_N, d_weight, n, dirs, p, d_acc, d_dom, d_conc, d_dir_area, acc, s);
     if (st != RC_OK) return st;
     if (!h_summary) return RC_OK;
-    long long sums[8];
-    RC_CUDA(cudaMemcpyAsync(sums, acc, sizeof sums, cudaMemcpyDeviceToHost, s));
+    unsigned char back[kVarPartOffset];
+    RC_CUDA(cudaMemcpyAsync(back, acc, sizeof back, cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaStreamSynchronize(s));
-    rc_summary& o = *h_summary;
-    memset(&o, 0, sizeof o);
-    const long long counted = sums[0];
-    o.n_points = n;
-    o.n_counted = counted;
-    o.n_zero_visible = n - counted;
-    for (int k = 0; k < 3; ++k) {
-        o.dom_count[k] = sums[1 + k];
-        o.axis_share[k] = counted ? (double)sums[1 + k] / (double)counted : 0.0;
-    }
-    o.count_sum = sums[4];
-    o.weighted_count_q = sums[5];
-    o.weight_sum_q = sums[6];
-    o.conc_sum_q = sums[7];
-    const long long den = sums[6] * (long long)p->n_dirs;
-    o.overall_access = den ? (double)sums[5] / (double)den : 0.0;
-    o.overall_access_unweighted = n ? (double)sums[4] / ((double)n * (double)p->n_dirs) : 0.0;
-    o.mean_conc = counted ? (double)sums[7] / (1099511627776.0 * (double)counted) : 0.0;
+    fill_summary((const long long*)back, (const double*)(back + kVarWsumOffset), n, p->n_dirs, d_weight != nullptr,
+                 h_summary);
     return RC_OK;
 }

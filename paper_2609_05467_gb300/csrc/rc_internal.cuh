@@ -44,6 +44,15 @@ constexpr int kStack4 = 96;        // 4-wide traversal stack entries (>= 3 * wid
 constexpr double kTau = 1e-9;      // relative ambiguity band of the occlusion test
 constexpr int kMaxDirs = 65536;
 
+// scratch of the variability reduction: kVarSums int64 sums, then the two
+// FP64 weighted sums, then the per-block FP64 partials (two rows of
+// kVarMaxBlocks); no per-direction scratch
+constexpr int kVarSums = 8;
+constexpr int kVarMaxBlocks = 2048;
+constexpr size_t kVarWsumOffset = 8 * kVarSums;
+constexpr size_t kVarPartOffset = kVarWsumOffset + 64;
+constexpr size_t kVarScratchBytes = kVarPartOffset + 2 * sizeof(double) * kVarMaxBlocks;   // 32,896 bytes
+
 // ---------------------------------------------------------------------------
 // handle
 // ---------------------------------------------------------------------------
@@ -85,6 +94,16 @@ struct BatchPart {
     int max_steps;
     float scene_maxabs;
 };
+
+// variability reduction (reduce.cu): queues the kernels on s; `scratch` is
+// kVarScratchBytes of device memory (cleared here)
+rc_status launch_variability(const uint32_t* bits, const float* N, const double* weight, int64_t n,
+                             const float4* dirs, const rc_params* p, float* acc, int8_t* dom, float* conc,
+                             double* dir_area, void* scratch, cudaStream_t s);
+// the part-level summary from the scratch's sums read back to the host
+// (sums: kVarSums int64; wsum: the two weighted FP64 sums)
+void fill_summary(const long long* sums, const double* wsum, int64_t n, int32_t n_dirs, bool weighted,
+                  rc_summary* out);
 
 }  // namespace rc
 

@@ -3,21 +3,19 @@
 // per-direction visible-area histogram, fixture faces and face classes with
 // the 64-bin histogram of reachable-axis masks for the setup cover.
 //
-// Every part-level sum is an int64 sum of fixed-point values, so results do
+// The counts, shares and concentrations are int64 sums of fixed-point
+// values, and the area-weighted sums are FP64 sums in a fixed order (per
+// warp, per block, then over the blocks by one warp), so the summary does
 // not depend on the order in which blocks finish.
 #include <math.h>
+#include <string.h>
 
 #include "rc_internal.cuh"
 
 namespace rc {
 
-enum { S_COUNTED = 0, S_DOM = 1, S_COUNT = 4, S_WCOUNT = 5, S_WSUM = 6, S_CONC = 7, S_N = 8 };
-
-__device__ __forceinline__ long long quant_weight(const double* w, int64_t i, double wmax)
-{
-    if (!w) return 1;
-    return llround(__dmul_rn(__ddiv_rn(w[i], wmax), 16777216.0));
-}
+enum { S_COUNTED = 0, S_DOM = 1, S_COUNT = 4, S_CONC = 5, S_N = 6 };
+static_assert(S_N <= kVarSums, "integer sums of the variability scratch");
 
 // round(x * 2^40) to nearest, ties to even, for an fp32 x with |x| < 8, in
 // fp32 arithmetic: x * 2^40 = hi * 2^22 + lo with hi = rint(x * 2^18) and
@@ -42,17 +40,18 @@ __device__ __forceinline__ void fixed40_split(float x, int& hi, int& lo)
 // words waits on memory once per 32 words instead of once per word.
 __global__ void __launch_bounds__(256)
 k_variability(const uint32_t* __restrict__ bits, const float* __restrict__ Nrm,
-              const double* __restrict__ weight, const double* __restrict__ wmax_p, int64_t n,
+              const double* __restrict__ weight, int64_t n,
               const float4* __restrict__ dirs, int n_dirs, int conc_mode, float* acc, int8_t* dom,
-              float* conc, unsigned long long* sums)
+              float* conc, unsigned long long* sums, double* wpart)
 {
     __shared__ long long blk[S_N];
+    __shared__ double wsh[2][8];
     if (threadIdx.x < S_N) blk[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int W = (n_dirs + 31) >> 5;
-    const double wmax = weight ? *wmax_p : 1.0;
-    long long loc[S_N] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long loc[S_N] = {0, 0, 0, 0, 0, 0};
+    double lwc = 0.0, lw = 0.0;   // lane 0: sum w_i count_i and sum w_i of the warp's points, in order
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
         const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
@@ -121,10 +120,12 @@ k_variability(const uint32_t* __restrict__ bits, const float* __restrict__ Nrm,
                 loc[S_DOM + dm] += 1;
                 loc[S_CONC] += llrint(__dmul_rn(cc, 1099511627776.0));
             }
-            const long long wq = quant_weight(weight, i, wmax);
             loc[S_COUNT] += cnt;
-            loc[S_WCOUNT] += wq * (long long)cnt;
-            loc[S_WSUM] += wq;
+            if (weight) {
+                const double wi = weight[i];
+                lwc = __dadd_rn(lwc, __dmul_rn(wi, (double)cnt));
+                lw = __dadd_rn(lw, wi);
+            }
             if (acc) acc[i] = __double2float_rn(__ddiv_rn((double)cnt, (double)n_dirs));
             if (dom) dom[i] = (int8_t)dm;
             if (conc) conc[i] = __double2float_rn(cc);
@@ -133,28 +134,56 @@ k_variability(const uint32_t* __restrict__ bits, const float* __restrict__ Nrm,
     if (lane == 0)
         for (int k = 0; k < S_N; ++k)
             if (loc[k]) atomicAdd((unsigned long long*)&blk[k], (unsigned long long)loc[k]);
+    if (weight && lane == 0) {
+        wsh[0][threadIdx.x >> 5] = lwc;
+        wsh[1][threadIdx.x >> 5] = lw;
+    }
     __syncthreads();
     if (threadIdx.x < S_N && blk[threadIdx.x])
         atomicAdd(&sums[threadIdx.x], (unsigned long long)blk[threadIdx.x]);
+    if (weight && threadIdx.x == 0) {
+        // the block's weighted sums, its warps in order; every block writes
+        // its slot (zero when it had no point)
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            a = __dadd_rn(a, wsh[0][k]);
+            b = __dadd_rn(b, wsh[1][k]);
+        }
+        wpart[blockIdx.x] = a;
+        wpart[kVarMaxBlocks + blockIdx.x] = b;
+    }
 }
 
-// max weight (weights >= 0) as ordered FP64 bits
-__global__ void k_wmax(const double* __restrict__ w, int64_t n, unsigned long long* out)
+// Sum of the blocks' weighted partials in a fixed order: lane l adds blocks
+// l, l + 32, ... in turn, then a fixed butterfly over the lanes.  One warp.
+__global__ void k_wsum_finish(const double* __restrict__ wpart, int nblocks, double* out /*[2]*/)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double m = 0.0;
-    for (; i < n; i += (int64_t)gridDim.x * blockDim.x) m = fmax(m, w[i]);
-    for (int off = 16; off; off >>= 1) m = fmax(m, __shfl_xor_sync(0xFFFFFFFFu, m, off));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+    const int lane = threadIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int k = lane; k < nblocks; k += 32) {
+        a = __dadd_rn(a, wpart[k]);
+        b = __dadd_rn(b, wpart[kVarMaxBlocks + k]);
+    }
+    for (int off = 16; off; off >>= 1) {
+        a = __dadd_rn(a, __shfl_xor_sync(0xFFFFFFFFu, a, off));
+        b = __dadd_rn(b, __shfl_xor_sync(0xFFFFFFFFu, b, off));
+    }
+    if (lane == 0) {
+        out[0] = a;
+        out[1] = b;
+    }
 }
 
-// Per-direction sums of quantised weights over points where the direction is
-// visible.  One warp per (word, chunk of points); lane = bit.
+// Per-direction visible weight: sum over points where direction j is
+// visible of w_i (1 for unit weights).  One warp per (word, chunk of
+// points), lane = bit; each warp adds its FP64 chunk sum atomically.  With
+// unit weights every sum is an integer below 2^53, so the result is exact
+// in any order; with real weights the order of the additions is not fixed
+// (relative differences of order 1e-16 between runs).
 constexpr int kDirChunk = 512;
 
-__global__ void k_dir_hist(const uint32_t* __restrict__ bits, int64_t n, int W,
-                           const double* __restrict__ weight, const double* __restrict__ wmax_p,
-                           unsigned long long* dirq)
+__global__ void k_dir_hist(const uint32_t* __restrict__ bits, int64_t n, int W, int n_dirs,
+                           const double* __restrict__ weight, double* dir_area)
 {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -162,24 +191,14 @@ __global__ void k_dir_hist(const uint32_t* __restrict__ bits, int64_t n, int W,
     if (wid >= nchunks * W) return;
     const int w = (int)(wid % W);
     const int64_t c = wid / W;
-    const double wmax = weight ? *wmax_p : 1.0;
-    long long s = 0;
+    double s = 0.0;
     const int64_t e = min64(n, (c + 1) * kDirChunk);
     for (int64_t i = c * kDirChunk; i < e; ++i) {
         const uint32_t word = __ldg(&bits[i * W + w]);
-        if ((word >> lane) & 1u) s += quant_weight(weight, i, wmax);
+        if ((word >> lane) & 1u) s = __dadd_rn(s, weight ? weight[i] : 1.0);
     }
-    if (s) atomicAdd(&dirq[32 * w + lane], (unsigned long long)s);
-}
-
-__global__ void k_dir_finish(const unsigned long long* __restrict__ dirq, int n_dirs,
-                             const double* __restrict__ weight, const double* __restrict__ wmax_p,
-                             double* out)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_dirs) return;
-    const double scale = weight ? __ddiv_rn(*wmax_p, 16777216.0) : 1.0;
-    out[j] = __dmul_rn(__ll2double_rn((long long)dirq[j]), scale);
+    const int j = 32 * w + lane;
+    if (s != 0.0 && j < n_dirs) atomicAdd(&dir_area[j], s);
 }
 
 // Fixture faces: all three vertices within tol of one frame bounding-box
@@ -261,39 +280,66 @@ __global__ void k_classes(const uint8_t* __restrict__ mask, const float* __restr
 // ---------------------------------------------------------------------------
 rc_status launch_variability(const uint32_t* bits, const float* N, const double* weight, int64_t n,
                              const float4* dirs, const rc_params* p, float* acc, int8_t* dom, float* conc,
-                             double* dir_area, unsigned long long* scratch /*S_N + 1 + n_dirs*/,
-                             cudaStream_t s)
+                             double* dir_area, void* scratch, cudaStream_t s)
 {
     const int nd = p->n_dirs;
-    unsigned long long* sums = scratch;
-    unsigned long long* wmaxb = scratch + S_N;
-    unsigned long long* dirq = scratch + S_N + 1;
-    const double* wmax_p = (const double*)wmaxb;
-    if (weight && n > 0) {
-        k_wmax<<<256, 256, 0, s>>>(weight, n, wmaxb);
-        RC_LAUNCHED();
-    }
+    unsigned long long* sums = (unsigned long long*)scratch;
+    double* wsum = (double*)((char*)scratch + kVarWsumOffset);
+    double* wpart = (double*)((char*)scratch + kVarPartOffset);
+    RC_CUDA(cudaMemsetAsync(scratch, 0, kVarWsumOffset + 2 * sizeof(double), s));
     if (n > 0) {
         int sm = 0, dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
         int64_t blocks = (n + 7) / 8;
         if (blocks > (int64_t)sm * 8) blocks = (int64_t)sm * 8;
-        k_variability<<<(unsigned)blocks, 256, 0, s>>>(bits, N, weight, wmax_p, n, dirs, nd, p->conc_mode, acc,
-                                                       dom, conc, sums);
+        if (blocks > kVarMaxBlocks) blocks = kVarMaxBlocks;
+        k_variability<<<(unsigned)blocks, 256, 0, s>>>(bits, N, weight, n, dirs, nd, p->conc_mode, acc, dom, conc,
+                                                       sums, wpart);
         RC_LAUNCHED();
+        if (weight) {
+            k_wsum_finish<<<1, 32, 0, s>>>(wpart, (int)blocks, wsum);
+            RC_LAUNCHED();
+        }
     }
     if (dir_area) {
+        RC_CUDA(cudaMemsetAsync(dir_area, 0, sizeof(double) * (size_t)nd, s));
         const int W = (nd + 31) / 32;
         const int64_t warps = ((n + kDirChunk - 1) / kDirChunk) * W;
         if (warps > 0) {
-            k_dir_hist<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(bits, n, W, weight, wmax_p, dirq);
+            k_dir_hist<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(bits, n, W, nd, weight, dir_area);
             RC_LAUNCHED();
         }
-        k_dir_finish<<<(nd + 255) / 256, 256, 0, s>>>(dirq, nd, weight, wmax_p, dir_area);
-        RC_LAUNCHED();
     }
     return RC_OK;
+}
+
+void fill_summary(const long long* sums, const double* wsum, int64_t n, int32_t n_dirs, bool weighted,
+                  rc_summary* out)
+{
+    rc_summary& o = *out;
+    memset(&o, 0, sizeof o);
+    const long long counted = sums[S_COUNTED];
+    o.n_points = n;
+    o.n_counted = counted;
+    o.n_zero_visible = n - counted;
+    for (int k = 0; k < 3; ++k) {
+        o.dom_count[k] = sums[S_DOM + k];
+        o.axis_share[k] = counted ? (double)sums[S_DOM + k] / (double)counted : 0.0;
+    }
+    o.count_sum = sums[S_COUNT];
+    o.conc_sum_q = sums[S_CONC];
+    if (weighted) {
+        o.weighted_count = wsum[0];
+        o.weight_sum = wsum[1];
+    } else {
+        o.weighted_count = (double)sums[S_COUNT];
+        o.weight_sum = (double)n;
+    }
+    const double den = o.weight_sum * (double)n_dirs;
+    o.overall_access = den > 0.0 ? o.weighted_count / den : 0.0;
+    o.overall_access_unweighted = n ? (double)sums[S_COUNT] / ((double)n * (double)n_dirs) : 0.0;
+    o.mean_conc = counted ? (double)sums[S_CONC] / (1099511627776.0 * (double)counted) : 0.0;
 }
 
 rc_status launch_classes(rc_bvh h, const uint8_t* mask, const float* travel, const int32_t* face, int64_t n,

@@ -485,10 +485,12 @@ rc_status rc_server_wait(rc_server s, int64_t req_id, double timeout_s, rc_reque
     return RC_OK;
 }
 
-rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, int32_t* h_count, int64_t n)
+rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, int64_t bits_words,
+                              int32_t* h_count, int64_t n)
 {
     RC_RANGE();
     if (!s) return set_error(RC_E_ARG, "server is NULL");
+    if (n < 0 || bits_words < 0) return set_error(RC_E_ARG, "n and bits_words must be >= 0");
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->cache.find(part_key);
     if (it == s->cache.end()) return set_error(RC_E_ARG, "part is not resident");
@@ -503,7 +505,10 @@ rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, 
     }
     SrvEntry* e = it->second;
     if (n != e->n) return set_error(RC_E_ARG, "n differs from the resident part's point count");
-    if (h_bits && n) RC_CUDA(cudaMemcpy(h_bits, e->bits, sizeof(uint32_t) * ((e->N + 31) / 32) * n, cudaMemcpyDeviceToHost));
+    const int64_t words = (int64_t)((e->N + 31) / 32) * n;
+    if (h_bits && bits_words < words)
+        return set_error(RC_E_ARG, "h_bits holds fewer than n * ceil(n_dirs / 32) words");
+    if (h_bits && n) RC_CUDA(cudaMemcpy(h_bits, e->bits, sizeof(uint32_t) * words, cudaMemcpyDeviceToHost));
     if (h_count && n) RC_CUDA(cudaMemcpy(h_count, e->count, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
     return RC_OK;
 }

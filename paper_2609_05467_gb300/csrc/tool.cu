@@ -43,11 +43,13 @@ extern "C" rc_status rc_tool_cast(rc_bvh h, const float* d_P, const float* d_N, 
     }
     double2* d_ring = nullptr;
     RC_CUDA(cudaMallocAsync(&d_ring, sizeof(double2) * ring.size(), s));
-    RC_CUDA(cudaMemcpyAsync(d_ring, ring.data(), sizeof(double2) * ring.size(), cudaMemcpyHostToDevice, s));
-    st = launch_tool_cast(h, d_P, d_N, n, p, tool_radius, d_ring, ring_rays, d_mask, (unsigned long long*)d_counters,
-                          s);
-    // the table is read by the kernel; keep it until the stream reaches here
-    RC_CUDA(cudaStreamSynchronize(s));
+    // a copy from pageable memory has read the host vector when it returns
+    const cudaError_t e = cudaMemcpyAsync(d_ring, ring.data(), sizeof(double2) * ring.size(),
+                                          cudaMemcpyHostToDevice, s);
+    st = e == cudaSuccess ? launch_tool_cast(h, d_P, d_N, n, p, tool_radius, d_ring, ring_rays, d_mask,
+                                             (unsigned long long*)d_counters, s)
+                          : cuda_error(e, "ring table upload");
+    // stream-ordered: released after the kernel that reads it
     cudaFreeAsync(d_ring, s);
     return st;
 }

@@ -1,10 +1,13 @@
 """Batched cast: many parts of uneven size in one graph-replayed launch give
+the oracle's visibility bits (bit for bit outside its ambiguous rays) and
 exactly the single-part results (bits and counts bit for bit), under every
 knob the autotuner may pick and on repeated replays."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
+from common import compare_bits
 
 pytestmark = pytest.mark.gpu
 
@@ -27,27 +30,33 @@ def _parts():
 
 
 def _setup(rc, N, counts):
+    """Each part with the oracle's seeded sample points (so no GPU output is
+    an oracle input), the oracle's own cast of them, and the single-part
+    GPU cast."""
     out = []
     for (V, F), n in zip(_parts(), counts):
         bvh = rc.Bvh(torch.from_numpy(V).cuda(), torch.from_numpy(F).cuda())
         p = rc.rc_params_default(n_dirs=N, seed=len(out))
-        P = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
-        Nn = torch.zeros_like(P)
-        f = torch.zeros(n, dtype=torch.int32, device="cuda")
-        rc.rc_sample_points(bvh.h, n, p, P, Nn, f)
+        hP, hN, _, _ = oracle.sample_area(V, F, n, seed=len(out))
+        ob, oa, oc = oracle.Mesh(V, F).hemisphere(hP, hN, N)
+        P = torch.from_numpy(hP).cuda()
+        Nn = torch.from_numpy(hN).cuda()
         ref_b = torch.zeros((n, (N + 31) // 32), dtype=torch.int32, device="cuda")
         ref_c = torch.zeros(n, dtype=torch.int32, device="cuda")
         rc.rc_hemisphere_cast(bvh.h, P, Nn, p, ref_b, ref_c)
-        out.append(dict(bvh=bvh, P=P, N=Nn, ref_b=ref_b, ref_c=ref_c,
+        out.append(dict(bvh=bvh, P=P, N=Nn, ref_b=ref_b, ref_c=ref_c, oracle=(ob, oa, oc), nV=len(V), T=len(F),
                         b=torch.full_like(ref_b, -1), c=torch.full_like(ref_c, -1),
                         ctr=torch.zeros(4, dtype=torch.int64, device="cuda")))
     torch.cuda.synchronize()
     return out
 
 
-def _check(parts, N):
+def _check(parts, N, against_oracle=False):
     torch.cuda.synchronize()
     for q in parts:
+        if against_oracle:
+            gb = q["b"].cpu().numpy().view(np.uint32)
+            compare_bits(gb, q["c"].cpu().numpy(), *q["oracle"], N)
         assert torch.equal(q["b"], q["ref_b"]) and torch.equal(q["c"], q["ref_c"])
         c = q["ctr"].cpu().numpy()
         assert c[0] == q["P"].shape[0] * N and c[3] == 0
@@ -62,7 +71,7 @@ def test_batch_equals_single_part(rc, N):
     for q in parts:
         rc.rc_batch_add_part(b, q["bvh"].h, q["P"], q["N"], q["b"], q["c"], q["ctr"])
     rc.rc_batch_launch(b)
-    _check(parts, N)
+    _check(parts, N, against_oracle=True)
     # replays of the captured graph
     for q in parts:
         q["b"].fill_(-1)
@@ -92,7 +101,7 @@ def test_batch_equals_single_part(rc, N):
     for q in parts:
         q["b"].fill_(-1)
     rc.rc_batch_launch(b)
-    _check(parts, N)
+    _check(parts, N, against_oracle=True)
     rc.rc_batch_clear(b)
     rc.rc_batch_launch(b)        # empty batch: no-op
     rc.rc_batch_destroy(b)
@@ -124,3 +133,28 @@ def test_single_part_knobs_do_not_change_results(rc):
     for bits, cnt in res[1:]:
         assert torch.equal(bits, res[0][0]) and torch.equal(cnt, res[0][1])
     bvh.close()
+
+
+def test_batch_budget_and_poll(rc):
+    """A part that would take the batch past its HBM budget is refused with
+    RC_E_OOM (and not added); rc_batch_poll reports 0 before the first launch
+    and 1 once the launch's work has completed."""
+    N = 64
+    parts = _setup(rc, N, [500, 300])
+    sizes = [12 * q["nV"] + 260 * q["T"] + q["P"].shape[0] * (24 + 4 * 2 + 8) + 64 for q in parts]
+    b = rc.rc_batch_create(rc.rc_params_default(n_dirs=N), hbm_budget_bytes=sizes[0] + sizes[1] - 1)
+    q0, q1 = parts
+    pid = rc.rc_batch_add_part(b, q0["bvh"].h, q0["P"], q0["N"], q0["b"], q0["c"], q0["ctr"])
+    with pytest.raises(rc.RcError) as ei:
+        rc.rc_batch_add_part(b, q1["bvh"].h, q1["P"], q1["N"], q1["b"], q1["c"], q1["ctr"])
+    assert ei.value.status == 3
+    assert rc.rc_batch_poll(b, pid) == 0
+    with pytest.raises(rc.RcError):
+        rc.rc_batch_poll(b, 1)                      # the refused part was not added
+    rc.rc_batch_launch(b)
+    torch.cuda.synchronize()
+    assert rc.rc_batch_poll(b, pid) == 1
+    _check(parts[:1], N, against_oracle=True)
+    rc.rc_batch_destroy(b)
+    for q in parts:
+        q["bvh"].close()

@@ -61,7 +61,7 @@ def test_face_level_stl_matches_oracle(rc, tmp_path, name, N):
     M, ac, dom, conc, c2 = oracle.variability(ob, Nn, N)
     s = oracle.summary(c2, dom, conc, N, weight=w)
     if amb == 0:
-        assert np.array_equal(bits, ob) and r.summary.overall_access == s["overall_access"]
+        assert np.array_equal(bits, ob) and abs(r.summary.overall_access - s["overall_access"]) <= 1e-12
         assert list(r.summary.axis_share) == s["axis_share"] and r.summary.mean_conc == s["mean_conc"]
         assert r.label == oracle.classify(s)
     else:

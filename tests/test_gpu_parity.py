@@ -231,17 +231,24 @@ def test_variability_parity(rc, conc_mode, mode, N):
     assert np.array_equal(conc.cpu().numpy(), oconc.astype(np.float32))
     assert np.array_equal(acc.cpu().numpy(), (ocnt / N).astype(np.float32))
     os_ = oracle.summary(ocnt, odom, oconc, N, weight=None if wt is None else w)
-    assert s.overall_access == os_["overall_access"]
+    if wt is None:
+        assert s.overall_access == os_["overall_access"]
+    else:
+        # FP64 sums in another order than the oracle's: far inside the 1e-4 bar
+        assert abs(s.overall_access - os_["overall_access"]) <= 1e-12
+        assert abs(s.weight_sum - float(np.sum(w))) <= 1e-12 * float(np.sum(w))
     assert list(s.axis_share) == os_["axis_share"]
     assert s.mean_conc == os_["mean_conc"]
     assert s.n_counted == os_["n_counted"] and s.n_zero_visible == os_["n_zero_visible"]
     lab = rc.rc_classify(s, p)
     assert lab == oracle.classify(os_)
     # per-direction visible weight
-    wq = oracle.quantised_weights(np.ones(n) if wt is None else w)
-    scale = 1.0 if wt is None else w.max() / 16777216.0
-    expect = (unpack(ob, N) * wq[:, None]).sum(0).astype(np.float64) * scale
-    assert np.array_equal(dira.cpu().numpy(), expect)
+    wv = np.ones(n) if wt is None else w
+    expect = (unpack(ob, N) * wv[:, None]).sum(0).astype(np.float64)
+    if wt is None:
+        assert np.array_equal(dira.cpu().numpy(), expect)
+    else:
+        assert np.allclose(dira.cpu().numpy(), expect, rtol=1e-12, atol=0)
     bvh.close()
 
 

@@ -1,11 +1,15 @@
-"""Serving loop: requests admitted while others run give exactly the result
-of the same request analysed alone (rc_analyze_part), resident parts are
+"""Serving loop: requests admitted while others run give the oracle's
+results (visibility bits outside its ambiguous rays, indicators, label and
+setups) and exactly the result of the same request analysed alone
+(rc_analyze_part); requests really run side by side; resident parts are
 refitted when their triangle list is unchanged, a request that can never fit
 the budget is rejected, and a failing request does not disturb the others."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
+from common import compare_bits, gpu_outcome, setup_outcomes, unpack
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +43,41 @@ def _same(a, b):
     assert list(a.cast_counters)[:1] == list(b.cast_counters)[:1]
 
 
+def _against_oracle(V, F, n, p, bits, cnt, res):
+    """A served request against the oracle run on the same seeded points:
+    bits and counts outside its ambiguous rays; indicators and label exactly
+    when no ray is ambiguous, else within the ambiguous rays' share; setups
+    among the outcomes its ambiguous axis rays allow."""
+    N = p.n_dirs
+    P, Nn, f, _ = oracle.sample_area(V, F, n, seed=p.seed)
+    m = oracle.Mesh(V, F)
+    ob, oa, oc = m.hemisphere(P, Nn, N)
+    compare_bits(bits, cnt, ob, oa, oc, N)
+    n_amb = int(unpack(oa, N).sum())
+    M, ac, dom, conc, c2 = oracle.variability(ob, Nn, N)
+    s = oracle.summary(c2, dom, conc, N)
+    g = res.summary
+    if n_amb == 0:
+        assert g.overall_access == s["overall_access"] and list(g.axis_share) == s["axis_share"]
+        assert g.mean_conc == s["mean_conc"] and res.label == oracle.classify(s)
+    else:
+        assert abs(g.overall_access - s["overall_access"]) <= max(1e-4, n_amb / (n * N))
+    if res.setups_ran:
+        om, oam = m.orthogonal(P, Nn)
+        outs, _, _ = setup_outcomes(om, oam, oracle.travel(V, P), f, oracle.fixture_faces(V, F), p.tool_length)
+        if outs is not None:
+            assert gpu_outcome(res.setups) in outs
+
+
+def _overlap(results):
+    """Some two requests whose [t_start, t_end] intervals overlap."""
+    for i, a in enumerate(results):
+        for b in results[i + 1:]:
+            if max(a.t_start, b.t_start) < min(a.t_end, b.t_end):
+                return True
+    return False
+
+
 def test_requests_in_a_mix_equal_requests_alone(rc):
     p = rc.rc_params_default(n_dirs=256, always_setups=1, tool_length=40.0)
     jobs = [
@@ -59,13 +98,43 @@ def test_requests_in_a_mix_equal_requests_alone(rc):
         alone, bits, cnt = _alone(rc, V, F, n, p)
         _same(r.result, alone)
     assert res[0].rebuilt == 1 and res[3].rebuilt == 0 and res[6].rebuilt == 0
-    # the resident maps are those of each key's last request
-    for key, (V, F), n in [jobs[3], jobs[2], jobs[6], jobs[4], jobs[5]]:
+    # the mix really ran side by side: some two requests were on the GPU at once
+    assert _overlap(res)
+    # the resident maps are those of each key's last request, and the oracle's
+    for j in (3, 2, 6, 4, 5):
+        key, (V, F), n = jobs[j]
         rb, rcnt = rc.rc_server_read_bits(srv, key, n, p.n_dirs)
         alone, bits, cnt = _alone(rc, V, F, n, p)
         assert np.array_equal(rb, bits) and np.array_equal(rcnt, cnt)
+        _against_oracle(V, F, n, p, rb, rcnt, res[j].result)
     st = rc.rc_server_get_stats(srv)
     assert st.completed == len(jobs) and st.failed == 0 and st.resident_parts == 5
+    rc.rc_server_destroy(srv)
+
+
+def test_served_direction_count_not_a_multiple_of_32(rc):
+    """The paper's 150 directions: rows of ceil(150/32) = 5 words, read back
+    whole; the results against the oracle; a bits buffer that is too small
+    is refused instead of overrun."""
+    p = rc.rc_params_default(n_dirs=150, always_setups=1, tool_length=40.0, seed=3)
+    jobs = [(21, synth.pocket_block(2), 700), (22, synth.prismatic(h=4.0), 1500), (23, synth.deep_hole(), 300)]
+    srv = rc.rc_server_create(p, slots=3, hbm_budget_bytes=4 << 30)
+    ids = [rc.rc_server_submit(srv, key, V, F, n) for key, (V, F), n in jobs]
+    res = [rc.rc_server_wait(srv, i, timeout_s=300.0) for i in ids]
+    for r, (key, (V, F), n) in zip(res, jobs):
+        assert r.status == 0, r.message
+        rb, rcnt = rc.rc_server_read_bits(srv, key, n, 150)
+        assert rb.shape == (n, 5) and not (rb[:, 4] >> 22).any()     # bits 150..159 are 0
+        alone, bits, cnt = _alone(rc, V, F, n, p)
+        assert np.array_equal(rb, bits) and np.array_equal(rcnt, cnt)
+        _same(r.result, alone)
+        _against_oracle(V, F, n, p, rb, rcnt, r.result)
+    import ctypes
+    key, (V, F), n = jobs[0]
+    small = np.zeros((n, 4), np.uint32)
+    st = rc.load().rc_server_read_bits(ctypes.c_void_p(srv), ctypes.c_uint64(key),
+                                       small.ctypes.data_as(ctypes.c_void_p), small.size, None, n)
+    assert st == 1 and b"h_bits" in rc.load().rc_last_error()
     rc.rc_server_destroy(srv)
 
 
