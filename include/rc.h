@@ -84,12 +84,7 @@ typedef struct {
     int32_t points_per_item; /* batched cast: points per work item (0 = 1) */
     int32_t launch_mode;     /* casts: 0 = persistent grid (default), 1 = one warp per point, grid sized to the work
                                 (short blocks, so concurrent casts on other streams interleave) */
-    int32_t fetch_mode;      /* hemispherical cast, persistent grid: 0 = lanes wait for their tile of 32 rays;
-                                1 (binary tree) = a lane takes the next ray of the warp's points as soon as its
-                                ray finishes; 2 (4-wide tree) = each lane walks its own list of the point's rays;
-                                3 = a warp casts one direction at a time from 32 Morton-adjacent points;
-                                4 (4-wide tree) = the warp walks each tile's 32 rays together over one shared
-                                stack whose entries carry the mask of lanes that entered the node */
+    int32_t fetch_mode;      /* reserved, must be 0 (the lanes of a warp cast one tile of 32 rays together) */
     int32_t tree_width;      /* casts: 0 or 4 = 4-wide tree (default), 2 = binary tree */
     double parallel_tol;     /* orthogonal cast: axis a is eligible when n.a >= -parallel_tol (FP64); a face
                                 parallel to the axis is side-milled, and the tolerance absorbs the tilt that
@@ -260,6 +255,19 @@ rc_status rc_direction_table(int32_t n_dirs, float* h_dirs);
 rc_status rc_hemisphere_cast(rc_bvh h, const float* d_P, const float* d_N, int64_t n,
                              const rc_params* p, uint32_t* d_bits, int32_t* d_count,
                              int64_t* d_counters, void* stream);
+
+/* The instrumented cast of rc_hemisphere_cast (as with p->collect_stats: the
+ * same rays and decisions, counters int64[8] with the node and triangle
+ * counts in [4] and [5]) that also lists the rays whose walk re-tested a
+ * pair in FP64 (Section 3.1's intersection test made exact; see the
+ * precision note above): d_list[k] = i * 65536 + j for point i and
+ * direction j, in no particular order, for the first min(cap, total) such
+ * rays; counters[6] receives the total.  For tests and measurement.
+ *   d_list int64[cap] (device, may be NULL when cap == 0).
+ * Asynchronous.  Errors: RC_E_ARG (NULL counters, cap < 0), RC_E_CUDA. */
+rc_status rc_hemisphere_cast_retests(rc_bvh h, const float* d_P, const float* d_N, int64_t n,
+                                     const rc_params* p, uint32_t* d_bits, int32_t* d_count,
+                                     int64_t* d_counters, int64_t* d_list, int64_t cap, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Section 3.3: directional variability and classification                */

@@ -164,6 +164,23 @@ def ray_dirs(normal, N):
     return d
 
 
+def rays_at(P, Nrm, N, i, j, eps=1e-4):
+    """Origins and directions of selected hemisphere rays (readings R3, R4):
+    ray k is direction j[k] of point i[k] (the same fp32 rays the
+    hemisphere cast traces)."""
+    _, h32 = direction_table(N)
+    P, Nrm = _c(P, np.float32), _c(Nrm, np.float32)
+    i = np.asarray(i, np.int64)
+    j = np.asarray(j, np.int64)
+    O = np.zeros((len(i), 3), np.float32)
+    D = np.zeros((len(i), 3), np.float32)
+    lib = _L()
+    for k in range(len(i)):
+        lib.or_ray_origin(_p(P[i[k]]), _p(Nrm[i[k]]), float(eps), _p(O[k]))
+        lib.or_ray_dirs(_p(Nrm[i[k]]), _p(h32[j[k]]), 1, _p(D[k]))
+    return O, D
+
+
 def ray_origins(P, Nrm, eps):
     """o = fl32(p + eps*n) in FP64 (reading R4)."""
     P, Nrm = _c(P, np.float32), _c(Nrm, np.float32)

@@ -22,7 +22,7 @@ import threading
 __all__ = [
     "RcError", "Params", "Summary", "Setups", "BvhInfo", "load", "lib_path",
     "rc_params_default", "rc_build_bvh", "rc_refit_bvh", "rc_destroy_bvh", "rc_bvh_get_info",
-    "rc_sample_points", "rc_direction_table", "rc_hemisphere_cast", "rc_direction_variability",
+    "rc_sample_points", "rc_direction_table", "rc_hemisphere_cast", "rc_hemisphere_cast_retests", "rc_direction_variability",
     "rc_direction_variability_noalloc",
     "rc_classify", "rc_orthogonal_cast", "rc_min_setups", "rc_setup_cover", "rc_analyze_part",
     "rc_launch_count", "rc_stream_status", "rc_bvh_validate", "Bvh", "PartResult", "rc_batch_create", "rc_batch_add_part", "rc_batch_clear",
@@ -172,6 +172,7 @@ def load(build_if_missing=True):
             "rc_sample_points": ([P, i64, ctypes.POINTER(Params), P, P, P, P, P], st),
             "rc_direction_table": ([i32, P], st),
             "rc_hemisphere_cast": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P], st),
+            "rc_hemisphere_cast_retests": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P, i64, P], st),
             "rc_direction_variability": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P,
                                           ctypes.POINTER(Summary), P], st),
             "rc_direction_variability_noalloc": ([P, P, P, i64, ctypes.POINTER(Params), P, P, P, P,
@@ -305,6 +306,14 @@ def rc_direction_table(n_dirs):
 def rc_hemisphere_cast(h, P, N, params, bits, count, counters=None, stream=None):
     _check(load().rc_hemisphere_cast(ctypes.c_void_p(h), _ptr(P), _ptr(N), P.shape[0], ctypes.byref(params),
                                      _ptr(bits), _ptr(count), _ptr(counters), _stream(stream)))
+
+
+def rc_hemisphere_cast_retests(h, P, N, params, bits, count, counters, lst, stream=None):
+    """Instrumented cast listing the rays an FP64 re-test took part in
+    (i * 65536 + j in `lst`, counters[6] = their total)."""
+    _check(load().rc_hemisphere_cast_retests(ctypes.c_void_p(h), _ptr(P), _ptr(N), P.shape[0],
+                                             ctypes.byref(params), _ptr(bits), _ptr(count), _ptr(counters),
+                                             _ptr(lst), lst.numel() if lst is not None else 0, _stream(stream)))
 
 
 def rc_direction_variability(bits, N, params, weight=None, acc=None, dom=None, conc=None, dir_area=None,

@@ -22,7 +22,7 @@ rc_status sample_points(rc_bvh h, int64_t n, const rc_params* p, float* P, float
                         double* weight, cudaStream_t s);
 rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
                             uint32_t* bits, int32_t* count, unsigned long long* counters, bool stats,
-                            cudaStream_t s);
+                            cudaStream_t s, long long* relist = nullptr, long long relist_cap = 0);
 rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
                             uint8_t* mask, float* travel, unsigned long long* counters, cudaStream_t s);
 rc_status frame_setup(rc_bvh h, const rc_params* p, FrameDev* d, cudaStream_t s);
@@ -151,7 +151,7 @@ static rc_status check_params(const rc_params* p)
     if (p->points_per_item < 0 || p->points_per_item > 64)
         return set_error(RC_E_ARG, "points_per_item must be in [0, 64]");
     if (p->launch_mode != 0 && p->launch_mode != 1) return set_error(RC_E_ARG, "launch_mode must be 0 or 1");
-    if (p->fetch_mode < 0 || p->fetch_mode > 4) return set_error(RC_E_ARG, "fetch_mode must be in [0, 4]");
+    if (p->fetch_mode != 0) return set_error(RC_E_ARG, "fetch_mode must be 0 (reserved)");
     if (p->tree_width != 0 && p->tree_width != 2 && p->tree_width != 4)
         return set_error(RC_E_ARG, "tree_width must be 0 (default), 2 or 4");
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return set_error(RC_E_ARG, "blocks_per_sm out of range");
@@ -385,6 +385,31 @@ rc_status rc_hemisphere_cast(rc_bvh h, const float* d_P, const float* d_N, int64
     h->tdirs = p->tile_mode == 1 ? dirs : tdirs;
     h->dirs_n = p->n_dirs;
     return launch_hemisphere(h, d_P, d_N, n, p, d_bits, d_count, (unsigned long long*)d_counters, stats, s);
+}
+
+rc_status rc_hemisphere_cast_retests(rc_bvh h, const float* d_P, const float* d_N, int64_t n, const rc_params* p,
+                                     uint32_t* d_bits, int32_t* d_count, int64_t* d_counters, int64_t* d_list,
+                                     int64_t cap, void* stream)
+{
+    RC_RANGE();
+    if (!h) return set_error(RC_E_ARG, "handle is NULL");
+    rc_status st = check_params(p);
+    if (st != RC_OK) return st;
+    if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
+    if (!d_counters) return set_error(RC_E_ARG, "the counters array is NULL");
+    if (cap < 0 || (cap > 0 && !d_list)) return set_error(RC_E_ARG, "list is NULL or cap < 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = use_device_of(h)) != RC_OK) return st;
+    RC_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(int64_t) * 8, s));
+    if (n == 0) return RC_OK;
+    if (!d_P || !d_N || !d_bits || !d_count) return set_error(RC_E_ARG, "array pointer is NULL");
+    const float4 *dirs = nullptr, *tdirs = nullptr;
+    if ((st = device_dirs(p->n_dirs, &dirs, &tdirs)) != RC_OK) return st;
+    h->dirs = dirs;
+    h->tdirs = p->tile_mode == 1 ? dirs : tdirs;
+    h->dirs_n = p->n_dirs;
+    return launch_hemisphere(h, d_P, d_N, n, p, d_bits, d_count, (unsigned long long*)d_counters, true, s,
+                             (long long*)d_list, cap);
 }
 
 rc_status rc_direction_variability(const uint32_t* d_bits, const float* d_N, const double* d_weight, int64_t n,

@@ -16,8 +16,7 @@
 // distance by 1 + 2*gamma_3 (Ize, JCGT 2013).
 //
 // Kernels: k_hemisphere (the default cast: persistent warps, one point per
-// warp in tiles of 32 directions, the last points in parts), its measured
-// alternatives k_hemisphere_dyn / _flat / _pkt / _wp (fetch_mode 1-4),
+// warp in tiles of 32 directions, the last points in parts),
 // k_hemisphere_update (re-cast after an edit), k_batch (many parts in one
 // launch), k_orthogonal_axis (one frame axis for 32 points per work item),
 // k_tool_cast_axis (the sampled ball-end tool), and the frame set-up
@@ -371,7 +370,7 @@ __device__ __forceinline__ int slab4(const float4* __restrict__ nd, const SlabRa
 }
 
 template <bool kStats>
-__device__ __forceinline__ TraceOut trace4_ifif(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
+__device__ __forceinline__ TraceOut trace4(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
                                            const Ray& r, int max_steps)
 {
     TraceOut out = {0, 0, 0, 0, 0};
@@ -432,254 +431,11 @@ __device__ __forceinline__ TraceOut trace4_ifif(const float4* __restrict__ wnode
     return out;
 }
 
-#ifndef RC_WHILE_WHILE
-#define RC_WHILE_WHILE 0
-#endif
-
-template <bool kStats>
-__device__ __forceinline__ TraceOut trace4(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
-                                           const Ray& r, int max_steps)
-{
-    TraceOut out = {0, 0, 0, 0, 0};
-    int stack[kStack4];
-    int sp = 0;
-    int cur = 0;
-    bool amb = false, ambhit = false;
-    const SlabRay sr = make_slab_ray(r, r.rs);
-    int steps = 0;
-    for (;;) {
-        // descend through interior nodes until a leaf is current (or the
-        // walk ends); lanes then test their leaves together
-        while (cur >= 0) {
-            if (++steps > max_steps) { out.overflow = 1; out.flags = 1; return out; }
-            if (kStats) ++out.nodes;
-            float d[4];
-            int c[4];
-            const int nh = slab4(wnodes + 8 * cur, sr, d, c);
-            if (nh == 0) {
-                if (sp == 0) {
-                    out.flags = (ambhit ? 1 : 0) | (amb ? 2 : 0);
-                    return out;
-                }
-                cur = stack[--sp];
-                continue;
-            }
-#define RC_CSWAP(a, b)                                              \
-    if (d[b] < d[a]) {                                              \
-        const float td = d[a]; d[a] = d[b]; d[b] = td;              \
-        const int tc = c[a]; c[a] = c[b]; c[b] = tc;                \
-    }
-            RC_CSWAP(0, 1) RC_CSWAP(2, 3) RC_CSWAP(0, 2) RC_CSWAP(1, 3) RC_CSWAP(1, 2)
-#undef RC_CSWAP
-            if (sp + nh - 1 > kStack4) { out.overflow = 1; out.flags = 1; return out; }
-            if (nh > 3) stack[sp++] = c[3];
-            if (nh > 2) stack[sp++] = c[2];
-            if (nh > 1) stack[sp++] = c[1];
-            cur = c[0];
-        }
-        // leaf
-        if (++steps > max_steps) { out.overflow = 1; out.flags = 1; return out; }
-        const int v = -1 - cur;
-        const int first = v >> 3, cnt = (v & 7) + 1;
-        for (int k = 0; k < cnt; ++k) {
-            const float4* t = tris + 3 * (first + k);
-            const float4 v0 = __ldg(t), v1 = __ldg(t + 1), v2 = __ldg(t + 2);
-            if (kStats) ++out.tris;
-            const int s = tri_test32(r, v0, v1, v2);
-            if (s == kHit) { out.flags = 1; return out; }
-            if (s == kUnsure) {
-                ++out.retests;
-                const Pair64 p = retest64(r, v0, v1, v2);
-                if (p.state == kHit) { out.flags = 1; return out; }
-                if (p.state == kUnsure) { amb = true; ambhit |= p.hit64; }
-            }
-        }
-        if (sp == 0) break;
-        cur = stack[--sp];
-    }
-    out.flags = (ambhit ? 1 : 0) | (amb ? 2 : 0);
-    return out;
-}
-
-// One step of the 4-wide walk (a node or a leaf) on explicit state, for the
-// flat per-lane ray loop.  Returns 0 while the walk goes on, 1 when the ray
-// is decided.  On return 1, *blocked tells whether it is obstructed.
-struct Walk4 {
-    int cur, sp, steps;
-    bool amb, ambhit;
-};
-
-__device__ __forceinline__ int step4(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
-                                     const Ray& r, int max_steps, Walk4& w, int* stack, bool& blocked,
-                                     CastAccFwd& acc)
-{
-    const float rob = 1.0f + 2.0f * 1.7881394e-7f;
-    if (++w.steps > max_steps) { ++acc.overflow; blocked = true; return 1; }
-    if (w.cur >= 0) {
-        const bool sx = signbit(r.ix), sy = signbit(r.iy), sz = signbit(r.iz);
-        const float4* nd = wnodes + 8 * w.cur;
-        const float4 lox = __ldg(nd + 0), hix = __ldg(nd + 1), loy = __ldg(nd + 2), hiy = __ldg(nd + 3);
-        const float4 loz = __ldg(nd + 4), hiz = __ldg(nd + 5), ci = __ldg(nd + 6);
-        float d[4];
-        int c[4];
-        const float lx[4] = {lox.x, lox.y, lox.z, lox.w}, hx[4] = {hix.x, hix.y, hix.z, hix.w};
-        const float ly[4] = {loy.x, loy.y, loy.z, loy.w}, hy[4] = {hiy.x, hiy.y, hiy.z, hiy.w};
-        const float lz[4] = {loz.x, loz.y, loz.z, loz.w}, hz[4] = {hiz.x, hiz.y, hiz.z, hiz.w};
-        const int cc[4] = {__float_as_int(ci.x), __float_as_int(ci.y), __float_as_int(ci.z), __float_as_int(ci.w)};
-        int nh = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float nx = ((sx ? hx[k] : lx[k]) - r.ox) * r.ix, fx = ((sx ? lx[k] : hx[k]) - r.ox) * r.ix;
-            const float ny = ((sy ? hy[k] : ly[k]) - r.oy) * r.iy, fy = ((sy ? ly[k] : hy[k]) - r.oy) * r.iy;
-            const float nz = ((sz ? hz[k] : lz[k]) - r.oz) * r.iz, fz = ((sz ? lz[k] : hz[k]) - r.oz) * r.iz;
-            const float tn = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.0f));
-            const float tf = fminf(fminf(fx, fy), fz) * rob;
-            const bool hit = tn <= tf;
-            d[k] = hit ? tn : INFINITY;
-            c[k] = cc[k];
-            nh += hit;
-        }
-        if (nh == 0) {
-            if (w.sp == 0) { blocked = w.ambhit; return 1; }
-            w.cur = stack[--w.sp];
-            return 0;
-        }
-#define RC_CSWAP(a, b)                                              \
-    if (d[b] < d[a]) {                                              \
-        const float td = d[a]; d[a] = d[b]; d[b] = td;              \
-        const int tc = c[a]; c[a] = c[b]; c[b] = tc;                \
-    }
-        RC_CSWAP(0, 1) RC_CSWAP(2, 3) RC_CSWAP(0, 2) RC_CSWAP(1, 3) RC_CSWAP(1, 2)
-#undef RC_CSWAP
-        if (w.sp + nh - 1 > kStack4) { ++acc.overflow; blocked = true; return 1; }
-        if (nh > 3) stack[w.sp++] = c[3];
-        if (nh > 2) stack[w.sp++] = c[2];
-        if (nh > 1) stack[w.sp++] = c[1];
-        w.cur = c[0];
-        return 0;
-    }
-    const int v = -1 - w.cur;
-    const int first = v >> 3, cnt = (v & 7) + 1;
-    for (int k = 0; k < cnt; ++k) {
-        const float4* t = tris + 3 * (first + k);
-        const float4 v0 = __ldg(t), v1 = __ldg(t + 1), v2 = __ldg(t + 2);
-        const int s = tri_test32(r, v0, v1, v2);
-        if (s == kHit) { blocked = true; return 1; }
-        if (s == kUnsure) {
-            ++acc.retests;
-            const Pair64 p = retest64(r, v0, v1, v2);
-            if (p.state == kHit) { blocked = true; return 1; }
-            if (p.state == kUnsure) { w.amb = true; w.ambhit |= p.hit64; }
-        }
-    }
-    if (w.sp == 0) { blocked = w.ambhit; return 1; }
-    w.cur = stack[--w.sp];
-    return 0;
-}
-
-// Any-hit walk of the 4-wide tree by a whole warp over one shared stack
-// (fetch_mode 4).  The 32 lanes hold the rays of one direction tile (one
-// origin).  A stack entry is a node and the mask of lanes whose rays entered
-// its box at the parent, so every lane takes part in exactly the nodes and
-// leaves its own walk would visit -- the same pairs are tested and the same
-// decisions made -- while the warp steps through their union with uniform
-// control flow and one (broadcast) fetch per node.  Children are ordered by
-// the entry distances of the lowest participating lane.  `stk` is the warp's
-// shared-memory stack of kStack4 entries.
-__device__ __forceinline__ TraceOut trace4_warp(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
-                                                const Ray& r, int max_steps, int2* stk)
-{
-    const unsigned FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31;
-    TraceOut out = {0, 0, 0, 0, 0};
-    bool amb = false, ambhit = false, blocked = false;
-    const SlabRay sr = make_slab_ray(r, r.rs);
-    unsigned active = FULL;          // lanes without a certain hit yet
-    int cur = 0;
-    unsigned cmask = FULL;
-    int sp = 0;
-    for (int steps = 0;; ++steps) {
-        if (steps > max_steps) {
-            if ((active >> lane) & 1u) { out.overflow = 1; blocked = true; }
-            break;
-        }
-        const unsigned m = cmask & active;
-        const bool in = (m >> lane) & 1u;
-        if (m != 0u && cur >= 0) {
-            float d[4];
-            int c[4];
-            slab4(wnodes + 8 * cur, sr, d, c);
-            unsigned cm[4];
-            float dl[4];
-            const int leader = __ffs(m) - 1;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                cm[k] = __ballot_sync(FULL, in && d[k] != INFINITY);
-                dl[k] = __shfl_sync(FULL, d[k], leader);
-                if (cm[k] == 0u) dl[k] = INFINITY;
-            }
-            // sort (distance, child, mask) of the leader: misses go last
-#define RC_WSWAP(a, b)                                                                      \
-    if (dl[b] < dl[a] || (cm[a] == 0u && cm[b] != 0u)) {                                     \
-        const float td = dl[a]; dl[a] = dl[b]; dl[b] = td;                                  \
-        const int tc = c[a]; c[a] = c[b]; c[b] = tc;                                        \
-        const unsigned tm = cm[a]; cm[a] = cm[b]; cm[b] = tm;                               \
-    }
-            RC_WSWAP(0, 1) RC_WSWAP(2, 3) RC_WSWAP(0, 2) RC_WSWAP(1, 3) RC_WSWAP(1, 2)
-#undef RC_WSWAP
-            const int nh = (cm[0] != 0u) + (cm[1] != 0u) + (cm[2] != 0u) + (cm[3] != 0u);
-            if (nh > 0) {
-                if (sp + nh - 1 > kStack4) {
-                    if ((active >> lane) & 1u) { out.overflow = 1; blocked = true; }
-                    break;
-                }
-                if (lane == 0) {
-                    if (nh > 3) stk[sp] = make_int2(c[3], (int)cm[3]);
-                    if (nh > 2) stk[sp + (nh > 3)] = make_int2(c[2], (int)cm[2]);
-                    if (nh > 1) stk[sp + (nh > 3) + (nh > 2)] = make_int2(c[1], (int)cm[1]);
-                }
-                sp += nh - 1;
-                cur = c[0];
-                cmask = cm[0];
-                __syncwarp();
-                continue;
-            }
-        } else if (m != 0u) {
-            if (in) {
-                const int v = -1 - cur;
-                const int first = v >> 3, cnt = (v & 7) + 1;
-                for (int k = 0; k < cnt; ++k) {
-                    const float4* t = tris + 3 * (first + k);
-                    const float4 v0 = __ldg(t), v1 = __ldg(t + 1), v2 = __ldg(t + 2);
-                    const int st = tri_test32(r, v0, v1, v2);
-                    if (st == kHit) { blocked = true; break; }
-                    if (st == kUnsure) {
-                        ++out.retests;
-                        const Pair64 pr = retest64(r, v0, v1, v2);
-                        if (pr.state == kHit) { blocked = true; break; }
-                        if (pr.state == kUnsure) { amb = true; ambhit |= pr.hit64; }
-                    }
-                }
-            }
-            active &= ~__ballot_sync(FULL, blocked);
-        }
-        if (sp == 0 || active == 0u) break;
-        --sp;
-        const int2 e = stk[sp];
-        cur = e.x;
-        cmask = (unsigned)e.y;
-    }
-    __syncwarp();
-    out.flags = blocked ? 1 : ((ambhit ? 1 : 0) | (amb ? 2 : 0));
-    return out;
-}
-
 template <bool kStats, bool kWide>
 __device__ __forceinline__ TraceOut trace_any(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                               const Ray& r, int max_steps)
 {
-    if (kWide) return RC_WHILE_WHILE ? trace4<kStats>(nodes, tris, r, max_steps)
-                                     : trace4_ifif<kStats>(nodes, tris, r, max_steps);
+    if (kWide) return trace4<kStats>(nodes, tris, r, max_steps);
     return trace<kStats>(nodes, tris, r, max_steps);
 }
 
@@ -738,7 +494,8 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
                                            const float* __restrict__ Nrm, int64_t i,
                                            const float4* __restrict__ tdirs, int W, double eps, uint32_t* row,
                                            uint32_t* __restrict__ bits, int32_t* __restrict__ count, CastAcc& acc,
-                                           int t0 = 0, int t1 = -1)
+                                           int t0 = 0, int t1 = -1, long long* relist = nullptr,
+                                           long long relist_cap = 0, unsigned long long* relist_ctr = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const bool whole = t1 < 0;
@@ -764,7 +521,15 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
         acc.retests += tr.retests;
         acc.overflow += tr.overflow;
         acc.amb += (j >= 0) & ((tr.flags >> 1) & 1);
-        if (kStats) { acc.nvis += tr.nodes; acc.ntri += tr.tris; }
+        if (kStats) {
+            acc.nvis += tr.nodes;
+            acc.ntri += tr.tris;
+            // the instrumented cast can list the rays an FP64 re-test took part in
+            if (relist && tr.retests > 0 && j >= 0) {
+                const unsigned long long k = atomicAdd(relist_ctr, 1ULL);
+                if (k < (unsigned long long)relist_cap) relist[k] = (long long)i * 65536 + j;
+            }
+        }
         const bool visible = (tr.flags & 1) == 0 && j >= 0;
         if (visible) atomicOr(&row[j >> 5], 1u << (j & 31));
         cnt += __popc(__ballot_sync(0xFFFFFFFFu, visible));
@@ -784,228 +549,13 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
     acc.rays += (t1 - t0) - (t1 == W && __float_as_int(__ldg(&tdirs[32 * (W - 1) + lane]).w) < 0 ? 1 : 0);
 }
 
-// The hemispherical cast of one point by one warp walking each tile's rays
-// together over a shared stack (trace4_warp); otherwise as cast_point.
-__device__ __forceinline__ void cast_point_wp(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
-                                              int max_steps, float scene_maxabs, const float* __restrict__ P,
-                                              const float* __restrict__ Nrm, int64_t i,
-                                              const float4* __restrict__ tdirs, int W, double eps, uint32_t* row,
-                                              int2* stk, uint32_t* __restrict__ bits, int32_t* __restrict__ count,
-                                              CastAcc& acc)
-{
-    const int lane = threadIdx.x & 31;
-    for (int w = lane; w < W; w += 32) row[w] = 0u;
-    __syncwarp();
-    const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
-    const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
-    const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
-    const Onb b = make_onb(nx, ny, nz);
-    int cnt = 0;
-    for (int t = 0; t < W; ++t) {
-        const float4 h = __ldg(&tdirs[32 * t + lane]);
-        const int j = __float_as_int(h.w);
-        float dx, dy, dz;
-        local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
-        Ray r;
-        setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-        const TraceOut tr = trace4_warp(wnodes, tris, r, max_steps, stk);
-        acc.retests += tr.retests;
-        acc.overflow += tr.overflow;
-        acc.amb += (j >= 0) & ((tr.flags >> 1) & 1);
-        const bool visible = (tr.flags & 1) == 0 && j >= 0;
-        if (visible) atomicOr(&row[j >> 5], 1u << (j & 31));
-        cnt += __popc(__ballot_sync(0xFFFFFFFFu, visible));
-    }
-    __syncwarp();
-    for (int w = lane; w < W; w += 32) bits[i * W + w] = row[w];
-    __syncwarp();
-    if (lane == 0) count[i] = cnt;
-    acc.rays += W - (__float_as_int(__ldg(&tdirs[32 * (W - 1) + lane]).w) < 0 ? 1 : 0);
-}
-
-#ifndef RC_WP_MIN_BLOCKS
-#define RC_WP_MIN_BLOCKS 6
-#endif
-
-// Hemispherical cast with warp-shared walks (fetch_mode 4, 4-wide tree):
-// persistent warps take points from the work counter; dynamic shared memory
-// holds each warp's bit row (W words) and then its stack (kStack4 int2).
-__global__ void __launch_bounds__(128, RC_WP_MIN_BLOCKS)
-k_hemisphere_wp(const float4* __restrict__ wnodes, const float4* __restrict__ tris, int max_steps,
-                float scene_maxabs, const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
-                const int32_t* __restrict__ order, const float4* __restrict__ tdirs, int n_dirs, double eps,
-                uint32_t* __restrict__ bits, int32_t* __restrict__ count, unsigned long long* counters,
-                unsigned long long* work)
-{
-    extern __shared__ uint32_t s_mem[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int W = (n_dirs + 31) >> 5;
-    uint32_t* row = s_mem + wid * W;
-    int2* stk = reinterpret_cast<int2*>(s_mem + (blockDim.x >> 5) * ((W + 1) & ~1)) + wid * kStack4;
-    CastAcc acc;
-    for (;;) {
-        unsigned long long k = 0;
-        if (lane == 0) k = atomicAdd(work, 1ULL);
-        k = __shfl_sync(0xFFFFFFFFu, k, 0);
-        if (k >= (unsigned long long)n) break;
-        const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
-        cast_point_wp(wnodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, stk, bits, count, acc);
-    }
-    warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow);
-}
-
-// The hemispherical cast of one point with each lane walking its own list
-// of rays (tile-order indices lane, lane+32, ...) in one flat loop: every
-// iteration a lane either starts its next ray or takes one step of its walk,
-// so a lane never waits for the other lanes' rays, only for the end of the
-// point.  Same rays and decisions as cast_point (4-wide tree only).
-__device__ __forceinline__ void cast_point_flat(const float4* __restrict__ nodes, const float4* __restrict__ tris,
-                                                int max_steps, float scene_maxabs, const float* __restrict__ P,
-                                                const float* __restrict__ Nrm, int64_t i,
-                                                const float4* __restrict__ tdirs, int W, double eps, uint32_t* row,
-                                                uint32_t* __restrict__ bits, int32_t* __restrict__ count,
-                                                CastAcc& acc)
-{
-    const int lane = threadIdx.x & 31;
-    for (int w = lane; w < W; w += 32) row[w] = 0u;
-    __syncwarp();
-    const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
-    const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
-    const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
-    const Onb b = make_onb(nx, ny, nz);
-    int cnt = 0, m = 0, j = 0;
-    bool active = false;
-    Ray r;
-    Walk4 wk;
-    int stack[kStack4];
-    for (;;) {
-        if (!active) {
-            if (m >= W) break;
-            const float4 h = __ldg(&tdirs[32 * m + lane]);
-            ++m;
-            j = __float_as_int(h.w);
-            if (j < 0) continue;                 // pad of the last tile
-            ++acc.rays;
-            float dx, dy, dz;
-            local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
-            setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-            wk.cur = 0;
-            wk.sp = 0;
-            wk.steps = 0;
-            wk.amb = wk.ambhit = false;
-            active = true;
-        }
-        bool blocked = false;
-        if (step4(nodes, tris, r, max_steps, wk, stack, blocked, acc)) {
-            if (!blocked && wk.amb) ++acc.amb;
-            if (!blocked) {
-                atomicOr(&row[j >> 5], 1u << (j & 31));
-                ++cnt;
-            }
-            active = false;
-        }
-    }
-    for (int off = 16; off; off >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, off);
-    __syncwarp();
-    for (int w = lane; w < W; w += 32) bits[i * W + w] = row[w];
-    __syncwarp();
-    if (lane == 0) count[i] = cnt;
-}
-
-#ifndef RC_FLAT_MIN_BLOCKS
-#define RC_FLAT_MIN_BLOCKS 6
-#endif
-
-__global__ void __launch_bounds__(128, RC_FLAT_MIN_BLOCKS)
-k_hemisphere_flat(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps,
-                  float scene_maxabs, const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
-                  const int32_t* __restrict__ order, const float4* __restrict__ tdirs, int n_dirs, double eps,
-                  uint32_t* __restrict__ bits, int32_t* __restrict__ count, unsigned long long* counters,
-                  unsigned long long* work)
-{
-    extern __shared__ uint32_t s_rows[];
-    const int lane = threadIdx.x & 31;
-    const int W = (n_dirs + 31) >> 5;
-    uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
-    CastAcc acc;
-    for (;;) {
-        unsigned long long k = 0;
-        if (lane == 0) k = atomicAdd(work, 1ULL);
-        k = __shfl_sync(0xFFFFFFFFu, k, 0);
-        if (k >= (unsigned long long)n) break;
-        const int64_t i = order ? (int64_t)__ldg(&order[k]) : (int64_t)k;
-        cast_point_flat(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits, count, acc);
-    }
-    warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow);
-}
-
-// Hemispherical cast by point packets: a warp holds 32 points that are
-// adjacent in Morton order, and all lanes cast the same local direction j at
-// a time -- near-parallel rays from nearby origins, which walk nearly the
-// same nodes.  Each lane assembles its own point's bit words in a register
-// (canonical j order) and writes them whole.  Same rays and decisions as
-// k_hemisphere.
-template <bool kWide>
-__global__ void __launch_bounds__(128, RC_HEMI_MIN_BLOCKS)
-k_hemisphere_pkt(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps,
-                 float scene_maxabs, const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
-                 const int32_t* __restrict__ order, const float4* __restrict__ dirs, int n_dirs, double eps,
-                 uint32_t* __restrict__ bits, int32_t* __restrict__ count, unsigned long long* counters,
-                 unsigned long long* work)
-{
-    const int lane = threadIdx.x & 31;
-    const int W = (n_dirs + 31) >> 5;
-    const unsigned long long chunks = (unsigned long long)((n + 31) / 32);
-    CastAcc acc;
-    // work item = (chunk of 32 points, word of 32 directions)
-    for (;;) {
-        unsigned long long it = 0;
-        if (lane == 0) it = atomicAdd(work, 1ULL);
-        it = __shfl_sync(0xFFFFFFFFu, it, 0);
-        if (it >= chunks * (unsigned long long)W) break;
-        const unsigned long long c = it / (unsigned long long)W;
-        const int w = (int)(it % (unsigned long long)W);
-        const int64_t k = (int64_t)c * 32 + lane;
-        const bool valid = k < n;
-        const int64_t i = valid ? (order ? (int64_t)__ldg(&order[k]) : k) : 0;
-        float px = 0.0f, py = 0.0f, pz = 0.0f, nx = 0.0f, ny = 0.0f, nz = 1.0f;
-        if (valid) {
-            px = P[3 * i]; py = P[3 * i + 1]; pz = P[3 * i + 2];
-            nx = Nrm[3 * i]; ny = Nrm[3 * i + 1]; nz = Nrm[3 * i + 2];
-        }
-        const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
-        const Onb b = make_onb(nx, ny, nz);
-        uint32_t word = 0;
-        const int nbits = min(32, n_dirs - 32 * w);
-        for (int bit = 0; bit < nbits; ++bit) {
-            if (!valid) break;
-            const float4 h = __ldg(&dirs[32 * w + bit]);
-            float dx, dy, dz;
-            local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
-            Ray r;
-            setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-            const TraceOut tr = trace_any<false, kWide>(nodes, tris, r, max_steps);
-            acc.retests += tr.retests;
-            acc.overflow += tr.overflow;
-            acc.amb += (tr.flags >> 1) & 1;
-            if ((tr.flags & 1) == 0) word |= 1u << bit;
-        }
-        if (valid) {
-            bits[i * W + w] = word;
-            atomicAdd(&count[i], __popc(word));
-            acc.rays += nbits;
-        }
-    }
-    warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow);
-}
-
 template <bool kStats, bool kWide>
 __global__ void __launch_bounds__(128, RC_HEMI_MIN_BLOCKS)
 k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
              const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
              const int32_t* __restrict__ order, const float4* __restrict__ tdirs, int n_dirs, double eps,
              uint32_t* __restrict__ bits, int32_t* __restrict__ count, unsigned long long* counters,
-             unsigned long long* work, int64_t n_whole, int splits)
+             unsigned long long* work, int64_t n_whole, int splits, long long* relist, long long relist_cap)
 {
     extern __shared__ uint32_t s_rows[];
     const int lane = threadIdx.x & 31;
@@ -1042,7 +592,7 @@ k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
         }
         const int64_t i = order ? (int64_t)__ldg(&order[r]) : r;
         cast_point<kStats, kWide>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits, count,
-                                  acc, t0, t1);
+                                  acc, t0, t1, relist, relist_cap, counters ? counters + 6 : nullptr);
     }
     warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow, acc.nvis, acc.ntri);
 }
@@ -1155,197 +705,6 @@ k_hemisphere_update(const float4* __restrict__ nodes, const float4* __restrict__
         for (int off = 16; off; off >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, off);
         if (lane == 0) count[i] = cnt;
         __syncwarp();
-    }
-    warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow);
-}
-
-// ---------------------------------------------------------------------------
-// Hemispherical cast with dynamic ray fetch (after Aila and Laine, HPG 2009):
-// the same rays and decisions as k_hemisphere, but a lane whose ray has
-// finished takes the next ray at once instead of waiting for the rest of its
-// tile.  A warp owns up to two points ("slots") at a time: it hands out the
-// current point's rays in tile order to idle lanes, opens the next point in
-// the free slot when the current one is exhausted, and writes a slot's bits
-// (shared-memory row, canonical order) and count once all of its rays are
-// done.  Each outer iteration every busy lane walks interior nodes until it
-// reaches a leaf (or finishes), then all such lanes test their leaves
-// together ("while-while").
-// ---------------------------------------------------------------------------
-#ifndef RC_DYN_MIN_BLOCKS
-#define RC_DYN_MIN_BLOCKS 6
-#endif
-
-struct SlotInfo {
-    long long i;               // point index
-    float ox, oy, oz;          // offset origin
-    float nx, ny, nz;          // normal
-    float t1x, t1y, t1z, t2x, t2y, t2z;
-    int pending;               // rays handed out and not finished
-    int count;                 // unobstructed rays so far
-};
-
-__global__ void __launch_bounds__(128, RC_DYN_MIN_BLOCKS)
-k_hemisphere_dyn(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps,
-                 float scene_maxabs, const float* __restrict__ P, const float* __restrict__ Nrm, int64_t n,
-                 const int32_t* __restrict__ order, const float4* __restrict__ tdirs, int n_dirs, double eps,
-                 uint32_t* __restrict__ bits, int32_t* __restrict__ count, unsigned long long* counters,
-                 unsigned long long* work)
-{
-    extern __shared__ uint32_t s_mem[];
-    __shared__ SlotInfo s_slot[4][2];
-    const unsigned FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int W = (n_dirs + 31) >> 5;
-    uint32_t* rows = s_mem + wid * (2 * W);
-    SlotInfo* si = s_slot[wid];
-
-    // per-lane ray state
-    bool has = false;
-    int slot = 0, j = 0, cur = 0, sp = 0, steps = 0;
-    bool amb = false, ambhit = false;
-    Ray r;
-    int stack[kStack];
-    // warp-uniform fetch state
-    int fetch = -1, next_k = 0;
-    bool live0 = false, live1 = false, exhausted = false;
-    CastAcc acc;
-
-    for (;;) {
-        // retire slots whose rays are all handed out and finished
-        __syncwarp();
-        for (int s2 = 0; s2 < 2; ++s2) {
-            const bool live = s2 ? live1 : live0;
-            if (!live || (s2 == fetch && next_k < n_dirs) || si[s2].pending != 0) continue;
-            const long long i = si[s2].i;
-            for (int w = lane; w < W; w += 32) bits[i * W + w] = rows[s2 * W + w];
-            if (lane == 0) count[i] = si[s2].count;
-            if (s2) live1 = false; else live0 = false;
-            if (s2 == fetch) fetch = -1;
-        }
-        __syncwarp();
-        // hand out rays to idle lanes, opening new points as needed
-        unsigned need = __ballot_sync(FULL, !has);
-        while (need && !exhausted) {
-            if (fetch < 0 || next_k == n_dirs) {
-                const int f = !live0 ? 0 : (!live1 ? 1 : -1);
-                if (f < 0) break;                     // both slots busy: traverse first
-                unsigned long long kk = 0;
-                if (lane == 0) kk = atomicAdd(work, 1ULL);
-                kk = __shfl_sync(FULL, kk, 0);
-                if (kk >= (unsigned long long)n) { exhausted = true; break; }
-                if (lane == 0) {
-                    const long long i = order ? (long long)__ldg(&order[kk]) : (long long)kk;
-                    const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
-                    const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
-                    const Onb b = make_onb(nx, ny, nz);
-                    SlotInfo& q = si[f];
-                    q.i = i;
-                    q.ox = offset_coord(px, nx, eps);
-                    q.oy = offset_coord(py, ny, eps);
-                    q.oz = offset_coord(pz, nz, eps);
-                    q.nx = nx; q.ny = ny; q.nz = nz;
-                    q.t1x = b.t1x; q.t1y = b.t1y; q.t1z = b.t1z;
-                    q.t2x = b.t2x; q.t2y = b.t2y; q.t2z = b.t2z;
-                    q.pending = 0;
-                    q.count = 0;
-                }
-                for (int w = lane; w < W; w += 32) rows[f * W + w] = 0u;
-                if (f) live1 = true; else live0 = true;
-                fetch = f;
-                next_k = 0;
-                __syncwarp();
-            }
-            const int take = min(__popc(need), n_dirs - next_k);
-            const int rank = __popc(need & ((1u << lane) - 1u));
-            if (!has && rank < take) {
-                const SlotInfo& q = si[fetch];
-                const float4 h = __ldg(&tdirs[next_k + rank]);
-                j = __float_as_int(h.w);
-                Onb b;
-                b.t1x = q.t1x; b.t1y = q.t1y; b.t1z = q.t1z;
-                b.t2x = q.t2x; b.t2y = q.t2y; b.t2z = q.t2z;
-                float dx, dy, dz;
-                local_to_world(b, q.nx, q.ny, q.nz, h.x, h.y, h.z, dx, dy, dz);
-                setup_ray(r, q.ox, q.oy, q.oz, dx, dy, dz, scene_maxabs);
-                slot = fetch;
-                cur = 0;
-                sp = 0;
-                steps = 0;
-                amb = ambhit = false;
-                has = true;
-            }
-            if (lane == 0) si[fetch].pending += take;
-            next_k += take;
-            __syncwarp();
-            need = __ballot_sync(FULL, !has);
-        }
-        if (!__any_sync(FULL, has)) {
-            if (exhausted && !live0 && !live1) break;
-            continue;
-        }
-        // walk interior nodes until a leaf (or the end of the walk)
-        bool fin = false, blocked = false;
-        if (has) {
-            while (cur >= 0) {
-                if (++steps > max_steps) { ++acc.overflow; fin = true; blocked = true; break; }
-                const float4 n0 = __ldg(&nodes[4 * cur + 0]);
-                const float4 n1 = __ldg(&nodes[4 * cur + 1]);
-                const float4 n2 = __ldg(&nodes[4 * cur + 2]);
-                const float4 n3 = __ldg(&nodes[4 * cur + 3]);
-                bool h0, h1;
-                float t0, t1;
-                box2(r, n0, n1, n2, h0, h1, t0, t1);
-                const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-                if (h0 && h1) {
-                    const bool first0 = t0 <= t1;
-                    if (sp >= kStack) { ++acc.overflow; fin = true; blocked = true; break; }
-                    stack[sp++] = first0 ? c1 : c0;
-                    cur = first0 ? c0 : c1;
-                } else if (h0) {
-                    cur = c0;
-                } else if (h1) {
-                    cur = c1;
-                } else if (sp == 0) {
-                    fin = true;
-                    break;
-                } else {
-                    cur = stack[--sp];
-                }
-            }
-        }
-        // test the leaves the lanes have reached
-        if (has && !fin) {
-            const int v = -1 - cur;
-            const int first = v >> 3, cnt = (v & 7) + 1;
-            for (int k = 0; k < cnt && !fin; ++k) {
-                const float4* t = tris + 3 * (first + k);
-                const float4 v0 = __ldg(t), v1 = __ldg(t + 1), v2 = __ldg(t + 2);
-                const int s = tri_test32(r, v0, v1, v2);
-                if (s == kHit) { fin = true; blocked = true; break; }
-                if (s == kUnsure) {
-                    ++acc.retests;
-                    const Pair64 pr = retest64(r, v0, v1, v2);
-                    if (pr.state == kHit) { fin = true; blocked = true; break; }
-                    if (pr.state == kUnsure) { amb = true; ambhit |= pr.hit64; }
-                }
-            }
-            if (!fin) {
-                if (sp == 0) fin = true;
-                else cur = stack[--sp];
-            }
-        }
-        // retire finished rays
-        if (has && fin) {
-            const bool hit = blocked || ambhit;
-            if (!blocked && amb) ++acc.amb;
-            if (!hit) {
-                atomicOr(&rows[slot * W + (j >> 5)], 1u << (j & 31));
-                atomicAdd(&si[slot].count, 1);
-            }
-            atomicSub(&si[slot].pending, 1);
-            ++acc.rays;
-            has = false;
-        }
     }
     warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow);
 }
@@ -1620,7 +979,7 @@ rc_status point_order(rc_bvh h, const float* P, int64_t n, int32_t* order, cudaS
 
 rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
                             uint32_t* bits, int32_t* count, unsigned long long* counters, bool stats,
-                            cudaStream_t s)
+                            cudaStream_t s, long long* relist, long long relist_cap)
 {
     unsigned long long* work = nullptr;
     unsigned long long* work_alloc = nullptr;
@@ -1652,54 +1011,7 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
         RC_CUDA(cudaFuncSetAttribute(k_hemisphere<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     const float4* tree = wide ? h->wnodes : h->nodes;
-    if (p->fetch_mode == 4 && !stats && work && wide) {
-        const size_t wsmem = (size_t)(threads / 32) * ((((p->n_dirs + 31) / 32) + 1) & ~1) * sizeof(uint32_t) +
-                             (size_t)(threads / 32) * kStack4 * sizeof(int2);
-        if (wsmem > 48 * 1024)
-            RC_CUDA(cudaFuncSetAttribute(k_hemisphere_wp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem));
-        int64_t wblocks = (int64_t)sm_count() * (p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_WP_MIN_BLOCKS);
-        if (wblocks > need) wblocks = need;
-        if (wblocks < 1) wblocks = 1;
-        k_hemisphere_wp<<<(unsigned)wblocks, threads, wsmem, s>>>(h->wnodes, h->tris, max_steps(h), h->scene_maxabs,
-                                                                 P, N, n, order, h->tdirs, p->n_dirs,
-                                                                 p->origin_offset, bits, count, counters, work);
-    } else if (p->fetch_mode == 3 && !stats && work) {
-        RC_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * n, s));
-        const int64_t chunks = (n + 31) / 32;
-        int64_t pblocks = (int64_t)sm_count() * (p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_HEMI_MIN_BLOCKS);
-        const int64_t pneed = (chunks * ((p->n_dirs + 31) / 32) * 32 + threads - 1) / threads;
-        if (pblocks > pneed) pblocks = pneed;
-        if (pblocks < 1) pblocks = 1;
-        if (wide)
-            k_hemisphere_pkt<true><<<(unsigned)pblocks, threads, 0, s>>>(tree, h->tris, max_steps(h),
-                                                                        h->scene_maxabs, P, N, n, order, h->dirs,
-                                                                        p->n_dirs, p->origin_offset, bits, count,
-                                                                        counters, work);
-        else
-            k_hemisphere_pkt<false><<<(unsigned)pblocks, threads, 0, s>>>(tree, h->tris, max_steps(h),
-                                                                         h->scene_maxabs, P, N, n, order, h->dirs,
-                                                                         p->n_dirs, p->origin_offset, bits, count,
-                                                                         counters, work);
-    } else if (p->fetch_mode == 2 && !stats && work && wide) {
-        if (smem > 48 * 1024)
-            RC_CUDA(cudaFuncSetAttribute(k_hemisphere_flat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int64_t fblocks = (int64_t)sm_count() * (p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_FLAT_MIN_BLOCKS);
-        if (fblocks > need) fblocks = need;
-        if (fblocks < 1) fblocks = 1;
-        k_hemisphere_flat<<<(unsigned)fblocks, threads, smem, s>>>(h->wnodes, h->tris, max_steps(h), h->scene_maxabs,
-                                                                   P, N, n, order, h->tdirs, p->n_dirs,
-                                                                   p->origin_offset, bits, count, counters, work);
-    } else if (p->fetch_mode == 1 && !stats && work && !wide) {
-        const size_t dsmem = 2 * smem;
-        if (dsmem > 48 * 1024)
-            RC_CUDA(cudaFuncSetAttribute(k_hemisphere_dyn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
-        int64_t dblocks = (int64_t)sm_count() * (p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_DYN_MIN_BLOCKS);
-        if (dblocks > need) dblocks = need;
-        if (dblocks < 1) dblocks = 1;
-        k_hemisphere_dyn<<<(unsigned)dblocks, threads, dsmem, s>>>(h->nodes, h->tris, max_steps(h), h->scene_maxabs,
-                                                                   P, N, n, order, h->tdirs, p->n_dirs,
-                                                                   p->origin_offset, bits, count, counters, work);
-    } else {
+    {
         // the last points (RC_TAIL_POINTS per resident warp) are cast in parts;
         // with a grid sized to the work (one item per warp) the parts are the
         // highest blocks, which the block scheduler starts last
@@ -1721,7 +1033,7 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
     k_hemisphere<ST, WD><<<(unsigned)blocks, threads, smem, s>>>(tree, h->tris, max_steps(h), h->scene_maxabs, \
                                                                  P, N, n, order, h->tdirs, p->n_dirs,         \
                                                                  p->origin_offset, bits, count, counters, work, \
-                                                                 n - n_split, splits)
+                                                                 n - n_split, splits, relist, relist_cap)
         if (stats && wide) RC_HEMI(true, true);
         else if (stats) RC_HEMI(true, false);
         else if (wide) RC_HEMI(false, true);

@@ -1,6 +1,6 @@
 """Host logic of the benchmark that needs no GPU: the code-only hash that
-decides whether the committed DRAM traffic belongs to the current traversal
-sources, and the lookup of that traffic."""
+decides whether a committed ncu summary belongs to the current traversal
+sources, and the lookup of its per-ray figures."""
 import os
 import sys
 
@@ -29,10 +29,12 @@ def test_comment_edits_keep_the_hash_code_edits_change_it():
     assert bench._code_only(a) == bench._code_only(b) != bench._code_only(c)
 
 
-def test_committed_traffic_matches_the_current_sources():
-    # the committed profile was taken on the current traversal sources, so
-    # the benchmark reports its DRAM bytes (a source edit would make it stale)
-    traffic, src = bench.committed_traffic("prismatic")
-    assert src in ("ncu", "stale")
-    if src == "ncu":
-        assert traffic > 0
+def test_committed_profile_lookup():
+    # a committed summary is used only when it was taken on the current
+    # traversal sources; otherwise the benchmark says why it has no figures
+    for w in ("impeller", "prismatic"):
+        prof = bench.committed_profile(w)
+        assert "source" in prof
+        if prof["source"].startswith("ncu, profiles/"):
+            assert prof["dram_bytes_per_ray"] is not None and prof["dram_bytes_per_ray"] > 0
+            assert 0 < prof["lanes_per_inst"] <= 32

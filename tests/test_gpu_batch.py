@@ -121,10 +121,9 @@ def test_single_part_knobs_do_not_change_results(rc):
     res = []
     for order in (0, 1):
         for tile in (0, 1):
-            for per_sm, fetch, launch, width in ((0, 0, 0, 0), (4, 0, 0, 0), (0, 1, 0, 2), (3, 1, 0, 2),
-                                                 (0, 0, 1, 0), (0, 0, 0, 2), (0, 0, 1, 2)):
+            for per_sm, launch, width in ((0, 0, 0), (4, 0, 0), (3, 0, 2), (0, 1, 0), (0, 0, 2), (0, 1, 2)):
                 q = rc.rc_params_default(n_dirs=N, point_order=order, tile_mode=tile, blocks_per_sm=per_sm,
-                                         fetch_mode=fetch, launch_mode=launch, tree_width=width)
+                                         launch_mode=launch, tree_width=width)
                 bits = torch.zeros((n, (N + 31) // 32), dtype=torch.int32, device="cuda")
                 cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
                 rc.rc_hemisphere_cast(bvh.h, P, Nn, q, bits, cnt)
