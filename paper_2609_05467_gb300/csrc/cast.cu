@@ -344,12 +344,21 @@ __device__ __forceinline__ SlabRay make_slab_ray(const Ray& r, float M)
 
 // Slab test of the four children of wide node nd: d[k] = entry distance of a
 // hit child (else +inf), c[k] = child index; returns the number of hits.
+// kShared: nd is a frontier group in shared memory (the same layout).
+template <bool kShared = false>
+__device__ __forceinline__ float4 node_ld(const float4* p)
+{
+    if (kShared) return *p;
+    return __ldg(p);
+}
+
+template <bool kShared = false>
 __device__ __forceinline__ int slab4(const float4* __restrict__ nd, const SlabRay& s, float d[4], int c[4])
 {
-    const float4 nxv = __ldg(nd + 0 + s.offx), fxv = __ldg(nd + 1 - s.offx);
-    const float4 nyv = __ldg(nd + 2 + s.offy), fyv = __ldg(nd + 3 - s.offy);
-    const float4 nzv = __ldg(nd + 4 + s.offz), fzv = __ldg(nd + 5 - s.offz);
-    const float4 ci = __ldg(nd + 6);
+    const float4 nxv = node_ld<kShared>(nd + 0 + s.offx), fxv = node_ld<kShared>(nd + 1 - s.offx);
+    const float4 nyv = node_ld<kShared>(nd + 2 + s.offy), fyv = node_ld<kShared>(nd + 3 - s.offy);
+    const float4 nzv = node_ld<kShared>(nd + 4 + s.offz), fzv = node_ld<kShared>(nd + 5 - s.offz);
+    const float4 ci = node_ld<kShared>(nd + 6);
     const float nx[4] = {nxv.x, nxv.y, nxv.z, nxv.w}, fx[4] = {fxv.x, fxv.y, fxv.z, fxv.w};
     const float ny[4] = {nyv.x, nyv.y, nyv.z, nyv.w}, fy[4] = {fyv.x, fyv.y, fyv.z, fyv.w};
     const float nz[4] = {nzv.x, nzv.y, nzv.z, nzv.w}, fz[4] = {fzv.x, fzv.y, fzv.z, fzv.w};
@@ -369,16 +378,152 @@ __device__ __forceinline__ int slab4(const float4* __restrict__ nd, const SlabRa
     return nh;
 }
 
+// ---------------------------------------------------------------------------
+// Per-point frontier of the 4-wide walk.  All hemisphere rays of a point
+// start at the same origin o, and a box that contains o is entered by every
+// one of them: its near slab distances are <= 0 and its far ones >= 0, and
+// the conservative margin only lowers the near and raises the far ones.  So
+// every ray's walk from the root visits the same nodes whose boxes contain o
+// (the origin set: the root and every child box containing o below it).
+// The warp finds that set once per point and keeps in shared memory what
+// each ray must still decide for itself: the triangles of the leaves whose
+// boxes contain o (local triangles), and the children of origin-set nodes
+// whose boxes do not contain o (the frontier, in the wide node's layout,
+// four entries per group).  A ray tests the local triangles, tests every
+// frontier box with its own slab test and walks the subtrees it enters:
+// exactly the triangles its walk from the root would test, so the same
+// decisions.  A local triangle wholly below the point's tangent plane is
+// dropped, because a hemisphere ray leaves that plane (d.n > 0 for every
+// direction of the set, N <= 65536) and meets no point of it at t > 0; that
+// exact FP64 test runs once per point.  A point whose frontier or local
+// triangles do not fit walks from the root instead.
+// ---------------------------------------------------------------------------
+constexpr int kFrontGroups = 12;   // frontier entries, four per group
+constexpr int kFrontTris = 12;     // local triangles kept per point
+constexpr int kStackF = kStack4 + 4 * kFrontGroups;
+
+struct Frontier {
+    float4 grp[kFrontGroups * 7];  // per group: lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of 4 entries, their codes
+    float4 tri[kFrontTris * 3];    // local triangle records
+    int ngroups, ntris, ok, nvis;
+};
+
+// n . (v - o) < 0 for the three vertices, in FP64: the differences of fp32
+// values are exact there and the products and sums round far below the
+// margin taken (4e-15 of the sum of the terms' magnitudes)
+__device__ __forceinline__ bool below_tangent(float4 v, float ox, float oy, float oz, float nx, float ny, float nz)
+{
+    const double a = (double)v.x - ox, b = (double)v.y - oy, c = (double)v.z - oz;
+    const double s = __dadd_rn(__dadd_rn(__dmul_rn((double)nx, a), __dmul_rn((double)ny, b)), __dmul_rn((double)nz, c));
+    const double m = fabs((double)nx * a) + fabs((double)ny * b) + fabs((double)nz * c);
+    return s < -4e-15 * m;
+}
+
+// Lane 0 of the warp: the origin set of o (a walk over the boxes that
+// contain o), its frontier and local triangles into *f.
+__device__ __noinline__ void build_frontier(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
+                                            int max_steps, float ox, float oy, float oz, float nx, float ny,
+                                            float nz, Frontier* f)
+{
+    int qs[kStack4];
+    int qsp = 0;
+    qs[qsp++] = 0;
+    int ne = 0, nt = 0, nvis = 0;
+    bool ok = true;
+    float* g = (float*)f->grp;
+    while (qsp > 0 && ok) {
+        if (++nvis > max_steps) { ok = false; break; }
+        const int cur = qs[--qsp];
+        const float4* nd = wnodes + 8 * (int64_t)cur;
+        const float4 lxv = __ldg(nd), hxv = __ldg(nd + 1), lyv = __ldg(nd + 2), hyv = __ldg(nd + 3);
+        const float4 lzv = __ldg(nd + 4), hzv = __ldg(nd + 5), civ = __ldg(nd + 6);
+        const float LX[4] = {lxv.x, lxv.y, lxv.z, lxv.w}, HX[4] = {hxv.x, hxv.y, hxv.z, hxv.w};
+        const float LY[4] = {lyv.x, lyv.y, lyv.z, lyv.w}, HY[4] = {hyv.x, hyv.y, hyv.z, hyv.w};
+        const float LZ[4] = {lzv.x, lzv.y, lzv.z, lzv.w}, HZ[4] = {hzv.x, hzv.y, hzv.z, hzv.w};
+        const int CI[4] = {__float_as_int(civ.x), __float_as_int(civ.y), __float_as_int(civ.z), __float_as_int(civ.w)};
+        for (int k = 0; k < 4 && ok; ++k) {
+            if (!(LX[k] <= HX[k])) continue;   // empty slot (its code -1 is also a leaf's)
+            const bool inside = LX[k] <= ox && ox <= HX[k] && LY[k] <= oy && oy <= HY[k] && LZ[k] <= oz &&
+                                oz <= HZ[k];
+            if (inside && CI[k] >= 0) {
+                if (qsp >= kStack4) { ok = false; break; }
+                qs[qsp++] = CI[k];
+            } else if (inside) {
+                const int v = -1 - CI[k], first = v >> 3, cnt = (v & 7) + 1;
+                for (int t = 0; t < cnt; ++t) {
+                    const float4* tp = tris + 3 * (int64_t)(first + t);
+                    const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+                    if (below_tangent(v0, ox, oy, oz, nx, ny, nz) && below_tangent(v1, ox, oy, oz, nx, ny, nz) &&
+                        below_tangent(v2, ox, oy, oz, nx, ny, nz))
+                        continue;
+                    if (nt >= kFrontTris) { ok = false; break; }
+                    f->tri[3 * nt] = v0;
+                    f->tri[3 * nt + 1] = v1;
+                    f->tri[3 * nt + 2] = v2;
+                    ++nt;
+                }
+            } else {
+                if (ne >= 4 * kFrontGroups) { ok = false; break; }
+                float* gp = g + 28 * (ne >> 2) + (ne & 3);
+                gp[0] = LX[k]; gp[4] = HX[k]; gp[8] = LY[k]; gp[12] = HY[k]; gp[16] = LZ[k]; gp[20] = HZ[k];
+                gp[24] = __int_as_float(CI[k]);
+                ++ne;
+            }
+        }
+    }
+    // the last group's unused slots: empty boxes, which no slab test enters
+    for (int e = ne; e < ((ne + 3) & ~3); ++e) {
+        float* gp = g + 28 * (e >> 2) + (e & 3);
+        gp[0] = INFINITY; gp[4] = -INFINITY; gp[8] = INFINITY; gp[12] = -INFINITY; gp[16] = INFINITY;
+        gp[20] = -INFINITY;
+        gp[24] = __int_as_float(-1);
+    }
+    f->ngroups = (ne + 3) >> 2;
+    f->ntris = nt;
+    f->ok = ok ? 1 : 0;
+    f->nvis = nvis;
+}
+
 template <bool kStats>
 __device__ __forceinline__ TraceOut trace4(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
-                                           const Ray& r, int max_steps)
+                                           const Ray& r, int max_steps, const Frontier* front = nullptr)
 {
     TraceOut out = {0, 0, 0, 0, 0};
-    int stack[kStack4];
+    int stack[kStackF];
     int sp = 0;
     int cur = 0;
     bool amb = false, ambhit = false;
     const SlabRay sr = make_slab_ray(r, r.rs);
+    if (front) {
+        // the point's local triangles, then its frontier boxes: the entered
+        // ones go on the stack, the deepest (nearest the origin) on top
+        for (int t = 0; t < front->ntris; ++t) {
+            const float4 v0 = front->tri[3 * t], v1 = front->tri[3 * t + 1], v2 = front->tri[3 * t + 2];
+            if (kStats) ++out.tris;
+            const int st = tri_test32(r, v0, v1, v2);
+            if (st == kHit) { out.flags = 1; return out; }
+            if (st == kUnsure) {
+                ++out.retests;
+                const Pair64 p = retest64(r, v0, v1, v2);
+                if (p.state == kHit) { out.flags = 1; return out; }
+                if (p.state == kUnsure) { amb = true; ambhit |= p.hit64; }
+            }
+        }
+        for (int gi = 0; gi < front->ngroups; ++gi) {
+            if (kStats) ++out.nodes;
+            float d[4];
+            int c[4];
+            slab4<true>(front->grp + 7 * gi, sr, d, c);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (d[k] != INFINITY) stack[sp++] = c[k];
+        }
+        if (sp == 0) {
+            out.flags = (ambhit ? 1 : 0) | (amb ? 2 : 0);
+            return out;
+        }
+        cur = stack[--sp];
+    }
     for (int steps = 0;; ++steps) {
         if (steps > max_steps) { out.overflow = 1; out.flags = 1; return out; }
         if (cur >= 0) {
@@ -401,7 +546,7 @@ __device__ __forceinline__ TraceOut trace4(const float4* __restrict__ wnodes, co
             // than the full network, and no more nodes visited)
             RC_CSWAP(0, 1) RC_CSWAP(2, 3) RC_CSWAP(0, 2)
 #undef RC_CSWAP
-            if (sp + nh - 1 > kStack4) { out.overflow = 1; out.flags = 1; return out; }
+            if (sp + nh - 1 > kStackF) { out.overflow = 1; out.flags = 1; return out; }
             if (d[3] != INFINITY) stack[sp++] = c[3];
             if (d[2] != INFINITY) stack[sp++] = c[2];
             if (d[1] != INFINITY) stack[sp++] = c[1];
@@ -433,9 +578,9 @@ __device__ __forceinline__ TraceOut trace4(const float4* __restrict__ wnodes, co
 
 template <bool kStats, bool kWide>
 __device__ __forceinline__ TraceOut trace_any(const float4* __restrict__ nodes, const float4* __restrict__ tris,
-                                              const Ray& r, int max_steps)
+                                              const Ray& r, int max_steps, const Frontier* front = nullptr)
 {
-    if (kWide) return trace4<kStats>(nodes, tris, r, max_steps);
+    if (kWide) return trace4<kStats>(nodes, tris, r, max_steps, front);
     return trace<kStats>(nodes, tris, r, max_steps);
 }
 
@@ -495,16 +640,20 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
                                            const float4* __restrict__ tdirs, int W, double eps, uint32_t* row,
                                            uint32_t* __restrict__ bits, int32_t* __restrict__ count, CastAcc& acc,
                                            int t0 = 0, int t1 = -1, long long* relist = nullptr,
-                                           long long relist_cap = 0, unsigned long long* relist_ctr = nullptr)
+                                           long long relist_cap = 0, unsigned long long* relist_ctr = nullptr,
+                                           Frontier* front = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const bool whole = t1 < 0;
     if (whole) t1 = W;
     for (int w = lane; w < W; w += 32) row[w] = 0u;
-    __syncwarp();
     const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
     const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
     const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
+    if (kWide && front && lane == 0) build_frontier(nodes, tris, max_steps, ox, oy, oz, nx, ny, nz, front);
+    __syncwarp();
+    const Frontier* fr = kWide && front && front->ok ? front : nullptr;
+    if (kStats && front && lane == 0) acc.nvis += front->nvis;
     const Onb b = make_onb(nx, ny, nz);
     int cnt = 0;
     for (int t = t0; t < t1; ++t) {
@@ -517,7 +666,7 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
         local_to_world(b, nx, ny, nz, h.x, h.y, h.z, dx, dy, dz);
         Ray r;
         setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
-        const TraceOut tr = trace_any<kStats, kWide>(nodes, tris, r, max_steps);
+        const TraceOut tr = trace_any<kStats, kWide>(nodes, tris, r, max_steps, fr);
         acc.retests += tr.retests;
         acc.overflow += tr.overflow;
         acc.amb += (j >= 0) & ((tr.flags >> 1) & 1);
@@ -549,6 +698,17 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
     acc.rays += (t1 - t0) - (t1 == W && __float_as_int(__ldg(&tdirs[32 * (W - 1) + lane]).w) < 0 ? 1 : 0);
 }
 
+// Dynamic shared memory of the point casts: each warp's bit row of W words,
+// then (4-wide tree) each warp's frontier, 16-byte aligned.
+__host__ __device__ __forceinline__ size_t rows_bytes(int warps, int W)
+{
+    return ((size_t)warps * W * sizeof(uint32_t) + 15) & ~(size_t)15;
+}
+__host__ __device__ __forceinline__ size_t cast_smem(int warps, int W, bool wide)
+{
+    return rows_bytes(warps, W) + (wide ? (size_t)warps * sizeof(Frontier) : 0);
+}
+
 template <bool kStats, bool kWide>
 __global__ void __launch_bounds__(128, RC_HEMI_MIN_BLOCKS)
 k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, int max_steps, float scene_maxabs,
@@ -557,10 +717,11 @@ k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
              uint32_t* __restrict__ bits, int32_t* __restrict__ count, unsigned long long* counters,
              unsigned long long* work, int64_t n_whole, int splits, long long* relist, long long relist_cap)
 {
-    extern __shared__ uint32_t s_rows[];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
     const int lane = threadIdx.x & 31;
     const int W = (n_dirs + 31) >> 5;
-    uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
+    uint32_t* row = (uint32_t*)s_dyn + (threadIdx.x >> 5) * W;
+    Frontier* front = kWide ? (Frontier*)(s_dyn + rows_bytes(blockDim.x >> 5, W)) + (threadIdx.x >> 5) : nullptr;
     CastAcc acc;
     // With a work counter the warps take work until none is left: the first
     // n_whole points of the processing order whole, then the last n - n_whole
@@ -592,7 +753,7 @@ k_hemisphere(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
         }
         const int64_t i = order ? (int64_t)__ldg(&order[r]) : r;
         cast_point<kStats, kWide>(nodes, tris, max_steps, scene_maxabs, P, Nrm, i, tdirs, W, eps, row, bits, count,
-                                  acc, t0, t1, relist, relist_cap, counters ? counters + 6 : nullptr);
+                                  acc, t0, t1, relist, relist_cap, counters ? counters + 6 : nullptr, front);
     }
     warp_add_counters(counters, acc.rays, acc.amb, acc.retests, acc.overflow, acc.nvis, acc.ntri);
 }
@@ -731,10 +892,11 @@ __global__ void __launch_bounds__(128, RC_BATCH_MIN_BLOCKS)
 k_batch(const BatchPart* __restrict__ parts, int n_parts, long long n_items, int ppi,
         const float4* __restrict__ tdirs, int n_dirs, double eps, unsigned long long* work)
 {
-    extern __shared__ uint32_t s_rows[];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
     const int lane = threadIdx.x & 31;
     const int W = (n_dirs + 31) >> 5;
-    uint32_t* row = s_rows + (threadIdx.x >> 5) * W;
+    uint32_t* row = (uint32_t*)s_dyn + (threadIdx.x >> 5) * W;
+    Frontier* front = kWide ? (Frontier*)(s_dyn + rows_bytes(blockDim.x >> 5, W)) + (threadIdx.x >> 5) : nullptr;
     CastAcc acc;
     int cur = -1;
     for (;;) {
@@ -757,7 +919,7 @@ k_batch(const BatchPart* __restrict__ parts, int n_parts, long long n_items, int
         for (long long q = q0; q < q1; ++q) {
             const int64_t i = bp.order ? (int64_t)__ldg(&bp.order[q]) : (int64_t)q;
             cast_point<kStats, kWide>(bp.nodes, bp.tris, bp.max_steps, bp.scene_maxabs, bp.P, bp.N, i, tdirs, W,
-                                      eps, row, bp.bits, bp.count, acc);
+                                      eps, row, bp.bits, bp.count, acc, 0, -1, nullptr, 0, nullptr, front);
         }
     }
     if (cur >= 0) flush_part_counters(parts[cur].counters, acc);
@@ -1002,8 +1164,8 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
     if (blocks < 1) blocks = 1;
     if (blocks > 0x7FFFFFFF) return set_error(RC_E_UNSUPPORTED, "too many points for one launch");
     if (p->launch_mode == 1) work = nullptr;
-    const size_t smem = (size_t)(threads / 32) * ((p->n_dirs + 31) / 32) * sizeof(uint32_t);
     const bool wide = use_wide(p);
+    const size_t smem = cast_smem(threads / 32, (p->n_dirs + 31) / 32, wide);
     if (smem > 48 * 1024) {
         RC_CUDA(cudaFuncSetAttribute(k_hemisphere<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         RC_CUDA(cudaFuncSetAttribute(k_hemisphere<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1236,7 +1398,7 @@ rc_status launch_batch(const BatchPart* d_parts, int n_parts, long long n_items,
                        const rc_params* p, unsigned long long* work, cudaStream_t s)
 {
     const int threads = 128;
-    const size_t smem = (size_t)(threads / 32) * ((p->n_dirs + 31) / 32) * sizeof(uint32_t);
+    const size_t smem = cast_smem(threads / 32, (p->n_dirs + 31) / 32, use_wide(p));
     const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_HEMI_MIN_BLOCKS;
     int64_t blocks = (int64_t)sm_count() * per_sm;
     const int64_t need = (n_items * 32 + threads - 1) / threads;
@@ -1254,7 +1416,7 @@ rc_status launch_batch(const BatchPart* d_parts, int n_parts, long long n_items,
 
 rc_status prepare_batch_kernel(int n_dirs)
 {
-    const size_t smem = (size_t)4 * ((n_dirs + 31) / 32) * sizeof(uint32_t);
+    const size_t smem = cast_smem(4, (n_dirs + 31) / 32, true);
     if (smem > 48 * 1024) {
         RC_CUDA(cudaFuncSetAttribute(k_batch<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         RC_CUDA(cudaFuncSetAttribute(k_batch<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
