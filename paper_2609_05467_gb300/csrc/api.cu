@@ -25,7 +25,6 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
                             cudaStream_t s, long long* relist = nullptr, long long relist_cap = 0);
 rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
                             uint8_t* mask, float* travel, unsigned long long* counters, cudaStream_t s);
-rc_status frame_setup(rc_bvh h, const rc_params* p, FrameDev* d, cudaStream_t s);
 rc_status launch_classes(rc_bvh h, const uint8_t* mask, const float* travel, const int32_t* face, int64_t n,
                          const rc_params* p, uint8_t* cls, const double* frame_d, const double* fbox_d,
                          uint8_t* fixture, unsigned long long* hist, cudaStream_t s);

@@ -677,7 +677,10 @@ __device__ __forceinline__ void wide_write(float4* wnodes, int32_t w, const floa
     nd[4] = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
     nd[5] = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
     nd[6] = make_float4(__int_as_float(ix[0]), __int_as_float(ix[1]), __int_as_float(ix[2]), __int_as_float(ix[3]));
-    nd[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    // the binary nodes the children were made from (-1: empty slot), for
+    // the boxes of the same tree in another coordinate frame
+    nd[7] = make_float4(__int_as_float(nch > 0 ? ch[0] : -1), __int_as_float(nch > 1 ? ch[1] : -1),
+                        __int_as_float(nch > 2 ? ch[2] : -1), __int_as_float(nch > 3 ? ch[3] : -1));
 }
 
 // one level of the top of the tree: each queued binary node becomes a wide
@@ -777,8 +780,9 @@ __global__ void k_wide_small(int64_t T, const float* __restrict__ tbox, float4* 
     wnodes[5] = make_float4(hi[2], -I, -I, -I);
     wnodes[6] = make_float4(__int_as_float(-1 - (int)(T - 1)), __int_as_float(-1), __int_as_float(-1),
                             __int_as_float(-1));
-    wnodes[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    wnodes[7] = make_float4(__int_as_float(kAllTris), __int_as_float(-1), __int_as_float(-1), __int_as_float(-1));
     sc->wide_depth = 1;
+    sc->wide_nodes = 1;
 }
 
 __global__ void k_wide_init(int32_t* q_bin, int32_t* q_wide, int* counts)
@@ -1052,7 +1056,7 @@ __global__ void k_init_scalars(DevScalars* sc)
     sc->max_depth = 0;
     sc->pad = 0;
     sc->wide_depth = 0;
-    sc->pad2 = 0;
+    sc->wide_nodes = 0;
 }
 
 static rc_status init_scalars(DevScalars* sc, cudaStream_t s)
@@ -1235,8 +1239,113 @@ static rc_status build_wide(rc_bvh h, const float* tbox, cudaStream_t s)
                                              h->wnodes, h->sc, level);
         RC_LAUNCHED();
     }
+    RC_CUDA(cudaMemcpyAsync(&h->sc->wide_nodes, counts + 2, sizeof(int), cudaMemcpyDeviceToDevice, s));
     RC_CUDA(cudaFreeAsync(q, s));
     RC_CUDA(cudaFreeAsync(counts, s));
+    return RC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The 4-wide tree with its child boxes in the coordinates of a machining
+// frame (rows of M = the frame's columns): the same nodes, codes and
+// triangles; each box is the bounding box of the frame coordinates of its
+// triangles' vertices, evaluated in FP64 and rounded outward to fp32.  The
+// axis walk of the orthogonal cast tests these boxes (its rays run along a
+// frame axis) and still tests triangles in world coordinates.
+// ---------------------------------------------------------------------------
+__global__ void k_frame_leaf_boxes(const float* __restrict__ V, const int32_t* __restrict__ F,
+                                   const int32_t* __restrict__ order, int64_t T, int64_t nV, int64_t n_int,
+                                   FrameArgs fa, float* __restrict__ nbox_f)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= T) return;
+    const int32_t f = order[k];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (f >= 0 && f < T)
+        for (int a = 0; a < 3; ++a) {
+            const int64_t v = F[3 * (int64_t)f + a];
+            if (v < 0 || v >= nV) continue;
+            const double x = V[3 * v], y = V[3 * v + 1], z = V[3 * v + 2];
+            for (int j = 0; j < 3; ++j) {
+                // frame coordinate j: column j of the row-major frame
+                const double q = __dadd_rn(__dadd_rn(__dmul_rn(x, (double)fa.f[j]), __dmul_rn(y, (double)fa.f[3 + j])),
+                                           __dmul_rn(z, (double)fa.f[6 + j]));
+                lo[j] = fmin(lo[j], q);
+                hi[j] = fmax(hi[j], q);
+            }
+        }
+    float* b = nbox_f + 6 * (n_int + k);
+    for (int j = 0; j < 3; ++j) {
+        b[j] = __double2float_rd(lo[j]);
+        b[3 + j] = __double2float_ru(hi[j]);
+    }
+}
+
+__global__ void k_frame_pack(const float4* __restrict__ wnodes, int64_t n_int, int64_t T,
+                             const DevScalars* __restrict__ sc, const float* __restrict__ nbox_f,
+                             const float* __restrict__ all_box, float4* __restrict__ ftree)
+{
+    const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w >= sc->wide_nodes || w >= n_int) return;
+    const float4* nd = wnodes + 8 * w;
+    const float4 idv = nd[7];
+    const int32_t ids[4] = {__float_as_int(idv.x), __float_as_int(idv.y), __float_as_int(idv.z), __float_as_int(idv.w)};
+    float lo[3][4], hi[3][4];
+    for (int k = 0; k < 4; ++k) {
+        const float* b = nullptr;
+        if (ids[k] == kAllTris) b = all_box;
+        else if (ids[k] >= 0 && ids[k] < n_int + T) b = nbox_f + 6 * (int64_t)ids[k];
+        for (int a = 0; a < 3; ++a) {
+            lo[a][k] = b ? b[a] : INFINITY;
+            hi[a][k] = b ? b[3 + a] : -INFINITY;
+        }
+    }
+    float4* o = ftree + 8 * w;
+    for (int a = 0; a < 3; ++a) {
+        o[2 * a] = make_float4(lo[a][0], lo[a][1], lo[a][2], lo[a][3]);
+        o[2 * a + 1] = make_float4(hi[a][0], hi[a][1], hi[a][2], hi[a][3]);
+    }
+    o[6] = nd[6];
+    o[7] = idv;
+}
+
+// box of all leaf slots [0, T) of nbox_f (tiny parts: the one-leaf root)
+__global__ void k_frame_all_box(const float* __restrict__ nbox_f, int64_t n_int, int64_t T, float* out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t k = 0; k < T; ++k)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fminf(lo[a], nbox_f[6 * (n_int + k) + a]);
+            hi[a] = fmaxf(hi[a], nbox_f[6 * (n_int + k) + 3 + a]);
+        }
+    for (int a = 0; a < 3; ++a) { out[a] = lo[a]; out[3 + a] = hi[a]; }
+}
+
+rc_status frame_tree(rc_bvh h, const float f9[9], float4* ftree, cudaStream_t s)
+{
+    const int64_t T = h->T, n_int = h->n_int;
+    FrameArgs fa;
+    for (int k = 0; k < 9; ++k) fa.f[k] = f9[k];
+    float* nbox_f = nullptr;
+    int32_t* visits = nullptr;
+    RC_CUDA(cudaMallocAsync(&nbox_f, sizeof(float) * 6 * (n_int + T + 1), s));
+    float* all_box = nbox_f + 6 * (n_int + T);
+    k_frame_leaf_boxes<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(h->V, h->F, h->order, T, h->nV, n_int, fa, nbox_f);
+    RC_LAUNCHED();
+    if (T > kLeafMax) {
+        RC_CUDA(cudaMallocAsync(&visits, sizeof(int32_t) * n_int, s));
+        RC_CUDA(cudaMemsetAsync(visits, 0, sizeof(int32_t) * n_int, s));
+        k_refit<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(T, n_int, h->parent, h->child, nbox_f, visits, h->sc);
+        RC_LAUNCHED();
+    } else {
+        k_frame_all_box<<<1, 32, 0, s>>>(nbox_f, n_int, T, all_box);
+        RC_LAUNCHED();
+    }
+    k_frame_pack<<<(unsigned)((n_int + 255) / 256), 256, 0, s>>>(h->wnodes, n_int, T, h->sc, nbox_f, all_box, ftree);
+    RC_LAUNCHED();
+    if (visits) RC_CUDA(cudaFreeAsync(visits, s));
+    RC_CUDA(cudaFreeAsync(nbox_f, s));
     return RC_OK;
 }
 

@@ -584,6 +584,135 @@ __device__ __forceinline__ TraceOut trace_any(const float4* __restrict__ nodes, 
     return trace<kStats>(nodes, tris, r, max_steps);
 }
 
+// ---------------------------------------------------------------------------
+// Axis rays (Section 3.2: rays along the six principal directions of the
+// machining frame).  Their walk tests the child boxes of the frame's own tree
+// (the same nodes with boxes in frame coordinates, FrameDev::tree) and the
+// triangles in world coordinates, exactly as the hemispherical walk does.
+// A ray o + t d, d = +-column k of the fp32 frame F, has frame coordinates
+// q(o) + t F^T d = q(o) +- t G[:, k] (G = F^T F): along k they grow (shrink)
+// with t, and across k they drift by at most t |G[j][k]|, a few ulps times
+// t for an fp32 frame.  Every hit lies in the part's box, so t is at most
+// (|o - c| + r) / |d| (c, r: the box's centre and half diagonal).  The ray
+// can therefore only meet triangles whose frame boxes overlap the band
+// [q_j(o) - tol_j, q_j(o) + tol_j] across k and lie on its side of q_k(o)
+// along k, where tol_j covers that drift, the 1e-9 R ambiguity band and the
+// FP64 rounding of q and of the boxes; the band is rounded outward to fp32.
+// For the identity frame the drift is zero and the tree is the world tree.
+// A ray along a wall 1e-4 mm above it, which the world boxes of a turned
+// part's wall triangles all admit, lies outside their frame boxes.
+// ---------------------------------------------------------------------------
+struct AxisRay {
+    float lo[3], hi[3];   // frame-coordinate band the ray can reach (+-inf on its far side along k)
+    int k;                // frame axis of the ray
+    int pos;              // 1: along +column k, 0: along -column k
+};
+
+__device__ __forceinline__ AxisRay make_axis_ray(const FrameDev& fd, int a, float ox, float oy, float oz, float rs)
+{
+    AxisRay ar;
+    const int k = a >> 1;
+    const bool pos = (a & 1) == 0;
+    const double x = ox, y = oy, z = oz;
+    double q[3], qs[3];
+    for (int j = 0; j < 3; ++j) {
+        q[j] = __dadd_rn(__dadd_rn(__dmul_rn(x, fd.frame[j]), __dmul_rn(y, fd.frame[3 + j])), __dmul_rn(z, fd.frame[6 + j]));
+        qs[j] = fabs(x * fd.frame[j]) + fabs(y * fd.frame[3 + j]) + fabs(z * fd.frame[6 + j]);
+    }
+    const double ex = x - fd.sc_c[0], ey = y - fd.sc_c[1], ez = z - fd.sc_c[2];
+    const double reach = 1.01 * (sqrt(ex * ex + ey * ey + ez * ez) + fd.sc_r) / sqrt(fd.gram[4 * k]) + 1e-6;
+    for (int j = 0; j < 3; ++j) {
+        double tol = 1e-9 * (double)rs + 1e-15 * (qs[j] + 4.0 * (double)rs + 1.0);
+        if (j != k) tol += reach * (fabs(fd.gram[3 * j + k]) + 1e-15);
+        double l = q[j] - tol, h = q[j] + tol;
+        if (j == k) {
+            if (pos) h = INFINITY;
+            else l = -INFINITY;
+        }
+        ar.lo[j] = __double2float_rd(l);
+        ar.hi[j] = __double2float_ru(h);
+    }
+    ar.k = k;
+    ar.pos = pos ? 1 : 0;
+    return ar;
+}
+
+template <bool kStats>
+__device__ __forceinline__ TraceOut trace_axis(const float4* __restrict__ ftree, const float4* __restrict__ tris,
+                                               const Ray& r, const AxisRay& ar, int max_steps)
+{
+    TraceOut out = {0, 0, 0, 0, 0};
+    int stack[kStack4];
+    int sp = 0;
+    int cur = 0;
+    bool amb = false, ambhit = false;
+    // near face of a child along the ray: lo of axis k going +, hi going -
+    const int near_off = 2 * ar.k + (ar.pos ? 0 : 1);
+    for (int steps = 0;; ++steps) {
+        if (steps > max_steps) { out.overflow = 1; out.flags = 1; return out; }
+        if (cur >= 0) {
+            if (kStats) ++out.nodes;
+            const float4* nd = ftree + 8 * (int64_t)cur;
+            const float4 lxv = __ldg(nd), hxv = __ldg(nd + 1), lyv = __ldg(nd + 2), hyv = __ldg(nd + 3);
+            const float4 lzv = __ldg(nd + 4), hzv = __ldg(nd + 5), ci = __ldg(nd + 6), ev = __ldg(nd + near_off);
+            const float LX[4] = {lxv.x, lxv.y, lxv.z, lxv.w}, HX[4] = {hxv.x, hxv.y, hxv.z, hxv.w};
+            const float LY[4] = {lyv.x, lyv.y, lyv.z, lyv.w}, HY[4] = {hyv.x, hyv.y, hyv.z, hyv.w};
+            const float LZ[4] = {lzv.x, lzv.y, lzv.z, lzv.w}, HZ[4] = {hzv.x, hzv.y, hzv.z, hzv.w};
+            const float E[4] = {ev.x, ev.y, ev.z, ev.w};
+            const int cc[4] = {__float_as_int(ci.x), __float_as_int(ci.y), __float_as_int(ci.z), __float_as_int(ci.w)};
+            float d[4];
+            int c[4];
+            int nh = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool hit = LX[q] <= ar.hi[0] && HX[q] >= ar.lo[0] && LY[q] <= ar.hi[1] && HY[q] >= ar.lo[1] &&
+                                 LZ[q] <= ar.hi[2] && HZ[q] >= ar.lo[2];
+                d[q] = hit ? (ar.pos ? E[q] : -E[q]) : INFINITY;
+                c[q] = cc[q];
+                nh += hit;
+            }
+            if (nh == 0) {
+                if (sp == 0) break;
+                cur = stack[--sp];
+                continue;
+            }
+#define RC_CSWAP(a, b)                                              \
+    if (d[b] < d[a]) {                                              \
+        const float td = d[a]; d[a] = d[b]; d[b] = td;              \
+        const int tc = c[a]; c[a] = c[b]; c[b] = tc;                \
+    }
+            RC_CSWAP(0, 1) RC_CSWAP(2, 3) RC_CSWAP(0, 2)
+#undef RC_CSWAP
+            if (sp + nh - 1 > kStack4) { out.overflow = 1; out.flags = 1; return out; }
+            if (d[3] != INFINITY) stack[sp++] = c[3];
+            if (d[2] != INFINITY) stack[sp++] = c[2];
+            if (d[1] != INFINITY) stack[sp++] = c[1];
+            cur = c[0];
+            continue;
+        } else {
+            const int v = -1 - cur;
+            const int first = v >> 3, cnt = (v & 7) + 1;
+            for (int k = 0; k < cnt; ++k) {
+                const float4* t = tris + 3 * (first + k);
+                const float4 v0 = __ldg(t), v1 = __ldg(t + 1), v2 = __ldg(t + 2);
+                if (kStats) ++out.tris;
+                const int st = tri_test32(r, v0, v1, v2);
+                if (st == kHit) { out.flags = 1; return out; }
+                if (st == kUnsure) {
+                    ++out.retests;
+                    const Pair64 p = retest64(r, v0, v1, v2);
+                    if (p.state == kHit) { out.flags = 1; return out; }
+                    if (p.state == kUnsure) { amb = true; ambhit |= p.hit64; }
+                }
+            }
+        }
+        if (sp == 0) break;
+        cur = stack[--sp];
+    }
+    out.flags = (ambhit ? 1 : 0) | (amb ? 2 : 0);
+    return out;
+}
+
 __device__ __forceinline__ void warp_add_counters(unsigned long long* counters, long long rays,
                                                   int amb, int retests, int overflow, long long nvis = 0,
                                                   long long ntri = 0)
@@ -985,9 +1114,15 @@ k_orthogonal_axis(const float4* __restrict__ nodes, const float4* __restrict__ t
         nd = __dadd_rn(nd, __dmul_rn((double)nz, (double)dz));
         if (nd >= -par_tol) {
             Ray r;
-            setup_ray(r, offset_coord(px, nx, eps), offset_coord(py, ny, eps), offset_coord(pz, nz, eps), dx, dy, dz,
-                      scene_maxabs);
-            const TraceOut t = trace_any<kStats, kWide>(nodes, tris, r, max_steps);
+            const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
+            setup_ray(r, ox, oy, oz, dx, dy, dz, scene_maxabs);
+            TraceOut t;
+            if (kWide) {
+                const AxisRay ar = make_axis_ray(fds[f], a, ox, oy, oz, r.rs);
+                t = trace_axis<kStats>(fds[f].tree, tris, r, ar, max_steps);
+            } else {
+                t = trace_any<kStats, kWide>(nodes, tris, r, max_steps);
+            }
             retests += t.retests;
             overflow += t.overflow;
             amb += (t.flags >> 1) & 1;
@@ -1071,7 +1206,13 @@ k_tool_cast_axis(const float4* __restrict__ nodes, const float4* __restrict__ tr
             }
             Ray ray;
             setup_ray(ray, ox, oy, oz, dx, dy, dz, scene_maxabs);
-            const TraceOut t = trace_any<false, kWide>(nodes, tris, ray, max_steps);
+            TraceOut t;
+            if (kWide) {
+                const AxisRay ar = make_axis_ray(*fd, a, ox, oy, oz, ray.rs);
+                t = trace_axis<false>(fd->tree, tris, ray, ar, max_steps);
+            } else {
+                t = trace_any<false, kWide>(nodes, tris, ray, max_steps);
+            }
             retests += t.retests;
             overflow += t.overflow;
             amb += (t.flags >> 1) & 1;
@@ -1258,6 +1399,15 @@ __global__ void k_frame_init(FrameArgs a, FrameDev* d)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     for (int k = 0; k < 9; ++k) d->frame[k] = (double)a.f[k];
+    d->tree = a.tree;
+    for (int j = 0; j < 3; ++j) {
+        d->sc_c[j] = a.sc_c[j];
+        for (int k = 0; k < 3; ++k)
+            d->gram[3 * j + k] = __dadd_rn(__dadd_rn(__dmul_rn((double)a.f[j], (double)a.f[k]),
+                                                     __dmul_rn((double)a.f[3 + j], (double)a.f[3 + k])),
+                                           __dmul_rn((double)a.f[6 + j], (double)a.f[6 + k]));
+    }
+    d->sc_r = a.sc_r;
     for (int k = 0; k < 3; ++k)
         for (int c = 0; c < 3; ++c) {
             d->axes[3 * (2 * k) + c] = a.f[3 * c + k];
@@ -1271,10 +1421,17 @@ __global__ void k_frame_init(FrameArgs a, FrameDev* d)
 
 // Frame axes, frame matrix (FP64) and the vertices' frame bounding box, all
 // on the device; the frame travels as a kernel argument (no host copy).
-rc_status frame_setup_f(rc_bvh h, const float* f9, FrameDev* d, cudaStream_t s)
+rc_status frame_setup_f(rc_bvh h, const float* f9, FrameDev* d, cudaStream_t s, const float4* tree)
 {
     FrameArgs a;
     for (int k = 0; k < 9; ++k) a.f[k] = f9[k];
+    a.tree = tree ? tree : h->wnodes;
+    double r2 = 0.0;
+    for (int j = 0; j < 3; ++j) {
+        a.sc_c[j] = 0.5 * ((double)h->lo[j] + (double)h->hi[j]);
+        r2 += ((double)h->hi[j] - (double)h->lo[j]) * ((double)h->hi[j] - (double)h->lo[j]);
+    }
+    a.sc_r = 0.5 * sqrt(r2);
     k_frame_init<<<1, 32, 0, s>>>(a, d);
     RC_LAUNCHED();
     const int64_t fb = std::min<int64_t>((h->nV + 255) / 256, (int64_t)sm_count() * 4);
@@ -1285,9 +1442,30 @@ rc_status frame_setup_f(rc_bvh h, const float* f9, FrameDev* d, cudaStream_t s)
     return RC_OK;
 }
 
-rc_status frame_setup(rc_bvh h, const rc_params* p, FrameDev* d, cudaStream_t s)
+rc_status frame_setup(rc_bvh h, const rc_params* p, FrameDev* d, cudaStream_t s, const float4* tree)
 {
-    return frame_setup_f(h, p->frame, d, s);
+    return frame_setup_f(h, p->frame, d, s, tree);
+}
+
+bool is_identity_frame(const float f9[9])
+{
+    for (int k = 0; k < 9; ++k)
+        if (f9[k] != ((k % 4) == 0 ? 1.0f : 0.0f)) return false;
+    return true;
+}
+
+rc_status make_frame_tree(rc_bvh h, const float f9[9], const rc_params* p, float4** ftree, cudaStream_t s)
+{
+    *ftree = nullptr;
+    if (!use_wide(p) || is_identity_frame(f9)) return RC_OK;
+    const int64_t nodes = h->host_sc.wide_nodes > 0 ? h->host_sc.wide_nodes : h->n_int;
+    RC_CUDA(cudaMallocAsync(ftree, sizeof(float4) * 8 * nodes, s));
+    const rc_status st = frame_tree(h, f9, *ftree, s);
+    if (st != RC_OK) {
+        cudaFreeAsync(*ftree, s);
+        *ftree = nullptr;
+    }
+    return st;
 }
 
 // Orthogonal cast of n points in nf frames (fds: device array of nf set-up
@@ -1337,9 +1515,12 @@ rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n,
                             uint8_t* mask, float* travel, unsigned long long* counters, cudaStream_t s)
 {
     FrameDev* fd = nullptr;
+    float4* ftree = nullptr;
     RC_CUDA(cudaMallocAsync(&fd, sizeof(FrameDev), s));
-    rc_status st = frame_setup(h, p, fd, s);
+    rc_status st = n > 0 ? make_frame_tree(h, p->frame, p, &ftree, s) : RC_OK;
+    if (st == RC_OK) st = frame_setup(h, p, fd, s, ftree);
     if (st == RC_OK) st = launch_orthogonal_frames(h, P, N, n, p, fd, 1, mask, travel, counters, s);
+    if (ftree) cudaFreeAsync(ftree, s);
     cudaFreeAsync(fd, s);
     return st;
 }
@@ -1365,7 +1546,9 @@ rc_status launch_tool_cast(rc_bvh h, const float* P, const float* N, int64_t n, 
     if (e == cudaSuccess) e = cudaMallocAsync(&mbits, sizeof(uint32_t) * (mw + 2), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(mbits, 0, sizeof(uint32_t) * (mw + 2), s);
     rc_status st = e == cudaSuccess ? RC_OK : cuda_error(e, "tool cast scratch");
-    if (st == RC_OK) st = frame_setup(h, p, fd, s);
+    float4* ftree = nullptr;
+    if (st == RC_OK) st = make_frame_tree(h, p->frame, p, &ftree, s);
+    if (st == RC_OK) st = frame_setup(h, p, fd, s, ftree);
     if (st == RC_OK && order) st = point_order(h, P, n, order, s);
     if (st == RC_OK) {
         int64_t blocks = (6 * ((n + 31) / 32) + 3) / 4;
@@ -1390,6 +1573,7 @@ rc_status launch_tool_cast(rc_bvh h, const float* P, const float* N, int64_t n, 
     }
     if (mbits) cudaFreeAsync(mbits, s);
     if (order) cudaFreeAsync(order, s);
+    if (ftree) cudaFreeAsync(ftree, s);
     if (fd) cudaFreeAsync(fd, s);
     return st;
 }

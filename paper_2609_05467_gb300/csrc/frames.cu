@@ -23,7 +23,6 @@
 
 namespace rc {
 
-rc_status frame_setup_f(rc_bvh h, const float* f9, FrameDev* d, cudaStream_t s);
 rc_status launch_orthogonal_frames(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
                                    const FrameDev* fds, int nf, uint8_t* mask, float* travel,
                                    unsigned long long* counters, cudaStream_t s);
@@ -612,6 +611,7 @@ rc_status rc_frame_select(rc_bvh h, const float* d_P, const float* d_N, const in
     unsigned long long* hist = (unsigned long long*)(base + ohist);
     std::vector<unsigned long long> hh(68 * (size_t)K);
     std::vector<FrameDev> hf(K);
+    std::vector<float4*> ftrees(K, nullptr);
     do {
         if (cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 68 * K, s) != cudaSuccess) {
             st = set_error(RC_E_CUDA, "memset failed");
@@ -622,7 +622,11 @@ rc_status rc_frame_select(rc_bvh h, const float* d_P, const float* d_N, const in
             st = set_error(RC_E_CUDA, "memset failed");
             break;
         }
-        for (int c = 0; c < K && st == RC_OK; ++c) st = frame_setup_f(h, io->frame[c], fds + c, s);
+        for (int c = 0; c < K && st == RC_OK; ++c) {
+            // each turned frame's axis rays walk the tree with boxes in its coordinates
+            if (n > 0) st = make_frame_tree(h, io->frame[c], p, &ftrees[c], s);
+            if (st == RC_OK) st = frame_setup_f(h, io->frame[c], fds + c, s, ftrees[c]);
+        }
         if (st != RC_OK) break;
         if (n > 0) {
             st = launch_orthogonal_frames(h, d_P, d_N, n, p, fds, K, mask, trav, (unsigned long long*)d_counters, s);
@@ -638,6 +642,8 @@ rc_status rc_frame_select(rc_bvh h, const float* d_P, const float* d_N, const in
             cudaMemcpyAsync(hf.data(), fds, sizeof(FrameDev) * K, cudaMemcpyDeviceToHost, s) != cudaSuccess)
             st = set_error(RC_E_CUDA, "result copy failed");
     } while (0);
+    for (float4* t : ftrees)
+        if (t) cudaFreeAsync(t, s);
     cudaFreeAsync(base, s);
     if (st != RC_OK) return st;
     RC_CUDA(cudaStreamSynchronize(s));

@@ -66,17 +66,23 @@ struct DevScalars {
     int max_depth;
     int pad;
     int wide_depth;
-    int pad2;
+    int wide_nodes;                // 4-wide nodes allocated
 };
 
+constexpr int kAllTris = -2;       // wide-node child made of all triangles (parts with <= kLeafMax of them)
+
 // machining frame on the device (Section 3.2)
-struct FrameArgs { float f[9]; };
+struct FrameArgs { float f[9]; const float4* tree; double sc_c[3]; double sc_r; };
 struct FrameDev {
     float axes[18];     // +X', -X', +Y', -Y', +Z', -Z' (fp32)
     float pad[2];
     double frame[9];    // row-major frame, FP64
     double fbox[6];     // frame-coordinate bounding box of the vertices (lo xyz, hi xyz)
     long long box[6];   // ordered-integer accumulators for fbox
+    const float4* tree; // 4-wide tree with child boxes in frame coordinates (the world tree for the identity)
+    double gram[9];     // G = F^T F of the fp32 frame F (FP64): how far the axes are from orthonormal
+    double sc_c[3];     // centre of the part's bounding box (world)
+    double sc_r;        // half its diagonal
 };
 
 // one part of a batched cast (device descriptor)
@@ -94,6 +100,19 @@ struct BatchPart {
     int max_steps;
     float scene_maxabs;
 };
+
+// machining frames on the device (cast.cu, build.cu): the frame's axes,
+// FP64 matrix, vertex box and Gram matrix, and the tree its axis rays walk
+// (nullptr: the world tree)
+rc_status frame_setup(rc_bvh h, const rc_params* p, FrameDev* d, cudaStream_t s, const float4* tree = nullptr);
+rc_status frame_setup_f(rc_bvh h, const float* f9, FrameDev* d, cudaStream_t s, const float4* tree = nullptr);
+// the 4-wide tree of h with its child boxes in the coordinates of frame f9
+// (ftree: as many nodes as h's 4-wide tree)
+rc_status frame_tree(rc_bvh h, const float f9[9], float4* ftree, cudaStream_t s);
+// *ftree = a new frame tree for f9, or nullptr when the axis rays walk the
+// world tree (identity frame, binary tree); release with cudaFreeAsync
+rc_status make_frame_tree(rc_bvh h, const float f9[9], const rc_params* p, float4** ftree, cudaStream_t s);
+bool is_identity_frame(const float f9[9]);
 
 // variability reduction (reduce.cu): queues the kernels on s; `scratch` is
 // kVarScratchBytes of device memory (cleared here)
