@@ -749,7 +749,11 @@ def run_batched(args):
         bits = torch.empty((n, (N + 31) // 32), dtype=torch.int32, device="cuda")
         cnt = torch.empty(n, dtype=torch.int32, device="cuda")
         ctr = torch.zeros(4, dtype=torch.int64, device="cuda")
-        items.append(dict(bvh=bvh, P=P, N=Nn, bits=bits, cnt=cnt, ctr=ctr, n=n))
+        mask = torch.empty(n, dtype=torch.uint8, device="cuda")
+        trav = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+        octr = torch.zeros(4, dtype=torch.int64, device="cuda")
+        items.append(dict(bvh=bvh, P=P, N=Nn, face=f, bits=bits, cnt=cnt, ctr=ctr, n=n, mask=mask, trav=trav,
+                          octr=octr))
     rays = float(sum(q["n"] for q in items) * N)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -787,6 +791,43 @@ def run_batched(args):
     launches = rc.rc_launch_count() - launches0
     c = torch.stack([q["ctr"] for q in items]).cpu().numpy()
     rc.rc_batch_destroy(b)
+
+    # the whole path of Sections 3.1-3.3 per part (cast, reduction and label,
+    # orthogonal cast, classes and covers), one part at a time through the
+    # single-part entry points, against the same in one graph-replayed batch
+    pw = rc.rc_params_default(n_dirs=N, seed=0, tool_length=60.0, blocks_per_sm=best.blocks_per_sm,
+                              points_per_item=best.points_per_item, point_order=best.point_order,
+                              tile_mode=best.tile_mode)
+    whole_labels = []
+
+    def whole_per_part():
+        whole_labels.clear()
+        for q in items:
+            rc.rc_hemisphere_cast(q["bvh"].h, q["P"], q["N"], pw, q["bits"], q["cnt"], q["ctr"], stream)
+            sm = rc.rc_direction_variability(q["bits"], q["N"], pw, stream=stream)
+            lab = rc.rc_classify(sm, pw)
+            rc.rc_orthogonal_cast(q["bvh"].h, q["P"], q["N"], pw, q["mask"], q["trav"], q["octr"], stream)
+            su = rc.rc_min_setups(q["bvh"].h, q["mask"], q["trav"], q["face"], pw, None, stream)
+            whole_labels.append((lab, su.setups_exact))
+    for _ in range(args.warmup):
+        whole_per_part()
+    t_wseq = timed(whole_per_part, args.steps)
+    bw = rc.rc_batch_create(pw)
+    for q in items:
+        rc.rc_batch_add_analysis(bw, q["bvh"].h, q["P"], q["N"], q["face"], q["bits"], q["cnt"])
+    batch_labels = []
+
+    def whole_batched():
+        rc.rc_batch_launch(bw, stream)
+        res = rc.rc_batch_results(bw, len(items))
+        batch_labels[:] = [(r.label, r.setups.setups_exact) for r in res]
+    for _ in range(args.warmup):
+        whole_batched()
+    wl0 = rc.rc_launch_count()
+    t_wb = timed(whole_batched, args.steps)
+    wl = rc.rc_launch_count() - wl0
+    rc.rc_batch_destroy(bw)
+    ortho_rays = float(sum(int(q["octr"][0].item()) for q in items))
     tris = [len(F) for _, _, F, _ in parts]
     out = {
         "metric": METRIC, "value": rays / (t_b / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -803,6 +844,14 @@ def run_batched(args):
                       "tile_mode": ["coherent tiles", "index"][best.tile_mode], "tune_s": tune_s},
         "gpu_launches": int(launches),
         "quality": {"ambiguous_rays": int(c[:, 1].sum()), "errors": int(c[:, 3].sum())},
+        "whole_path": {
+            "what": "per part: hemispherical cast, reduction + label, orthogonal cast, classes + covers (results on "
+                    "the host); hemispherical + orthogonal rays per second",
+            "batched_graph": {"value": (rays + ortho_rays) / (t_wb / 1e3), "ms_per_step": t_wb,
+                              "graph_launches_per_step": int(wl) // max(1, args.steps)},
+            "one_part_at_a_time": {"value": (rays + ortho_rays) / (t_wseq / 1e3), "ms_per_step": t_wseq},
+            "same_labels_and_setups": batch_labels == whole_labels,
+        },
     }
     print(json.dumps(out), flush=True)
     for q in items:

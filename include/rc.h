@@ -388,6 +388,16 @@ rc_status rc_min_setups(rc_bvh h, const uint8_t* d_mask, const float* d_travel,
 /* Batches: many parts in one persistent launch                           */
 /* ---------------------------------------------------------------------- */
 
+/* Result of rc_analyze_part and of a batch's analysis part (host struct). */
+typedef struct {
+    rc_summary summary;          /* Section 3.3 indicators */
+    rc_setups setups;            /* zero unless the setup stage ran */
+    int32_t label;               /* 0 = 3-axis, 1 = multi-axis */
+    int32_t setups_ran;          /* 1 if the orthogonal cast and setup search ran */
+    int64_t cast_counters[4];    /* hemispherical cast: rays, ambiguous rays, FP64 re-tests, errors */
+    int64_t ortho_counters[4];   /* orthogonal cast: same */
+} rc_part_result;
+
 typedef struct rc_batch_s* rc_batch;
 
 /* Create an empty batch for the hemispherical cast of many parts with the
@@ -408,6 +418,29 @@ rc_status rc_batch_create(const rc_params* p, int64_t hbm_budget_bytes, rc_batch
  * RC_E_OOM (the part would exceed the budget; it is not added). */
 rc_status rc_batch_add_part(rc_batch b, rc_bvh h, const float* d_P, const float* d_N, int64_t n,
                             uint32_t* d_bits, int32_t* d_count, int64_t* d_counters, int64_t* part_id);
+
+/* Add a part for the whole path of Sections 3.1-3.3 (an analysis part): the
+ * arrays of rc_batch_add_part plus the points' face ids d_face [n] (as from
+ * rc_sample_points; kept until clear/destroy like the other pointers).  Its
+ * launch casts the part's rays with the others, then -- in the same graph --
+ * reduces its bits to the indicators of rc_direction_variability (unit
+ * weights), casts the six axes of p->frame (rc_orthogonal_cast) and counts
+ * its face classes and reachable-axis masks (rc_min_setups); the batch owns
+ * the masks, travel, classes and per-part scratch (6 + 30 n + T + ~33 KB
+ * bytes), which count against its budget with the part's other bytes.
+ * Errors: as rc_batch_add_part, RC_E_ARG (NULL face ids). */
+rc_status rc_batch_add_analysis(rc_batch b, rc_bvh h, const float* d_P, const float* d_N, const int32_t* d_face,
+                                int64_t n, uint32_t* d_bits, int32_t* d_count, int64_t* part_id);
+
+/* Part-level results of the most recent launch for parts [0, n_out): for an
+ * analysis part the summary, label, setups (both covers, class counts,
+ * mask histogram; setups_ran = 1 for every part, whatever its label) and the
+ * cast's and the orthogonal cast's counters, as rc_analyze_part reports
+ * them for the same points; a part added with rc_batch_add_part gets zeros
+ * (its bits, counts and counters are in its own arrays).  Waits for the
+ * launch; reads every analysis part's record in one copy.  Errors: RC_E_ARG
+ * (no launch yet, n_out outside [0, parts]), RC_E_CUDA. */
+rc_status rc_batch_results(rc_batch b, rc_part_result* h_out, int64_t n_out);
 
 /* Remove every part (the batch can then be refilled). */
 rc_status rc_batch_clear(rc_batch b);
@@ -438,16 +471,6 @@ rc_status rc_batch_autotune(rc_batch b, void* stream, int32_t repeats, rc_params
 
 /* Release a batch (not its parts' handles or arrays). */
 rc_status rc_batch_destroy(rc_batch b);
-
-/* Result of rc_analyze_part (host struct). */
-typedef struct {
-    rc_summary summary;          /* Section 3.3 indicators */
-    rc_setups setups;            /* zero unless the setup stage ran */
-    int32_t label;               /* 0 = 3-axis, 1 = multi-axis */
-    int32_t setups_ran;          /* 1 if the orthogonal cast and setup search ran */
-    int64_t cast_counters[4];    /* hemispherical cast: rays, ambiguous rays, FP64 re-tests, errors */
-    int64_t ortho_counters[4];   /* orthogonal cast: same */
-} rc_part_result;
 
 /* The whole pipeline of Sections 3.1-3.3 on HOST arrays, in one call: copy
  * the mesh to the device, build the BVH, sample n points (centroid mode

@@ -26,7 +26,7 @@ __all__ = [
     "rc_direction_variability_noalloc",
     "rc_classify", "rc_orthogonal_cast", "rc_min_setups", "rc_setup_cover", "rc_analyze_part",
     "rc_launch_count", "rc_stream_status", "rc_bvh_validate", "Bvh", "PartResult", "rc_batch_create", "rc_batch_add_part", "rc_batch_clear",
-    "rc_batch_set_params", "rc_batch_launch", "rc_batch_poll", "rc_batch_autotune", "rc_batch_destroy", "rc_server_create",
+    "rc_batch_set_params", "rc_batch_launch", "rc_batch_poll", "rc_batch_add_analysis", "rc_batch_results", "rc_batch_autotune", "rc_batch_destroy", "rc_server_create",
     "rc_server_submit", "rc_server_wait", "rc_server_read_bits", "rc_server_get_stats", "rc_server_destroy",
 ]
 
@@ -183,6 +183,8 @@ def load(build_if_missing=True):
             "rc_setup_cover": ([P, ctypes.POINTER(Setups)], st),
             "rc_batch_create": ([ctypes.POINTER(Params), i64, ctypes.POINTER(P)], st),
             "rc_batch_poll": ([P, i64, ctypes.POINTER(i32)], st),
+            "rc_batch_add_analysis": ([P, P, P, P, P, i64, P, P, ctypes.POINTER(i64)], st),
+            "rc_batch_results": ([P, ctypes.POINTER(PartResult), i64], st),
             "rc_batch_add_part": ([P, P, P, P, i64, P, P, P, ctypes.POINTER(i64)], st),
             "rc_batch_clear": ([P], st),
             "rc_batch_set_params": ([P, ctypes.POINTER(Params)], st),
@@ -470,6 +472,22 @@ def rc_batch_create(params, hbm_budget_bytes=0):
     b = ctypes.c_void_p()
     _check(load().rc_batch_create(ctypes.byref(params), int(hbm_budget_bytes), ctypes.byref(b)))
     return b.value
+
+
+def rc_batch_add_analysis(b, h, P, N, face, bits, count):
+    """Add a part whose launch runs the whole path (cast, reduction,
+    orthogonal cast, classes); returns its id."""
+    pid = ctypes.c_int64()
+    _check(load().rc_batch_add_analysis(ctypes.c_void_p(b), ctypes.c_void_p(h), _ptr(P), _ptr(N), _ptr(face),
+                                        P.shape[0], _ptr(bits), _ptr(count), ctypes.byref(pid)))
+    return pid.value
+
+
+def rc_batch_results(b, n_parts):
+    """Part-level results of the last launch, one PartResult per part."""
+    out = (PartResult * n_parts)()
+    _check(load().rc_batch_results(ctypes.c_void_p(b), out, n_parts))
+    return list(out)
 
 
 def rc_batch_poll(b, part_id):

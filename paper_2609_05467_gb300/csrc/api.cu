@@ -163,6 +163,8 @@ static rc_status check_params(const rc_params* p)
 rc_status check_params_public(const rc_params* p) { return check_params(p); }
 
 // Direction table a cast uses: tile order (default) or canonical order.
+rc_status device_dirs_canonical(int32_t N, const float4** canon) { return device_dirs(N, canon); }
+
 rc_status device_dirs_for_cast(const rc_params* p, const float4** tdirs)
 {
     const float4 *canon = nullptr, *tiled = nullptr;

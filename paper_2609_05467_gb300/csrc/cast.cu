@@ -1470,21 +1470,20 @@ rc_status make_frame_tree(rc_bvh h, const float f9[9], const rc_params* p, float
 
 // Orthogonal cast of n points in nf frames (fds: device array of nf set-up
 // frames); mask [nf][n], travel [nf][n][6].
-rc_status launch_orthogonal_frames(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
-                                   const FrameDev* fds, int nf, uint8_t* mask, float* travel,
-                                   unsigned long long* counters, cudaStream_t s)
+// Orthogonal cast into caller-provided scratch: order (n points in their
+// processing order, or null for index order; filled by the caller) and
+// mbits (ortho_scratch_words(nf, n) words, cleared here).  Allocates nothing,
+// so it can be captured in a graph.
+int64_t ortho_scratch_words(int nf, int64_t n) { return ((((int64_t)nf * n) + 1) & ~(int64_t)1) + 2; }
+
+rc_status launch_orthogonal_frames_into(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
+                                        const FrameDev* fds, int nf, uint8_t* mask, float* travel,
+                                        unsigned long long* counters, const int32_t* order, uint32_t* mbits,
+                                        cudaStream_t s)
 {
     if (n == 0) return RC_OK;
-    int32_t* order = nullptr;
-    if (p->point_order == 0 && n > 1) {
-        RC_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * n, s));
-        rc_status pst = point_order(h, P, n, order, s);
-        if (pst != RC_OK) return pst;
-    }
     const int64_t m = (int64_t)nf * n;
-    uint32_t* mbits = nullptr;                 // m words, then the item counter
-    const int64_t mw = (m + 1) & ~(int64_t)1;
-    RC_CUDA(cudaMallocAsync(&mbits, sizeof(uint32_t) * (mw + 2), s));
+    const int64_t mw = (m + 1) & ~(int64_t)1;   // m words, then the item counter
     RC_CUDA(cudaMemsetAsync(mbits, 0, sizeof(uint32_t) * (mw + 2), s));
     unsigned long long* work = (unsigned long long*)(mbits + mw);
     const int64_t items = (int64_t)nf * 6 * ((n + 31) / 32);
@@ -1506,9 +1505,26 @@ rc_status launch_orthogonal_frames(rc_bvh h, const float* P, const float* N, int
     RC_LAUNCHED();
     k_mask_pack<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(mbits, m, mask);
     RC_LAUNCHED();
-    RC_CUDA(cudaFreeAsync(mbits, s));
-    if (order) RC_CUDA(cudaFreeAsync(order, s));
     return RC_OK;
+}
+
+rc_status launch_orthogonal_frames(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
+                                   const FrameDev* fds, int nf, uint8_t* mask, float* travel,
+                                   unsigned long long* counters, cudaStream_t s)
+{
+    if (n == 0) return RC_OK;
+    int32_t* order = nullptr;
+    if (p->point_order == 0 && n > 1) {
+        RC_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * n, s));
+        rc_status pst = point_order(h, P, n, order, s);
+        if (pst != RC_OK) return pst;
+    }
+    uint32_t* mbits = nullptr;
+    RC_CUDA(cudaMallocAsync(&mbits, sizeof(uint32_t) * ortho_scratch_words(nf, n), s));
+    const rc_status st = launch_orthogonal_frames_into(h, P, N, n, p, fds, nf, mask, travel, counters, order, mbits, s);
+    cudaFreeAsync(mbits, s);
+    if (order) cudaFreeAsync(order, s);
+    return st;
 }
 
 rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from common import compare_bits
+from common import compare_bits, gpu_outcome, setup_outcomes, unpack
 
 pytestmark = pytest.mark.gpu
 
@@ -154,6 +154,88 @@ def test_batch_budget_and_poll(rc):
     torch.cuda.synchronize()
     assert rc.rc_batch_poll(b, pid) == 1
     _check(parts[:1], N, against_oracle=True)
+    rc.rc_batch_destroy(b)
+    for q in parts:
+        q["bvh"].close()
+
+
+def _single_chain(rc, q, p):
+    """The single-part entry points on the same points: reduction,
+    classification, orthogonal cast, setups."""
+    n = q["P"].shape[0]
+    s = rc.rc_direction_variability(q["ref_b"], q["N"], p)
+    lab = rc.rc_classify(s, p)
+    mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    trav = torch.zeros((n, 6), dtype=torch.float32, device="cuda")
+    ctr = torch.zeros(4, dtype=torch.int64, device="cuda")
+    rc.rc_orthogonal_cast(q["bvh"].h, q["P"], q["N"], p, mask, trav, ctr)
+    su = rc.rc_min_setups(q["bvh"].h, mask, trav, q["face"], p)
+    return s, lab, su, mask, ctr.cpu().numpy()
+
+
+@pytest.mark.parametrize("frame", [None, [0.8, -0.6, 0, 0.6, 0.8, 0, 0, 0, 1]])
+def test_batch_whole_path_equals_single_part_and_oracle(rc, frame):
+    """Analysis parts: one graph casts every part, then reduces, casts the six
+    axes and counts classes per part.  Each part's results equal the
+    single-part entry points on the same points exactly, and the oracle's
+    (bits outside its ambiguous rays; indicators and label exactly when it
+    saw no ambiguous ray; setups among the outcomes its ambiguous axis rays
+    allow); a cast-only part in the same batch is unaffected; a replay gives
+    the same results."""
+    N = 128
+    kw = {} if frame is None else {"frame": frame}
+    p = rc.rc_params_default(n_dirs=N, tool_length=40.0, **kw)
+    counts = [900, 700, 1200, 1, 333, 64]
+    parts = _setup(rc, N, counts)
+    meshes = _parts()
+    b = rc.rc_batch_create(p)
+    ids = []
+    for k, q in enumerate(parts):
+        V, F = meshes[k]
+        _, _, f, _ = oracle.sample_area(V, F, q["P"].shape[0], seed=k)
+        q["face"] = torch.from_numpy(f).cuda()
+        if k == 3:
+            ids.append(rc.rc_batch_add_part(b, q["bvh"].h, q["P"], q["N"], q["b"], q["c"], q["ctr"]))
+        else:
+            ids.append(rc.rc_batch_add_analysis(b, q["bvh"].h, q["P"], q["N"], q["face"], q["b"], q["c"]))
+    rc.rc_batch_launch(b)
+    res = rc.rc_batch_results(b, len(parts))
+    torch.cuda.synchronize()
+    for k, (q, r) in enumerate(zip(parts, res)):
+        V, F = meshes[k]
+        n = q["P"].shape[0]
+        gb = q["b"].cpu().numpy().view(np.uint32)
+        compare_bits(gb, q["c"].cpu().numpy(), *q["oracle"], N)
+        assert torch.equal(q["b"], q["ref_b"]) and torch.equal(q["c"], q["ref_c"])
+        if k == 3:
+            assert r.setups_ran == 0 and q["ctr"].cpu().numpy()[0] == n * N
+            continue
+        s, lab, su, mask, octr = _single_chain(rc, q, p)
+        assert r.summary.overall_access == s.overall_access and r.summary.mean_conc == s.mean_conc
+        assert list(r.summary.axis_share) == list(s.axis_share) and r.label == lab
+        assert r.setups_ran == 1 and (r.setups.setups_exact, r.setups.setups_greedy) == (su.setups_exact, su.setups_greedy)
+        assert list(r.setups.class_counts) == list(su.class_counts) and list(r.setups.mask_hist) == list(su.mask_hist)
+        assert r.cast_counters[0] == n * N and r.cast_counters[3] == 0 and r.ortho_counters[0] == octr[0]
+        # against the oracle
+        hP, hN = q["P"].cpu().numpy(), q["N"].cpu().numpy()
+        ob, oa, oc = q["oracle"]
+        n_amb = int(unpack(oa, N).sum())
+        M, ac, dom, conc, c2 = oracle.variability(ob, hN, N)
+        os_ = oracle.summary(c2, dom, conc, N)
+        if n_amb == 0:
+            assert r.summary.overall_access == os_["overall_access"] and r.label == oracle.classify(os_)
+        m = oracle.Mesh(V, F)
+        om, oam = m.orthogonal(hP, hN, frame=frame)
+        outs, _, _ = setup_outcomes(om, oam, oracle.travel(V, hP, frame=frame), q["face"].cpu().numpy(),
+                                    oracle.fixture_faces(V, F, frame=frame), p.tool_length)
+        if outs is not None:
+            assert gpu_outcome(r.setups) in outs
+    # a replay of the graph gives the same results
+    rc.rc_batch_launch(b)
+    res2 = rc.rc_batch_results(b, len(parts))
+    for r, r2 in zip(res, res2):
+        assert r.summary.overall_access == r2.summary.overall_access and r.setups.setups_exact == r2.setups.setups_exact
+        assert list(r.setups.mask_hist) == list(r2.setups.mask_hist)
     rc.rc_batch_destroy(b)
     for q in parts:
         q["bvh"].close()
