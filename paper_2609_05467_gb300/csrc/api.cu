@@ -174,6 +174,19 @@ rc_status device_dirs_for_cast(const rc_params* p, const float4** tdirs)
     return RC_OK;
 }
 
+// Scene bounds = the union of the binary root's two child boxes (every
+// referenced vertex); read after every build and refit.
+static rc_status scene_box(rc_bvh h)
+{
+    float4 root[3];
+    if (cudaMemcpy(root, h->nodes, sizeof root, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return set_error(RC_E_CUDA, "reading the root node failed");
+    h->lo[0] = fminf(root[0].x, root[1].x); h->hi[0] = fmaxf(root[0].y, root[1].y);
+    h->lo[1] = fminf(root[0].z, root[1].z); h->hi[1] = fmaxf(root[0].w, root[1].w);
+    h->lo[2] = fminf(root[2].x, root[2].z); h->hi[2] = fmaxf(root[2].y, root[2].w);
+    return RC_OK;
+}
+
 static rc_status use_device_of(rc_bvh h)
 {
     int dev = 0;
@@ -290,13 +303,7 @@ rc_status rc_build_bvh_ex(const float* d_V, int64_t nV, const int32_t* d_F, int6
 #undef RC_TRY
     rc_status st = build_bvh(h, s);
     if (st != RC_OK) return fail(st);
-    // scene bounds = union of the root's two child boxes
-    float4 root[3];
-    if (cudaMemcpy(root, h->nodes, sizeof root, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return fail(set_error(RC_E_CUDA, "reading the root node failed"));
-    h->lo[0] = fminf(root[0].x, root[1].x); h->hi[0] = fmaxf(root[0].y, root[1].y);
-    h->lo[1] = fminf(root[0].z, root[1].z); h->hi[1] = fmaxf(root[0].w, root[1].w);
-    h->lo[2] = fminf(root[2].x, root[2].z); h->hi[2] = fmaxf(root[2].y, root[2].w);
+    if ((st = scene_box(h)) != RC_OK) return fail(st);
     *out = h;
     return RC_OK;
 }
@@ -309,7 +316,9 @@ rc_status rc_refit_bvh(rc_bvh h, const float* d_V, void* stream)
     if (st != RC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     RC_CUDA(cudaMemcpyAsync(h->V, d_V, sizeof(float) * 3 * h->nV, cudaMemcpyDeviceToDevice, s));
-    return refit_bvh(h, s);
+    st = refit_bvh(h, s);
+    if (st != RC_OK) return st;
+    return scene_box(h);
 }
 
 rc_status rc_destroy_bvh(rc_bvh h)

@@ -590,3 +590,28 @@ def test_translation_by_an_exact_offset(rc):
     assert abs(c0.sum() - c1.sum()) <= 1e-3 * c0.sum()
     b0.close()
     b1.close()
+
+
+def test_turned_frame_after_a_refit_that_grows_the_part(rc):
+    """A refit to vertices far outside the old bounding box, then the
+    orthogonal cast in a turned frame (frame-space boxes, whose band
+    tolerance scales with the part's reach): masks equal the oracle's on
+    the refitted geometry outside its ambiguous axes."""
+    V0, F = PARTS["multi_pocket"]()
+    Vt0, Ft = gpu_mesh(V0, F)
+    bvh = rc.Bvh(Vt0, Ft)
+    V1 = (V0.astype(np.float64) * 2.5 + np.array([300.0, -120.0, 75.0])).astype(np.float32)
+    rc.rc_refit_bvh(bvh.h, torch.from_numpy(V1).cuda())
+    info = rc.rc_bvh_get_info(bvh.h)
+    assert np.allclose(info.scene_lo, V1.min(0)) and np.allclose(info.scene_hi, V1.max(0))
+    frame = [0.8, -0.6, 0, 0.6, 0.8, 0, 0, 0, 1]
+    p = rc.rc_params_default(frame=frame)
+    P, Nn, f, w = _points(V1, F, 3000, p)
+    Pt, Nt = torch.from_numpy(P).cuda(), torch.from_numpy(Nn).cuda()
+    mask = torch.zeros(len(P), dtype=torch.uint8, device="cuda")
+    trav = torch.zeros((len(P), 6), dtype=torch.float32, device="cuda")
+    rc.rc_orthogonal_cast(bvh.h, Pt, Nt, p, mask, trav)
+    om, oam = oracle.Mesh(V1, F).orthogonal(P, Nn, frame=frame)
+    gm = mask.cpu().numpy()
+    assert np.array_equal(gm & ~oam, om & ~oam)
+    bvh.close()
