@@ -439,7 +439,8 @@ rc_status rc_batch_add_analysis(rc_batch b, rc_bvh h, const float* d_P, const fl
  * them for the same points; a part added with rc_batch_add_part gets zeros
  * (its bits, counts and counters are in its own arrays).  Waits for the
  * launch; reads every analysis part's record in one copy.  Errors: RC_E_ARG
- * (no launch yet, n_out outside [0, parts]), RC_E_CUDA. */
+ * (no launch yet, parts or parameters changed since the last launch, n_out
+ * outside [0, parts]), RC_E_CUDA. */
 rc_status rc_batch_results(rc_batch b, rc_part_result* h_out, int64_t n_out);
 
 /* Remove every part (the batch can then be refilled). */

@@ -353,6 +353,7 @@ rc_status rc_batch_results(rc_batch b, rc_part_result* h_out, int64_t n_out)
     if (!b || (!h_out && n_out > 0)) return set_error(RC_E_ARG, "batch or results is NULL");
     if (n_out < 0 || n_out > (int64_t)b->parts.size()) return set_error(RC_E_ARG, "n_out outside [0, parts]");
     if (!b->launched) return set_error(RC_E_ARG, "the batch has not been launched");
+    if (b->dirty) return set_error(RC_E_ARG, "parts or parameters changed since the last launch");
     RC_CUDA(cudaEventSynchronize(b->done));
     std::vector<char> rec(kRecBytes * (size_t)b->n_full);
     if (b->n_full > 0) RC_CUDA(cudaMemcpy(rec.data(), b->records, rec.size(), cudaMemcpyDeviceToHost));

@@ -230,6 +230,10 @@ def test_batch_whole_path_equals_single_part_and_oracle(rc, frame):
                                     oracle.fixture_faces(V, F, frame=frame), p.tool_length)
         if outs is not None:
             assert gpu_outcome(r.setups) in outs
+    # results refer to the last launch: after a change they wait for the next one
+    rc.rc_batch_set_params(b, p)
+    with pytest.raises(rc.RcError):
+        rc.rc_batch_results(b, len(parts))
     # a replay of the graph gives the same results
     rc.rc_batch_launch(b)
     res2 = rc.rc_batch_results(b, len(parts))
