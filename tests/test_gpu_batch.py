@@ -243,3 +243,53 @@ def test_batch_whole_path_equals_single_part_and_oracle(rc, frame):
     rc.rc_batch_destroy(b)
     for q in parts:
         q["bvh"].close()
+
+
+@pytest.mark.slow
+def test_full_size_batched(rc):
+    """The batched configuration at full size, in the benchmark's launch: 64
+    parts from the three families (10k-500k triangles, log-uniform), 2 points
+    per mm^2 up to 200k, 512 directions, all added for analysis and run in
+    one graph.  Every part: all 512 rays of 48 random points against the
+    oracle (bit for bit outside its ambiguous rays) and its ray counter;
+    four parts' part-level results against the single-part chain."""
+    import bench
+    from common import gpu_mesh
+    rng = np.random.default_rng(0)
+    N = 512
+    p = rc.rc_params_default(n_dirs=N, seed=0, tool_length=60.0)
+    b = rc.rc_batch_create(p)
+    items = []
+    for k in range(64):
+        fam = int(rng.integers(3))
+        t = float(np.exp(rng.uniform(np.log(1e4), np.log(5e5))))
+        V, F = synth.part_family(fam, t, rng)
+        n = int(min(200_000, round(2.0 * bench._area(V, F))))
+        hP, hN, hf, _ = oracle.sample_area(V, F, n, seed=0)
+        bvh = rc.Bvh(*gpu_mesh(V, F))
+        q = dict(V=V, F=F, bvh=bvh, P=torch.from_numpy(hP).cuda(), N=torch.from_numpy(hN).cuda(),
+                 face=torch.from_numpy(hf).cuda(), b=torch.zeros((n, N // 32), dtype=torch.int32, device="cuda"),
+                 c=torch.zeros(n, dtype=torch.int32, device="cuda"), hP=hP, hN=hN)
+        rc.rc_batch_add_analysis(b, bvh.h, q["P"], q["N"], q["face"], q["b"], q["c"])
+        items.append(q)
+    rc.rc_batch_launch(b)
+    res = rc.rc_batch_results(b, len(items))
+    torch.cuda.synchronize()
+    pick = np.random.default_rng(1)
+    for k, (q, r) in enumerate(zip(items, res)):
+        n = q["hP"].shape[0]
+        assert r.cast_counters[0] == n * N and r.cast_counters[3] == 0 and r.ortho_counters[3] == 0
+        idx = np.sort(pick.choice(n, size=min(48, n), replace=False))
+        gb = q["b"].cpu().numpy().view(np.uint32)
+        gc = q["c"].cpu().numpy()
+        ob, oa, oc = oracle.Mesh(q["V"], q["F"]).hemisphere(q["hP"][idx], q["hN"][idx], N)
+        compare_bits(gb[idx], gc[idx], ob, oa, oc, N)
+        if k < 4:
+            q["ref_b"] = q["b"]
+            s, lab, su, mask, octr = _single_chain(rc, q, p)
+            assert r.summary.overall_access == s.overall_access and r.label == lab
+            assert (r.setups.setups_exact, r.setups.setups_greedy) == (su.setups_exact, su.setups_greedy)
+            assert list(r.setups.mask_hist) == list(su.mask_hist)
+    rc.rc_batch_destroy(b)
+    for q in items:
+        q["bvh"].close()
