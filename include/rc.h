@@ -69,7 +69,8 @@ typedef struct {
     int32_t sample_mode;     /* RC_SAMPLE_* */
     double origin_offset;    /* mm; rays start at fl32(p + origin_offset * n) (Section 3.1) */
     uint64_t seed;           /* area-random sampling seed */
-    float frame[9];          /* row-major 3x3 machining frame; its columns are X', Y', Z' (Section 3.2) */
+    float frame[9];          /* row-major 3x3 machining frame; its columns are X', Y', Z' (Section 3.2); finite,
+                                no zero column (RC_E_ARG) */
     float tool_length;       /* mm; reachability threshold (Section 3.3) */
     int32_t conc_mode;       /* 0: share of visible rays along the dominant axis; 1: |mean direction| along it */
     double t_acc;            /* multi-axis if overall accessibility < t_acc (Section 3.3) */

@@ -143,6 +143,9 @@ static rc_status check_params(const rc_params* p)
     if (p->conc_mode != 0 && p->conc_mode != 1) return set_error(RC_E_ARG, "conc_mode must be 0 or 1");
     for (int k = 0; k < 9; ++k)
         if (!isfinite(p->frame[k])) return set_error(RC_E_ARG, "frame must be finite");
+    for (int c = 0; c < 3; ++c)
+        if (p->frame[c] == 0.0f && p->frame[3 + c] == 0.0f && p->frame[6 + c] == 0.0f)
+            return set_error(RC_E_ARG, "frame columns (the machining axes) must be non-zero");
     if (p->block_threads != 0 && p->block_threads != 128)
         return set_error(RC_E_UNSUPPORTED, "block_threads must be 0 (default) or 128");
     if (p->point_order != 0 && p->point_order != 1) return set_error(RC_E_ARG, "point_order must be 0 or 1");

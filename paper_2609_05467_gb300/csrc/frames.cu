@@ -588,9 +588,13 @@ rc_status rc_frame_select(rc_bvh h, const float* d_P, const float* d_N, const in
     rc_status st = check_params_public(p);
     if (st != RC_OK) return st;
     if (io->k < 1 || io->k > RC_MAX_FRAMES) return set_error(RC_E_ARG, "frames.k must be in [1, RC_MAX_FRAMES]");
-    for (int c = 0; c < io->k; ++c)
+    for (int c = 0; c < io->k; ++c) {
         for (int k = 0; k < 9; ++k)
             if (!isfinite(io->frame[c][k])) return set_error(RC_E_ARG, "frame must be finite");
+        for (int a = 0; a < 3; ++a)
+            if (io->frame[c][a] == 0.0f && io->frame[c][3 + a] == 0.0f && io->frame[c][6 + a] == 0.0f)
+                return set_error(RC_E_ARG, "frame columns (the machining axes) must be non-zero");
+    }
     if (n < 0) return set_error(RC_E_ARG, "n must be >= 0");
     if (n > 0 && (!d_P || !d_N || !d_face)) return set_error(RC_E_ARG, "array pointer is NULL");
     if (p->collect_stats && !d_counters) return set_error(RC_E_ARG, "collect_stats needs the counters array");

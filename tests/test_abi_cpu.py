@@ -161,7 +161,14 @@ def test_argument_validation_needs_no_gpu(rc):
         fr.k = k
         assert L.rc_frame_select(ctypes.c_void_p(16), None, None, None, 0, ctypes.byref(ok), ctypes.byref(fr),
                                  None, None) == 1 and b"frames.k" in L.rc_last_error()
+    z = rc.rc_params_default(frame=[1, 0, 0, 0, 0, 0, 0, 0, 1])          # Y' column is zero
+    assert L.rc_hemisphere_cast(ctypes.c_void_p(16), None, None, 1, ctypes.byref(z), None, None, None,
+                                None) == 1 and b"non-zero" in L.rc_last_error()
     fr.k = 1
+    fr.frame[0][:] = [1, 0, 0, 0, 0, 0, 0, 0, 1]
+    assert L.rc_frame_select(ctypes.c_void_p(16), None, None, None, 0, ctypes.byref(ok), ctypes.byref(fr),
+                             None, None) == 1 and b"non-zero" in L.rc_last_error()
+    fr.frame[0][:] = [1, 0, 0, 0, 1, 0, 0, 0, 1]
     fr.frame[0][4] = float("nan")
     assert L.rc_frame_select(ctypes.c_void_p(16), None, None, None, 0, ctypes.byref(ok), ctypes.byref(fr),
                              None, None) == 1 and b"finite" in L.rc_last_error()
