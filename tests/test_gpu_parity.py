@@ -184,6 +184,54 @@ def test_pocket_floor_centre_fraction_on_gpu(rc):
     bvh.close()
 
 
+def _funnel(K, r=20.0, h=20.0):
+    """Concave funnel: K side triangles from the apex (origin) to a rim of
+    radius r at height h, wound so that their normals face the hollow."""
+    th = 2 * np.pi * np.arange(K) / K
+    V = np.concatenate([[[0.0, 0.0, 0.0]], np.stack([r * np.cos(th), r * np.sin(th), np.full(K, h)], 1)])
+    F = np.array([[0, 1 + (i + 1) % K, 1 + i] for i in range(K)], np.int32)
+    a, b, c = V[F[0, 0]], V[F[0, 1]], V[F[0, 2]]
+    if np.cross(b - a, c - a)[2] < 0:
+        F = F[:, [0, 2, 1]]
+    return V.astype(np.float32), F
+
+
+@pytest.mark.parametrize("K", [64, 128])
+def test_points_whose_frontier_does_not_fit(rc, K):
+    """Points at and near the apex of a concave funnel: more than 12 triangles have
+    boxes that contain the ray origin and are not wholly below the point's
+    tangent plane, so the per-point frontier (12 local triangles at most)
+    does not fit and the warp walks from the root instead.  The premise is
+    checked on the host; the bits must still be the oracle's."""
+    V, F = _funnel(K)
+    Vd = V.astype(np.float64)
+    P, Nn = [], []
+    for f in F:
+        a, b, c = Vd[f]
+        n = np.cross(b - a, c - a)
+        n /= np.linalg.norm(n)
+        for s in (0.0, 0.002, 0.01, 0.03):     # s = 0: the apex itself, shared by every face
+            P.append(a + s * (b - a) + s * (c - a))
+            Nn.append(n)
+    P = np.array(P, np.float32)
+    Nn = np.array(Nn, np.float32)
+    lo, hi = Vd[F].min(1), Vd[F].max(1)
+    for o, n in zip(P.astype(np.float64) + 1e-4 * Nn, Nn.astype(np.float64)):
+        inside = ((lo <= o) & (o <= hi)).all(1)
+        below = ((Vd[F] - o) @ n < 0).all(1)
+        assert (inside & ~below).sum() > 12
+    N = 256
+    bvh = _build(rc, V, F)
+    p = rc.rc_params_default(n_dirs=N)
+    gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
+    ob, oa, oc = oracle.Mesh(V, F).hemisphere(P, Nn, N)
+    cmp_, amb = compare_bits(gb, gc, ob, oa, oc, N)
+    assert cmp_ + amb == len(P) * N
+    assert ctr[0] == len(P) * N and ctr[3] == 0
+    assert 0 < gc.sum() < len(P) * N
+    bvh.close()
+
+
 def test_cast_is_deterministic(rc):
     V, F = PARTS["prismatic_coarse"]()
     bvh = _build(rc, V, F)
