@@ -307,6 +307,9 @@ FRAMES = {
     "identity": None,
     "quarter_z": [0, -1, 0, 1, 0, 0, 0, 0, 1],
     "tilted": [0.8, -0.6, 0, 0.6, 0.8, 0, 0, 0, 1],
+    # neither orthogonal nor unit columns: G = F^T F has off-diagonal terms
+    # of 0.1-0.6, which the frame-space box test must widen its band by
+    "sheared": [1.0, 0.3, 0.0, 0.0, 2.0, 0.25, 0.1, 0.0, 0.5],
 }
 
 
