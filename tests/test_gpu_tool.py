@@ -37,7 +37,11 @@ PARTS = {
 def test_tool_cast_matches_oracle(rc, name, radius, K):
     V, F = PARTS[name]()
     bvh = rc.Bvh(*gpu_mesh(V, F))
-    frame = [0.8, -0.6, 0, 0.6, 0.8, 0, 0, 0, 1] if name == "multi_pocket" and K == 8 else None
+    frame = None
+    if name == "multi_pocket" and K == 8:
+        frame = [0.8, -0.6, 0, 0.6, 0.8, 0, 0, 0, 1]
+    elif name == "prismatic_coarse" and K == 16:
+        frame = [1.0, 0.3, 0.0, 0.0, 2.0, 0.25, 0.1, 0.0, 0.5]    # sheared, non-unit columns
     kw = {} if frame is None else {"frame": frame}
     p = rc.rc_params_default(**kw)
     P, Nn, f, _ = oracle.sample_area(V, F, 1500, seed=6)
