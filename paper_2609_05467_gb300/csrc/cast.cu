@@ -398,7 +398,7 @@ __device__ __forceinline__ int slab4(const float4* __restrict__ nd, const SlabRa
 // exact FP64 test runs once per point.  A point whose frontier or local
 // triangles do not fit walks from the root instead.
 // ---------------------------------------------------------------------------
-constexpr int kFrontGroups = 12;   // frontier entries, four per group
+constexpr int kFrontGroups = 16;   // frontier entries, four per group
 constexpr int kFrontTris = 12;     // local triangles kept per point
 constexpr int kStackF = kStack4 + 4 * kFrontGroups;
 
