@@ -395,7 +395,8 @@ __device__ __forceinline__ int slab4(const float4* __restrict__ nd, const SlabRa
 // decisions.  A local triangle wholly below the point's tangent plane is
 // dropped, because a hemisphere ray leaves that plane (d.n > 0 for every
 // direction of the set, N <= 65536) and meets no point of it at t > 0; that
-// exact FP64 test runs once per point.  A point whose frontier or local
+// exact FP64 test runs once per point.  For the same reason a frontier box
+// wholly below the plane is dropped (a conservative fp32 test).  A point whose frontier or local
 // triangles do not fit walks from the root instead.
 // ---------------------------------------------------------------------------
 constexpr int kFrontGroups = 16;   // frontier entries, four per group
@@ -417,6 +418,21 @@ __device__ __forceinline__ bool below_tangent(float4 v, float ox, float oy, floa
     const double s = __dadd_rn(__dadd_rn(__dmul_rn((double)nx, a), __dmul_rn((double)ny, b)), __dmul_rn((double)nz, c));
     const double m = fabs((double)nx * a) + fabs((double)ny * b) + fabs((double)nz * c);
     return s < -4e-15 * m;
+}
+
+// A box wholly below the tangent plane through o: the largest n.(x - o) over
+// its corners, sum over the axes of max(n_k (lo_k - o_k), n_k (hi_k - o_k)),
+// is negative beyond the rounding of its fp32 evaluation (each difference,
+// product and sum rounds once: under 4u of the sum of the terms' magnitudes,
+// 8u taken).  Every triangle inside such a box is wholly below the plane too.
+__device__ __forceinline__ bool box_below_tangent(float lx, float hx, float ly, float hy, float lz, float hz,
+                                                  float ox, float oy, float oz, float nx, float ny, float nz)
+{
+    const float mx = fmaxf(nx * (lx - ox), nx * (hx - ox));
+    const float my = fmaxf(ny * (ly - oy), ny * (hy - oy));
+    const float mz = fmaxf(nz * (lz - oz), nz * (hz - oz));
+    const float u = 5.9604644775390625e-8f;
+    return (mx + my) + mz < -8.0f * u * (fabsf(mx) + fabsf(my) + fabsf(mz));
 }
 
 // Lane 0 of the warp: the origin set of o (a walk over the boxes that
@@ -463,6 +479,8 @@ __device__ __noinline__ void build_frontier(const float4* __restrict__ wnodes, c
                     ++nt;
                 }
             } else {
+                // a box below the tangent plane holds no hit of any ray of the point
+                if (box_below_tangent(LX[k], HX[k], LY[k], HY[k], LZ[k], HZ[k], ox, oy, oz, nx, ny, nz)) continue;
                 if (ne >= 4 * kFrontGroups) { ok = false; break; }
                 float* gp = g + 28 * (ne >> 2) + (ne & 3);
                 gp[0] = LX[k]; gp[4] = HX[k]; gp[8] = LY[k]; gp[12] = HY[k]; gp[16] = LZ[k]; gp[20] = HZ[k];
