@@ -396,7 +396,8 @@ __device__ __forceinline__ int slab4(const float4* __restrict__ nd, const SlabRa
 // dropped, because a hemisphere ray leaves that plane (d.n > 0 for every
 // direction of the set, N <= 65536) and meets no point of it at t > 0; that
 // exact FP64 test runs once per point.  For the same reason a frontier box
-// wholly below the plane is dropped (a conservative fp32 test).  A point whose frontier or local
+// wholly below the plane is dropped, and so is a frontier leaf whose
+// triangles all lie below it (conservative fp32 tests).  A point whose frontier or local
 // triangles do not fit walks from the root instead.
 // ---------------------------------------------------------------------------
 constexpr int kFrontGroups = 16;   // frontier entries, four per group
@@ -479,8 +480,21 @@ __device__ __noinline__ void build_frontier(const float4* __restrict__ wnodes, c
                     ++nt;
                 }
             } else {
-                // a box below the tangent plane holds no hit of any ray of the point
+                // a box below the tangent plane holds no hit of any ray of the
+                // point, and neither does a leaf whose triangles all lie below it
                 if (box_below_tangent(LX[k], HX[k], LY[k], HY[k], LZ[k], HZ[k], ox, oy, oz, nx, ny, nz)) continue;
+                if (CI[k] < 0) {
+                    const int v = -1 - CI[k], first = v >> 3, cnt = (v & 7) + 1;
+                    bool below = true;
+                    for (int t = 0; t < cnt && below; ++t) {
+                        const float4* tp = tris + 3 * (int64_t)(first + t);
+                        for (int q = 0; q < 3 && below; ++q) {
+                            const float4 w = __ldg(tp + q);
+                            below = box_below_tangent(w.x, w.x, w.y, w.y, w.z, w.z, ox, oy, oz, nx, ny, nz);
+                        }
+                    }
+                    if (below) continue;
+                }
                 if (ne >= 4 * kFrontGroups) { ok = false; break; }
                 float* gp = g + 28 * (ne >> 2) + (ne & 3);
                 gp[0] = LX[k]; gp[4] = HX[k]; gp[8] = LY[k]; gp[12] = HY[k]; gp[16] = LZ[k]; gp[20] = HZ[k];
