@@ -778,7 +778,7 @@ __device__ __forceinline__ void warp_add_counters(unsigned long long* counters, 
 // order once the point is done; the count is the sum of the tile ballots.
 // ---------------------------------------------------------------------------
 #ifndef RC_HEMI_MIN_BLOCKS
-#define RC_HEMI_MIN_BLOCKS 6
+#define RC_HEMI_MIN_BLOCKS 7
 #endif
 #ifndef RC_TAIL_SPLITS
 #define RC_TAIL_SPLITS 4
@@ -1631,7 +1631,7 @@ rc_status launch_batch(const BatchPart* d_parts, int n_parts, long long n_items,
 {
     const int threads = 128;
     const size_t smem = cast_smem(threads / 32, (p->n_dirs + 31) / 32, use_wide(p));
-    const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_HEMI_MIN_BLOCKS;
+    const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : RC_BATCH_MIN_BLOCKS;
     int64_t blocks = (int64_t)sm_count() * per_sm;
     const int64_t need = (n_items * 32 + threads - 1) / threads;
     if (blocks > need) blocks = need;
