@@ -23,7 +23,13 @@
  *    a caller pointer after it returns, except where stated (batches).
  *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
  *    default stream).  Work is queued asynchronously on it unless the call
- *    says it synchronises.  Calls never use another stream.
+ *    says it synchronises.  A call that forks work onto streams of its own
+ *    (rc_analyze_part, the batch's graph branches, the server's slots) joins
+ *    them before it returns or orders them before later work on `stream`.
+ *  - Devices: a call that takes a BVH handle runs on the device the handle
+ *    was built on; it makes that device current on the calling thread and
+ *    leaves it current (rc_destroy_bvh and the server calls restore the
+ *    caller's device), so `stream` must belong to that device.
  *  - Layouts: points, normals and vertices are row-major float32 xyz
  *    ([n][3]); faces are int32 vertex indices ([T][3]), wound
  *    counter-clockwise seen from outside (the normal is the right-hand rule

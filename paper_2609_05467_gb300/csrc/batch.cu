@@ -448,9 +448,25 @@ rc_status rc_batch_autotune(rc_batch b, void* stream, int32_t repeats, rc_params
     const rc_params base = b->p;
     rc_params win = base;
     float best_ms = -1.0f;
-    cudaEvent_t e0, e1;
-    RC_CUDA(cudaEventCreate(&e0));
-    RC_CUDA(cudaEventCreate(&e1));
+    // the timing events are destroyed, and on a failure the batch's own
+    // parameters restored, on every path out
+    struct Tune {
+        rc_batch b;
+        rc_params base;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        bool ok = false;
+        ~Tune()
+        {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            if (!ok) {
+                b->p = base;
+                b->dirty = true;
+            }
+        }
+    } tune{b, base};
+    RC_CUDA(cudaEventCreate(&tune.e0));
+    RC_CUDA(cudaEventCreate(&tune.e1));
     const int per_sm[] = {4, 6, 8};
     const int ppis[] = {1, 2, 4};
     for (int order = 0; order < 2; ++order)
@@ -465,17 +481,16 @@ rc_status rc_batch_autotune(rc_batch b, void* stream, int32_t repeats, rc_params
                     b->p = c;
                     b->dirty = true;
                     rc_status st = rc_batch_launch(b, stream);   // capture + warm-up
-                    if (st != RC_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); b->p = base; return st; }
-                    RC_CUDA(cudaEventRecord(e0, s));
+                    if (st != RC_OK) return st;
+                    RC_CUDA(cudaEventRecord(tune.e0, s));
                     for (int r = 0; r < repeats; ++r) RC_CUDA(cudaGraphLaunch(b->exec, s));
-                    RC_CUDA(cudaEventRecord(e1, s));
-                    RC_CUDA(cudaEventSynchronize(e1));
+                    RC_CUDA(cudaEventRecord(tune.e1, s));
+                    RC_CUDA(cudaEventSynchronize(tune.e1));
                     float ms = 0.0f;
-                    RC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    RC_CUDA(cudaEventElapsedTime(&ms, tune.e0, tune.e1));
                     if (best_ms < 0.0f || ms < best_ms) { best_ms = ms; win = c; }
                 }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    tune.ok = true;
     b->p = win;
     b->dirty = true;
     if (best) *best = win;

@@ -367,6 +367,17 @@ static double box_volume(const long long* box6)
     return (e[0] * e[1]) * e[2];
 }
 
+// device scratch freed in stream order when the scope ends, on every path
+struct ScratchFree {
+    cudaStream_t s;
+    void* p[3] = {nullptr, nullptr, nullptr};
+    ~ScratchFree()
+    {
+        for (void* q : p)
+            if (q) cudaFreeAsync(q, s);
+    }
+};
+
 static rc_status on_device(rc_bvh h)
 {
     int dev = 0;
@@ -381,7 +392,9 @@ static rc_status principal_frame(rc_bvh h, cudaStream_t s, double w[3], bool* ok
     *ok = false;
     w[0] = w[1] = w[2] = 0.0;
     double* part = nullptr;
+    ScratchFree sf{s};
     RC_CUDA(cudaMallocAsync(&part, sizeof(double) * 10 * (kMomentBlocks + 1), s));
+    sf.p[0] = part;
     const double r[3] = {0.5 * ((double)h->lo[0] + (double)h->hi[0]), 0.5 * ((double)h->lo[1] + (double)h->hi[1]),
                          0.5 * ((double)h->lo[2] + (double)h->hi[2])};
     k_moments<<<kMomentBlocks, kMomentThreads, 0, s>>>(h->V, h->F, h->farea, h->T, r[0], r[1], r[2], part);
@@ -390,7 +403,6 @@ static rc_status principal_frame(rc_bvh h, cudaStream_t s, double w[3], bool* ok
     RC_LAUNCHED();
     double m[10];
     RC_CUDA(cudaMemcpyAsync(m, part + 10 * kMomentBlocks, sizeof m, cudaMemcpyDeviceToHost, s));
-    RC_CUDA(cudaFreeAsync(part, s));
     RC_CUDA(cudaStreamSynchronize(s));
     const double S0 = m[0];
     if (!(S0 > 0.0)) return RC_OK;
@@ -502,26 +514,27 @@ rc_status rc_frame_candidates(rc_bvh h, const rc_params* p, rc_frames* out, void
     std::vector<double> G;
     for (int b = 0; b < nb; ++b) box_rotations(bases[b], G);
     const int nf = (int)(G.size() / 9);
+    const int64_t chunks = std::max<int64_t>(1, (h->nV + kBoxChunk - 1) / kBoxChunk);
+    if (chunks > 0x7FFFFFFF) return set_error(RC_E_UNSUPPORTED, "too many vertices");
     double* dG = nullptr;
     long long* dbox = nullptr;
     int* dbox32 = nullptr;
+    ScratchFree sf{s};
     RC_CUDA(cudaMallocAsync(&dG, sizeof(double) * G.size(), s));
+    sf.p[0] = dG;
     RC_CUDA(cudaMallocAsync(&dbox, sizeof(long long) * 6 * nf, s));
+    sf.p[1] = dbox;
     RC_CUDA(cudaMallocAsync(&dbox32, sizeof(int) * 9 * nf, s));
+    sf.p[2] = dbox32;
     RC_CUDA(cudaMemcpyAsync(dG, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice, s));
     k_box_init<<<(9 * nf + 255) / 256, 256, 0, s>>>(dbox, dbox32, nf);
     RC_LAUNCHED();
-    const int64_t chunks = std::max<int64_t>(1, (h->nV + kBoxChunk - 1) / kBoxChunk);
-    if (chunks > 0x7FFFFFFF) return set_error(RC_E_UNSUPPORTED, "too many vertices");
     k_box_pass32<<<dim3((unsigned)chunks, (unsigned)nf), kBoxThreads, 0, s>>>(h->V, h->nV, dG, dbox32);
     RC_LAUNCHED();
     k_box_pass64<<<dim3((unsigned)chunks, (unsigned)nf), kBoxThreads, 0, s>>>(h->V, h->nV, dG, dbox32, dbox);
     RC_LAUNCHED();
     std::vector<long long> box(6 * (size_t)nf);
     RC_CUDA(cudaMemcpyAsync(box.data(), dbox, sizeof(long long) * 6 * nf, cudaMemcpyDeviceToHost, s));
-    RC_CUDA(cudaFreeAsync(dG, s));
-    RC_CUDA(cudaFreeAsync(dbox, s));
-    RC_CUDA(cudaFreeAsync(dbox32, s));
     RC_CUDA(cudaStreamSynchronize(s));
     // candidates: each base, then its best rotation, negative zeros made
     // positive; a frame whose axes are (up to sign and order) those of an

@@ -237,10 +237,22 @@ static rc_status run_request(rc_server s, SrvRequest* r, SrvEntry* e, cudaStream
     // computes it after delivering the result, before the part is released)
     const bool candidate = e->h && e->T == r->T && e->nV == r->nV;
     const uint64_t fh = candidate ? hash_faces(r->F.data(), r->T * 3) : 0;
+    // the request's scratch (vertices, faces, changed-face flags) is freed
+    // in stream order when this function returns, on every path
+    struct Scratch {
+        cudaStream_t st;
+        void* p[3] = {nullptr, nullptr, nullptr};
+        ~Scratch()
+        {
+            for (void* q : p)
+                if (q) cudaFreeAsync(q, st);
+        }
+    } tmp{st};
     // geometry: refit when the triangle list is unchanged, else (re)build
     float* dV = nullptr;
     int32_t* dF = nullptr;
     SRV_CUDA(cudaMallocAsync(&dV, sizeof(float) * 3 * r->nV, st));
+    tmp.p[0] = dV;
     SRV_CUDA(cudaMemcpyAsync(dV, r->V.data(), sizeof(float) * 3 * r->nV, cudaMemcpyHostToDevice, st));
     rc_status rs;
     const bool same_topology = candidate && e->fhash_valid && e->fhash == fh;
@@ -253,12 +265,8 @@ static rc_status run_request(rc_server s, SrvRequest* r, SrvEntry* e, cudaStream
     if (incremental) {
         // compare with the resident vertices before the refit replaces them
         SRV_CUDA(cudaMallocAsync(&changed, (size_t)r->T, st));
-        rs = rc_changed_faces(e->h->V, dV, r->nV, e->h->F, r->T, changed, box, &n_changed, st);
-        if (rs != RC_OK) {
-            cudaFreeAsync(changed, st);
-            cudaFreeAsync(dV, st);
-            return rs;
-        }
+        tmp.p[2] = changed;
+        SRV_TRY(rc_changed_faces(e->h->V, dV, r->nV, e->h->F, r->T, changed, box, &n_changed, st));
     }
     if (same_topology) {
         rs = rc_refit_bvh(e->h, dV, st);
@@ -267,16 +275,12 @@ static rc_status run_request(rc_server s, SrvRequest* r, SrvEntry* e, cudaStream
         if (e->h) rc_destroy_bvh(e->h);
         e->h = nullptr;
         SRV_CUDA(cudaMallocAsync(&dF, sizeof(int32_t) * 3 * r->T, st));
+        tmp.p[1] = dF;
         SRV_CUDA(cudaMemcpyAsync(dF, r->F.data(), sizeof(int32_t) * 3 * r->T, cudaMemcpyHostToDevice, st));
         rs = rc_build_bvh(dV, r->nV, dF, r->T, st, &e->h);
         r->res.rebuilt = 1;
     }
-    cudaFreeAsync(dV, st);
-    if (dF) cudaFreeAsync(dF, st);
-    if (rs != RC_OK) {
-        if (changed) cudaFreeAsync(changed, st);
-        return rs;
-    }
+    if (rs != RC_OK) return rs;
     e->T = r->T;
     e->nV = r->nV;
     e->fhash = fh;
@@ -305,7 +309,6 @@ static rc_status run_request(rc_server s, SrvRequest* r, SrvEntry* e, cudaStream
         if (rs == RC_OK)
             rs = rc_hemisphere_update(e->h, e->P, e->Nn, e->face, n, changed, box, &p, e->bits, e->count, e->ctr,
                                       st);
-        cudaFreeAsync(changed, st);
         if (rs != RC_OK) return rs;
         r->res.updated = 1;
     } else {
@@ -326,6 +329,21 @@ static rc_status run_request(rc_server s, SrvRequest* r, SrvEntry* e, cudaStream
     r->res.resident_bytes = resident_bytes(r->nV, r->T, n, N);
     return RC_OK;
 }
+
+// The server's device is current for the scope of an API call made from
+// the caller's thread, and the caller's device is restored afterwards.
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceScope()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 static void worker(rc_server s, int slot)
 {
@@ -508,8 +526,22 @@ rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, 
     const int64_t words = (int64_t)((e->N + 31) / 32) * n;
     if (h_bits && bits_words < words)
         return set_error(RC_E_ARG, "h_bits holds fewer than n * ceil(n_dirs / 32) words");
-    if (h_bits && n) RC_CUDA(cudaMemcpy(h_bits, e->bits, sizeof(uint32_t) * words, cudaMemcpyDeviceToHost));
-    if (h_count && n) RC_CUDA(cudaMemcpy(h_count, e->count, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    // copy with the lock released; the part stays busy meanwhile, so it is
+    // neither re-analysed nor evicted
+    e->busy = true;
+    lk.unlock();
+    cudaError_t ce = cudaSuccess;
+    {
+        DeviceScope ds(s->device);
+        if (h_bits && n) ce = cudaMemcpy(h_bits, e->bits, sizeof(uint32_t) * words, cudaMemcpyDeviceToHost);
+        if (ce == cudaSuccess && h_count && n) ce = cudaMemcpy(h_count, e->count, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+    }
+    lk.lock();
+    e->busy = false;
+    e->last_use = ++s->tick;
+    s->cv_work.notify_all();
+    s->cv_done.notify_all();
+    if (ce != cudaSuccess) return cuda_error(ce, "cudaMemcpy (resident bits)");
     return RC_OK;
 }
 
@@ -535,6 +567,7 @@ rc_status rc_server_destroy(rc_server s)
     }
     s->cv_work.notify_all();
     for (std::thread& t : s->workers) t.join();
+    DeviceScope ds(s->device);
     for (cudaStream_t q : s->streams) cudaStreamSynchronize(q);
     for (auto& kv : s->cache) free_entry(kv.second);
     for (auto& kv : s->reqs) delete kv.second;

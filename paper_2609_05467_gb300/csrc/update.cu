@@ -127,6 +127,16 @@ __global__ void k_changed_init(int* box, unsigned long long* n_changed, unsigned
     }
 }
 
+// one device scratch buffer, freed in stream order when the scope ends
+struct ScratchOne {
+    cudaStream_t s;
+    void* p = nullptr;
+    ~ScratchOne()
+    {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+
 static rc_status on_device(rc_bvh h)
 {
     int dev = 0;
@@ -154,7 +164,9 @@ rc_status rc_sample_points_on_faces(rc_bvh h, int64_t n, const rc_params* p, con
     if ((st = on_device(h)) != RC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned long long* bad = nullptr;
+    ScratchOne sf{s};
     RC_CUDA(cudaMallocAsync(&bad, sizeof(unsigned long long), s));
+    sf.p = bad;
     RC_CUDA(cudaMemsetAsync(bad, 0xFF, sizeof(unsigned long long), s));
     k_sample_on_faces<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->V, h->F, h->T, h->fnorm, n, p->seed,
                                                                   p->sample_mode == RC_SAMPLE_FACE_CENTROID, d_face,
@@ -162,7 +174,6 @@ rc_status rc_sample_points_on_faces(rc_bvh h, int64_t n, const rc_params* p, con
     RC_LAUNCHED();
     unsigned long long hb = 0;
     RC_CUDA(cudaMemcpyAsync(&hb, bad, sizeof hb, cudaMemcpyDeviceToHost, s));
-    RC_CUDA(cudaFreeAsync(bad, s));
     RC_CUDA(cudaStreamSynchronize(s));
     if (hb != ~0ULL) return set_error(RC_E_ARG, "face of point " + std::to_string(hb) + " is outside [0, T)");
     return RC_OK;
@@ -178,7 +189,9 @@ rc_status rc_changed_faces(const float* d_V_old, const float* d_V_new, int64_t n
     cudaStream_t s = (cudaStream_t)stream;
     struct Scratch { int box[6]; int pad[2]; unsigned long long n, bad; };
     Scratch* d = nullptr;
+    ScratchOne sf{s};
     RC_CUDA(cudaMallocAsync(&d, sizeof(Scratch), s));
+    sf.p = d;
     k_changed_init<<<1, 32, 0, s>>>(d->box, &d->n, &d->bad);
     RC_LAUNCHED();
     if (T > 0) {
@@ -188,7 +201,6 @@ rc_status rc_changed_faces(const float* d_V_old, const float* d_V_new, int64_t n
     }
     Scratch hs;
     RC_CUDA(cudaMemcpyAsync(&hs, d, sizeof hs, cudaMemcpyDeviceToHost, s));
-    RC_CUDA(cudaFreeAsync(d, s));
     RC_CUDA(cudaStreamSynchronize(s));
     if (hs.bad != ~0ULL) return set_error(RC_E_ARG, "face " + std::to_string(hs.bad) + " has a vertex index outside [0, nV)");
     *h_n_changed = (int64_t)hs.n;
