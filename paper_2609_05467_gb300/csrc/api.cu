@@ -190,6 +190,17 @@ static rc_status scene_box(rc_bvh h)
     return RC_OK;
 }
 
+// device scratch freed in stream order when the scope ends, on every path
+struct ScratchFree {
+    cudaStream_t s;
+    void* p[3] = {nullptr, nullptr, nullptr};
+    ~ScratchFree()
+    {
+        for (void* q : p)
+            if (q) cudaFreeAsync(q, s);
+    }
+};
+
 static rc_status use_device_of(rc_bvh h)
 {
     int dev = 0;
@@ -438,14 +449,15 @@ rc_status rc_direction_variability(const uint32_t* d_bits, const float* d_N, con
     const float4* dirs = nullptr;
     if ((st = device_dirs(p->n_dirs, &dirs)) != RC_OK) return st;
     void* scratch = nullptr;
-    RC_CUDA(cudaMallocAsync(&scratch, kVarScratchBytes, s));
-    st = launch_variability(d_bits, d_N, d_weight, n, dirs, p, d_acc, d_dom, d_conc, d_dir_area, scratch, s);
-    if (st != RC_OK) { cudaFreeAsync(scratch, s); return st; }
     unsigned char back[kVarPartOffset];
-    if (h_summary) {
-        RC_CUDA(cudaMemcpyAsync(back, scratch, sizeof back, cudaMemcpyDeviceToHost, s));
+    {
+        ScratchFree sf{s};
+        RC_CUDA(cudaMallocAsync(&scratch, kVarScratchBytes, s));
+        sf.p[0] = scratch;
+        st = launch_variability(d_bits, d_N, d_weight, n, dirs, p, d_acc, d_dom, d_conc, d_dir_area, scratch, s);
+        if (st != RC_OK) return st;
+        if (h_summary) RC_CUDA(cudaMemcpyAsync(back, scratch, sizeof back, cudaMemcpyDeviceToHost, s));
     }
-    RC_CUDA(cudaFreeAsync(scratch, s));
     if (!h_summary) return RC_OK;
     RC_CUDA(cudaStreamSynchronize(s));
     fill_summary((const long long*)back, (const double*)(back + kVarWsumOffset), n, p->n_dirs, d_weight != nullptr,
@@ -495,19 +507,21 @@ rc_status rc_min_setups(rc_bvh h, const uint8_t* d_mask, const float* d_travel, 
     FrameDev* fd = nullptr;
     uint8_t* fixture = nullptr;
     unsigned long long* hist = nullptr;
-    RC_CUDA(cudaMallocAsync(&fd, sizeof(FrameDev), s));
-    RC_CUDA(cudaMallocAsync(&fixture, h->T, s));
-    RC_CUDA(cudaMallocAsync(&hist, sizeof(unsigned long long) * 68, s));
-    RC_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 68, s));
-    st = frame_setup(h, p, fd, s);
-    if (st == RC_OK)
-        st = launch_classes(h, d_mask, d_travel, d_face, n, p, d_class, fd->frame, fd->fbox, fixture, hist, s);
     unsigned long long hh[68];
-    if (st == RC_OK) RC_CUDA(cudaMemcpyAsync(hh, hist, sizeof hh, cudaMemcpyDeviceToHost, s));
-    cudaFreeAsync(fd, s);
-    cudaFreeAsync(fixture, s);
-    cudaFreeAsync(hist, s);
-    if (st != RC_OK) return st;
+    {
+        ScratchFree sf{s};
+        RC_CUDA(cudaMallocAsync(&fd, sizeof(FrameDev), s));
+        sf.p[0] = fd;
+        RC_CUDA(cudaMallocAsync(&fixture, h->T, s));
+        sf.p[1] = fixture;
+        RC_CUDA(cudaMallocAsync(&hist, sizeof(unsigned long long) * 68, s));
+        sf.p[2] = hist;
+        RC_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 68, s));
+        if ((st = frame_setup(h, p, fd, s)) != RC_OK) return st;
+        st = launch_classes(h, d_mask, d_travel, d_face, n, p, d_class, fd->frame, fd->fbox, fixture, hist, s);
+        if (st != RC_OK) return st;
+        RC_CUDA(cudaMemcpyAsync(hh, hist, sizeof hh, cudaMemcpyDeviceToHost, s));
+    }
     RC_CUDA(cudaStreamSynchronize(s));
     memset(h_out, 0, sizeof *h_out);
     for (int k = 0; k < 64; ++k) h_out->mask_hist[k] = (int64_t)hh[k];
