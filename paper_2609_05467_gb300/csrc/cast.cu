@@ -1312,20 +1312,32 @@ static int sm_count()
 
 rc_status point_order(rc_bvh h, const float* P, int64_t n, int32_t* order, cudaStream_t s);
 
+// device scratch of a launch, freed in stream order when the scope ends
+struct LaunchScratch {
+    cudaStream_t s;
+    void* p[3] = {nullptr, nullptr, nullptr};
+    ~LaunchScratch()
+    {
+        for (void* q : p)
+            if (q) cudaFreeAsync(q, s);
+    }
+};
+
 rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
                             uint32_t* bits, int32_t* count, unsigned long long* counters, bool stats,
                             cudaStream_t s, long long* relist, long long relist_cap)
 {
+    LaunchScratch ls{s};
     unsigned long long* work = nullptr;
-    unsigned long long* work_alloc = nullptr;
     if (p->launch_mode == 0) {
-        RC_CUDA(cudaMallocAsync(&work_alloc, sizeof(unsigned long long), s));
-        RC_CUDA(cudaMemsetAsync(work_alloc, 0, sizeof(unsigned long long), s));
-        work = work_alloc;
+        RC_CUDA(cudaMallocAsync(&work, sizeof(unsigned long long), s));
+        ls.p[0] = work;
+        RC_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
     }
     int32_t* order = nullptr;
     if (p->point_order == 0 && n > 1) {
         RC_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * n, s));
+        ls.p[1] = order;
         rc_status st = point_order(h, P, n, order, s);
         if (st != RC_OK) return st;
     }
@@ -1376,8 +1388,6 @@ rc_status launch_hemisphere(rc_bvh h, const float* P, const float* N, int64_t n,
 #undef RC_HEMI
     }
     RC_LAUNCHED();
-    if (work_alloc) RC_CUDA(cudaFreeAsync(work_alloc, s));
-    if (order) RC_CUDA(cudaFreeAsync(order, s));
     return RC_OK;
 }
 
@@ -1388,12 +1398,15 @@ rc_status launch_hemisphere_update(rc_bvh h, const float* P, const float* N, int
                                    const rc_params* p, uint32_t* bits, int32_t* count, unsigned long long* counters,
                                    cudaStream_t s)
 {
+    LaunchScratch ls{s};
     unsigned long long* work = nullptr;
     RC_CUDA(cudaMallocAsync(&work, sizeof(unsigned long long), s));
+    ls.p[0] = work;
     RC_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
     int32_t* order = nullptr;
     if (p->point_order == 0 && n > 1) {
         RC_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * n, s));
+        ls.p[1] = order;
         rc_status st = point_order(h, P, n, order, s);
         if (st != RC_OK) return st;
     }
@@ -1422,8 +1435,6 @@ rc_status launch_hemisphere_update(rc_bvh h, const float* P, const float* N, int
                                                                           p->origin_offset, bits, count, counters,
                                                                           work);
     RC_LAUNCHED();
-    RC_CUDA(cudaFreeAsync(work, s));
-    if (order) RC_CUDA(cudaFreeAsync(order, s));
     return RC_OK;
 }
 
@@ -1545,18 +1556,18 @@ rc_status launch_orthogonal_frames(rc_bvh h, const float* P, const float* N, int
                                    unsigned long long* counters, cudaStream_t s)
 {
     if (n == 0) return RC_OK;
+    LaunchScratch ls{s};
     int32_t* order = nullptr;
     if (p->point_order == 0 && n > 1) {
         RC_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * n, s));
+        ls.p[0] = order;
         rc_status pst = point_order(h, P, n, order, s);
         if (pst != RC_OK) return pst;
     }
     uint32_t* mbits = nullptr;
     RC_CUDA(cudaMallocAsync(&mbits, sizeof(uint32_t) * ortho_scratch_words(nf, n), s));
-    const rc_status st = launch_orthogonal_frames_into(h, P, N, n, p, fds, nf, mask, travel, counters, order, mbits, s);
-    cudaFreeAsync(mbits, s);
-    if (order) cudaFreeAsync(order, s);
-    return st;
+    ls.p[1] = mbits;
+    return launch_orthogonal_frames_into(h, P, N, n, p, fds, nf, mask, travel, counters, order, mbits, s);
 }
 
 rc_status launch_orthogonal(rc_bvh h, const float* P, const float* N, int64_t n, const rc_params* p,
