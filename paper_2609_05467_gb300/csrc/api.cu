@@ -191,10 +191,10 @@ static rc_status scene_box(rc_bvh h)
 }
 
 // device scratch freed in stream order when the scope ends, on every path
-struct ScratchFree {
+struct ApiScratch {
     cudaStream_t s;
     void* p[3] = {nullptr, nullptr, nullptr};
-    ~ScratchFree()
+    ~ApiScratch()
     {
         for (void* q : p)
             if (q) cudaFreeAsync(q, s);
@@ -451,7 +451,7 @@ rc_status rc_direction_variability(const uint32_t* d_bits, const float* d_N, con
     void* scratch = nullptr;
     unsigned char back[kVarPartOffset];
     {
-        ScratchFree sf{s};
+        ApiScratch sf{s};
         RC_CUDA(cudaMallocAsync(&scratch, kVarScratchBytes, s));
         sf.p[0] = scratch;
         st = launch_variability(d_bits, d_N, d_weight, n, dirs, p, d_acc, d_dom, d_conc, d_dir_area, scratch, s);
@@ -509,7 +509,7 @@ rc_status rc_min_setups(rc_bvh h, const uint8_t* d_mask, const float* d_travel, 
     unsigned long long* hist = nullptr;
     unsigned long long hh[68];
     {
-        ScratchFree sf{s};
+        ApiScratch sf{s};
         RC_CUDA(cudaMallocAsync(&fd, sizeof(FrameDev), s));
         sf.p[0] = fd;
         RC_CUDA(cudaMallocAsync(&fixture, h->T, s));

@@ -24,6 +24,19 @@
 
 namespace rc {
 
+// device scratch of a build step, freed in stream order when the scope ends
+// (on every path, error returns included)
+struct BuildScratch {
+    cudaStream_t s;
+    void* p[3] = {nullptr, nullptr, nullptr};
+    ~BuildScratch()
+    {
+        for (void* q : p)
+            if (q) cudaFreeAsync(q, s);
+    }
+};
+
+
 // ---------------------------------------------------------------------------
 // face preparation and validation
 // ---------------------------------------------------------------------------
@@ -886,7 +899,9 @@ static rc_status scan_inclusive(long long* x, int64_t n, cudaStream_t s)
     if (n <= 0) return RC_OK;
     const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
     long long* bs = nullptr;
+    BuildScratch g{s};
     RC_CUDA(cudaMallocAsync(&bs, sizeof(long long) * nb, s));
+    g.p[0] = bs;
     k_scan_block<<<(unsigned)nb, kScanBlock, 0, s>>>(x, n, bs);
     RC_LAUNCHED();
     if (nb > 1) {
@@ -895,7 +910,6 @@ static rc_status scan_inclusive(long long* x, int64_t n, cudaStream_t s)
         k_scan_add<<<(unsigned)nb, kScanBlock, 0, s>>>(x, n, bs);
         RC_LAUNCHED();
     }
-    RC_CUDA(cudaFreeAsync(bs, s));
     return RC_OK;
 }
 
@@ -1001,9 +1015,13 @@ static rc_status sort_pairs(unsigned long long* keys, int32_t* vals, int64_t n, 
     int64_t tile = (n + 2 * sms - 1) / (2 * sms);
     tile = std::min<int64_t>(kSortTile, std::max<int64_t>(512, (tile + kSortThreads - 1) / kSortThreads * kSortThreads));
     const int nblk = (int)((n + tile - 1) / tile);
+    BuildScratch g{s};
     RC_CUDA(cudaMallocAsync(&k1, sizeof(unsigned long long) * n, s));
+    g.p[0] = k1;
     RC_CUDA(cudaMallocAsync(&v1, sizeof(int32_t) * n, s));
+    g.p[1] = v1;
     RC_CUDA(cudaMallocAsync(&counts, sizeof(unsigned int) * (256 * (size_t)nblk + 256), s));   // counts, then digit totals
+    g.p[2] = counts;
     unsigned long long *kin = keys, *kout = k1;
     int32_t *vin = vals, *vout = v1;
     for (int pass = 0; pass < passes; ++pass) {
@@ -1018,9 +1036,6 @@ static rc_status sort_pairs(unsigned long long* keys, int32_t* vals, int64_t n, 
         std::swap(kin, kout);
         std::swap(vin, vout);
     }
-    RC_CUDA(cudaFreeAsync(k1, s));
-    RC_CUDA(cudaFreeAsync(v1, s));
-    RC_CUDA(cudaFreeAsync(counts, s));
     return RC_OK;
 }
 
@@ -1029,7 +1044,9 @@ static rc_status sort_pairs(unsigned long long* keys, int32_t* vals, int64_t n, 
 rc_status point_order(rc_bvh h, const float* P, int64_t n, int32_t* order, cudaStream_t s)
 {
     unsigned long long* keys = nullptr;
+    BuildScratch g{s};
     RC_CUDA(cudaMallocAsync(&keys, sizeof(unsigned long long) * n, s));
+    g.p[0] = keys;
     float sc[3];
     for (int k = 0; k < 3; ++k) {
         const float ext = h->hi[k] - h->lo[k];
@@ -1038,10 +1055,7 @@ rc_status point_order(rc_bvh h, const float* P, int64_t n, int32_t* order, cudaS
     k_point_morton<<<nblocks(n, 256), 256, 0, s>>>(P, n, h->lo[0], h->lo[1], h->lo[2], sc[0], sc[1], sc[2], keys,
                                                    order);
     RC_LAUNCHED();
-    rc_status st = sort_pairs(keys, order, n, 4, (unsigned int*)&h->sc->pad, s);
-    if (st != RC_OK) return st;
-    RC_CUDA(cudaFreeAsync(keys, s));
-    return RC_OK;
+    return sort_pairs(keys, order, n, 4, (unsigned int*)&h->sc->pad, s);
 }
 
 __global__ void k_init_scalars(DevScalars* sc)
@@ -1118,7 +1132,9 @@ static rc_status build_ploc(rc_bvh h, const float* tbox, cudaStream_t s)
     const size_t o_szi = take(4 * n_int), o_nid = take(4 * n_int), o_ls = take(4 * n_int), o_pos = take(4 * T);
     const size_t o_ord = take(4 * T);
     char* base = nullptr;
+    BuildScratch g{s};
     RC_CUDA(cudaMallocAsync((void**)&base, off, s));
+    g.p[0] = base;
     int32_t* cl_a = (int32_t*)(base + o_cla);
     int32_t* cl_t = (int32_t*)(base + o_clt);
     float* cb_a = (float*)(base + o_cba);
@@ -1144,10 +1160,7 @@ static rc_status build_ploc(rc_bvh h, const float* tbox, cudaStream_t s)
     const int kRoundsPerCheck = 8;
     int rounds = 0;
     while (n_host > 1) {
-        if (rounds > 64 + 8 * 64) {
-            cudaFreeAsync(base, s);
-            return set_error(RC_E_DEVICE, "PLOC build did not converge");
-        }
+        if (rounds > 64 + 8 * 64) return set_error(RC_E_DEVICE, "PLOC build did not converge");
         const unsigned g_nn = (unsigned)((n_host + kPlocThreads - 1) / kPlocThreads);
         const unsigned g_c = (unsigned)((n_host + kCompact - 1) / kCompact);
         for (int r = 0; r < kRoundsPerCheck; ++r, ++rounds) {
@@ -1168,10 +1181,8 @@ static rc_status build_ploc(rc_bvh h, const float* tbox, cudaStream_t s)
         RC_CUDA(cudaMemcpyAsync(hn, dn, sizeof hn, cudaMemcpyDeviceToHost, s));
         RC_CUDA(cudaStreamSynchronize(s));
         n_host = hn[cur];
-        if (n_host == 1 && hn[2] != n_int) {
-            cudaFreeAsync(base, s);
+        if (n_host == 1 && hn[2] != n_int)
             return set_error(RC_E_DEVICE, "PLOC build made a wrong number of interior nodes");
-        }
     }
     // depth-first renumbering into the Karras layout
     RC_CUDA(cudaMemsetAsync(h->visits, 0, sizeof(int32_t) * n_int, s));
@@ -1187,7 +1198,6 @@ static rc_status build_ploc(rc_bvh h, const float* tbox, cudaStream_t s)
     RC_CUDA(cudaMemcpyAsync(h->order, order_out, sizeof(int32_t) * T, cudaMemcpyDeviceToDevice, s));
     int herr = 0;
     RC_CUDA(cudaMemcpyAsync(&herr, dn + 3, sizeof herr, cudaMemcpyDeviceToHost, s));
-    RC_CUDA(cudaFreeAsync(base, s));
     RC_CUDA(cudaStreamSynchronize(s));
     if (herr) return set_error(RC_E_DEVICE, "PLOC tree walk exceeded its bound");
     return RC_OK;
@@ -1207,8 +1217,11 @@ static rc_status build_wide(rc_bvh h, const float* tbox, cudaStream_t s)
     const int64_t n_int = h->n_int;
     int32_t* q = nullptr;
     int* counts = nullptr;
+    BuildScratch g{s};
     RC_CUDA(cudaMallocAsync(&q, sizeof(int32_t) * 4 * n_int, s));
+    g.p[0] = q;
     RC_CUDA(cudaMallocAsync(&counts, sizeof(int) * 4, s));
+    g.p[1] = counts;
     int32_t *qa_bin = q, *qa_wide = q + n_int, *qb_bin = q + 2 * n_int, *qb_wide = q + 3 * n_int;
     int *ca = counts, *cb = counts + 1;
     k_wide_init<<<1, 32, 0, s>>>(qa_bin, qa_wide, counts);
@@ -1240,8 +1253,6 @@ static rc_status build_wide(rc_bvh h, const float* tbox, cudaStream_t s)
         RC_LAUNCHED();
     }
     RC_CUDA(cudaMemcpyAsync(&h->sc->wide_nodes, counts + 2, sizeof(int), cudaMemcpyDeviceToDevice, s));
-    RC_CUDA(cudaFreeAsync(q, s));
-    RC_CUDA(cudaFreeAsync(counts, s));
     return RC_OK;
 }
 
@@ -1329,12 +1340,15 @@ rc_status frame_tree(rc_bvh h, const float f9[9], float4* ftree, cudaStream_t s)
     for (int k = 0; k < 9; ++k) fa.f[k] = f9[k];
     float* nbox_f = nullptr;
     int32_t* visits = nullptr;
+    BuildScratch g{s};
     RC_CUDA(cudaMallocAsync(&nbox_f, sizeof(float) * 6 * (n_int + T + 1), s));
+    g.p[0] = nbox_f;
     float* all_box = nbox_f + 6 * (n_int + T);
     k_frame_leaf_boxes<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(h->V, h->F, h->order, T, h->nV, n_int, fa, nbox_f);
     RC_LAUNCHED();
     if (T > kLeafMax) {
         RC_CUDA(cudaMallocAsync(&visits, sizeof(int32_t) * n_int, s));
+        g.p[1] = visits;
         RC_CUDA(cudaMemsetAsync(visits, 0, sizeof(int32_t) * n_int, s));
         k_refit<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(T, n_int, h->parent, h->child, nbox_f, visits, h->sc);
         RC_LAUNCHED();
@@ -1344,8 +1358,6 @@ rc_status frame_tree(rc_bvh h, const float f9[9], float4* ftree, cudaStream_t s)
     }
     k_frame_pack<<<(unsigned)((n_int + 255) / 256), 256, 0, s>>>(h->wnodes, n_int, T, h->sc, nbox_f, all_box, ftree);
     RC_LAUNCHED();
-    if (visits) RC_CUDA(cudaFreeAsync(visits, s));
-    RC_CUDA(cudaFreeAsync(nbox_f, s));
     return RC_OK;
 }
 
@@ -1353,7 +1365,9 @@ rc_status build_bvh(rc_bvh h, cudaStream_t s)
 {
     const int64_t T = h->T;
     float* tbox = nullptr;
+    BuildScratch g{s};
     RC_CUDA(cudaMallocAsync(&tbox, sizeof(float) * 6 * T, s));
+    g.p[0] = tbox;
     // No host synchronisation until the end: a bad mesh is reported from the
     // one final readback (every kernel in between guards its gathers).
     rc_status st = face_data(h, tbox, s);
@@ -1374,6 +1388,7 @@ rc_status build_bvh(rc_bvh h, cudaStream_t s)
     } else {
         unsigned long long* k0 = nullptr;
         RC_CUDA(cudaMallocAsync(&k0, sizeof(unsigned long long) * T, s));
+        g.p[1] = k0;
         k_morton<<<nblocks(T, 256), 256, 0, s>>>(tbox, T, h->sc, k0, h->order);
         RC_LAUNCHED();
         rc_status sst = sort_pairs(k0, h->order, T, kMortonPasses, (unsigned int*)&h->sc->pad, s);
@@ -1399,13 +1414,11 @@ rc_status build_bvh(rc_bvh h, cudaStream_t s)
         RC_LAUNCHED();
         k_pack<<<nblocks(n_int, 256), 256, 0, s>>>(n_int, h->child, h->range, h->nbox, h->nodes);
         RC_LAUNCHED();
-        RC_CUDA(cudaFreeAsync(k0, s));
     }
     st = build_wide(h, tbox, s);
     if (st != RC_OK) return st;
     k_tri_records<<<nblocks(T, 256), 256, 0, s>>>(h->V, h->nV, h->F, h->order, T, h->tris);
     RC_LAUNCHED();
-    RC_CUDA(cudaFreeAsync(tbox, s));
     RC_CUDA(cudaMemcpyAsync(&h->host_sc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaStreamSynchronize(s));
     if ((st = checked_scalars(h)) != RC_OK) return st;
@@ -1426,11 +1439,13 @@ rc_status refit_bvh(rc_bvh h, cudaStream_t s)
 {
     const int64_t T = h->T;
     float* tbox = nullptr;
+    BuildScratch g{s};
     RC_CUDA(cudaMallocAsync(&tbox, sizeof(float) * 6 * T, s));
+    g.p[0] = tbox;
     rc_status st = face_data(h, tbox, s);
     if (st != RC_OK) return st;
     st = check_scalars(h, s);
-    if (st != RC_OK) { cudaFreeAsync(tbox, s); return st; }
+    if (st != RC_OK) return st;
     if (T <= kLeafMax) {
         k_pack_small<<<1, 32, 0, s>>>(T, tbox, h->nodes);
         RC_LAUNCHED();
@@ -1448,7 +1463,6 @@ rc_status refit_bvh(rc_bvh h, cudaStream_t s)
     if (st != RC_OK) return st;
     k_tri_records<<<nblocks(T, 256), 256, 0, s>>>(h->V, h->nV, h->F, h->order, T, h->tris);
     RC_LAUNCHED();
-    RC_CUDA(cudaFreeAsync(tbox, s));
     RC_CUDA(cudaMemcpyAsync(&h->host_sc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaStreamSynchronize(s));
     h->wide_depth = h->host_sc.wide_depth;

@@ -368,10 +368,10 @@ static double box_volume(const long long* box6)
 }
 
 // device scratch freed in stream order when the scope ends, on every path
-struct ScratchFree {
+struct FrameScratch {
     cudaStream_t s;
     void* p[3] = {nullptr, nullptr, nullptr};
-    ~ScratchFree()
+    ~FrameScratch()
     {
         for (void* q : p)
             if (q) cudaFreeAsync(q, s);
@@ -392,7 +392,7 @@ static rc_status principal_frame(rc_bvh h, cudaStream_t s, double w[3], bool* ok
     *ok = false;
     w[0] = w[1] = w[2] = 0.0;
     double* part = nullptr;
-    ScratchFree sf{s};
+    FrameScratch sf{s};
     RC_CUDA(cudaMallocAsync(&part, sizeof(double) * 10 * (kMomentBlocks + 1), s));
     sf.p[0] = part;
     const double r[3] = {0.5 * ((double)h->lo[0] + (double)h->hi[0]), 0.5 * ((double)h->lo[1] + (double)h->hi[1]),
@@ -519,7 +519,7 @@ rc_status rc_frame_candidates(rc_bvh h, const rc_params* p, rc_frames* out, void
     double* dG = nullptr;
     long long* dbox = nullptr;
     int* dbox32 = nullptr;
-    ScratchFree sf{s};
+    FrameScratch sf{s};
     RC_CUDA(cudaMallocAsync(&dG, sizeof(double) * G.size(), s));
     sf.p[0] = dG;
     RC_CUDA(cudaMallocAsync(&dbox, sizeof(long long) * 6 * nf, s));
