@@ -249,7 +249,11 @@ rc_status rc_direction_table(int32_t n_dirs, float* h_dirs);
  * For point i and direction j the ray is o_i = fl32(p_i + eps*n_i) (FP64),
  * d_ij = (t1*hx + t2*hy) + n*hz in float32 with (t1, t2) the orthonormal
  * basis of Duff et al. (2017); it is obstructed iff some triangle meets it
- * at t > 0.
+ * at t > 0.  Normals are taken as given: unit normals (such as
+ * rc_sample_points writes) let the walk skip what lies below a point's
+ * tangent plane, and a normal whose squared length is further than
+ * (1/(64 ceil(n_dirs/32)) - 2e-6) / 4 from 1 is cast without that shortcut,
+ * with the same result for the rays as defined.
  *   d_P, d_N [n][3]; d_bits [n][W] uint32, W = ceil(n_dirs/32), (written); d_count [n]
  *   int32 unobstructed counts (written); d_counters int64[4] (written, may be
  *   NULL): rays cast, rays decided by an ambiguous pair, ray/triangle pairs

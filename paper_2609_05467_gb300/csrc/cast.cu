@@ -394,7 +394,8 @@ __device__ __forceinline__ int slab4(const float4* __restrict__ nd, const SlabRa
 // exactly the triangles its walk from the root would test, so the same
 // decisions.  A local triangle wholly below the point's tangent plane is
 // dropped, because a hemisphere ray leaves that plane (d.n > 0 for every
-// direction of the set, N <= 65536) and meets no point of it at t > 0; that
+// direction of the set, N <= 65536, when n is of unit length to within the
+// rounding of an fp32 normal) and meets no point of it at t > 0; that
 // exact FP64 test runs once per point.  For the same reason a frontier box
 // wholly below the plane is dropped, and so is a frontier leaf whose
 // triangles all lie below it (conservative fp32 tests).  A point whose frontier or local
@@ -440,7 +441,7 @@ __device__ __forceinline__ bool box_below_tangent(float lx, float hx, float ly, 
 // contain o), its frontier and local triangles into *f.
 __device__ __noinline__ void build_frontier(const float4* __restrict__ wnodes, const float4* __restrict__ tris,
                                             int max_steps, float ox, float oy, float oz, float nx, float ny,
-                                            float nz, Frontier* f)
+                                            float nz, bool drop, Frontier* f)
 {
     int qs[kStack4];
     int qsp = 0;
@@ -470,8 +471,8 @@ __device__ __noinline__ void build_frontier(const float4* __restrict__ wnodes, c
                 for (int t = 0; t < cnt; ++t) {
                     const float4* tp = tris + 3 * (int64_t)(first + t);
                     const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-                    if (below_tangent(v0, ox, oy, oz, nx, ny, nz) && below_tangent(v1, ox, oy, oz, nx, ny, nz) &&
-                        below_tangent(v2, ox, oy, oz, nx, ny, nz))
+                    if (drop && below_tangent(v0, ox, oy, oz, nx, ny, nz) &&
+                        below_tangent(v1, ox, oy, oz, nx, ny, nz) && below_tangent(v2, ox, oy, oz, nx, ny, nz))
                         continue;
                     if (nt >= kFrontTris) { ok = false; break; }
                     f->tri[3 * nt] = v0;
@@ -482,8 +483,9 @@ __device__ __noinline__ void build_frontier(const float4* __restrict__ wnodes, c
             } else {
                 // a box below the tangent plane holds no hit of any ray of the
                 // point, and neither does a leaf whose triangles all lie below it
-                if (box_below_tangent(LX[k], HX[k], LY[k], HY[k], LZ[k], HZ[k], ox, oy, oz, nx, ny, nz)) continue;
-                if (CI[k] < 0) {
+                if (drop && box_below_tangent(LX[k], HX[k], LY[k], HY[k], LZ[k], HZ[k], ox, oy, oz, nx, ny, nz))
+                    continue;
+                if (drop && CI[k] < 0) {
                     const int v = -1 - CI[k], first = v >> 3, cnt = (v & 7) + 1;
                     bool below = true;
                     for (int t = 0; t < cnt && below; ++t) {
@@ -811,7 +813,14 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
     const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
     const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
     const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
-    if (kWide && front && lane == 0) build_frontier(nodes, tris, max_steps, ox, oy, oz, nx, ny, nz, front);
+    if (kWide && front && lane == 0) {
+        // the tangent-plane drops need every direction of the set above the
+        // plane: d.n >= z_min - 3 | |n|^2 - 1 | - 1e-6 with z_min = 1/(2N) >=
+        // 1/(64 W); a normal further from unit length keeps everything
+        const double nn = (double)nx * nx + (double)ny * ny + (double)nz * nz;
+        const bool drop = fabs(nn - 1.0) <= 0.25 * (1.0 / (64.0 * W) - 2e-6);
+        build_frontier(nodes, tris, max_steps, ox, oy, oz, nx, ny, nz, drop, front);
+    }
     __syncwarp();
     const Frontier* fr = kWide && front && front->ok ? front : nullptr;
     if (kStats && front && lane == 0) acc.nvis += front->nvis;

@@ -232,6 +232,32 @@ def test_points_whose_frontier_does_not_fit(rc, K):
     bvh.close()
 
 
+@pytest.mark.parametrize("scale", [2.0, 0.5, "mixed"])
+def test_normals_that_are_not_unit(rc, scale):
+    """The cast takes the caller's normals as given: a normal that is not of
+    unit length gives a basis whose directions can dip below the point's
+    tangent plane, so the walk must not drop the triangles and boxes below
+    that plane for such a point.  The bits must still be the oracle's for
+    the rays as defined (offset origin and directions from the given
+    normal)."""
+    V, F = PARTS["pocket"]()
+    p = rc.rc_params_default(n_dirs=256)
+    P, Nn, f, w = _points(V, F, 400, p)
+    if scale == "mixed":
+        k = np.random.default_rng(3).uniform(0.3, 3.0, size=(len(Nn), 1))
+        k[::3] = 1.0
+        Nn = (Nn * k).astype(np.float32)
+    else:
+        Nn = (Nn * np.float32(scale)).astype(np.float32)
+    bvh = _build(rc, V, F)
+    gb, gc, ctr = gpu_cast(rc, bvh.h, P, Nn, p)
+    ob, oa, oc = oracle.Mesh(V, F).hemisphere(P, Nn, 256)
+    cmp_, amb = compare_bits(gb, gc, ob, oa, oc, 256)
+    assert cmp_ + amb == len(P) * 256
+    assert ctr[0] == len(P) * 256 and ctr[3] == 0
+    bvh.close()
+
+
 def test_cast_is_deterministic(rc):
     V, F = PARTS["prismatic_coarse"]()
     bvh = _build(rc, V, F)
