@@ -291,7 +291,10 @@ rc_status rc_hemisphere_cast_retests(rc_bvh h, const float* d_P, const float* d_
  * dom = argmax_k |M_k| (ties to the lower axis; -1 if nothing is visible);
  * conc (conc_mode 0) = share of visible rays whose largest |component| is
  * axis dom, (conc_mode 1) = |M_dom| / (2^40 count).
- *   d_bits [n][W], d_N [n][3]; d_weight [n] (NULL = unit weights);
+ *   d_bits [n][W], d_N [n][3] unit normals (the world directions d_ij are
+ *   rebuilt from them as in rc_hemisphere_cast; the fixed-point sums are
+ *   exact for |d_ij,k| < 16, which unit normals keep far inside);
+ *   d_weight [n] (NULL = unit weights);
  *   outputs (each may be NULL): d_acc [n] float32, d_dom [n] int8,
  *   d_conc [n] float32, d_dir_area [N] double (sum over points of weight
  *   times visibility of direction j: exact for unit weights; with real
