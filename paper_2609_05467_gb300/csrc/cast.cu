@@ -422,6 +422,16 @@ __device__ __forceinline__ bool below_tangent(float4 v, float ox, float oy, floa
     return s < -4e-15 * m;
 }
 
+// Shortcuts that skip what lies below a point's tangent plane need every
+// direction of the set above it.  With |n|^2 = 1 + delta the basis tilts by
+// about |delta|, so d.n >= z_min - 3 |delta| - 1e-6 with z_min = 1/(2N) >=
+// 1/(64 W) (W = ceil(N/32)); a normal further from unit length takes none.
+__device__ __forceinline__ bool tangent_shortcuts_ok(float nx, float ny, float nz, int W)
+{
+    const double nn = (double)nx * nx + (double)ny * ny + (double)nz * nz;
+    return fabs(nn - 1.0) <= 0.25 * (1.0 / (64.0 * W) - 2e-6);
+}
+
 // A box wholly below the tangent plane through o: the largest n.(x - o) over
 // its corners, sum over the axes of max(n_k (lo_k - o_k), n_k (hi_k - o_k)),
 // is negative beyond the rounding of its fp32 evaluation (each difference,
@@ -813,14 +823,8 @@ __device__ __forceinline__ void cast_point(const float4* __restrict__ nodes, con
     const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
     const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
     const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
-    if (kWide && front && lane == 0) {
-        // the tangent-plane drops need every direction of the set above the
-        // plane: d.n >= z_min - 3 | |n|^2 - 1 | - 1e-6 with z_min = 1/(2N) >=
-        // 1/(64 W); a normal further from unit length keeps everything
-        const double nn = (double)nx * nx + (double)ny * ny + (double)nz * nz;
-        const bool drop = fabs(nn - 1.0) <= 0.25 * (1.0 / (64.0 * W) - 2e-6);
-        build_frontier(nodes, tris, max_steps, ox, oy, oz, nx, ny, nz, drop, front);
-    }
+    if (kWide && front && lane == 0)
+        build_frontier(nodes, tris, max_steps, ox, oy, oz, nx, ny, nz, tangent_shortcuts_ok(nx, ny, nz, W), front);
     __syncwarp();
     const Frontier* fr = kWide && front && front->ok ? front : nullptr;
     if (kStats && front && lane == 0) acc.nvis += front->nvis;
@@ -1006,7 +1010,8 @@ k_hemisphere_update(const float4* __restrict__ nodes, const float4* __restrict__
         const float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
         const float nx = Nrm[3 * i], ny = Nrm[3 * i + 1], nz = Nrm[3 * i + 2];
         const float ox = offset_coord(px, nx, eps), oy = offset_coord(py, ny, eps), oz = offset_coord(pz, nz, eps);
-        if (!moved && !box_in_front(blo, bhi, ox, oy, oz, nx, ny, nz)) continue;   // nothing can change
+        if (!moved && tangent_shortcuts_ok(nx, ny, nz, W) && !box_in_front(blo, bhi, ox, oy, oz, nx, ny, nz))
+            continue;   // nothing can change
         for (int w = lane; w < W; w += 32) row[w] = moved ? 0u : bits[i * W + w];
         __syncwarp();
         const Onb b = make_onb(nx, ny, nz);

@@ -99,6 +99,44 @@ def test_update_equals_full_recast_and_oracle(rc, shift, deepen, N, centroid):
     compare_bits(r["bits"], r["cnt"], ob, oa, oc, N)
 
 
+def test_update_with_normals_that_are_not_unit(rc):
+    """A caller's normals of other than unit length: the update must not skip
+    a point because the changed box lies behind its tangent plane (its
+    directions can dip below that plane), and its bits must equal the full
+    re-cast with the same normals and the oracle's cast."""
+    V0, F = synth.perturbed_part(3, 0.0)
+    V1, _ = synth.perturbed_part(3, 2.5)
+    p = rc.rc_params_default(n_dirs=128, seed=2)
+    n = 1500
+    Vt0, Ft = gpu_mesh(V0, F)
+    Vt1, _ = gpu_mesh(V1, F)
+    b0, b1 = rc.Bvh(Vt0, Ft), rc.Bvh(Vt1, Ft)
+    P0 = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    N0 = torch.zeros_like(P0)
+    f = torch.zeros(n, dtype=torch.int32, device="cuda")
+    rc.rc_sample_points(b0.h, n, p, P0, N0, f)
+    k = torch.from_numpy(np.random.default_rng(9).uniform(0.4, 2.5, size=(n, 1)).astype(np.float32)).cuda()
+    bits, cnt, _ = _cast(rc, b0.h, P0, N0 * k, p)
+    changed = torch.zeros(len(F), dtype=torch.uint8, device="cuda")
+    nc, box = rc.rc_changed_faces(Vt0, Vt1, Ft, changed)
+    P1 = torch.zeros_like(P0)
+    N1 = torch.zeros_like(P0)
+    rc.rc_sample_points_on_faces(b1.h, p, f, P1, N1)
+    N1k = N1 * k
+    ctr = torch.zeros(4, dtype=torch.int64, device="cuda")
+    rc.rc_hemisphere_update(b1.h, P1, N1k, f, changed, box, p, bits, cnt, ctr)
+    full_bits, full_cnt, full_ctr = _cast(rc, b1.h, P1, N1k, p)
+    torch.cuda.synchronize()
+    gb = bits.cpu().numpy().view(np.uint32)
+    diff = int(np.unpackbits((gb ^ full_bits.cpu().numpy().view(np.uint32)).view(np.uint8)).sum())
+    assert diff <= int(ctr[1].item() + full_ctr[1].item())
+    hP1, hN1k = P1.cpu().numpy(), N1k.cpu().numpy()
+    ob, oa, oc = oracle.Mesh(V1, F).hemisphere(hP1, hN1k, 128)
+    compare_bits(gb, cnt.cpu().numpy(), ob, oa, oc, 128)
+    b0.close()
+    b1.close()
+
+
 def test_update_without_and_with_everything_changed(rc):
     V0, F = synth.perturbed_part(2, 0.0)
     p = rc.rc_params_default(n_dirs=128, seed=1)
