@@ -954,7 +954,8 @@ __global__ void k_zero_split(const int32_t* __restrict__ order, int64_t n_whole,
 // enter that box (the conservative slab test of the traversal, monotone in
 // the box) keeps its old bit.  Points on moved faces are cast in full; an
 // unmoved point whose tangent plane has the whole box behind it (every
-// hemisphere direction has d.n > 0) is skipped outright.  Rays whose old
+// hemisphere direction has d.n > 0 when its normal is of unit length, see
+// tangent_shortcuts_ok) is skipped outright.  Rays whose old
 // and new decisions are both made only by FP64-ambiguous pairs may differ
 // from a full re-cast; they are counted as ambiguous like any other.
 // ---------------------------------------------------------------------------
