@@ -222,7 +222,8 @@ def peaks():
         return 6800.0, "fallback"
 
 
-TRAVERSAL_SOURCES = ("cast.cu", "build.cu", "rc_internal.cuh")
+# the kernel, the tree it walks and the direction tile order it casts
+TRAVERSAL_SOURCES = ("cast.cu", "build.cu", "rc_internal.cuh", "api.cu")
 
 
 def _code_only(text):

@@ -66,9 +66,11 @@ static void fibonacci_hemisphere(int32_t N, float* out /*N x 3*/)
     }
 }
 
-// Tile order for the cast: directions sorted by the Morton code of their
-// Lambert equal-area projection (ties by index), so each run of 32 is a
-// compact patch of the hemisphere.  Returns the canonical index per slot.
+// Tile order for the cast: directions sorted by their position along the
+// Hilbert curve over their Lambert equal-area projection (ties by index), so
+// each run of 32 is a compact patch of the hemisphere and consecutive runs
+// are neighbours (a Morton order's runs jump at quadrant boundaries).
+// Returns the canonical index per slot.
 static std::vector<int32_t> tile_order(int32_t N, const float* h)
 {
     std::vector<std::pair<uint64_t, int32_t>> key(N);
@@ -79,8 +81,17 @@ static std::vector<int32_t> tile_order(int32_t N, const float* h)
         const double r2 = sqrt(2.0);
         uint32_t qx = (uint32_t)std::min(65535.0, std::max(0.0, (X + r2) / (2 * r2) * 65536.0));
         uint32_t qy = (uint32_t)std::min(65535.0, std::max(0.0, (Y + r2) / (2 * r2) * 65536.0));
+        // position along the Hilbert curve of the 65536 x 65536 grid
         uint64_t code = 0;
-        for (int b = 0; b < 16; ++b) code |= (uint64_t)((qx >> b) & 1) << (2 * b) | (uint64_t)((qy >> b) & 1) << (2 * b + 1);
+        uint32_t cx = qx, cy = qy;
+        for (uint32_t sq = 1u << 15; sq > 0; sq >>= 1) {
+            const uint32_t rx = (cx & sq) ? 1u : 0u, ry = (cy & sq) ? 1u : 0u;
+            code += (uint64_t)sq * sq * ((3u * rx) ^ ry);
+            if (ry == 0) {
+                if (rx == 1) { cx = 65535u - cx; cy = 65535u - cy; }
+                const uint32_t t = cx; cx = cy; cy = t;
+            }
+        }
         key[j] = {code, j};
     }
     std::sort(key.begin(), key.end());
