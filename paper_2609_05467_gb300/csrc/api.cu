@@ -67,19 +67,23 @@ static void fibonacci_hemisphere(int32_t N, float* out /*N x 3*/)
 }
 
 // Tile order for the cast: directions sorted by their position along the
-// Hilbert curve over their stereographic projection onto the unit disk
-// (r = tan(theta/2); ties by index), so each run of 32 is a compact patch of
-// the hemisphere -- the projection is conformal, so a patch stays about as
-// wide as long even near the horizon, where an equal-area map stretches it
-// -- and consecutive runs are neighbours (a Morton order's runs jump at
-// quadrant boundaries).  Returns the canonical index per slot.
+// Hilbert curve over a projection onto the unit disk (ties by index), so each
+// run of 32 is a compact patch of the hemisphere and consecutive runs are
+// neighbours (a Morton order's runs jump at quadrant boundaries).  The
+// projection puts a direction at polar angle theta at radius
+// r = tan^2(theta/2) = (1 - cos theta) / (1 + cos theta): its radial scale is
+// everywhere twice its tangential one, so a square cell of the disk spans half
+// as much elevation as azimuth.  Walk lengths change fastest with elevation
+// (the grazing rays near the horizon are the longest), and patches narrow in
+// elevation keep a tile's walks alike.  Returns the canonical index per slot.
 static std::vector<int32_t> tile_order(int32_t N, const float* h)
 {
     std::vector<std::pair<uint64_t, int32_t>> key(N);
     for (int32_t j = 0; j < N; ++j) {
         const double x = h[3 * j], y = h[3 * j + 1], z = h[3 * j + 2];
         const double rho = sqrt(x * x + y * y);
-        const double rr = tan(0.5 * acos(std::min(1.0, std::max(-1.0, z))));   // in [0, 1]
+        const double zc = std::min(1.0, std::max(0.0, z));
+        const double rr = (1.0 - zc) / (1.0 + zc);   // in [0, 1]
         const double r2 = sqrt(2.0);
         const double X = rho > 0.0 ? x / rho * rr * r2 : 0.0, Y = rho > 0.0 ? y / rho * rr * r2 : 0.0;
         uint32_t qx = (uint32_t)std::min(65535.0, std::max(0.0, (X + r2) / (2 * r2) * 65536.0));
