@@ -77,15 +77,16 @@ typedef struct {
     uint64_t seed;           /* area-random sampling seed */
     float frame[9];          /* row-major 3x3 machining frame; its columns are X', Y', Z' (Section 3.2); finite,
                                 no zero column (RC_E_ARG) */
-    float tool_length;       /* mm; reachability threshold (Section 3.3) */
+    float tool_length;       /* mm; reachability threshold (Section 3.3); >= 0, +inf = no limit (RC_E_ARG otherwise) */
     int32_t conc_mode;       /* 0: share of visible rays along the dominant axis; 1: |mean direction| along it */
     double t_acc;            /* multi-axis if overall accessibility < t_acc (Section 3.3) */
     double t_share;          /* ... or the largest dominant-axis share < t_share */
-    double t_conc;           /* ... or the mean axis concentration > t_conc */
+    double t_conc;           /* ... or the mean axis concentration > t_conc (none of the three NaN: RC_E_ARG) */
     int32_t block_threads;   /* traversal kernel: threads per block (0 = default; only 128 is supported) */
     int32_t blocks_per_sm;   /* traversal kernel: resident blocks per SM (0 = tuned default) */
     int32_t collect_stats;   /* 1: casts run the instrumented traversal (counters[4..5]) */
-    int32_t always_setups;   /* rc_analyze_part: 1 = orthogonal cast and setups for every part, 0 = 3-axis parts only */
+    int32_t always_setups;   /* rc_analyze_part: 1 = orthogonal cast and setups for every part, 0 = 3-axis parts only
+                                (0 or 1: RC_E_ARG otherwise) */
     int32_t point_order;     /* hemispherical cast: 0 = cast points in Morton order (default), 1 = in index order */
     int32_t tile_mode;       /* hemispherical cast: 0 = directions in coherent tiles of 32 (default), 1 = index order */
     int32_t points_per_item; /* batched cast: points per work item (0 = 1) */
@@ -167,15 +168,17 @@ rc_status rc_stream_status(void* stream);
 /* Build the part's device acceleration structure (Section 3.1: "for each
  * triangular face, the centroid, surface normal and area are computed";
  * the BVH itself is not in the paper).  Steps, all on `stream`: FP64 face
- * normal/area/centroid, 63-bit Morton codes of triangle-box centres, LSD
- * radix sort, Karras binary radix tree, bottom-up AABB refit, packing into
- * the traversal layout, integer area CDF for sampling.
+ * normal/area/centroid, 48-bit Morton codes of triangle-box centres (16
+ * bits per axis), LSD radix sort, Karras binary radix tree, bottom-up AABB
+ * refit, packing into the traversal layout, collapse into the 4-wide tree
+ * the default walk uses, integer area CDF for sampling.
  *   d_V [nV][3] float32, d_F [T][3] int32 (device, caller-owned; read
  *   during the call only -- the handle keeps its own copies).
  * Synchronises `stream` before returning (validation result).
  * Errors: RC_E_ARG for NULL pointers, nV < 3, T < 1, T > 2^28, an index
- * outside [0, nV) or a non-finite vertex; RC_E_UNSUPPORTED if the tree is
- * deeper than the traversal stack (64); RC_E_OOM; RC_E_CUDA. */
+ * outside [0, nV) or a non-finite vertex; RC_E_UNSUPPORTED if a tree is
+ * deeper than its traversal stack holds (binary depth 64 or more, or a
+ * 4-wide depth d with 3d + 1 >= 96); RC_E_OOM; RC_E_CUDA. */
 rc_status rc_build_bvh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t T, void* stream,
                        rc_bvh* out);
 
@@ -343,7 +346,8 @@ rc_status rc_direction_variability_noalloc(const uint32_t* d_bits, const float* 
 /* Threshold classification (Section 3.3: "if any threshold is exceeded, the
  * part is classified as requiring multi-axis machining").  *label = 1
  * (multi-axis) iff overall_access < t_acc, or max axis_share < t_share, or
- * mean_conc > t_conc; else 0 (3-axis).  Host only.  Errors: RC_E_ARG. */
+ * mean_conc > t_conc; else 0 (3-axis).  Host only.  Errors: RC_E_ARG for a
+ * NULL argument or a NaN threshold. */
 rc_status rc_classify(const rc_summary* s, const rc_params* p, int32_t* label);
 
 /* ---------------------------------------------------------------------- */

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -150,6 +151,15 @@ static rc_status device_dirs(int32_t N, const float4** canon, const float4** til
     return RC_OK;
 }
 
+// The classification thresholds (Section 3.3): any value but NaN, which no
+// comparison would decide.
+static rc_status check_thresholds(const rc_params* p)
+{
+    if (std::isnan(p->t_acc) || std::isnan(p->t_share) || std::isnan(p->t_conc))
+        return set_error(RC_E_ARG, "t_acc, t_share and t_conc must not be NaN");
+    return RC_OK;
+}
+
 static rc_status check_params(const rc_params* p)
 {
     if (!p) return set_error(RC_E_ARG, "params is NULL");
@@ -178,7 +188,9 @@ static rc_status check_params(const rc_params* p)
     if (p->collect_stats != 0 && p->collect_stats != 1) return set_error(RC_E_ARG, "collect_stats must be 0 or 1");
     if (!(p->parallel_tol >= 0.0 && p->parallel_tol <= 0.5))
         return set_error(RC_E_ARG, "parallel_tol must be in [0, 0.5]");
-    return RC_OK;
+    if (p->always_setups != 0 && p->always_setups != 1) return set_error(RC_E_ARG, "always_setups must be 0 or 1");
+    if (!(p->tool_length >= 0.0f)) return set_error(RC_E_ARG, "tool_length must be >= 0 (+inf: no limit)");
+    return check_thresholds(p);
 }
 
 rc_status check_params_public(const rc_params* p) { return check_params(p); }
@@ -487,6 +499,8 @@ rc_status rc_classify(const rc_summary* s, const rc_params* p, int32_t* label)
 {
     RC_RANGE();
     if (!s || !p || !label) return set_error(RC_E_ARG, "NULL argument");
+    rc_status st = check_thresholds(p);
+    if (st != RC_OK) return st;
     const double mx = std::max(s->axis_share[0], std::max(s->axis_share[1], s->axis_share[2]));
     *label = (s->overall_access < p->t_acc || mx < p->t_share || s->mean_conc > p->t_conc) ? 1 : 0;
     return RC_OK;

@@ -175,6 +175,42 @@ def test_argument_validation_needs_no_gpu(rc):
     assert rc.rc_launch_count() == 0
 
 
+def test_analysis_parameters_are_validated(rc):
+    """tool_length (Section 3.3's reach threshold) takes any value >= 0 and
+    +inf; the three classification thresholds take anything but NaN, which
+    no comparison would decide; always_setups is 0 or 1.  A cast and the
+    classification refuse anything else before touching the device."""
+    L = rc.load()
+
+    def cast_status(**kw):
+        q = rc.rc_params_default(**kw)
+        return L.rc_hemisphere_cast(ctypes.c_void_p(16), None, None, 1, ctypes.byref(q), None, None, None, None)
+
+    nan, inf = float("nan"), float("inf")
+    for kw, word in (({"tool_length": -1.0}, b"tool_length"), ({"tool_length": nan}, b"tool_length"),
+                     ({"t_acc": nan}, b"NaN"), ({"t_share": nan}, b"NaN"), ({"t_conc": nan}, b"NaN"),
+                     ({"always_setups": 2}, b"always_setups"), ({"always_setups": -1}, b"always_setups")):
+        assert cast_status(**kw) == 1 and word in L.rc_last_error(), kw
+    s = rc.Summary()
+    label = ctypes.c_int32()
+    for kw in ({"t_acc": nan}, {"t_share": nan}, {"t_conc": nan}):
+        q = rc.rc_params_default(**kw)
+        assert L.rc_classify(ctypes.byref(s), ctypes.byref(q), ctypes.byref(label)) == 1
+        assert b"NaN" in L.rc_last_error()
+    # accepted limits: classification runs on the host and gives the label the
+    # oracle's rule gives
+    s.overall_access, s.mean_conc = 0.5, 0.3
+    for k in range(3):
+        s.axis_share[k] = 1.0 / 3.0
+    for kw in ({"tool_length": 0.0}, {"tool_length": inf}, {"t_acc": -inf, "t_share": -inf, "t_conc": inf},
+               {"t_acc": inf}, {"always_setups": 1}):
+        q = rc.rc_params_default(**kw)
+        assert L.rc_classify(ctypes.byref(s), ctypes.byref(q), ctypes.byref(label)) == 0
+        d = {"overall_access": s.overall_access, "axis_share": list(s.axis_share), "mean_conc": s.mean_conc}
+        assert label.value == oracle.classify(d, t_acc=q.t_acc, t_share=q.t_share, t_conc=q.t_conc), kw
+    assert rc.rc_launch_count() == 0
+
+
 def test_product_path_does_not_touch_the_oracle():
     """The library package imports nothing from oracle/ and its sources name
     no oracle file."""
