@@ -131,6 +131,11 @@ def test_ray_directions_rotate_hemisphere_to_normal(orc):
         assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=2e-6)
         # angles between directions are preserved (a rotation)
         assert np.allclose(d @ d.T, h64 @ h64.T, atol=5e-6)
+        # and it is a rotation, not a reflection: the map h -> d fitted over
+        # the set has determinant +1 and takes the local z axis to n
+        Q = np.linalg.lstsq(h64, d, rcond=None)[0].T
+        assert abs(np.linalg.det(Q) - 1.0) < 1e-5
+        assert np.allclose(Q[:, 2], n, atol=2e-6)
     # axis-aligned normal +z maps the table to itself up to a reflection
     d = orc.ray_dirs(np.array([0, 0, 1], np.float32), N)
     assert np.allclose(np.abs(d), np.abs(h64), atol=1e-7)
@@ -191,6 +196,12 @@ def test_pair_boundary_cases_are_ambiguous(orc):
     assert orc.pair(np.array([1, 1, -3], np.float32), down, A, B, C) == orc.MISS
     # origin on the plane inside the triangle: crossing at t = 0
     assert orc.pair(np.array([1, 1, 0], np.float32), down, A, B, C) == orc.AMB
+    # the band (reading R6, tau*R = 4e-9 here since R = 4): a line within it
+    # of an edge line is ambiguous on either side, one farther is decided;
+    # the same for a crossing within it of the origin along the ray
+    for p, expect in (([2, 1e-9, 3], orc.AMB), ([2, -1e-9, 3], orc.AMB), ([2, 1e-7, 3], orc.HIT),
+                      ([2, -1e-7, 3], orc.MISS), ([1, 1, 1e-9], orc.AMB), ([1, 1, 1e-6], orc.HIT)):
+        assert orc.pair(np.array(p, np.float32), down, A, B, C) == expect, p
     # ray in the plane of the triangle
     assert orc.pair(np.array([-1, 1, 0], np.float32), np.array([1, 0, 0], np.float32),
                     A, B, C) == orc.AMB
@@ -377,6 +388,11 @@ def test_area_sampling_on_faces_and_proportional_to_area(orc):
     v = (d11 * d20 - d01 * d21) / den
     ww = (d00 * d21 - d01 * d20) / den
     assert (v > -1e-6).all() and (ww > -1e-6).all() and (v + ww < 1 + 1e-6).all()
+    # uniform within the triangle: each barycentric coordinate has density
+    # 2(1 - u) on [0, 1], so a quarter of the points lie where it exceeds 1/2
+    # (the corner triangle cut off by the mid-edges); 5 sigma at 60,000 points
+    for u in (1.0 - v - ww, v, ww):
+        assert abs((u > 0.5).mean() - 0.25) < 5 * math.sqrt(0.25 * 0.75 / len(P))
     assert np.array_equal(Nn, n_f[fc])
     # chi-square of per-face counts against the area distribution
     cnt = np.bincount(fc, minlength=len(F))
@@ -419,6 +435,26 @@ def test_open_flat_face_axis_and_concentration(orc):
         Nn = np.array([n], np.float32)
         _, _, dom, _, _ = orc.variability(bits, Nn, N)
         assert dom[0] == int(np.argmax(np.abs(n)))
+    # a normal along another axis sees the same two limits (a permutation of
+    # the axes maps the +z hemisphere onto it)
+    for n in ([1, 0, 0], [0, -1, 0]):
+        Nn = np.array([n], np.float32)
+        _, _, _, c0, _ = orc.variability(bits, Nn, N, conc_mode=0)
+        _, _, _, c1, _ = orc.variability(bits, Nn, N, conc_mode=1)
+        assert abs(c0[0] - 1 / 3) < 2e-3 and abs(c1[0] - 0.5) < 1e-4
+    # only a cone of half-angle 30 degrees about the normal visible: in every
+    # visible direction the normal's axis is the largest component (cos 30 >
+    # sin 30), so the mode-0 concentration is exactly 1, and the mode-1 one
+    # is the mean height of the cone's directions
+    h64, _ = orc.direction_table(N)
+    cone = h64[:, 2] > math.cos(math.pi / 6)
+    cbits = np.packbits(cone.astype(np.uint8), bitorder="little").view(np.uint32)[None, :]
+    for n, axis in (([1, 0, 0], 0), ([0, -1, 0], 1)):
+        Nn = np.array([n], np.float32)
+        _, _, dom, c0, cnt = orc.variability(cbits, Nn, N, conc_mode=0)
+        _, _, _, c1, _ = orc.variability(cbits, Nn, N, conc_mode=1)
+        assert dom[0] == axis and cnt[0] == cone.sum() and c0[0] == 1.0
+        assert abs(c1[0] - h64[cone, 2].mean()) < 1e-6
 
 
 def test_deep_hole_concentration_tends_to_one(orc):
@@ -442,6 +478,67 @@ def test_summary_shares_sum_to_one(orc):
     assert abs(sum(s["axis_share"]) - 1.0) < 1e-12
     assert s["n_counted"] + s["n_zero_visible"] == 500
     assert abs(s["overall_access"] - cnt.sum() / (500 * 64)) < 1e-15
+
+
+def test_summary_worked_example(orc):
+    """Four points, N = 8, one with nothing visible: the shares and the mean
+    concentration are over the three counted points, the accessibility over
+    all four (weighted: sum w c / (N sum w))."""
+    cnt = np.array([0, 6, 3, 8], np.int64)
+    dom = np.array([-1, 2, 0, 2], np.int8)
+    conc = np.array([0.0, 0.5, 1.0, 0.25])
+    s = orc.summary(cnt, dom, conc, 8)
+    assert s["axis_share"] == [1 / 3, 0.0, 2 / 3]
+    assert s["mean_conc"] == 1.75 / 3 and s["n_counted"] == 3 and s["n_zero_visible"] == 1
+    assert s["overall_access"] == 17 / 32 and s["overall_access_unweighted"] == 17 / 32
+    sw = orc.summary(cnt, dom, conc, 8, weight=np.array([1.0, 2.0, 3.0, 4.0]))
+    assert abs(sw["overall_access"] - 53 / 80) <= 1e-15 and sw["overall_access_unweighted"] == 17 / 32
+
+
+def test_classify_any_indicator_suffices(orc):
+    """Section 3.3: the part is multi-axis if any one threshold is crossed."""
+    base = {"overall_access": 0.70, "axis_share": [0.50, 0.25, 0.25], "mean_conc": 0.30}
+    assert orc.classify(base) == 0
+    for key, val in (("overall_access", 0.59), ("axis_share", [0.44, 0.28, 0.28]), ("mean_conc", 0.42)):
+        s = dict(base)
+        s[key] = val
+        assert orc.classify(s) == 1, key
+
+
+def test_travel_closed_form(orc):
+    """Tool travel to the bounding box along each machining direction: the
+    box [0,100] x [0,60] x [0,40] and the point (10, 20, 30), in the part's
+    frame and in a frame whose axes X', Y', Z' are the part's y, z, x."""
+    V = np.array([[x, y, z] for x in (0, 100) for y in (0, 60) for z in (0, 40)], np.float32)
+    P = np.array([[10, 20, 30]], np.float32)
+    assert np.array_equal(orc.travel(V, P)[0], [90, 10, 40, 20, 10, 30])
+    frame = np.array([[0, 0, 1], [1, 0, 0], [0, 1, 0]], np.float32)      # columns: y, z, x
+    assert np.array_equal(orc.travel(V, P, frame=frame.ravel())[0], [40, 20, 10, 30, 90, 10])
+
+
+def test_face_classes_worked_example(orc):
+    """Section 3.3: directions whose travel exceeds the tool length are
+    discarded (travel equal to it is kept); a face with a kept direction is
+    viable, one whose accessible directions were all discarded
+    over-threshold, one with none fully inaccessible; fixture faces are
+    excluded whatever their access."""
+    mask = np.array([0b000001, 0b000001, 0, 0b010000, 0b100010], np.uint8)
+    trav = np.full((5, 6), 99.0, np.float32)
+    trav[0, 0], trav[1, 0], trav[3, 4], trav[4, 1], trav[4, 5] = 10.0, 10.5, 1.0, 20.0, 5.0
+    face = np.array([0, 1, 2, 3, 4], np.int32)
+    fixture = np.array([False, False, False, True, False])
+    cls, reach = orc.face_classes(mask, trav, face, fixture, 10.0)
+    assert cls.tolist() == [0, 1, 2, 3, 0]
+    assert reach[0] == 0b000001 and reach[1] == 0 and reach[4] == 0b100000
+
+
+def test_cover_tie_rules(orc):
+    """Readings of the covers' ties: the exact cover takes the smallest
+    bitmask among the smallest sets, the greedy cover the lower axis."""
+    assert orc.setups_exact([0b011, 0b011]) == (1, 0b001)
+    assert orc.setups_exact([0b0110, 0b1100]) == (1, 0b0100)
+    assert orc.setups_greedy([0b011]) == (1, 0b001)
+    assert orc.setups_greedy([0b0011, 0b1100]) == (2, 0b0101)
 
 
 def test_setups_on_hand_built_parts(orc):
