@@ -27,6 +27,12 @@ def test_triangle_second_moment_closed_form():
     assert S0 == 0.5
     assert np.allclose(S1, [1 / 6, 1 / 6, 0], rtol=0, atol=1e-15)
     assert np.allclose(S2, [[1 / 12, 1 / 24, 0], [1 / 24, 1 / 12, 0], [0, 0, 0]], rtol=0, atol=1e-15)
+    # about its centroid (1/3, 1/3, 0) -- away from the bounding-box midpoint
+    # the moments are taken from -- by the parallel-axis theorem:
+    # 1/12 - (1/2)(1/3)^2 = 1/36 and 1/24 - (1/2)(1/3)(1/3) = -1/72
+    M, cen = fr.central_second_moment(V, F)
+    assert np.allclose(cen, [1 / 3, 1 / 3, 0], rtol=0, atol=1e-15)
+    assert np.allclose(M, [[1 / 36, -1 / 72, 0], [-1 / 72, 1 / 36, 0], [0, 0, 0]], rtol=0, atol=1e-15)
 
 
 @pytest.mark.parametrize("subdiv", [0, 2])
@@ -48,6 +54,7 @@ def test_principal_frame_follows_a_rotation():
     V, F = synth.box_with_pockets((100.0, 60.0, 40.0), pockets=(), subdiv=1)
     R = synth.rotation(25.0, -40.0, 70.0)
     P, w = fr.principal_frame(synth.rotate(V, R), F)
+    assert P is not None                             # three distinct eigenvalues
     # columns = rotated x, y, z (largest extent first), eigenvalues invariant
     assert np.allclose(np.abs(np.sum(P * R, axis=0)), 1.0, atol=2e-6)
     a, b, c = 50.0, 30.0, 20.0
@@ -69,6 +76,7 @@ def test_normals_frame_of_a_rotated_box():
     V, F = synth.box_with_pockets((100.0, 60.0, 40.0), pockets=(), subdiv=1)
     R = synth.rotation(-15.0, 35.0, 10.0)
     Nf = fr.normals_frame(synth.rotate(V, R), F)
+    assert Nf is not None
     assert abs(abs(Nf[:, 2] @ R[:, 2]) - 1.0) < 1e-6     # Z' along the rotated z
     assert abs(abs(Nf[:, 0] @ R[:, 1]) - 1.0) < 1e-6     # X' along the rotated y
     assert abs(np.linalg.det(Nf) - 1.0) < 1e-12
@@ -153,6 +161,20 @@ def test_box_search_is_the_brute_force_minimum():
             if best is None or v < best[0] * (1 - 1e-9):
                 best = (v, aa, jj)
     assert (a, j) == best[1:] and abs(vol - best[0]) <= 1e-9 * best[0]
+
+
+def test_select_frame_order():
+    """F6 on hand-made scores: fewest setups first, then fewest over-threshold
+    plus inaccessible points, then the smallest box volume, then the lowest
+    index."""
+    def pick(vol, setups, bad):
+        cands = [{"volume": v} for v in vol]
+        evals = [{"setups_exact": k, "class_counts": [0, b, 0, 0]} for k, b in zip(setups, bad)]
+        return fr.select_frame(cands, evals)
+    assert pick([1.0, 9.0, 8.0], [2, 1, 1], [0, 4, 2]) == 2        # setups, then flagged points
+    assert pick([1.0, 9.0, 8.0], [2, 1, 1], [0, 1, 2]) == 1        # flagged points before volume
+    assert pick([5.0, 3.0, 4.0], [1, 1, 1], [0, 0, 0]) == 1        # then volume
+    assert pick([3.0, 3.0, 3.0], [1, 1, 1], [2, 2, 2]) == 0        # then the index
 
 
 def test_auto_frame_undoes_a_rotation():

@@ -13,7 +13,9 @@ import types
 
 import pytest
 
+import test_oracle_frames as frame_pins
 import test_oracle_pins as pins
+import test_oracle_tool as tool_pins
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE_C = os.path.join(ROOT, "oracle", "oracle.c")
@@ -92,15 +94,54 @@ PY_MUTATIONS = [
     ("greedy cover ties to the higher axis", "if c > bc:", "if c >= bc:"),
 ]
 
+# (file under oracle/, what is wrong, text, its replacement): the automatic
+# frame and the tool model, pinned by test_oracle_frames.py and
+# test_oracle_tool.py
+SUB_MUTATIONS = [
+    ("frames.py", "second moment over 6", "S2 = ((A / 12.0)", "S2 = ((A / 6.0)"),
+    ("frames.py", "vertex sum drops a vertex", "s = a + b + c\n    S0 = A.sum()", "s = a + b\n    S0 = A.sum()"),
+    ("frames.py", "central moment adds the centroid term", "return S2 - S0 * np.outer(cen, cen), cen + r",
+     "return S2 + S0 * np.outer(cen, cen), cen + r"),
+    ("frames.py", "eigenvalues in ascending order", "order = np.argsort(-w, kind=\"stable\")",
+     "order = np.argsort(w, kind=\"stable\")"),
+    ("frames.py", "two equal largest eigenvalues accepted", "if not w[0] > 0.0 or (w[0] - w[1]) <= GAP * w[0] or",
+     "if not w[0] > 0.0 or"),
+    ("frames.py", "snapped sign rule reversed", "if w[k] < 0.0:", "if w[k] > 0.0:"),
+    ("frames.py", "left-handed frame", "ec = _cross(ea, eb) if (col_a + 1) % 3 == col_b else _cross(eb, ea)",
+     "ec = _cross(eb, ea) if (col_a + 1) % 3 == col_b else _cross(ea, eb)"),
+    ("frames.py", "second column not made orthogonal",
+     "eb = _unit([w[0] - d * ea[0], w[1] - d * ea[1], w[2] - d * ea[2]])", "eb = _unit(w)"),
+    ("frames.py", "halves of the area quantisation rounded down", "(fl + (x - fl >= 0.5))", "(fl + (x - fl > 0.5))"),
+    ("frames.py", "normal cell of a line depends on its sign", "sgn = np.where(nk < 0.0, -1.0, 1.0)",
+     "sgn = np.where(nk < 0.0, 1.0, 1.0)"),
+    ("frames.py", "cell components swapped", "u = (n[rows, (k + 1) % 3] * sgn) / m",
+     "u = (n[rows, (k + 2) % 3] * sgn) / m"),
+    ("frames.py", "normals frame with Z' and X' exchanged", "return frame_from(2, u1, 0, u2)",
+     "return frame_from(0, u1, 2, u2)"),
+    ("frames.py", "box volume of two extents", "return (ext[0] * ext[1]) * ext[2]", "return ext[0] * ext[1]"),
+    ("frames.py", "box rotation not a rotation", "G[:, c] = cs * B[:, c] - sn * B[:, b]",
+     "G[:, c] = cs * B[:, c] + sn * B[:, b]"),
+    ("frames.py", "rotation angle halved", "sn = (2.0 * t) / den", "sn = t / den"),
+    ("frames.py", "box search ties to the last", "if best is None or vol < best[3]:",
+     "if best is None or vol <= best[3]:"),
+    ("frames.py", "volume before flagged points", "keys = [(e[\"setups_exact\"], e[\"class_counts\"][1] + e[\"class_counts\"][2], c[\"volume\"], i)",
+     "keys = [(e[\"setups_exact\"], c[\"volume\"], e[\"class_counts\"][1] + e[\"class_counts\"][2], i)"),
+    ("tool.py", "ring angle's sine replaced", "math.sin(2.0 * math.pi * k / K)) for k in range(K)]",
+     "math.cos(2.0 * math.pi * k / K)) for k in range(K)]"),
+    ("tool.py", "basis vector sign", "v = (bb, sg + (ay * ay) * q, -ay)", "v = (bb, sg + (ay * ay) * q, ay)"),
+    ("tool.py", "ring radius dropped", "rc, rs = radius * cs, radius * sn", "rc, rs = 0.0 * cs, 0.0 * sn"),
+    ("tool.py", "eligibility without the tolerance", "elig = nd >= -parallel_tol", "elig = nd > parallel_tol"),
+]
+
 # the three pins that take a second or more run last
 _SLOW = ("test_pair_matches_exact_rational_predicate", "test_pocket_block_matches_exact_visibility",
          "test_bvh_matches_brute_force")
 
 
-def _pin_calls():
+def _pin_calls(module=pins):
     calls = []
-    for name in sorted(vars(pins), key=lambda nm: (nm in _SLOW, _SLOW.index(nm) if nm in _SLOW else 0, nm)):
-        fn = getattr(pins, name)
+    for name in sorted(vars(module), key=lambda nm: (nm in _SLOW, _SLOW.index(nm) if nm in _SLOW else 0, nm)):
+        fn = getattr(module, name)
         if not name.startswith("test_") or not callable(fn):
             continue
         cases = [{}]
@@ -142,6 +183,41 @@ def _compiled_copy(tmp_path, old=None, new=None):
     return so
 
 
+def _submodule_copy(fname, old=None, new=None):
+    """oracle/<fname> executed afresh, inside the real oracle package (its
+    relative imports resolve there), with one replacement in its source."""
+    path = os.path.join(ROOT, "oracle", fname)
+    src = open(path).read()
+    if old is not None:
+        assert src.count(old) == 1, old
+        src = src.replace(old, new)
+    mod = types.ModuleType("oracle." + fname[:-3] + "_copy")
+    mod.__file__ = path
+    mod.__package__ = "oracle"
+    exec(compile(src, path, "exec"), mod.__dict__)
+    return mod
+
+
+_SUB_PINS = {"frames.py": (frame_pins, "fr"), "tool.py": (tool_pins, "tool")}
+
+
+def _first_failing_sub_pin(fname, mod):
+    """Runs the pins of one oracle submodule with its module global bound to
+    ``mod``; restores it afterwards."""
+    pin_module, attr = _SUB_PINS[fname]
+    saved = getattr(pin_module, attr)
+    setattr(pin_module, attr, mod)
+    try:
+        for name, fn, kw in _pin_calls(pin_module):
+            try:
+                fn(**kw)
+            except (AssertionError, pytest.fail.Exception) as e:   # a pin's own check failed
+                return name, type(e).__name__
+    finally:
+        setattr(pin_module, attr, saved)
+    return None
+
+
 def _first_failing_pin(mod):
     for name, fn, kw in _pin_calls():
         try:
@@ -154,6 +230,8 @@ def _first_failing_pin(mod):
 def test_unchanged_copy_passes_every_pin(tmp_path):
     assert _first_failing_pin(_oracle_copy(so=_compiled_copy(tmp_path))) is None
     assert _first_failing_pin(_oracle_copy(py=("Q40 = float(2 ** 40)", "Q40 = float(2 ** 40)"))) is None
+    for fname in _SUB_PINS:
+        assert _first_failing_sub_pin(fname, _submodule_copy(fname)) is None
 
 
 @pytest.mark.parametrize("what,old,new", C_MUTATIONS, ids=[m[0] for m in C_MUTATIONS])
@@ -165,4 +243,10 @@ def test_planted_mistake_in_the_compiled_oracle_fails_a_pin(tmp_path, what, old,
 @pytest.mark.parametrize("what,old,new", PY_MUTATIONS, ids=[m[0] for m in PY_MUTATIONS])
 def test_planted_mistake_in_the_python_oracle_fails_a_pin(what, old, new):
     hit = _first_failing_pin(_oracle_copy(py=(old, new)))
+    assert hit is not None, "no pin catches: " + what
+
+
+@pytest.mark.parametrize("fname,what,old,new", SUB_MUTATIONS, ids=[m[0][:-3] + ": " + m[1] for m in SUB_MUTATIONS])
+def test_planted_mistake_in_the_frame_and_tool_oracle_fails_a_pin(fname, what, old, new):
+    hit = _first_failing_sub_pin(fname, _submodule_copy(fname, old, new))
     assert hit is not None, "no pin catches: " + what
