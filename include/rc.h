@@ -14,8 +14,12 @@
  * Conventions (apply to every call):
  *  - Status: every call returns rc_status.  RC_OK is 0.  A failing call
  *    stores a message retrievable with rc_last_error() (thread-local).
- *    Argument errors are detected on the host and returned before any work
- *    is queued.
+ *    Errors in pointers, sizes and parameters are detected on the host and
+ *    returned before any work is queued.  The contents of device arrays
+ *    (vertex indices, vertex coordinates, face ids) are checked on the
+ *    device by the calls that say so (rc_build_bvh, rc_refit_bvh,
+ *    rc_sample_points_on_faces, rc_changed_faces): they synchronise
+ *    `stream`, free their scratch and return RC_E_ARG.
  *  - Memory: arrays named d_* are DEVICE pointers owned by the caller
  *    (e.g. torch CUDA tensors); arrays named h_* are host pointers owned by
  *    the caller.  The library owns only the opaque handles it returns and
@@ -199,7 +203,10 @@ rc_status rc_build_bvh_ex(const float* d_V, int64_t nV, const int32_t* d_F, int6
 /* Refit an existing handle to moved vertices of the same triangle list
  * (same F, same nV): recomputes face data, leaf and node boxes bottom-up
  * and the area CDF; the tree topology is kept.  Synchronises `stream`.
- * Errors as rc_build_bvh (non-finite vertices -> RC_E_ARG). */
+ * Errors as rc_build_bvh (non-finite vertices -> RC_E_ARG).  After a failed
+ * refit the handle keeps its topology and index arrays, so later calls stay
+ * within its buffers, but its geometry is undefined until a refit with
+ * valid vertices succeeds; destroy or refit it. */
 rc_status rc_refit_bvh(rc_bvh h, const float* d_V, void* stream);
 
 /* Release a handle and its device memory.  NULL is accepted.  The memory
@@ -585,7 +592,7 @@ rc_status rc_server_wait(rc_server s, int64_t req_id, double timeout_s, rc_reque
  * capacity of h_bits in uint32 words and must be at least n * W.  A part
  * in use is read once it is idle again (waiting at most 60 s).
  * Errors: RC_E_ARG (not resident, n differs, h_bits too small),
- * RC_E_TIMEOUT. */
+ * RC_E_TIMEOUT, RC_E_CUDA (the copy failed). */
 rc_status rc_server_read_bits(rc_server s, uint64_t part_key, uint32_t* h_bits, int64_t bits_words,
                               int32_t* h_count, int64_t n);
 
@@ -704,7 +711,8 @@ typedef struct {
  *      area second moment about its area centroid, sum over faces of the
  *      exact triangle integral A/12 (a a^T + b b^T + c c^T + s s^T),
  *      s = a + b + c; X' = largest eigenvalue, Y' = second, Z' = X' x Y';
- *      absent when two eigenvalues lie within 1e-3 of the largest;
+ *      absent when two adjacent eigenvalues (descending) differ by at most
+ *      1e-3 times the largest;
  *   3. dominant normals (RC_FRAME_NORMALS): face normals binned as lines on
  *      a 3 x 32 x 32 cube map, weighted by llround(A / A_max * 2^32); Z' =
  *      normal of the largest face of the heaviest cell, X' = that of the

@@ -14,8 +14,9 @@ F1  Principal axes.  The area second moment of the surface about its area
     centroid, M = sum_f int_f (x - c)(x - c)^T dA, using the exact triangle
     integral int_f x x^T dA = A_f / 12 (a a^T + b b^T + c c^T + s s^T) with
     s = a + b + c.  Eigenvectors by descending eigenvalue give X' and Y';
-    Z' = X' x Y'.  When two eigenvalues lie within 1e-3 of the largest one the
-    axes are not determined and this candidate is absent.
+    Z' = X' x Y'.  When two adjacent eigenvalues (descending) differ by at most
+    1e-3 times the largest one the axes are not determined and this candidate
+    is absent.
 F2  Dominant normals.  Face normals are binned as lines (n and -n together)
     on a cube map of 3 x 32 x 32 cells, weighted by the quantised face areas
     llround(A_f / A_max * 2^32).  Z' is the normal of the largest face of the
