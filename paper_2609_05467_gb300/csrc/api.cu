@@ -67,44 +67,44 @@ static void fibonacci_hemisphere(int32_t N, float* out /*N x 3*/)
     }
 }
 
-// Tile order for the cast: directions sorted by their position along the
-// Hilbert curve over a projection onto the unit disk (ties by index), so each
-// run of 32 is a compact patch of the hemisphere and consecutive runs are
-// neighbours (a Morton order's runs jump at quadrant boundaries).  The
-// projection puts a direction at polar angle theta at radius
-// r = tan^2(theta/2) = (1 - cos theta) / (1 + cos theta): its radial scale is
-// everywhere twice its tangential one, so a square cell of the disk spans half
-// as much elevation as azimuth.  Walk lengths change fastest with elevation
-// (the grazing rays near the horizon are the longest), and patches narrow in
-// elevation keep a tile's walks alike.  Returns the canonical index per slot.
+// Tile order for the cast.  The direction set's z is uniform in its index,
+// so runs of consecutive indices are elevation bands.  Each band holds a
+// whole number m of tiles of 32 directions sorted by azimuth, so that every
+// tile is an azimuth sector of one band.  A band of 32 m directions at polar
+// angle theta spans dz = 32 m / N, that is d(theta) = dz / sin(theta) of
+// elevation, and each of its sectors an arc of 2 pi sin(theta) / m;
+// m = sin(theta) sqrt(2 pi N / (32 kTileAspect)) makes the arc kTileAspect
+// times the elevation span.  Walk lengths change fastest with elevation (the
+// grazing rays near the horizon walk longest), so tiles narrow in elevation
+// keep a tile's walks alike.  Consecutive bands sweep the azimuth in
+// alternate directions, so consecutive tiles are neighbours; the last
+// N mod 32 directions form the partial tile.  Returns the canonical index
+// per slot.
 static std::vector<int32_t> tile_order(int32_t N, const float* h)
 {
-    std::vector<std::pair<uint64_t, int32_t>> key(N);
-    for (int32_t j = 0; j < N; ++j) {
-        const double x = h[3 * j], y = h[3 * j + 1], z = h[3 * j + 2];
-        const double rho = sqrt(x * x + y * y);
-        const double zc = std::min(1.0, std::max(0.0, z));
-        const double rr = (1.0 - zc) / (1.0 + zc);   // in [0, 1]
-        const double r2 = sqrt(2.0);
-        const double X = rho > 0.0 ? x / rho * rr * r2 : 0.0, Y = rho > 0.0 ? y / rho * rr * r2 : 0.0;
-        uint32_t qx = (uint32_t)std::min(65535.0, std::max(0.0, (X + r2) / (2 * r2) * 65536.0));
-        uint32_t qy = (uint32_t)std::min(65535.0, std::max(0.0, (Y + r2) / (2 * r2) * 65536.0));
-        // position along the Hilbert curve of the 65536 x 65536 grid
-        uint64_t code = 0;
-        uint32_t cx = qx, cy = qy;
-        for (uint32_t sq = 1u << 15; sq > 0; sq >>= 1) {
-            const uint32_t rx = (cx & sq) ? 1u : 0u, ry = (cy & sq) ? 1u : 0u;
-            code += (uint64_t)sq * sq * ((3u * rx) ^ ry);
-            if (ry == 0) {
-                if (rx == 1) { cx = 65535u - cx; cy = 65535u - cy; }
-                const uint32_t t = cx; cx = cy; cy = t;
-            }
+    constexpr double kTileAspect = 3.0;
+    std::vector<int32_t> ord;
+    ord.reserve(N);
+    std::vector<std::pair<double, int32_t>> key;
+    const int32_t ntiles = N / 32;
+    int32_t j = 0, t = 0, band = 0;
+    while (t < ntiles) {
+        const double z = 1.0 - ((double)j + 0.5) / (double)N;
+        const double s = sqrt(std::max(0.0, 1.0 - z * z));
+        int32_t m = (int32_t)llround(s * sqrt(2.0 * M_PI * (double)N / (32.0 * kTileAspect)));
+        m = std::max(1, std::min(m, ntiles - t));
+        key.clear();
+        for (int32_t k = j; k < j + 32 * m; ++k) {
+            const double phi = atan2((double)h[3 * k + 1], (double)h[3 * k]);
+            key.push_back({(band & 1) ? -phi : phi, k});
         }
-        key[j] = {code, j};
+        std::sort(key.begin(), key.end());
+        for (const auto& e : key) ord.push_back(e.second);
+        j += 32 * m;
+        t += m;
+        ++band;
     }
-    std::sort(key.begin(), key.end());
-    std::vector<int32_t> ord(N);
-    for (int32_t k = 0; k < N; ++k) ord[k] = key[k].second;
+    for (int32_t k = j; k < N; ++k) ord.push_back(k);
     return ord;
 }
 
