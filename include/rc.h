@@ -15,7 +15,8 @@
  *  - Status: every call returns rc_status.  RC_OK is 0.  A failing call
  *    stores a message retrievable with rc_last_error() (thread-local).
  *    Errors in pointers, sizes and parameters are detected on the host and
- *    returned before any work is queued.  The contents of device arrays
+ *    returned before any kernel is launched (a cast may already have queued
+ *    the zeroing of its d_counters array).  The contents of device arrays
  *    (vertex indices, vertex coordinates, face ids) are checked on the
  *    device by the calls that say so (rc_build_bvh, rc_refit_bvh,
  *    rc_sample_points_on_faces, rc_changed_faces): they synchronise
